@@ -1,0 +1,309 @@
+"""ctypes front end of the FP64 CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's CPU
+baseline are the only callers.  Nothing in the product package imports this module.
+
+Also holds the oracle's own host post-scale (Sect. 5 of the paper): geometric albedo
+A_g = pi S, phase function Phi = S(alpha)/S(0), emission L_p = (L_tot/N) sum f,
+I_p = L_p / (pi R_TOA^2), F_p = pi I_p, and the transmission integral
+<I_p> = (R_TOA - R0)/N sum W (1 - e^-tau) b with (R_p/R_star)^2 R_star^2 = R0^2 + 2 <I_p>.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+MAX_OBS = 32
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (plain C11, no architecture flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Grid_c(C.Structure):
+    _fields_ = [("nlon", C.c_int32), ("nlat", C.c_int32), ("nr", C.c_int32), ("pad", C.c_int32),
+                ("r_edges", C.POINTER(C.c_double)), ("lat_edges", C.POINTER(C.c_double)),
+                ("lon_edges", C.POINTER(C.c_double))]
+
+
+class Cells_c(C.Structure):
+    _fields_ = [("alpha", C.POINTER(C.c_double)), ("omega", C.POINTER(C.c_double)),
+                ("g", C.POINTER(C.c_double)), ("pgas", C.POINTER(C.c_double)),
+                ("cdf", C.POINTER(C.c_double)), ("wcell", C.POINTER(C.c_double)),
+                ("cdf_total", C.c_double), ("pad", C.c_double)]
+
+
+class Source_c(C.Structure):
+    _fields_ = [("star", C.c_double * 3), ("n_obs", C.c_int32), ("survival", C.c_int32),
+                ("obs", (C.c_double * 3) * MAX_OBS),
+                ("w_rr", C.c_double), ("p_surv", C.c_double), ("tau_peel_cut", C.c_double),
+                ("tau_vert_max", C.c_double), ("beta_emis", C.c_double), ("hg_iso_eps", C.c_double),
+                ("scatter_emission", C.c_int32), ("pad", C.c_int32), ("max_steps", C.c_int64)]
+
+
+class Run_c(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("job_key", C.c_uint32), ("seed", C.c_uint64),
+                ("n_packets", C.c_int64), ("packet0", C.c_int64), ("n_run", C.c_int64),
+                ("nthreads", C.c_int32), ("n_trace", C.c_int32), ("max_trace", C.c_int32), ("pad", C.c_int32),
+                ("tally", C.POINTER(C.c_double)), ("ledger", C.POINTER(C.c_double)),
+                ("steps", C.POINTER(C.c_int64)), ("pk_f", C.POINTER(C.c_double)),
+                ("pk_steps", C.POINTER(C.c_int64)), ("pk_tau", C.POINTER(C.c_double)),
+                ("tr_cell", C.POINTER(C.c_int32)), ("tr_len", C.POINTER(C.c_double)),
+                ("tr_n", C.POINTER(C.c_int32))]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            D, P = C.c_double, C.POINTER
+            _lib.orc_philox.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
+            for name in ("orc_sample_iso", "orc_sample_rayleigh", "orc_phase_rayleigh"):
+                getattr(_lib, name).argtypes = [D]
+                getattr(_lib, name).restype = D
+            _lib.orc_sample_hg.argtypes = [D, D, D]
+            _lib.orc_sample_hg.restype = D
+            _lib.orc_phase_hg.argtypes = [D, D]
+            _lib.orc_phase_hg.restype = D
+            _lib.orc_theta.argtypes = [D, D, D]
+            _lib.orc_theta.restype = D
+            _lib.orc_planck.argtypes = [D, D]
+            _lib.orc_planck.restype = D
+            _lib.orc_turn.argtypes = [P(D), D, D, P(D)]
+            _lib.orc_trace_ray.argtypes = [P(Grid_c), P(D), P(D), P(D), C.c_int32, C.c_int32, C.c_int32,
+                                           P(C.c_int32), P(D), P(C.c_int32)]
+            _lib.orc_trace_ray.restype = C.c_int
+            _lib.orc_prep_albedo.argtypes = [C.c_int64, P(D), P(D), D, D, D, D, D, P(D), P(D), P(D), P(D)]
+            _lib.orc_prep_emission.argtypes = [P(Grid_c), P(D), P(D), P(D), P(C.c_float), C.c_int, C.c_int,
+                                               P(D), P(D), D, D, D, P(D), P(D), P(D), P(D), P(D), P(D),
+                                               P(C.c_int64)]
+            _lib.orc_prep_xsec.argtypes = [P(Grid_c), P(D), P(D), P(D), P(D), P(C.c_float), C.c_int, C.c_int,
+                                           C.c_int, P(D), P(D), P(D), D, D, D, D, P(D), P(D)]
+            _lib.orc_run.argtypes = [P(Grid_c), P(Cells_c), P(Source_c), P(Run_c)]
+            _lib.orc_run.restype = C.c_int
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+class _GridHandle:
+    """Keeps the FP64 arrays alive while C holds pointers to them."""
+
+    def __init__(self, grid):
+        self.r = _f64(grid.r_edges)
+        self.lat = _f64(grid.lat_edges)
+        self.lon = _f64(grid.lon_edges)
+        self.c = Grid_c(grid.nlon, grid.nlat, grid.nr, 0, _dp(self.r), _dp(self.lat), _dp(self.lon))
+
+
+# ------------------------------------------------------------------ primitives
+
+def philox(ctr, key):
+    c = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (C.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    out = (C.c_uint32 * 4)()
+    lib().orc_philox(c, k, out)
+    return [int(x) for x in out]
+
+
+def sample_rayleigh(z):
+    return lib().orc_sample_rayleigh(float(z))
+
+
+def sample_hg(g, z, eps=1e-4):
+    return lib().orc_sample_hg(float(g), float(z), float(eps))
+
+
+def phase_hg(mu, g):
+    return lib().orc_phase_hg(float(mu), float(g))
+
+
+def phase_rayleigh(mu):
+    return lib().orc_phase_rayleigh(float(mu))
+
+
+def theta(mu, pgas, g):
+    return lib().orc_theta(float(mu), float(pgas), float(g))
+
+
+def planck(lam, T):
+    return lib().orc_planck(float(lam), float(T))
+
+
+def turn(d, mu, psi):
+    d = (C.c_double * 3)(*map(float, d))
+    out = (C.c_double * 3)()
+    lib().orc_turn(d, float(mu), float(psi), out)
+    return np.array(list(out))
+
+
+def trace_ray(grid, alpha, o, d, cell_flat, entry=-1, max_seg=100000):
+    G = _GridHandle(grid)
+    a = _f64(alpha)
+    o = np.ascontiguousarray(o, np.float64)
+    d = np.ascontiguousarray(d, np.float64)
+    cells = np.zeros(max_seg, np.int32)
+    lens = np.zeros(max_seg, np.float64)
+    st = C.c_int32(0)
+    n = lib().orc_trace_ray(C.byref(G.c), _dp(a), _dp(o), _dp(d), int(cell_flat), int(entry), int(max_seg),
+                            cells.ctypes.data_as(C.POINTER(C.c_int32)), _dp(lens), C.byref(st))
+    return cells[:n].copy(), lens[:n].copy(), int(st.value)
+
+
+# ------------------------------------------------------------------ S1 cell tables
+
+def prep_albedo(grid, opac, lam_idx):
+    n = grid.ncell
+    rho = _f64(grid.rho)
+    acld = _f64(opac.acld) if opac.acld is not None else None
+    out = {k: np.zeros(n) for k in ("alpha", "omega", "g", "pgas")}
+    lib().orc_prep_albedo(n, _dp(rho), _dp(acld), float(opac.kabs[lam_idx]), float(opac.kray[lam_idx]),
+                          float(opac.qcld[lam_idx]), float(opac.wcld[lam_idx]), float(opac.gcld[lam_idx]),
+                          _dp(out["alpha"]), _dp(out["omega"]), _dp(out["g"]), _dp(out["pgas"]))
+    return out
+
+
+def prep_emission(grid, kt, band, gidx, opts):
+    n = grid.ncell
+    G = _GridHandle(grid)
+    T, p, rho = _f64(grid.T), _f64(grid.p), _f64(grid.rho)
+    sl = np.ascontiguousarray(kt.k[band, gidx], dtype=np.float32)
+    Tg, pg = _f64(kt.Tg), _f64(kt.pg)
+    out = {k: np.zeros(n) for k in ("alpha", "L", "cdf", "wcell")}
+    Ltot, ctot, ninc = C.c_double(), C.c_double(), C.c_int64()
+    lib().orc_prep_emission(C.byref(G.c), _dp(T), _dp(p), _dp(rho), sl.ctypes.data_as(C.POINTER(C.c_float)),
+                            len(Tg), len(pg), _dp(Tg), _dp(pg), float(kt.lam[band]), float(opts.tau_vert_max),
+                            float(opts.beta_emis), _dp(out["alpha"]), _dp(out["L"]), _dp(out["cdf"]),
+                            _dp(out["wcell"]), C.byref(Ltot), C.byref(ctot), C.byref(ninc))
+    out.update(L_tot=Ltot.value, cdf_total=ctot.value, n_incl=ninc.value)
+    return out
+
+
+def prep_xsec(grid, xs, lam_idx):
+    n = grid.ncell
+    G = _GridHandle(grid)
+    T, p, rho = _f64(grid.T), _f64(grid.p), _f64(grid.rho)
+    wind = _f64(grid.wind.reshape(-1)) if grid.wind is not None else None
+    sig = np.ascontiguousarray(xs.sigma, dtype=np.float32)
+    lamg, Tg, pg = _f64(xs.lam), _f64(xs.Tg), _f64(xs.pg)
+    alpha = np.zeros(n)
+    vlos = np.zeros(n)
+    lib().orc_prep_xsec(C.byref(G.c), _dp(T), _dp(p), _dp(rho), _dp(wind), sig.ctypes.data_as(C.POINTER(C.c_float)),
+                        len(lamg), len(Tg), len(pg), _dp(lamg), _dp(Tg), _dp(pg), float(xs.lam[lam_idx]),
+                        float(xs.view_theta), float(xs.view_phi), float(xs.omega_rot), _dp(alpha), _dp(vlos))
+    return {"alpha": alpha, "vlos": vlos}
+
+
+def prep_cells(wl, job):
+    """S1 for one job of a workload (dispatch on the opacity kind)."""
+    if wl.mode == 0:
+        return prep_albedo(wl.grid, wl.opac, job.lam_idx)
+    if wl.mode == 1:
+        return prep_emission(wl.grid, wl.opac, job.lam_idx, job.g_idx, wl.source.opts)
+    return prep_xsec(wl.grid, wl.opac, job.lam_idx)
+
+
+# ------------------------------------------------------------------ packets
+
+def _source_struct(src, obs):
+    s = Source_c()
+    for i in range(3):
+        s.star[i] = float(src.star[i])
+    obs = np.atleast_2d(np.asarray(obs, np.float64))
+    if len(obs) > MAX_OBS:
+        raise ValueError("too many observer directions")
+    s.n_obs = len(obs)
+    for o in range(len(obs)):
+        for i in range(3):
+            s.obs[o][i] = float(obs[o][i])
+    op = src.opts
+    s.survival = int(op.survival)
+    s.w_rr, s.p_surv, s.tau_peel_cut = float(op.w_rr), float(op.p_surv), float(op.tau_peel_cut)
+    s.tau_vert_max, s.beta_emis, s.hg_iso_eps = float(op.tau_vert_max), float(op.beta_emis), float(op.hg_iso_eps)
+    s.scatter_emission = int(op.scatter_emission)
+    s.max_steps = int(op.max_steps)
+    return s, len(obs)
+
+
+def job_observers(wl, job):
+    obs = np.atleast_2d(wl.source.obs)
+    if getattr(job, "obs_idx", -1) >= 0:
+        return obs[job.obs_idx:job.obs_idx + 1]
+    return obs
+
+
+def run(wl, job, cells=None, packet0=0, n_run=None, nthreads=1, per_packet=False, n_trace=0, max_trace=0):
+    """Run packets of one job through the oracle; returns tallies, ledger, step count and
+    (optionally) per-packet f, steps, tau and segment traces."""
+    if cells is None:
+        cells = prep_cells(wl, job)
+    G = _GridHandle(wl.grid)
+    keep = {k: _f64(cells.get(k)) for k in ("alpha", "omega", "g", "pgas", "cdf", "wcell")}
+    cc = Cells_c(_dp(keep["alpha"]), _dp(keep["omega"]), _dp(keep["g"]), _dp(keep["pgas"]), _dp(keep["cdf"]),
+                 _dp(keep["wcell"]), float(cells.get("cdf_total", 0.0)), 0.0)
+    obs = job_observers(wl, job)
+    sc, nobs = _source_struct(wl.source, obs)
+    n_run = job.n_packets - packet0 if n_run is None else int(n_run)
+    tally = np.zeros(nobs)
+    ledger = np.zeros(8)
+    steps = np.zeros(1, np.int64)
+    pk_f = np.zeros((n_run, nobs)) if per_packet else None
+    pk_steps = np.zeros(n_run, np.int64) if per_packet else None
+    pk_tau = np.zeros(n_run) if per_packet else None
+    n_trace = min(int(n_trace), n_run)
+    tr_cell = np.zeros((n_trace, max_trace), np.int32) if n_trace else None
+    tr_len = np.zeros((n_trace, max_trace)) if n_trace else None
+    tr_n = np.zeros(n_trace, np.int32) if n_trace else None
+    ip = lambda a, t: a.ctypes.data_as(C.POINTER(t)) if a is not None else None  # noqa: E731
+    ra = Run_c(int(wl.mode), int(job.key) & 0xFFFFFFFF, int(wl.seed), int(job.n_packets), int(packet0), n_run,
+               int(nthreads), n_trace, int(max_trace), 0, _dp(tally), _dp(ledger), ip(steps, C.c_int64),
+               _dp(pk_f), ip(pk_steps, C.c_int64), _dp(pk_tau), ip(tr_cell, C.c_int32), _dp(tr_len),
+               ip(tr_n, C.c_int32))
+    rc = lib().orc_run(C.byref(G.c), C.byref(cc), C.byref(sc), C.byref(ra))
+    if rc != 0:
+        raise RuntimeError(f"oracle run failed: {rc}")
+    out = dict(tally=tally, ledger=ledger, steps=int(steps[0]), n_run=n_run, cells=cells)
+    if per_packet:
+        out.update(pk_f=pk_f, pk_steps=pk_steps, pk_tau=pk_tau)
+    if n_trace:
+        out.update(tr_cell=tr_cell, tr_len=tr_len, tr_n=tr_n)
+    return out
+
+
+# ------------------------------------------------------------------ S9 host post-scale (Sect. 5)
+
+def postscale(wl, job, tally_sum, n_packets, cells=None):
+    """Observables from one job's tally sum (sum over packets of f)."""
+    g = wl.grid
+    if wl.mode == 0:
+        S = np.asarray(tally_sum) / n_packets
+        return {"S": S, "A_g_toa": math.pi * S, "A_g_R0": math.pi * S * (g.R_toa / g.R0) ** 2}
+    if wl.mode == 1:
+        Ltot = cells["L_tot"]
+        Lp = Ltot / n_packets * np.asarray(tally_sum)
+        Ip = Lp / (math.pi * g.R_toa ** 2)
+        return {"L_p": Lp, "I_p": Ip, "F_p": math.pi * Ip}
+    Ip = (g.R_toa - g.R0) / n_packets * g.R_toa * np.asarray(tally_sum)
+    return {"I_p": Ip, "area_over_pi": g.R0 ** 2 + 2.0 * Ip}

@@ -1,0 +1,470 @@
+"""Seeded synthetic inputs shaped like the gCMCRT workloads.
+
+This module builds *inputs only*: spherical grids (longitude x latitude x
+pressure level), per-cell temperature, pressure, density and wind, and the
+opacity tables a job reads (grey/Rayleigh/cloud parameters, a correlated-k
+table, a Doppler cross-section table).  It holds none of the Monte Carlo
+method's arithmetic: no cell-table preparation, no sampling, no ray marching.
+Both the CUDA path and the CPU oracle read what this module returns.
+
+The paper post-processes GCM outputs (Sect. 9-13) that are not available
+here, so every field below is an analytic, seeded stand-in with the sizes and
+structure of the paper's cases:
+
+* radial grid: N_r cells between N_r + 1 log-uniform pressure edges, with edge
+  heights from the hypsometric relation dz = (k_B T / (mu m_u g)) ln(p_lo/p_hi)
+  using the horizontally averaged layer temperature, bottom radius R0 = 1 R_J;
+  the cell density is the hydrostatic layer mean rho = dp / (g dz), so a
+  cell's vertical optical depth is kappa dp / g exactly (the paper uses a
+  height grid, Sect. 6, and takes T, p, rho per cell from the GCM, Sect. 7);
+* temperature: day/night blend T_h = T_n + (T_d - T_n) max(0, cos(lon - 15 deg) cos(lat))
+  with a Guillot-like vertical profile (closed form in `guillot_T`);
+* correlated-k table: k(b, g, T, p) = k_med(b) (T/1500)^aT (p/1 bar)^ap exp(sigma_ln * Phi^-1(g)),
+  k_med log-uniform over 4 dex, sigma_ln = 2, 8 Gauss-Legendre g-ordinates;
+* cross-section table: 5000 pseudo-Voigt lines (Thompson, Cox & Hastings 1987
+  FWHM and mixing parameter), Doppler width from T for mass 18 u, Lorentz width
+  proportional to p (296/T)^0.5, on a log-uniform lambda grid at R = 1e5;
+* wind: 5 km/s cos^2(lat) eastward jet plus a 3 km/s day-to-night flow along
+  great circles from the substellar point, proportional to sin(angular distance).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+K_B = 1.380649e-23          # J/K
+M_U = 1.66053906660e-27     # kg
+H_PLANCK = 6.62607015e-34   # J s
+C_LIGHT = 2.99792458e8      # m/s
+R_JUP = 7.1492e7            # m
+BAR = 1.0e5                 # Pa
+
+MODE_ALBEDO = 0
+MODE_EMISSION = 1
+MODE_TRANSMISSION = 2
+
+OPAC_ALBEDO = 0       # per-lambda grey absorption + Rayleigh + per-cell cloud profile
+OPAC_KTABLE = 1       # correlated-k table k[band][g][T][p]
+OPAC_XSEC = 2         # high-resolution cross-section table sigma[lambda][T][p]
+
+
+@dataclasses.dataclass
+class Grid:
+    nlon: int
+    nlat: int
+    nr: int
+    r_edges: np.ndarray      # float64 [nr+1], m, r_edges[0] = R0 (bottom)
+    lat_edges: np.ndarray    # float64 [nlat+1], rad, -pi/2 .. pi/2
+    lon_edges: np.ndarray    # float64 [nlon+1], rad, span 2 pi
+    T: np.ndarray            # float32 [ncell], K,  flattened [k][j][i] (lon fastest)
+    p: np.ndarray            # float32 [ncell], Pa
+    rho: np.ndarray          # float32 [ncell], kg/m^3
+    wind: Optional[np.ndarray] = None   # float32 [3][ncell] (u east, v north, w up), m/s
+
+    @property
+    def ncell(self) -> int:
+        return self.nlon * self.nlat * self.nr
+
+    @property
+    def R0(self) -> float:
+        return float(self.r_edges[0])
+
+    @property
+    def R_toa(self) -> float:
+        return float(self.r_edges[-1])
+
+
+@dataclasses.dataclass
+class AlbedoOpacity:
+    """alpha_ext = rho (kabs + kray) + acld * qcld ; scattering from Rayleigh and cloud."""
+    kabs: np.ndarray         # float64 [nlam], m^2/kg, grey gas absorption per wavelength
+    kray: np.ndarray         # float64 [nlam], m^2/kg, Rayleigh scattering per wavelength
+    qcld: np.ndarray         # float64 [nlam], cloud extinction scale per wavelength
+    wcld: np.ndarray         # float64 [nlam], cloud single-scattering albedo
+    gcld: np.ndarray         # float64 [nlam], cloud HG asymmetry factor
+    acld: Optional[np.ndarray] = None   # float32 [ncell], m^-1 cloud extinction profile
+    kind: int = OPAC_ALBEDO
+
+    @property
+    def nlam(self) -> int:
+        return len(self.kray)
+
+
+@dataclasses.dataclass
+class KTable:
+    lam: np.ndarray          # float64 [nb] band-centre wavelength, m
+    wg: np.ndarray           # float64 [ng] g-ordinate weights (sum 1)
+    gpts: np.ndarray         # float64 [ng] g-ordinates in (0,1)
+    Tg: np.ndarray           # float64 [nT] K, increasing
+    pg: np.ndarray           # float64 [np] Pa, increasing
+    k: np.ndarray            # float32 [nb][ng][nT][np] m^2/kg
+    kind: int = OPAC_KTABLE
+
+
+@dataclasses.dataclass
+class XsecTable:
+    lam: np.ndarray          # float64 [nl] table wavelengths, m, increasing
+    Tg: np.ndarray           # float64 [nT]
+    pg: np.ndarray           # float64 [np]
+    sigma: np.ndarray        # float32 [nl][nT][np] mass cross-section, m^2/kg
+    view_theta: float = 0.5 * math.pi   # viewing polar angle (colatitude) of the observer
+    view_phi: float = math.pi           # viewing longitude of the observer
+    omega_rot: float = 0.0              # planetary rotation rate, rad/s
+    kind: int = OPAC_XSEC
+
+
+@dataclasses.dataclass
+class Options:
+    survival: int = 1            # 1 survival biasing (W <- W omega), 0 analog absorb/scatter
+    w_rr: float = 1.0e-3         # Russian roulette when W < w_rr * W_launch
+    p_surv: float = 0.1          # roulette survival probability
+    tau_peel_cut: float = 50.0   # stop a peel-off / chord march beyond this optical depth
+    tau_vert_max: float = 30.0   # emission: only cells with vertical tau above them < this emit
+    beta_emis: float = 0.5       # emission: hybrid biasing fraction of the uniform-in-cell pdf
+    scatter_emission: int = 0    # emission: follow packets after the launch peel-off
+    max_steps: int = 1 << 22     # per-packet cap on cell segments
+    hg_iso_eps: float = 1.0e-4   # |g| below this samples isotropically
+
+
+@dataclasses.dataclass
+class Source:
+    star: np.ndarray                 # float64 [3] unit vector from planet centre towards the star
+    obs: np.ndarray                  # float64 [n_obs][3] unit vectors towards the observer(s)
+    opts: Options = dataclasses.field(default_factory=Options)
+
+
+@dataclasses.dataclass
+class Job:
+    lam_idx: int
+    g_idx: int                       # g-ordinate (emission) or phase / observer index (albedo)
+    n_packets: int
+    key: int                         # 32-bit job key (Philox counter word 3)
+    obs_idx: int = -1                # albedo: which observer of the source this job tallies (-1: all)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    mode: int
+    grid: Grid
+    opac: object
+    source: Source
+    jobs: list
+    seed: int
+    notes: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def total_packets(self) -> int:
+        return int(sum(j.n_packets for j in self.jobs))
+
+
+# --------------------------------------------------------------------------- grids
+
+def pressure_edges(p_top_bar: float, p_bot_bar: float, nr: int) -> np.ndarray:
+    """N_r + 1 log-uniform pressure edges in Pa, index 0 at the bottom."""
+    return np.logspace(math.log10(p_bot_bar), math.log10(p_top_bar), nr + 1) * BAR
+
+
+def lat_lon_edges(nlon: int, nlat: int):
+    lat = np.linspace(-0.5 * math.pi, 0.5 * math.pi, nlat + 1)
+    lon = np.linspace(-math.pi, math.pi, nlon + 1)
+    return lat, lon
+
+
+def cell_centres(nlon, nlat, lat_edges, lon_edges):
+    latc = 0.5 * (lat_edges[:-1] + lat_edges[1:])
+    lonc = 0.5 * (lon_edges[:-1] + lon_edges[1:])
+    LAT, LON = np.meshgrid(latc, lonc, indexing="ij")   # [nlat][nlon]
+    return LAT, LON
+
+
+def guillot_T(T_h, p_pa, gamma=0.5, T_int=400.0, p_ref=0.1 * BAR):
+    """Guillot (2010)-like profile with tau = p / p_ref:
+    T^4 = 3/4 T_int^4 (2/3 + tau) + 3/4 T_h^4 [2/3 + 1/(gamma sqrt3) + (gamma/sqrt3 - 1/(gamma sqrt3)) exp(-gamma tau sqrt3)]."""
+    tau = p_pa / p_ref
+    s3 = math.sqrt(3.0)
+    irr = 2.0 / 3.0 + 1.0 / (gamma * s3) + (gamma / s3 - 1.0 / (gamma * s3)) * np.exp(-gamma * tau * s3)
+    T4 = 0.75 * T_int ** 4 * (2.0 / 3.0 + tau) + 0.75 * T_h ** 4 * irr
+    return T4 ** 0.25
+
+
+def hotjupiter_T(nlon, nlat, nr, lat_edges, lon_edges, p_cell, T_day=2200.0, T_night=1000.0,
+                 hotspot_deg=15.0):
+    LAT, LON = cell_centres(nlon, nlat, lat_edges, lon_edges)
+    m = np.maximum(0.0, np.cos(LON - math.radians(hotspot_deg)) * np.cos(LAT))
+    T_h = T_night + (T_day - T_night) * m                     # [nlat][nlon]
+    T = guillot_T(T_h[None, :, :], p_cell[:, None, None])     # [nr][nlat][nlon]
+    return T, m
+
+
+def build_grid(nlon, nlat, nr, p_top_bar, p_bot_bar, T_cells, mu=2.3, grav=10.0, R0=R_JUP,
+               lat_edges=None, lon_edges=None, wind=None):
+    """Hypsometric radial grid from the area-weighted mean layer temperature."""
+    if lat_edges is None or lon_edges is None:
+        lat_edges, lon_edges = lat_lon_edges(nlon, nlat)
+    pe = pressure_edges(p_top_bar, p_bot_bar, nr)
+    T3 = np.asarray(T_cells, dtype=np.float64).reshape(nr, nlat, nlon)
+    area = (np.sin(lat_edges[1:]) - np.sin(lat_edges[:-1]))[:, None] * np.diff(lon_edges)[None, :]
+    Tmean = (T3 * area[None]).sum(axis=(1, 2)) / area.sum()
+    H = K_B * Tmean / (mu * M_U * grav)
+    dz = H * np.log(pe[:-1] / pe[1:])
+    r_edges = R0 + np.concatenate([[0.0], np.cumsum(dz)])
+    p_cell = np.sqrt(pe[:-1] * pe[1:])
+    rho_layer = (pe[:-1] - pe[1:]) / (grav * dz)
+    ncell = nlon * nlat * nr
+    p = np.broadcast_to(p_cell[:, None, None], (nr, nlat, nlon)).reshape(ncell)
+    rho = np.broadcast_to(rho_layer[:, None, None], (nr, nlat, nlon)).reshape(ncell)
+    return Grid(nlon=nlon, nlat=nlat, nr=nr, r_edges=r_edges.astype(np.float64),
+                lat_edges=np.asarray(lat_edges, np.float64), lon_edges=np.asarray(lon_edges, np.float64),
+                T=T3.reshape(ncell).astype(np.float32), p=p.astype(np.float32),
+                rho=rho.astype(np.float32), wind=wind)
+
+
+def uniform_grid(nlon, nlat, nr, R0, R_toa, rho=1.0, T=1000.0, p=1.0e4, lat_edges=None, lon_edges=None,
+                 r_edges=None):
+    """Homogeneous test grid: constant rho, T, p (used for analytic cases)."""
+    if lat_edges is None or lon_edges is None:
+        lat_edges, lon_edges = lat_lon_edges(nlon, nlat)
+    if r_edges is None:
+        r_edges = np.linspace(R0, R_toa, nr + 1)
+    ncell = nlon * nlat * nr
+    return Grid(nlon=nlon, nlat=nlat, nr=nr, r_edges=np.asarray(r_edges, np.float64),
+                lat_edges=np.asarray(lat_edges, np.float64), lon_edges=np.asarray(lon_edges, np.float64),
+                T=np.full(ncell, T, np.float32), p=np.full(ncell, p, np.float32),
+                rho=np.full(ncell, rho, np.float32))
+
+
+def phase_dirs(phases_deg):
+    a = np.radians(np.asarray(phases_deg, dtype=np.float64))
+    return np.stack([np.cos(a), np.sin(a), np.zeros_like(a)], axis=1)
+
+
+# --------------------------------------------------------------------------- configurations
+
+def config1_albedo(n_packets=100_000, seed=1, nlon=32, nlat=16, nr=20, omega=0.5, tau_vert=10.0,
+                   survival=1):
+    """Albedo, plain: 32 x 16 x 20 cells, 1e-5..100 bar, isothermal 1500 K, mu = 2.3, g = 10,
+    grey extinction with vertical tau = 10 at the bottom, uniform Rayleigh scattering with
+    omega = 0.5, star and observer at phase 0, one wavelength."""
+    grav = 10.0
+    p_top, p_bot = 1e-5, 100.0
+    T = np.full(nlon * nlat * nr, 1500.0)
+    grid = build_grid(nlon, nlat, nr, p_top, p_bot, T, grav=grav)
+    kext = tau_vert * grav / ((p_bot - p_top) * BAR)        # = 1.0000001e-5 m^2/kg
+    opac = AlbedoOpacity(kabs=np.array([(1 - omega) * kext]), kray=np.array([omega * kext]),
+                         qcld=np.zeros(1), wcld=np.zeros(1), gcld=np.zeros(1), acld=None)
+    src = Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[1.0, 0.0, 0.0]]),
+                 opts=Options(survival=survival))
+    jobs = [Job(lam_idx=0, g_idx=0, n_packets=int(n_packets), key=0)]
+    return Workload("albedo_32x16x20_1e5", MODE_ALBEDO, grid, opac, src, jobs, seed,
+                    notes=dict(kext=kext, grav=grav))
+
+
+def hotjupiter_grid(nlon=128, nlat=64, nr=50, p_top=1e-6, p_bot=100.0, wind=False, grav=10.0):
+    lat_e, lon_e = lat_lon_edges(nlon, nlat)
+    pe = pressure_edges(p_top, p_bot, nr)
+    p_cell = np.sqrt(pe[:-1] * pe[1:])
+    T3, m = hotjupiter_T(nlon, nlat, nr, lat_e, lon_e, p_cell)
+    W = wind_field(nlon, nlat, nr, lat_e, lon_e) if wind else None
+    return build_grid(nlon, nlat, nr, p_top, p_bot, T3, grav=grav, lat_edges=lat_e, lon_edges=lon_e, wind=W), m
+
+
+def make_ktable(rng, nb=30, ng=8, nT=20, npr=15, lam_lo=1e-6, lam_hi=5e-6, sigma_ln=2.0, aT=1.0, ap=0.3):
+    from scipy.special import ndtri
+    lam = np.geomspace(lam_lo, lam_hi, nb)
+    x, w = np.polynomial.legendre.leggauss(ng)
+    gpts = 0.5 * (x + 1.0)
+    wg = 0.5 * w
+    Tg = np.geomspace(500.0, 3000.0, nT)
+    pg = np.geomspace(1e-6 * BAR, 100.0 * BAR, npr)
+    kmed = 10.0 ** rng.uniform(-5.0, -1.0, nb)
+    k = (kmed[:, None, None, None]
+         * (Tg[None, None, :, None] / 1500.0) ** aT
+         * (pg[None, None, None, :] / BAR) ** ap
+         * np.exp(sigma_ln * ndtri(gpts))[None, :, None, None])
+    return KTable(lam=lam, wg=wg, gpts=gpts, Tg=Tg, pg=pg, k=k.astype(np.float32))
+
+
+def config2_emission(n_packets=1_000_000, seed=2, nlon=128, nlat=64, nr=50, nb=30, ng=8,
+                     bands=None, gpoints=None, obs=None):
+    """Emission: 128 x 64 x 50 hot-Jupiter grid (1e-6..100 bar), correlated-k 30 bands x 8
+    g-ordinates, scattering off, observer at the substellar direction, 1e6 packets per (band, g)."""
+    rng = np.random.default_rng(seed)
+    grid, _ = hotjupiter_grid(nlon, nlat, nr)
+    kt = make_ktable(rng, nb=nb, ng=ng)
+    if obs is None:
+        obs = np.array([[1.0, 0.0, 0.0]])
+    src = Source(star=np.array([1.0, 0.0, 0.0]), obs=np.asarray(obs, np.float64),
+                 opts=Options(scatter_emission=0))
+    bands = range(nb) if bands is None else bands
+    gpoints = range(ng) if gpoints is None else gpoints
+    jobs = [Job(lam_idx=b, g_idx=g, n_packets=int(n_packets), key=(b << 8) | g) for b in bands for g in gpoints]
+    return Workload(f"emission_{nlon}x{nlat}x{nr}_{nb}bx{ng}g", MODE_EMISSION, grid, kt, src, jobs, seed)
+
+
+def cloud_profile(grid: Grid, m_day, tau_cld=5.0, p_peak=0.1 * BAR, width_dex=0.5, day_thin=0.6):
+    """Log-normal cloud deck: layer tau proportional to exp(-(log10(p/p_peak))^2 / (2 w^2)),
+    column tau = tau_cld (thinned by (1 - day_thin * m) towards the hot spot)."""
+    nr, nlat, nlon = grid.nr, grid.nlat, grid.nlon
+    p_layer = grid.p.reshape(nr, nlat, nlon)[:, 0, 0].astype(np.float64)
+    gk = np.exp(-(np.log10(p_layer / p_peak)) ** 2 / (2.0 * width_dex ** 2))
+    dtau = tau_cld * gk / gk.sum()
+    dz = np.diff(grid.r_edges)
+    a = (dtau / dz)[:, None, None] * (1.0 - day_thin * m_day)[None, :, :]
+    return np.broadcast_to(a, (nr, nlat, nlon)).reshape(grid.ncell).astype(np.float32)
+
+
+def config3_phase_curve(seed=3, nlon=128, nlat=64, nr=50, nlam=40, nphase=24, n_lo=10_000, n_hi=1_000_000,
+                        lam_lo=0.3e-6, lam_hi=1.0e-6):
+    """Batched albedo phase curve: C2's grid + Rayleigh gas + log-normal cloud deck (peak 0.1 bar,
+    0.5 dex, omega = 0.9, HG g = 0.6); 24 phase angles x 40 wavelengths, packets per job uniform in
+    [1e4, 1e6]."""
+    rng = np.random.default_rng(seed)
+    grid, m = hotjupiter_grid(nlon, nlat, nr)
+    lam = np.geomspace(lam_lo, lam_hi, nlam)
+    kray = 3.1e-5 * (lam / 0.5e-6) ** -4
+    kabs = 5.0e-5 * 10.0 ** (0.5 * np.sin(12.0 * np.log(lam / lam_lo)))
+    opac = AlbedoOpacity(kabs=kabs, kray=kray, qcld=np.ones(nlam), wcld=np.full(nlam, 0.9),
+                         gcld=np.full(nlam, 0.6), acld=cloud_profile(grid, m))
+    phases = np.arange(nphase) * (360.0 / nphase)
+    src = Source(star=np.array([1.0, 0.0, 0.0]), obs=phase_dirs(phases), opts=Options())
+    npk = rng.integers(n_lo, n_hi + 1, size=(nlam, nphase))
+    jobs = [Job(lam_idx=l, g_idx=ph, n_packets=int(npk[l, ph]), key=(l << 8) | ph, obs_idx=ph)
+            for l in range(nlam) for ph in range(nphase)]
+    return Workload(f"phasecurve_{nlon}x{nlat}x{nr}_{nlam}lx{nphase}ph", MODE_ALBEDO, grid, opac, src, jobs,
+                    seed, notes=dict(phases_deg=phases.tolist()))
+
+
+def wind_field(nlon, nlat, nr, lat_edges, lon_edges, u_jet=5000.0, v_dn=3000.0):
+    """(u east, v north, w up) in m/s: cos^2(lat) eastward jet + day->night great-circle flow
+    |v| = v_dn sin(angular distance from the substellar point at lon 0, lat 0)."""
+    LAT, LON = cell_centres(nlon, nlat, lat_edges, lon_edges)
+    n = np.stack([np.cos(LAT) * np.cos(LON), np.cos(LAT) * np.sin(LON), np.sin(LAT)], axis=-1)
+    s = np.array([1.0, 0.0, 0.0])
+    tang = s[None, None, :] - (n @ s)[..., None] * n          # points towards the substellar point
+    vdn = -v_dn * tang
+    east = np.stack([-np.sin(LON), np.cos(LON), np.zeros_like(LON)], axis=-1)
+    north = np.stack([-np.sin(LAT) * np.cos(LON), -np.sin(LAT) * np.sin(LON), np.cos(LAT)], axis=-1)
+    u = u_jet * np.cos(LAT) ** 2 + (vdn * east).sum(-1)
+    v = (vdn * north).sum(-1)
+    w = np.zeros_like(u)
+    W = np.stack([u, v, w], axis=0)                             # [3][nlat][nlon]
+    W = np.broadcast_to(W[:, None, :, :], (3, nr, nlat, nlon)).reshape(3, nr * nlat * nlon)
+    return np.ascontiguousarray(W, dtype=np.float32)
+
+
+def pseudo_voigt_fwhm_eta(fG, fL):
+    """Thompson, Cox & Hastings (1987) pseudo-Voigt total FWHM and Lorentz fraction."""
+    f = (fG ** 5 + 2.69269 * fG ** 4 * fL + 2.42843 * fG ** 3 * fL ** 2 + 4.47163 * fG ** 2 * fL ** 3
+         + 0.07842 * fG * fL ** 4 + fL ** 5) ** 0.2
+    x = fL / f
+    eta = 1.36603 * x - 0.47719 * x ** 2 + 0.11116 * x ** 3
+    return f, eta
+
+
+def make_xsec_table(rng, n_lines=5000, R=1.0e5, lam0=1.0e-6, n_lam=9532, margin=8, nT=20, npr=15,
+                    p_top=1e-6, p_bot=100.0, sigma_cont=3.0e-5, s_max=1.5e-2, mass_u=18.0):
+    """sigma(lambda, T, p) in m^2/kg on lambda_i = lam0 exp((i - margin)/R), i = 0 .. n_lam + 2 margin - 1.
+    Lines are deposited on the index grid and convolved (FFT) with a unit-area pseudo-Voigt profile."""
+    nl = n_lam + 2 * margin
+    lam = lam0 * np.exp((np.arange(nl) - margin) / R)
+    Tg = np.geomspace(500.0, 3000.0, nT)
+    pg = np.geomspace(p_top * BAR, p_bot * BAR, npr)
+    centres = rng.uniform(margin, margin + n_lam, n_lines)          # in index units
+    strength = s_max * 10.0 ** rng.uniform(-6.0, 0.0, n_lines)
+    pad = 4096
+    nfft = 1 << int(math.ceil(math.log2(nl + 2 * pad)))
+    stick = np.zeros(nfft)
+    i0 = np.floor(centres).astype(np.int64)
+    fr = centres - i0
+    np.add.at(stick, i0 + pad, strength * (1.0 - fr))
+    np.add.at(stick, i0 + 1 + pad, strength * fr)
+    S = np.fft.rfft(stick)
+    off = np.arange(nfft)
+    off = np.where(off < nfft // 2, off, off - nfft).astype(np.float64)
+    sigma = np.empty((nl, nT, npr), dtype=np.float64)
+    m_kg = mass_u * M_U
+    for a, T in enumerate(Tg):
+        fG = R * math.sqrt(8.0 * K_B * T * math.log(2.0) / m_kg) / C_LIGHT      # FWHM in index units
+        for b, p in enumerate(pg):
+            fL = 2.0 * 0.05 * (p / 101325.0) * math.sqrt(296.0 / T) * 1.0e-4 * R   # 0.05 cm^-1/atm HWHM at 1e4 cm^-1
+            f, eta = pseudo_voigt_fwhm_eta(fG, fL)
+            g = math.sqrt(4.0 * math.log(2.0) / math.pi) / f * np.exp(-4.0 * math.log(2.0) * off ** 2 / f ** 2)
+            lor = (f / (2.0 * math.pi)) / (off ** 2 + 0.25 * f ** 2)
+            kern = eta * lor + (1.0 - eta) * g
+            kern /= kern.sum()
+            spec = np.fft.irfft(S * np.fft.rfft(kern), nfft)[pad:pad + nl]
+            sigma[:, a, b] = sigma_cont + np.maximum(spec, 0.0)
+    return XsecTable(lam=lam, Tg=Tg, pg=pg, sigma=sigma.astype(np.float32)), margin
+
+
+def config4_transmission(n_packets=10_000, seed=4, nlon=96, nlat=48, nr=60, n_lam=9532, lam_subset=None,
+                         n_lines=5000, p_top=1e-6, p_bot=100.0, rot_period_days=3.5):
+    """High-resolution transmission: 96 x 48 x 60 grid with winds, sigma(lambda, T, p) at R = 1e5 over
+    1.0-1.1 um, per-cell Doppler shift, 1e4 limb chords per wavelength."""
+    rng = np.random.default_rng(seed)
+    grid, _ = hotjupiter_grid(nlon, nlat, nr, p_top=p_top, p_bot=p_bot, wind=True)
+    xs, margin = make_xsec_table(rng, n_lines=n_lines, n_lam=n_lam)
+    xs.omega_rot = 2.0 * math.pi / (rot_period_days * 86400.0)
+    xs.view_theta = 0.5 * math.pi      # observer on the -x axis: colatitude 90 deg, longitude 180 deg
+    xs.view_phi = math.pi
+    src = Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[-1.0, 0.0, 0.0]]), opts=Options())
+    lams = range(n_lam) if lam_subset is None else lam_subset
+    jobs = [Job(lam_idx=margin + l, g_idx=0, n_packets=int(n_packets), key=l) for l in lams]
+    return Workload(f"transmission_{nlon}x{nlat}x{nr}_{n_lam}l", MODE_TRANSMISSION, grid, xs, src, jobs, seed,
+                    notes=dict(margin=margin))
+
+
+# --------------------------------------------------------------------------- small analytic cases
+
+def uniform_absorber_sphere(alpha=2.0e-6, R0=R_JUP, H_atm=5.0e6, nlon=4, nlat=4, nr=4, n_packets=20000,
+                            seed=11):
+    """Pure-absorber shell R0..R0+H with constant alpha (rho = 1, kappa = alpha): chord tau(b) =
+    2 alpha sqrt(R_toa^2 - b^2) for b >= R0."""
+    grid = uniform_grid(nlon, nlat, nr, R0, R0 + H_atm, rho=1.0)
+    xs_lam = np.array([1.0e-6, 1.1e-6])
+    xs = XsecTable(lam=xs_lam, Tg=np.array([500.0, 3000.0]), pg=np.array([1.0, 1.0e7]),
+                   sigma=np.full((2, 2, 2), alpha, np.float32), omega_rot=0.0)
+    src = Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[-1.0, 0.0, 0.0]]), opts=Options())
+    jobs = [Job(lam_idx=0, g_idx=0, n_packets=n_packets, key=0)]
+    return Workload("uniform_absorber", MODE_TRANSMISSION, grid, xs, src, jobs, seed)
+
+
+def slab_sphere_albedo(omega=0.5, tau=20.0, phase="iso", g=0.0, n_packets=100_000, seed=12, thin=1.0e-4,
+                       nlon=8, nlat=8, survival=1):
+    """Homogeneous one-layer atmosphere of thickness thin * R0 and vertical optical depth tau on a
+    black sphere: locally a plane-parallel slab.  phase = 'iso' (HG with g = 0), 'hg' or 'rayleigh'."""
+    R0 = R_JUP
+    H = thin * R0
+    grid = uniform_grid(nlon, nlat, 1, R0, R0 + H, rho=1.0)
+    kext = tau / H
+    if phase == "rayleigh":
+        opac = AlbedoOpacity(kabs=np.array([(1 - omega) * kext]), kray=np.array([omega * kext]),
+                             qcld=np.zeros(1), wcld=np.zeros(1), gcld=np.zeros(1))
+    else:
+        opac = AlbedoOpacity(kabs=np.array([0.0]), kray=np.array([0.0]), qcld=np.ones(1),
+                             wcld=np.array([omega]), gcld=np.array([g if phase == "hg" else 0.0]),
+                             acld=np.full(grid.ncell, kext, np.float32))
+    src = Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[1.0, 0.0, 0.0]]),
+                 opts=Options(survival=survival, w_rr=1e-4))
+    jobs = [Job(lam_idx=0, g_idx=0, n_packets=n_packets, key=0)]
+    return Workload(f"slab_{phase}_w{omega}_t{tau}", MODE_ALBEDO, grid, opac, src, jobs, seed)
+
+
+def isothermal_emitter(tau=2.0, T=1500.0, thin=1.0e-4, nlon=8, nlat=8, nr=4, n_packets=100_000, seed=13,
+                       lam=2.0e-6):
+    """Isothermal, uniform-kappa shell with scattering off: escaping intensity B (1 - exp(-tau/mu))."""
+    R0 = R_JUP
+    H = thin * R0
+    grid = uniform_grid(nlon, nlat, nr, R0, R0 + H, rho=1.0, T=T, p=1.0e4)
+    kap = tau / H
+    kt = KTable(lam=np.array([lam]), wg=np.array([1.0]), gpts=np.array([0.5]),
+                Tg=np.array([500.0, 3000.0]), pg=np.array([1.0, 1.0e7]),
+                k=np.full((1, 1, 2, 2), kap, np.float32))
+    src = Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[1.0, 0.0, 0.0]]),
+                 opts=Options(scatter_emission=0))
+    jobs = [Job(lam_idx=0, g_idx=0, n_packets=n_packets, key=0)]
+    return Workload("isothermal_emitter", MODE_EMISSION, grid, kt, src, jobs, seed)
