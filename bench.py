@@ -1,0 +1,305 @@
+#!/usr/bin/env python
+"""Benchmark of the photon-transport hot path on GB300.
+
+Workload (default): thermal emission spectrum of a hot-Jupiter-shaped grid, 128 lon x 64 lat x 50
+levels (1e-6..100 bar), correlated-k with 30 bands x 8 g-ordinates, 1e6 packets per (band, g) job,
+FP32 march with FP64 emission CDF and fixed-point tallies.  One step = the whole path for all 240
+jobs: cell tables (S1) and one persistent transport launch (S2-S8) with device tallies.
+
+Prints ONE JSON line (rank 0): packet-steps/s of the batched form (value), the plain one-launch-
+per-job form beside it, spectra/s, the end-to-end number through the C ABI from pinned host
+buffers, the roofline of the transport kernel, the oracle's CPU baseline and the clocks seen.
+`--impl reference` times the FP64 CPU oracle on the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+OPS_PER_STEP = 64          # FP32-pipe operations of one cell step (count in the design doc)
+PEAK_FP32_OPS = 152 * 128 * 2.07e9   # GB300: SMs x FP32 lanes x max SM clock (an FMA counts as one op)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gcmc", choices=["gcmc", "reference"])
+    ap.add_argument("--packets", type=int, default=1_000_000, help="packets per (band, g) job")
+    ap.add_argument("--bands", type=int, default=30)
+    ap.add_argument("--gpoints", type=int, default=8)
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--interval", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args, rank):
+    from paper_2110_15640_gb300 import synth
+    wl = synth.config2_emission(n_packets=args.packets, nb=30, ng=8, bands=range(args.bands),
+                                gpoints=range(args.gpoints))
+    wl.seed = 2 + 7919 * rank          # distinct packets per rank (weak scaling)
+    return wl
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = [l.split(",") for l in (self.out or "").strip().splitlines() if l.count(",") >= 6]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if "Active" in r[3 + q] and "Not" not in r[3 + q]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_uuid(dev):
+    try:
+        import torch
+        u = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+        return f"GPU-{u}" if u is not None else None
+    except Exception:  # noqa: BLE001
+        return None
+
+
+def cpu_oracle_rate(wl, n_jobs, n_packets, nthreads):
+    """Oracle (FP64 CPU) packet-steps/s on a sample of the workload's jobs, S1 included."""
+    from oracle import oracle as O
+    steps = 0
+    t0 = time.perf_counter()
+    for job in wl.jobs[:n_jobs]:
+        cells = O.prep_cells(wl, job)
+        r = O.run(wl, job, cells=cells, packet0=0, n_run=n_packets, nthreads=nthreads)
+        steps += r["steps"]
+    dt = time.perf_counter() - t0
+    return steps / dt, dt, steps
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    wl = workload(args, 0)
+    cores = os.cpu_count() or 1
+    nj, npk = 2, min(args.packets, 200_000)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(wl, 1, 20_000, cores)
+    rates, total_steps, total_t = [], 0, 0.0
+    for _ in range(args.steps):
+        r, dt, st = cpu_oracle_rate(wl, nj, npk, cores)
+        rates.append(r)
+        total_steps += st
+        total_t += dt
+    value = total_steps / total_t
+    sample = f"{nj} of {len(wl.jobs)} (band, g) jobs x {npk} packets per step (S1 + transport), full 128x64x50 grid"
+    line = {"metric": "packet-steps/s", "value": value, "unit": "packet-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": wl.name, "jobs": len(wl.jobs), "packets_per_job": args.packets},
+            "cpu_baseline": {"value": value, "unit": "packet-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "packet-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2110_15640_gb300 import build, gcmc
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    wl = workload(args, rank)
+    stream = torch.cuda.Stream()
+    ctx = gcmc.Context(local, stream=stream)
+    cfg = gcmc.gcmc_launch_cfg(args.block, 0, args.chunk, args.interval)
+    with torch.cuda.stream(stream):
+        gid, oid, sid, jobs = gcmc.load_workload(ctx, wl, gcmc.FP32, device_inputs=True)
+        tall = torch.zeros((len(jobs), gcmc.MAX_OBS), dtype=torch.float64, device="cuda")
+        _, sts = ctx.run_batch(jobs, cfg=cfg)                       # untimed: exact packet-step count
+    steps_per_step = int(sum(s.steps for s in sts))
+    packets_per_step = int(sum(s.packets for s in sts))
+    capped = float(sum(s.ledger[6] for s in sts))
+
+    # ---------------- batched form: value
+    for _ in range(args.warmup):
+        ctx.run_batch(jobs, cfg=cfg, tallies=tall, stats=False)
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    l0 = gcmc.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_uuid(local)) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.run_batch(jobs, cfg=cfg, tallies=tall, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = gcmc.kernel_launches() - l0
+    prep_ms, tr_ms, ntr = ctx.get_profile()
+    ctx.set_profiling(False)
+    t = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        tt = torch.tensor([t], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t = float(tt.item())
+    value = steps_per_step * args.steps * world / t
+
+    # ---------------- plain form: one launch per job (same work)
+    outp = torch.zeros(gcmc.MAX_OBS, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        for j in jobs[:8]:
+            ctx.run_packets(j, tallies=outp)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.plain_steps):
+        for j in jobs:
+            ctx.run_packets(j, tallies=outp)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = p0.elapsed_time(p1) / 1e3
+    plain_value = steps_per_step * args.plain_steps / t_plain
+
+    # ---------------- end to end through the C ABI from pinned host buffers
+    ga, oa = gcmc.workload_arrays(wl, "pinned")
+    h2d = gcmc.array_bytes(ga) + gcmc.array_bytes(oa)
+    d2h = len(jobs) * (32 * 8 + 4 * 8)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    F_band = None
+    for _ in range(args.e2e_steps):
+        g2 = ctx.upload_grid(wl.grid, device_arrays=ga, memory=gcmc.MEM_HOST)
+        o2 = ctx.upload_opacity(g2, wl.opac, device_arrays=oa, memory=gcmc.MEM_HOST)
+        s2 = ctx.set_source(g2, wl.source, gcmc.FP32)
+        jb = [gcmc.Context.job(g2, o2, s2, j.mode, j.lam_idx, j.g_idx, j.n_packets, j.seed, j.job_key) for j in jobs]
+        tl, st2 = ctx.run_batch(jb, cfg=cfg)
+        F = np.zeros((args.bands, args.gpoints))
+        for q, j in enumerate(wl.jobs):
+            ob = ctx.postscale(g2, gcmc.EMISSION, tl[q][0], j.n_packets, st2[q].l_tot)
+            F[j.lam_idx, j.g_idx] = ob["F_p"]
+        F_band = F @ wl.opac.wg[:args.gpoints]
+        ctx.release_grid(g2)
+    torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - te) / args.e2e_steps
+    e2e_value = steps_per_step / t_e2e
+
+    # ---------------- roofline of the transport kernel and the gather roofline
+    tr_avg = tr_ms / max(ntr, 1) / 1e3
+    achieved = OPS_PER_STEP * steps_per_step / tr_avg / 1e12
+    gather = ctx.gather_bench(wl.grid.ncell, 4, 1 << 30)
+    clocks = clk.summary()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores = os.cpu_count() or 1
+        rate, dt, _ = cpu_oracle_rate(wl, 4, min(args.packets, 1_000_000), cores)
+        cpu = {"value": rate, "unit": "packet-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"4 of {len(jobs)} (band, g) jobs x {min(args.packets, 1_000_000)} packets, S1 + transport, "
+                         f"{dt:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": "packet-steps/s", "value": value, "unit": "packet-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "spectra_per_s": world * args.steps / t,
+            "config": {"workload": wl.name, "jobs": len(jobs), "packets_per_job": args.packets,
+                       "grid": "128x64x50", "packet_steps_per_step": steps_per_step,
+                       "packets_per_step": packets_per_step, "capped_weight": capped,
+                       "l2": "inputs larger than L2 (per-step cell tables ~2 GB)",
+                       "precision": "FP32 march, FP64 emission pdf, 64-bit fixed-point tallies",
+                       "launch": {"block": args.block or 128, "chunk": args.chunk or 1024,
+                                  "interval": args.interval or 1}},
+            "plain_form": {"value": plain_value, "unit": "packet-steps/s", "ms_per_step": 1e3 * t_plain / args.plain_steps,
+                           "launches_per_step": len(jobs)},
+            "batched_over_plain": value / plain_value,
+            "e2e": {"value": e2e_value, "unit": "packet-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": 1e3 * t_e2e},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_OPS / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved / (PEAK_FP32_OPS / 1e12), "traffic": None,
+                         "kernel": "k_transport_persistent<float>", "ops_per_step": OPS_PER_STEP,
+                         "kernel_ms": 1e3 * tr_avg, "prep_ms": prep_ms / max(ntr, 1)},
+            "gather_roofline": {"gathers_per_s": gather, "table_records": wl.grid.ncell, "record_bytes": 4,
+                                "frac": (steps_per_step / tr_avg) / gather},
+            "cpu_baseline": cpu,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "spectrum_F_p_band_mean": float(np.mean(F_band)) if F_band is not None else None,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,270 @@
+/*
+ * gcmc.h -- C ABI of libgcmc: GB300-native Monte Carlo radiative transfer of photon packets
+ * through a 3D spherical (longitude x latitude x pressure-level) exoplanet atmosphere, after
+ * the gCMCRT method (Lee et al. 2022, arXiv:2110.15640).
+ *
+ * The calls follow the paper's statement of the problem (Sect. 2): the host prepares the grid
+ * and the opacity structure and hands them to GPU memory ("global GPU modules"), packets are
+ * run on the GPU, and the image/spectrum tallies come back to the host.  Three modes:
+ *   GCMC_ALBEDO        scattered starlight with peel-off towards the observer (Sect. 4.6, 5.2)
+ *   GCMC_EMISSION      thermal emission from the atmospheric volume (Sect. 4.3, 4.6, 5.3)
+ *   GCMC_TRANSMISSION  limb chords through the annulus (Sect. 5.1), with per-cell Doppler-shifted
+ *                      high-resolution opacity (Sect. 7)
+ *
+ * Conventions
+ *  - Status: every call returns 0 (GCMC_OK) or a negative GCMC_ERR_* code; no exceptions cross
+ *    the ABI.  gcmc_last_error() gives a one-line message for the last failure of a context.
+ *  - Memory: input pointers are host or device memory as the descriptor's `memory` field says
+ *    (GCMC_MEM_HOST / GCMC_MEM_DEVICE).  The library copies what it needs during the call; the
+ *    caller keeps ownership of its buffers.  Device memory the library needs (resident grids,
+ *    opacity tables, per-job cell tables, work queues) is obtained through the context's
+ *    allocator (cudaMalloc unless gcmc_set_allocator installs another) and released by
+ *    gcmc_destroy.
+ *  - Streams: all work of a context is ordered on its stream (gcmc_set_stream; default: the
+ *    legacy default stream).  Calls that return host results synchronise that stream.
+ *  - Threads: a context is not thread-safe; use one context per host thread.
+ *  - Determinism: tallies depend only on (grid, opacity, source, mode, lambda, g, N, seed, job
+ *    key).  Packets draw counter-based Philox4x32-10 numbers keyed by (seed; packet, event, job
+ *    key); tallies are accumulated as 64-bit fixed point (2^-32 resolution), so the result of a
+ *    job is bit-identical whether it runs alone or batched with other jobs.
+ *  - Units: SI (m, m^-1, m^2/kg, kg/m^3, K, Pa, W).  Per-cell arrays are flattened [k][j][i]
+ *    with longitude fastest; k = 0 is the bottom shell.
+ */
+#ifndef GCMC_H
+#define GCMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GCMC_MAX_OBS 8
+
+typedef struct gcmc_ctx gcmc_ctx;
+typedef int gcmc_status;
+
+enum {
+    GCMC_OK = 0,
+    GCMC_ERR_ARG = -1,        /* invalid argument (sizes, ids, NULL, non-monotone edges) */
+    GCMC_ERR_OOM = -2,        /* the allocator returned NULL */
+    GCMC_ERR_CUDA = -3,       /* a CUDA runtime call failed (message in gcmc_last_error) */
+    GCMC_ERR_STEP_CAP = -4,   /* reported in stats: packets stopped by the per-packet step cap */
+    GCMC_ERR_TIMEOUT = -5,    /* a bounded wait gave up */
+    GCMC_ERR_NOT_READY = -6,  /* gcmc_poll: the ticket's work is still running */
+    GCMC_ERR_NAN = -7,        /* NaN, infinite or negative values in an upload */
+    GCMC_ERR_RANGE = -8       /* a size exceeds a compiled limit */
+};
+
+enum { GCMC_ALBEDO = 0, GCMC_EMISSION = 1, GCMC_TRANSMISSION = 2 };
+enum { GCMC_MEM_HOST = 0, GCMC_MEM_DEVICE = 1 };
+enum { GCMC_FP32 = 0, GCMC_FP64 = 1 };
+enum { GCMC_OPAC_ALBEDO = 0, GCMC_OPAC_KTABLE = 1, GCMC_OPAC_XSEC = 2 };
+
+typedef void *(*gcmc_alloc_fn)(size_t bytes, void *user);
+typedef void (*gcmc_free_fn)(void *ptr, void *user);
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  *out receives the handle. */
+gcmc_status gcmc_create(int device, gcmc_ctx **out);
+/* Release every device buffer of the context and the context itself. */
+gcmc_status gcmc_destroy(gcmc_ctx *ctx);
+/* Order all later work of the context on `cuda_stream` (a cudaStream_t; NULL = default stream). */
+gcmc_status gcmc_set_stream(gcmc_ctx *ctx, void *cuda_stream);
+/* Route the context's device allocations through alloc/free (e.g. a framework's caching
+   allocator).  Must be called before the first upload.  NULL restores cudaMalloc/cudaFree. */
+gcmc_status gcmc_set_allocator(gcmc_ctx *ctx, gcmc_alloc_fn alloc, gcmc_free_fn free_fn, void *user);
+/* Message of the last failing call on this context ("" if none).  Owned by the context. */
+const char *gcmc_last_error(gcmc_ctx *ctx);
+
+/* ---------------------------------------------------------------- grid (Sect. 2, 7) */
+
+typedef struct {
+    int32_t nlon, nlat, nr;   /* cells in longitude, latitude, radius; nlon >= 1, nlat >= 1, nr >= 1 */
+    int32_t memory;           /* GCMC_MEM_HOST or GCMC_MEM_DEVICE for every pointer below */
+    const double *r_edges;    /* [nr+1] shell radii, m, strictly increasing; r_edges[0] = R0 (black bottom) */
+    const double *lat_edges;  /* [nlat+1] latitude edges, rad, strictly increasing, -pi/2 .. pi/2 */
+    const double *lon_edges;  /* [nlon+1] longitude edges, rad, strictly increasing, span exactly 2 pi */
+    const float *T;           /* [ncell] temperature, K (> 0) */
+    const float *p;           /* [ncell] pressure, Pa (> 0) */
+    const float *rho;         /* [ncell] density, kg/m^3 (>= 0) */
+    const float *wind;        /* [3][ncell] (u east, v north, w up), m/s, or NULL */
+} gcmc_grid_desc;
+
+/* Copy a grid to the device; *grid_id receives its id.  Errors: GCMC_ERR_ARG (sizes, edges),
+   GCMC_ERR_NAN (non-finite or non-positive T, p; negative rho), GCMC_ERR_OOM, GCMC_ERR_CUDA. */
+gcmc_status gcmc_upload_grid(gcmc_ctx *ctx, const gcmc_grid_desc *desc, int *grid_id);
+
+/* ---------------------------------------------------------------- opacity (Sect. 3.6, 7) */
+
+typedef struct {
+    int32_t kind;             /* GCMC_OPAC_ALBEDO, GCMC_OPAC_KTABLE or GCMC_OPAC_XSEC */
+    int32_t memory;           /* where the pointers live */
+    /* GCMC_OPAC_ALBEDO: per wavelength l, alpha_ext = rho (kabs + kray) + acld qcld,
+       alpha_sca = rho kray + wcld acld qcld, omega = alpha_sca / alpha_ext,
+       P_gas = rho kray / alpha_sca (Sect. 3.6), HG asymmetry g = gcld */
+    int32_t nlam;
+    const double *kabs, *kray, *qcld, *wcld, *gcld;   /* [nlam] each */
+    const float *acld;                                /* [ncell] cloud extinction, 1/m, or NULL */
+    /* GCMC_OPAC_KTABLE: k[b][g][T][p] (m^2/kg), bilinear in (ln T, ln p) of ln k, clamped */
+    int32_t nb, ng, nT, np;
+    const double *lam;        /* [nb] band-centre wavelength (m), for the Planck function */
+    const double *Tg, *pg;    /* [nT], [np] strictly increasing table axes */
+    const float *k;           /* [nb][ng][nT][np] */
+    /* GCMC_OPAC_XSEC: sigma[l][T][p] (m^2/kg) on wavelengths xlam[nl]; uses Tg, pg, nT, np above */
+    int32_t nl, pad;
+    const double *xlam;       /* [nl] strictly increasing, m */
+    const float *sigma;       /* [nl][nT][np] > 0 */
+    double view_theta;        /* observer polar angle (colatitude), rad, for v_LOS (Sect. 7) */
+    double view_phi;          /* observer longitude, rad */
+    double omega_rot;         /* planetary rotation rate, rad/s */
+} gcmc_opacity_desc;
+
+/* Copy an opacity description for grid `grid_id` to the device.  *opac_id receives its id.
+   Errors: GCMC_ERR_ARG, GCMC_ERR_NAN (negative or non-finite opacities), GCMC_ERR_OOM, GCMC_ERR_CUDA. */
+gcmc_status gcmc_upload_opacity(gcmc_ctx *ctx, int grid_id, const gcmc_opacity_desc *desc, int *opac_id);
+
+/* ---------------------------------------------------------------- source and options (Sect. 4, 5) */
+
+typedef struct {
+    double star[3];           /* unit vector from the planet centre towards the star */
+    int32_t n_obs;            /* 1 .. GCMC_MAX_OBS observer directions */
+    int32_t survival;         /* 1 survival biasing W <- W omega (Sect. 4.4); 0 analog absorb/scatter */
+    double obs[GCMC_MAX_OBS][3]; /* unit vectors towards the observer(s) */
+    double w_rr;              /* Russian roulette (Sect. 4.5) when W < w_rr * W_launch */
+    double p_surv;            /* roulette survival probability (weight / p_surv on survival) */
+    double tau_peel_cut;      /* peel-off / chord marches stop beyond this optical depth */
+    double tau_vert_max;      /* emission: cells with vertical tau above them >= this do not emit (Sect. 4.6) */
+    double beta_emis;         /* emission: hybrid biasing fraction of the uniform-in-cell pdf (Sect. 4.3) */
+    double hg_iso_eps;        /* |g| below this samples HG isotropically */
+    int32_t scatter_emission; /* emission: 1 = follow packets after the launch peel-off */
+    int32_t precision;        /* GCMC_FP32 (FP32 march, FP64 near-tangent roots) or GCMC_FP64 */
+    int64_t max_steps;        /* per-packet cap on cell segments (stats count capped packets) */
+} gcmc_source_desc;
+
+/* Register a source description; *source_id receives its id.  Errors: GCMC_ERR_ARG. */
+gcmc_status gcmc_set_source(gcmc_ctx *ctx, int grid_id, const gcmc_source_desc *desc, int *source_id);
+
+/* ---------------------------------------------------------------- running packets */
+
+typedef struct {
+    int64_t packets;          /* packets run */
+    int64_t steps;            /* packet-steps: cell segments processed in flights, peel-offs and chords */
+    double ledger[8];         /* sum of weights: emitted, escaped, absorbed, bottom, roulette gain,
+                                 roulette loss, step-capped, lost (emitted + gain = the rest) */
+    double l_tot;             /* emission: total luminosity of the emitting cells, W/m (Sect. 5.3) */
+    double cdf_total;         /* emission: total of the hybrid pdf (1 up to rounding) */
+    int64_t n_emit_cells;     /* emission: cells above the tau_vert cut */
+} gcmc_stats;
+
+typedef struct {
+    int32_t grid_id, opac_id, source_id, mode;
+    int32_t lam_idx;          /* wavelength (albedo, xsec) or band (k-table) index */
+    int32_t g_idx;            /* g-ordinate (k-table); ignored otherwise */
+    int32_t obs_idx;          /* -1: tally every observer of the source; else only observer obs_idx */
+    uint32_t job_key;         /* 32-bit key of the job in the Philox counter */
+    int64_t n_packets;
+    uint64_t seed;
+} gcmc_job;
+
+/* Plain form: one job, one cell-table preparation and one transport launch (one thread per packet).
+   tallies_out: [n_obs] sums over packets of f (the host divides by N, see gcmc_postscale), in
+   host or device memory per tallies_memory.  stats_out may be NULL.  Synchronises the stream
+   when tallies_memory is GCMC_MEM_HOST or stats_out is not NULL. */
+gcmc_status gcmc_run_packets(gcmc_ctx *ctx, const gcmc_job *job, double *tallies_out, int tallies_memory,
+                             gcmc_stats *stats_out);
+
+typedef struct {
+    int32_t block;            /* threads per block (multiple of 32), 0 = default */
+    int32_t blocks_per_sm;    /* resident blocks per SM of the persistent grid, 0 = default */
+    int32_t chunk;            /* packets per warp work item (multiple of 32), 0 = default (1024) */
+    int32_t interval;         /* march steps between warp refill checks, 0 = default (1) */
+    int32_t refill_min;       /* refill a warp's idle lanes only when at least this many (1..32) are idle,
+                                 or when its work item has no packets left to start; 0 = default (16) */
+    int32_t pad;
+} gcmc_launch_cfg;
+
+/* Batched form: cell tables of every job, then ONE persistent transport launch that drains a
+   device work queue of (job, packet range) items.  tallies_out: [n_jobs][GCMC_MAX_OBS].
+   stats_out: [n_jobs] or NULL.  cfg may be NULL (defaults). */
+gcmc_status gcmc_run_batch(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, const gcmc_launch_cfg *cfg,
+                           double *tallies_out, int tallies_memory, gcmc_stats *stats_out);
+
+/* Asynchronous batched form for request loops: enqueue the work on the context's stream and
+   return a ticket at once; gcmc_poll returns GCMC_ERR_NOT_READY until the ticket's work has
+   finished, then fills tallies_out [n_jobs][GCMC_MAX_OBS] (host) and stats_out (may be NULL). */
+gcmc_status gcmc_submit(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, const gcmc_launch_cfg *cfg,
+                        uint64_t *ticket);
+gcmc_status gcmc_poll(gcmc_ctx *ctx, uint64_t ticket, double *tallies_out, gcmc_stats *stats_out);
+
+/* Parity/debug form of gcmc_run_packets: runs packets [packet0, packet0 + n_run) of `job` and
+   writes per-packet results to HOST arrays: pk_f [n_run][n_obs] (f per observer), pk_steps
+   [n_run], pk_tau [n_run] (optical depth of the packet's first peel-off or chord march), and for
+   the first n_trace packets the segment list: tr_cell [n_trace][max_trace] (flat cell index, or
+   -1 before a flight, -2 before a peel-off, -3 before a chord), tr_len, tr_n [n_trace].
+   Any output pointer may be NULL. */
+gcmc_status gcmc_run_packets_debug(gcmc_ctx *ctx, const gcmc_job *job, int64_t packet0, int64_t n_run,
+                                   double *pk_f, int64_t *pk_steps, double *pk_tau, int32_t n_trace,
+                                   int32_t max_trace, int32_t *tr_cell, double *tr_len, int32_t *tr_n,
+                                   double *tallies_out, gcmc_stats *stats_out);
+
+/* S1 only: the cell table of `job` copied to HOST arrays of length ncell (any may be NULL):
+   alpha (extinction, 1/m), omega, g, pgas (albedo), lum (emission L_i, W/m), cdf, wcell
+   (emission cumulative hybrid pdf and launch weight). */
+gcmc_status gcmc_prep_cells(gcmc_ctx *ctx, const gcmc_job *job, double *alpha, double *omega, double *g,
+                            double *pgas, double *lum, double *cdf, double *wcell, gcmc_stats *stats_out);
+
+/* ---------------------------------------------------------------- host post-scale (Sect. 5) */
+
+typedef struct {
+    double S;                 /* albedo: tally / N (reflected fraction per steradian, flux 1 on R_TOA disk) */
+    double A_g;               /* albedo: pi S, referenced to the R_TOA disk (Sect. 5.2) */
+    double A_g_R0;            /* albedo: pi S (R_TOA / R0)^2, referenced to the R0 disk */
+    double L_p;               /* emission: (L_tot / N) tally, W m^-1 sr^-1 (Sect. 5.3) */
+    double I_p;               /* emission: L_p / (pi R_TOA^2); transmission: <I_p> (Sect. 5.1) */
+    double F_p;               /* emission: pi I_p */
+    double area;              /* transmission: R0^2 + 2 <I_p>  (= (R_p/R_star)^2 R_star^2) */
+} gcmc_observables;
+
+/* Observables of one job from its tally sum over N packets (l_tot from the job's stats for emission). */
+gcmc_status gcmc_postscale(gcmc_ctx *ctx, int grid_id, int mode, double tally, int64_t n_packets, double l_tot,
+                           gcmc_observables *out);
+
+/* ---------------------------------------------------------------- resources and measurement */
+
+/* Free the device memory of a grid (and of every opacity uploaded for it) or of one opacity.
+   The ids are not reused.  Errors: GCMC_ERR_ARG for unknown or already released ids. */
+gcmc_status gcmc_release_grid(gcmc_ctx *ctx, int grid_id);
+gcmc_status gcmc_release_opacity(gcmc_ctx *ctx, int opac_id);
+
+/* Profiling: when on, every run records CUDA events on the context's stream around its cell-table
+   kernels and its transport kernel.  gcmc_get_profile synchronises those events and returns the
+   summed milliseconds since profiling was switched on (then starts a new sum). */
+gcmc_status gcmc_set_profiling(gcmc_ctx *ctx, int on);
+gcmc_status gcmc_get_profile(gcmc_ctx *ctx, double *prep_ms, double *transport_ms, int64_t *transport_launches);
+
+/* Process-wide number of kernels libgcmc has launched so far. */
+int64_t gcmc_kernel_launches(void);
+
+/* Random-gather rate of this device: n_gathers loads of record_bytes (4 or 16) from a table of
+   n_records records at Philox-random indices, one record per thread per iteration (the access
+   pattern of the cell march with no arithmetic).  Writes gathers per second. */
+gcmc_status gcmc_gather_bench(gcmc_ctx *ctx, int64_t n_records, int record_bytes, int64_t n_gathers,
+                              double *gathers_per_s);
+
+/* ---------------------------------------------------------------- self tests */
+
+/* Philox4x32-10 of the library and cuRAND's curand_Philox4x32_10 on the device for n
+   counters/keys (host arrays ctr [n][4], key [n][2]); results to out_lib, out_curand [n][4]. */
+gcmc_status gcmc_selftest_philox(gcmc_ctx *ctx, const uint32_t *ctr, const uint32_t *key, int n,
+                                 uint32_t *out_lib, uint32_t *out_curand);
+
+/* Library version string. */
+const char *gcmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GCMC_H */

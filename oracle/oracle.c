@@ -641,8 +641,9 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
         }
     } else {
         /* emission launch: stratified draw over the hybrid pdf */
-        double xi = ((double)n + u[0]) / (double)A->n_packets;
-        double target = xi * C->cdf_total;
+        /* stratified draw: packet n takes the point (n + z) / N of the cumulative pdf, i.e.
+           (n + z) * (cdf_total / N) on the un-normalised cumulative sum */
+        double target = ((double)n + u[0]) * (C->cdf_total / (double)A->n_packets);
         int64_t ncell = (int64_t)G->nlon * G->nlat * G->nr;
         int64_t lo = 0, hi = ncell - 1;
         while (lo < hi) {

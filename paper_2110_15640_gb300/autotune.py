@@ -1,0 +1,86 @@
+"""Launch-parameter autotuner for the persistent transport kernel.
+
+Searches block size, packets per work item (chunk), refill threshold and refill interval of
+gcmc_run_batch on a sample of the caller's jobs, timing each candidate with CUDA events on the
+context's stream, and returns the fastest gcmc_launch_cfg.  Results do not depend on the launch
+parameters (tallies are order-independent fixed point), so tuning never changes a spectrum.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+
+from . import gcmc
+
+DEFAULT_SPACE = {
+    "block": [64, 128, 256],
+    "chunk": [512, 1024, 2048],
+    "refill_min": [8, 16, 24, 32],
+    "interval": [1, 2],
+}
+
+
+def _time_cfg(ctx, jobs, cfg, reps, stream):
+    import torch
+
+    out = torch.zeros((len(jobs), gcmc.MAX_OBS), dtype=torch.float64, device="cuda")
+    ctx.run_batch(jobs, cfg=cfg, tallies=out, stats=False)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        ctx.run_batch(jobs, cfg=cfg, tallies=out, stats=False)
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def tune(ctx, jobs, stream, space=None, reps=2, coordinate=True, log=None):
+    """Return (best gcmc_launch_cfg, table of (cfg dict, ms)).  coordinate=True searches one axis at a
+    time from the defaults (about a dozen runs) instead of the full product."""
+    space = space or DEFAULT_SPACE
+    best = {"block": 128, "chunk": 1024, "refill_min": 16, "interval": 1}
+    table = []
+
+    def run(c):
+        cfg = gcmc.gcmc_launch_cfg(c["block"], 0, c["chunk"], c["interval"], c["refill_min"], 0)
+        ms = _time_cfg(ctx, jobs, cfg, reps, stream)
+        table.append((dict(c), ms))
+        if log:
+            log(f"autotune {c} {ms:.2f} ms")
+        return ms
+
+    if coordinate:
+        best_ms = run(best)
+        for _ in range(2):
+            for axis, values in space.items():
+                for v in values:
+                    if v == best[axis]:
+                        continue
+                    c = dict(best, **{axis: v})
+                    ms = run(c)
+                    if ms < best_ms:
+                        best, best_ms = c, ms
+    else:
+        keys = list(space)
+        best_ms = float("inf")
+        for vals in itertools.product(*(space[k] for k in keys)):
+            c = dict(zip(keys, vals))
+            ms = run(c)
+            if ms < best_ms:
+                best, best_ms = c, ms
+    cfg = gcmc.gcmc_launch_cfg(best["block"], 0, best["chunk"], best["interval"], best["refill_min"], 0)
+    return cfg, best, table
+
+
+def save(path, best, table):
+    with open(path, "w") as f:
+        json.dump({"best": best, "table": [{"cfg": c, "ms": ms} for c, ms in table]}, f, indent=1)
+
+
+def load(path):
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        b = json.load(f)["best"]
+    return gcmc.gcmc_launch_cfg(b["block"], 0, b["chunk"], b["interval"], b["refill_min"], 0), b

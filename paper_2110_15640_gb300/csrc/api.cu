@@ -1,0 +1,1185 @@
+// api.cu -- the C ABI of libgcmc (declared in include/gcmc.h): contexts, validated uploads, the
+// per-run workspace, S1 grouping, plain / batched / asynchronous runs, debug outputs, post-scale.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace gcmc;
+
+namespace {
+
+struct GridH {
+    DevGrid dg{};
+    std::vector<double> r, lat, lon;
+    std::vector<void *> owned;
+};
+
+struct OpacH {
+    int kind = 0, grid = -1, nlam = 0;
+    AlbDev alb{};
+    KtabDev kt{};
+    XsecDev xs{};
+    std::vector<double> lam;          // band centres (k-table) or table wavelengths (xsec)
+    std::vector<void *> owned;
+};
+
+struct Ticket {
+    cudaEvent_t done = nullptr;
+    int n_jobs = 0;
+    unsigned long long *h_acc = nullptr;   // pinned [n_jobs][ACC_SLOTS]
+    double *h_info = nullptr;              // pinned [n_jobs][4]: L_tot, n_incl, cdf_total, mode
+    void *ws = nullptr;                    // this ticket's workspace
+};
+
+}  // namespace
+
+struct gcmc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    gcmc_alloc_fn alloc = nullptr;
+    gcmc_free_fn free_fn = nullptr;
+    void *user = nullptr;
+    std::vector<GridH> grids;
+    std::vector<OpacH> opacs;
+    std::vector<gcmc_source_desc> sources;
+    DevGrid *d_grids = nullptr;
+    int grid_cap = 256;
+    void *arena = nullptr;
+    size_t arena_n = 0;
+    unsigned long long *h_acc = nullptr;   // pinned readback staging
+    double *h_info = nullptr;
+    size_t h_cap = 0;
+    std::map<uint64_t, Ticket> tickets;
+    uint64_t next_ticket = 1;
+    std::string err;
+    bool prof = false;                     // profiling: events around S1 and transport of each run
+    std::vector<cudaEvent_t> prof_ev;      // triples (before S1, before transport, after transport)
+};
+
+namespace {
+
+gcmc_status fail(gcmc_ctx *c, gcmc_status s, const std::string &m)
+{
+    if (c) c->err = m;
+    return s;
+}
+
+gcmc_status cuda_fail(gcmc_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, GCMC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+void *dalloc(gcmc_ctx *ctx, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    if (ctx->alloc) return ctx->alloc(bytes, ctx->user);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    return p;
+}
+
+void dfree(gcmc_ctx *ctx, void *p)
+{
+    if (!p) return;
+    if (ctx->free_fn) ctx->free_fn(p, ctx->user);
+    else cudaFree(p);
+}
+
+template <typename T> T *dput(gcmc_ctx *ctx, std::vector<void *> &owned, const T *src, size_t n, cudaError_t &e)
+{
+    T *d = (T *)dalloc(ctx, n * sizeof(T));
+    if (!d) {
+        e = cudaErrorMemoryAllocation;
+        return nullptr;
+    }
+    owned.push_back(d);
+    if (src && n) e = cudaMemcpyAsync(d, src, n * sizeof(T), cudaMemcpyDefault, ctx->stream);
+    return d;
+}
+
+template <typename T> bool fetch(gcmc_ctx *ctx, const T *src, size_t n, int memory, std::vector<T> &out)
+{
+    out.resize(n);
+    if (!src) return false;
+    if (!n) return true;
+    if (memory == GCMC_MEM_DEVICE) {
+        if (cudaMemcpyAsync(out.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+            return false;
+        return cudaStreamSynchronize(ctx->stream) == cudaSuccess;
+    }
+    std::memcpy(out.data(), src, n * sizeof(T));
+    return true;
+}
+
+bool strictly_increasing(const std::vector<double> &v)
+{
+    for (size_t i = 0; i + 1 < v.size(); ++i)
+        if (!(v[i + 1] > v[i])) return false;
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+void perp_basis(const double s[3], double e1[3], double e2[3])
+{
+    double a[3] = {0.0, 0.0, 1.0};
+    if (std::fabs(s[2]) >= 0.9) {
+        a[0] = 1.0;
+        a[2] = 0.0;
+    }
+    e1[0] = s[1] * a[2] - s[2] * a[1];
+    e1[1] = s[2] * a[0] - s[0] * a[2];
+    e1[2] = s[0] * a[1] - s[1] * a[0];
+    const double n = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (int i = 0; i < 3; ++i) e1[i] /= n;
+    e2[0] = s[1] * e1[2] - s[2] * e1[1];
+    e2[1] = s[2] * e1[0] - s[0] * e1[2];
+    e2[2] = s[0] * e1[1] - s[1] * e1[0];
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ------------------------------------------------------------------ run planning
+struct Group {
+    int grid, opac, mode, precision, source;
+    std::vector<int> members;
+};
+
+struct Plan {
+    std::vector<DevJob> jobs;
+    std::vector<PrepJob> prep;          // in group order (members of a group are contiguous)
+    std::vector<int> prep_pos;          // position of job q in `prep`
+    std::vector<Group> groups;
+    std::vector<size_t> off_rec, off_cdf, off_w, off_info, off_bsum, off_bcnt;
+    std::vector<size_t> g_off_ab, g_off_w, g_off_fac, g_first;
+    size_t off_jobs = 0, off_prep = 0, off_acc = 0, off_work = 0, off_gather = 0, ws_bytes = 0;
+    int64_t total_items = 0;
+    bool scatter = false;               // some job follows scattered packets (albedo)
+};
+
+gcmc_status check_job(gcmc_ctx *ctx, const gcmc_job &j)
+{
+    if (j.grid_id < 0 || j.grid_id >= (int)ctx->grids.size()) return fail(ctx, GCMC_ERR_ARG, "bad grid_id");
+    if (j.opac_id < 0 || j.opac_id >= (int)ctx->opacs.size()) return fail(ctx, GCMC_ERR_ARG, "bad opac_id");
+    if (j.source_id < 0 || j.source_id >= (int)ctx->sources.size()) return fail(ctx, GCMC_ERR_ARG, "bad source_id");
+    const OpacH &o = ctx->opacs[j.opac_id];
+    if (!ctx->grids[j.grid_id].dg.r) return fail(ctx, GCMC_ERR_ARG, "grid was released");
+    if (o.grid != j.grid_id) return fail(ctx, GCMC_ERR_ARG, "opacity released or belongs to another grid");
+    if (j.mode < 0 || j.mode > 2) return fail(ctx, GCMC_ERR_ARG, "bad mode");
+    const int want = j.mode == GCMC_ALBEDO ? GCMC_OPAC_ALBEDO : j.mode == GCMC_EMISSION ? GCMC_OPAC_KTABLE : GCMC_OPAC_XSEC;
+    if (o.kind != want) return fail(ctx, GCMC_ERR_ARG, "opacity kind does not match the mode");
+    if (j.n_packets < 0) return fail(ctx, GCMC_ERR_ARG, "negative n_packets");
+    const gcmc_source_desc &s = ctx->sources[j.source_id];
+    if (j.obs_idx >= s.n_obs) return fail(ctx, GCMC_ERR_ARG, "obs_idx out of range");
+    if (j.mode == GCMC_EMISSION && s.scatter_emission)
+        return fail(ctx, GCMC_ERR_ARG, "scattering after emission needs scattering opacities (not in k-tables)");
+    if (o.kind == GCMC_OPAC_ALBEDO || o.kind == GCMC_OPAC_XSEC) {
+        if (j.lam_idx < 0 || j.lam_idx >= o.nlam) return fail(ctx, GCMC_ERR_ARG, "lam_idx out of range");
+    } else if (j.lam_idx < 0 || j.lam_idx >= o.kt.nb || j.g_idx < 0 || j.g_idx >= o.kt.ng) {
+        return fail(ctx, GCMC_ERR_ARG, "band / g index out of range");
+    }
+    return GCMC_OK;
+}
+
+gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan &P)
+{
+    if (n <= 0 || !jobs) return fail(ctx, GCMC_ERR_ARG, "no jobs");
+    if (chunk <= 0 || chunk % 32) return fail(ctx, GCMC_ERR_ARG, "chunk must be a positive multiple of 32");
+    for (int q = 0; q < n; ++q) {
+        const gcmc_status s = check_job(ctx, jobs[q]);
+        if (s) return s;
+    }
+    P.jobs.resize(n);
+    P.prep_pos.resize(n);
+    P.off_rec.assign(n, 0);
+    P.off_cdf.assign(n, 0);
+    P.off_w.assign(n, 0);
+    P.off_info.assign(n, 0);
+    P.off_bsum.assign(n, 0);
+    P.off_bcnt.assign(n, 0);
+    for (int q = 0; q < n; ++q) {
+        const gcmc_job &j = jobs[q];
+        const gcmc_source_desc &s = ctx->sources[j.source_id];
+        const int prec = s.precision == GCMC_FP64 ? GCMC_FP64 : GCMC_FP32;
+        int gi = -1;
+        for (size_t g = 0; g < P.groups.size(); ++g) {
+            const Group &G = P.groups[g];
+            if (G.grid == j.grid_id && G.opac == j.opac_id && G.mode == j.mode && G.precision == prec &&
+                (j.mode != GCMC_EMISSION || G.source == j.source_id))
+                gi = (int)g;
+        }
+        if (gi < 0) {
+            P.groups.push_back({j.grid_id, j.opac_id, j.mode, prec, j.source_id, {}});
+            gi = (int)P.groups.size() - 1;
+        }
+        P.groups[gi].members.push_back(q);
+    }
+    size_t ws = 0;
+    for (int q = 0; q < n; ++q) {
+        const gcmc_job &j = jobs[q];
+        const int prec = ctx->sources[j.source_id].precision == GCMC_FP64 ? GCMC_FP64 : GCMC_FP32;
+        const int64_t ncell = ctx->grids[j.grid_id].dg.ncell;
+        const size_t esz = prec == GCMC_FP64 ? 8 : 4;
+        P.off_rec[q] = ws;
+        ws += align256((size_t)ncell * (j.mode == GCMC_ALBEDO ? 4 * esz : esz));
+        if (j.mode == GCMC_EMISSION) {
+            const int64_t nblk = (ncell + EMIS_SCAN_BLOCK - 1) / EMIS_SCAN_BLOCK;
+            P.off_cdf[q] = ws;
+            ws += align256(ncell * 8);
+            P.off_w[q] = ws;
+            ws += align256(ncell * 8);
+            P.off_info[q] = ws;
+            ws += 256;
+            P.off_bsum[q] = ws;
+            ws += align256(nblk * 8);
+            P.off_bcnt[q] = ws;
+            ws += align256(nblk * 8);
+        }
+    }
+    const size_t ng = P.groups.size();
+    P.g_off_ab.resize(ng);
+    P.g_off_w.resize(ng);
+    P.g_off_fac.resize(ng);
+    P.g_first.resize(ng);
+    for (size_t g = 0; g < ng; ++g) {
+        const int64_t ncell = ctx->grids[P.groups[g].grid].dg.ncell;
+        P.g_off_ab[g] = ws;
+        ws += align256(ncell * sizeof(int2));
+        P.g_off_w[g] = ws;
+        ws += align256(ncell * sizeof(double2));
+        P.g_off_fac[g] = ws;
+        ws += align256(ncell * sizeof(double));
+    }
+    P.off_jobs = ws;
+    ws += align256(n * sizeof(DevJob));
+    P.off_prep = ws;
+    ws += align256(n * sizeof(PrepJob));
+    P.off_acc = ws;
+    ws += align256((size_t)n * ACC_SLOTS * 8);
+    P.off_work = ws;
+    ws += 256;
+    P.off_gather = ws;
+    ws += align256((size_t)n * 4 * sizeof(double));
+    P.ws_bytes = ws;
+
+    int64_t items = 0;
+    P.prep.clear();
+    for (size_t g = 0; g < ng; ++g) {
+        P.g_first[g] = P.prep.size();
+        for (int q : P.groups[g].members) {
+            P.prep_pos[q] = (int)P.prep.size();
+            PrepJob pj;
+            std::memset(&pj, 0, sizeof(pj));
+            const gcmc_job &j = jobs[q];
+            const OpacH &o = ctx->opacs[j.opac_id];
+            pj.lam = j.lam_idx;
+            pj.g = j.g_idx;
+            pj.lam_hint = j.lam_idx;
+            if (o.kind == GCMC_OPAC_KTABLE) {
+                pj.lam_m = o.lam[j.lam_idx];
+                pj.c1 = 2.0 * 6.62607015e-34 * 2.99792458e8 * 2.99792458e8 / std::pow(pj.lam_m, 5.0);
+            } else if (o.kind == GCMC_OPAC_XSEC) {
+                pj.lam_m = o.lam[j.lam_idx];
+            }
+            P.prep.push_back(pj);
+        }
+    }
+    for (int q = 0; q < n; ++q) {
+        const gcmc_job &j = jobs[q];
+        const gcmc_source_desc &s = ctx->sources[j.source_id];
+        DevJob &d = P.jobs[q];
+        std::memset(&d, 0, sizeof(d));
+        d.mode = j.mode;
+        if (j.mode == GCMC_ALBEDO) P.scatter = true;
+        d.grid_slot = j.grid_id;
+        d.survival = s.survival;
+        d.precision = s.precision == GCMC_FP64 ? GCMC_FP64 : GCMC_FP32;
+        d.key = j.job_key;
+        d.seed = j.seed;
+        d.n_packets = j.n_packets;
+        d.max_steps = s.max_steps > 0 ? s.max_steps : ((int64_t)1 << 40);
+        for (int a = 0; a < 3; ++a) d.star[a] = s.star[a];
+        perp_basis(d.star, d.e1, d.e2);
+        if (j.obs_idx >= 0) {
+            d.n_obs = 1;
+            for (int a = 0; a < 3; ++a) d.obs[0][a] = s.obs[j.obs_idx][a];
+        } else {
+            d.n_obs = j.mode == GCMC_TRANSMISSION ? 1 : s.n_obs;
+            for (int o = 0; o < d.n_obs; ++o)
+                for (int a = 0; a < 3; ++a) d.obs[o][a] = s.obs[o][a];
+        }
+        d.w_rr = s.w_rr;
+        d.p_surv = s.p_surv;
+        d.tau_cut = s.tau_peel_cut;
+        d.hg_eps = s.hg_iso_eps;
+        d.chunk_begin = items;
+        items += (j.n_packets + chunk - 1) / chunk;
+    }
+    P.total_items = items;
+    return GCMC_OK;
+}
+
+__global__ void k_finalize_jobs(DevJob *jobs, int n)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    if (jobs[q].mode == GCMC_EMISSION) {
+        const double tot = jobs[q].info[2];
+        jobs[q].cdf_total = tot;
+        jobs[q].cdf_step = jobs[q].n_packets > 0 ? tot / (double)jobs[q].n_packets : 0.0;
+    }
+}
+
+// S1 for every job of the plan, then the device job array, accumulators and work counter.
+gcmc_status stage(gcmc_ctx *ctx, Plan &P, char *base, double *lum = nullptr)
+{
+    const int n = (int)P.jobs.size();
+    for (int q = 0; q < n; ++q) {
+        DevJob &d = P.jobs[q];
+        PrepJob &pj = P.prep[P.prep_pos[q]];
+        pj.rec = base + P.off_rec[q];
+        d.rec = pj.rec;
+        d.acc = reinterpret_cast<unsigned long long *>(base + P.off_acc) + (size_t)q * ACC_SLOTS;
+        if (d.mode == GCMC_EMISSION) {
+            pj.cdf = reinterpret_cast<double *>(base + P.off_cdf[q]);
+            pj.wcell = reinterpret_cast<double *>(base + P.off_w[q]);
+            pj.info = reinterpret_cast<double *>(base + P.off_info[q]);
+            pj.bsum = reinterpret_cast<double *>(base + P.off_bsum[q]);
+            pj.bcnt = reinterpret_cast<double *>(base + P.off_bcnt[q]);
+            pj.lum = lum;
+            d.cdf = pj.cdf;
+            d.wcell = pj.wcell;
+            d.info = pj.info;
+        }
+    }
+    PrepJob *dprep = reinterpret_cast<PrepJob *>(base + P.off_prep);
+    DevJob *djobs = reinterpret_cast<DevJob *>(base + P.off_jobs);
+    CK(cudaMemcpyAsync(dprep, P.prep.data(), n * sizeof(PrepJob), cudaMemcpyHostToDevice, ctx->stream));
+    for (size_t g = 0; g < P.groups.size(); ++g) {
+        const Group &G = P.groups[g];
+        const PrepJob *gp = dprep + P.g_first[g];
+        const int m = (int)G.members.size();
+        const GridH &gh = ctx->grids[G.grid];
+        const OpacH &oh = ctx->opacs[G.opac];
+        int2 *ab = reinterpret_cast<int2 *>(base + P.g_off_ab[g]);
+        double2 *ww = reinterpret_cast<double2 *>(base + P.g_off_w[g]);
+        double *fac = reinterpret_cast<double *>(base + P.g_off_fac[g]);
+        cudaError_t e;
+        if (G.mode == GCMC_ALBEDO) {
+            e = prep_albedo(G.precision, ctx->d_grids + G.grid, gh.dg, oh.alb, gp, m, ctx->stream);
+        } else if (G.mode == GCMC_EMISSION) {
+            const gcmc_source_desc &s = ctx->sources[G.source];
+            e = prep_emission(G.precision, ctx->d_grids + G.grid, gh.dg, oh.kt, gp, m, s.tau_vert_max, s.beta_emis, ab,
+                              ww, ctx->stream);
+        } else {
+            e = prep_xsec(G.precision, ctx->d_grids + G.grid, gh.dg, oh.xs, gp, m, ab, ww, fac, ctx->stream);
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cell-table kernels");
+    }
+    CK(cudaMemcpyAsync(djobs, P.jobs.data(), n * sizeof(DevJob), cudaMemcpyHostToDevice, ctx->stream));
+    count_launch(1);
+    k_finalize_jobs<<<(n + 127) / 128, 128, 0, ctx->stream>>>(djobs, n);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(base + P.off_acc, 0, (size_t)n * ACC_SLOTS * 8, ctx->stream));
+    CK(cudaMemsetAsync(base + P.off_work, 0, 256, ctx->stream));
+    return GCMC_OK;
+}
+
+void prof_mark(gcmc_ctx *ctx)
+{
+    if (!ctx->prof) return;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) == cudaSuccess) {
+        cudaEventRecord(e, ctx->stream);
+        ctx->prof_ev.push_back(e);
+    }
+}
+
+gcmc_status ensure_arena(gcmc_ctx *ctx, size_t bytes)
+{
+    if (ctx->arena_n >= bytes) return GCMC_OK;
+    if (ctx->arena) {
+        cudaStreamSynchronize(ctx->stream);
+        dfree(ctx, ctx->arena);
+        ctx->arena = nullptr;
+        ctx->arena_n = 0;
+    }
+    const size_t want = bytes + bytes / 8;
+    ctx->arena = dalloc(ctx, want);
+    if (!ctx->arena) return fail(ctx, GCMC_ERR_OOM, "workspace allocation failed");
+    ctx->arena_n = want;
+    return GCMC_OK;
+}
+
+gcmc_status ensure_host(gcmc_ctx *ctx, size_t njobs)
+{
+    if (ctx->h_cap >= njobs) return GCMC_OK;
+    if (ctx->h_acc) cudaFreeHost(ctx->h_acc);
+    if (ctx->h_info) cudaFreeHost(ctx->h_info);
+    ctx->h_acc = nullptr;
+    ctx->h_info = nullptr;
+    CK(cudaMallocHost((void **)&ctx->h_acc, njobs * ACC_SLOTS * 8));
+    CK(cudaMallocHost((void **)&ctx->h_info, njobs * 4 * sizeof(double)));
+    ctx->h_cap = njobs;
+    return GCMC_OK;
+}
+
+__global__ void k_gather_info(const DevJob *jobs, int n, double *out)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    if (jobs[q].mode == GCMC_EMISSION) {
+        out[4 * q] = jobs[q].info[0];
+        out[4 * q + 1] = jobs[q].info[1];
+        out[4 * q + 2] = jobs[q].info[2];
+    } else {
+        out[4 * q] = out[4 * q + 1] = out[4 * q + 2] = 0.0;
+    }
+    out[4 * q + 3] = (double)jobs[q].mode;
+}
+
+// convert one job's accumulators into tallies and stats
+void unpack(const unsigned long long *acc, const double *info, int n_obs, double *tally, gcmc_stats *st)
+{
+    for (int o = 0; o < MAX_OBS; ++o) tally[o] = o < n_obs ? (double)(long long)acc[o] / FIX_SCALE : 0.0;
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        st->packets = (int64_t)acc[ACC_PACKETS];
+        st->steps = (int64_t)acc[ACC_STEPS];
+        for (int q = 0; q < 8; ++q) st->ledger[q] = (double)(long long)acc[ACC_LEDGER + q] / FIX_SCALE;
+        st->l_tot = info[0];
+        st->n_emit_cells = (int64_t)info[1];
+        st->cdf_total = info[2];
+    }
+}
+
+// enqueue readback of accumulators and emission info into host staging buffers
+gcmc_status enqueue_readback(gcmc_ctx *ctx, Plan &P, char *base, unsigned long long *h_acc, double *h_info,
+                             double *info_dev)
+{
+    const int n = (int)P.jobs.size();
+    count_launch(1);
+    k_gather_info<<<(n + 127) / 128, 128, 0, ctx->stream>>>(reinterpret_cast<DevJob *>(base + P.off_jobs), n, info_dev);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h_acc, base + P.off_acc, (size_t)n * ACC_SLOTS * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(h_info, info_dev, (size_t)n * 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    return GCMC_OK;
+}
+
+__global__ void k_acc_to_tallies(const unsigned long long *acc, int n, double *out)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n * MAX_OBS) return;
+    const int j = q / MAX_OBS, o = q % MAX_OBS;
+    out[q] = (double)(long long)acc[(size_t)j * ACC_SLOTS + o] / FIX_SCALE;
+}
+
+gcmc_status finish_run(gcmc_ctx *ctx, Plan &P, char *base, double *tallies_out, int tallies_memory, gcmc_stats *stats,
+                       int stats_stride_jobs)
+{
+    const int n = (int)P.jobs.size();
+    if (tallies_memory == GCMC_MEM_DEVICE && tallies_out) {
+        count_launch(1);
+        k_acc_to_tallies<<<(n * MAX_OBS + 127) / 128, 128, 0, ctx->stream>>>(
+            reinterpret_cast<unsigned long long *>(base + P.off_acc), n, tallies_out);
+        CK(cudaGetLastError());
+        if (!stats) return GCMC_OK;
+    }
+    gcmc_status s = ensure_host(ctx, n);
+    if (s) return s;
+    s = enqueue_readback(ctx, P, base, ctx->h_acc, ctx->h_info, reinterpret_cast<double *>(base + P.off_gather));
+    if (s) return s;
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int q = 0; q < n; ++q) {
+        double t[MAX_OBS];
+        unpack(ctx->h_acc + (size_t)q * ACC_SLOTS, ctx->h_info + 4 * q, P.jobs[q].n_obs, t,
+               stats ? stats + (stats_stride_jobs ? q : 0) : nullptr);
+        if (tallies_out && tallies_memory == GCMC_MEM_HOST) {
+            if (stats_stride_jobs) std::memcpy(tallies_out + (size_t)q * MAX_OBS, t, sizeof(t));
+            else std::memcpy(tallies_out, t, sizeof(double) * P.jobs[q].n_obs);
+        }
+    }
+    return GCMC_OK;
+}
+
+}  // namespace
+
+// ==================================================================== C ABI
+extern "C" {
+
+const char *gcmc_version(void) { return "gcmc 0.1 (sm_103a)"; }
+
+gcmc_status gcmc_create(int device, gcmc_ctx **out)
+{
+    if (!out) return GCMC_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return GCMC_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return GCMC_ERR_CUDA;
+    gcmc_ctx *ctx = new gcmc_ctx();
+    ctx->device = device;
+    if (cudaMalloc(&ctx->d_grids, sizeof(DevGrid) * ctx->grid_cap) != cudaSuccess) {
+        delete ctx;
+        return GCMC_ERR_OOM;
+    }
+    *out = ctx;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_destroy(gcmc_ctx *ctx)
+{
+    if (!ctx) return GCMC_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : ctx->tickets) {
+        cudaEventDestroy(kv.second.done);
+        cudaFreeHost(kv.second.h_acc);
+        cudaFreeHost(kv.second.h_info);
+        dfree(ctx, kv.second.ws);
+    }
+    for (auto &g : ctx->grids)
+        for (void *p : g.owned) dfree(ctx, p);
+    for (auto &o : ctx->opacs)
+        for (void *p : o.owned) dfree(ctx, p);
+    dfree(ctx, ctx->arena);
+    if (ctx->h_acc) cudaFreeHost(ctx->h_acc);
+    if (ctx->h_info) cudaFreeHost(ctx->h_info);
+    cudaFree(ctx->d_grids);
+    delete ctx;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_set_stream(gcmc_ctx *ctx, void *stream)
+{
+    if (!ctx) return GCMC_ERR_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_set_allocator(gcmc_ctx *ctx, gcmc_alloc_fn alloc, gcmc_free_fn free_fn, void *user)
+{
+    if (!ctx) return GCMC_ERR_ARG;
+    if (!ctx->grids.empty() || !ctx->opacs.empty() || ctx->arena)
+        return fail(ctx, GCMC_ERR_ARG, "set the allocator before the first upload");
+    if ((alloc == nullptr) != (free_fn == nullptr)) return fail(ctx, GCMC_ERR_ARG, "alloc and free go together");
+    ctx->alloc = alloc;
+    ctx->free_fn = free_fn;
+    ctx->user = user;
+    return GCMC_OK;
+}
+
+const char *gcmc_last_error(gcmc_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+gcmc_status gcmc_upload_grid(gcmc_ctx *ctx, const gcmc_grid_desc *d, int *grid_id)
+{
+    if (!ctx || !d || !grid_id) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    if (d->nlon < 1 || d->nlat < 1 || d->nr < 1) return fail(ctx, GCMC_ERR_ARG, "grid sizes must be >= 1");
+    if ((int)ctx->grids.size() >= ctx->grid_cap) return fail(ctx, GCMC_ERR_RANGE, "too many grids in one context");
+    const int64_t ncell = (int64_t)d->nlon * d->nlat * d->nr;
+    if (ncell > ((int64_t)1 << 31) - 1) return fail(ctx, GCMC_ERR_RANGE, "more than 2^31 - 1 cells");
+    if (!d->T || !d->p || !d->rho) return fail(ctx, GCMC_ERR_ARG, "T, p and rho are required");
+    GridH G;
+    if (!fetch(ctx, d->r_edges, d->nr + 1, d->memory, G.r) || !fetch(ctx, d->lat_edges, d->nlat + 1, d->memory, G.lat) ||
+        !fetch(ctx, d->lon_edges, d->nlon + 1, d->memory, G.lon))
+        return fail(ctx, GCMC_ERR_ARG, "edge arrays missing or unreadable");
+    if (!strictly_increasing(G.r) || !(G.r[0] > 0.0)) return fail(ctx, GCMC_ERR_ARG, "r_edges must be positive, increasing");
+    if (!strictly_increasing(G.lat) || G.lat.front() < -0.5 * PI - 1e-12 || G.lat.back() > 0.5 * PI + 1e-12)
+        return fail(ctx, GCMC_ERR_ARG, "lat_edges must increase within [-pi/2, pi/2]");
+    if (!strictly_increasing(G.lon) || std::fabs(G.lon.back() - G.lon.front() - 2.0 * PI) > 1e-9)
+        return fail(ctx, GCMC_ERR_ARG, "lon_edges must increase and span 2 pi");
+    // per-cell fields: validate on the host copy
+    std::vector<float> T, p, rho;
+    if (!fetch(ctx, d->T, ncell, d->memory, T) || !fetch(ctx, d->p, ncell, d->memory, p) ||
+        !fetch(ctx, d->rho, ncell, d->memory, rho))
+        return fail(ctx, GCMC_ERR_CUDA, "reading the cell fields failed");
+    for (int64_t i = 0; i < ncell; ++i)
+        if (!(T[i] > 0.0f) || !std::isfinite(T[i]) || !(p[i] > 0.0f) || !std::isfinite(p[i]) || !(rho[i] >= 0.0f) ||
+            !std::isfinite(rho[i]))
+            return fail(ctx, GCMC_ERR_NAN, "T, p must be positive and finite, rho non-negative and finite");
+    const int nr = d->nr, nlat = d->nlat, nlon = d->nlon;
+    std::vector<double> r2(nr + 1), slat(nlat + 1), s2lat(nlat + 1), clon(nlon + 1), slon(nlon + 1);
+    std::vector<float> r_f(nr + 1), r2hi(nr + 1), r2lo(nr + 1), lat_f(nlat + 1), slat_f(nlat + 1), s2lat_f(nlat + 1),
+        lon_f(nlon + 1), clon_f(nlon + 1), slon_f(nlon + 1);
+    std::vector<float> shA(nr);
+    for (int k = 0; k < nr; ++k) {
+        const double q = G.r[k + 1] / G.r[k];
+        shA[k] = (float)(q * q * q - 1.0);
+    }
+    for (int k = 0; k <= nr; ++k) {
+        r2[k] = G.r[k] * G.r[k];
+        r_f[k] = (float)G.r[k];
+        r2hi[k] = (float)r2[k];
+        r2lo[k] = (float)(r2[k] - (double)r2hi[k]);
+    }
+    for (int j = 0; j <= nlat; ++j) {
+        slat[j] = std::sin(G.lat[j]);
+        s2lat[j] = slat[j] * slat[j];
+        lat_f[j] = (float)G.lat[j];
+        slat_f[j] = (float)slat[j];
+        s2lat_f[j] = (float)s2lat[j];
+    }
+    for (int i = 0; i <= nlon; ++i) {
+        clon[i] = std::cos(G.lon[i]);
+        slon[i] = std::sin(G.lon[i]);
+        lon_f[i] = (float)G.lon[i];
+        clon_f[i] = (float)clon[i];
+        slon_f[i] = (float)slon[i];
+    }
+    std::vector<double> vol(ncell);
+    for (int64_t idx = 0; idx < ncell; ++idx) {
+        const int64_t i = idx % nlon, j = (idx / nlon) % nlat, k = idx / ((int64_t)nlon * nlat);
+        const double r1 = G.r[k], r2v = G.r[k + 1];
+        vol[idx] = (r2v * r2v * r2v - r1 * r1 * r1) / 3.0 * (std::sin(G.lat[j + 1]) - std::sin(G.lat[j])) *
+                   (G.lon[i + 1] - G.lon[i]);
+    }
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaSuccess;
+    DevGrid &g = G.dg;
+    g.nlon = nlon;
+    g.nlat = nlat;
+    g.nr = nr;
+    g.ncell = ncell;
+    g.R0 = G.r[0];
+    g.Rtoa = G.r[nr];
+    g.lon0 = G.lon[0];
+    g.r = dput(ctx, G.owned, G.r.data(), nr + 1, e);
+    g.r2 = dput(ctx, G.owned, r2.data(), nr + 1, e);
+    g.lat = dput(ctx, G.owned, G.lat.data(), nlat + 1, e);
+    g.slat = dput(ctx, G.owned, slat.data(), nlat + 1, e);
+    g.s2lat = dput(ctx, G.owned, s2lat.data(), nlat + 1, e);
+    g.lon = dput(ctx, G.owned, G.lon.data(), nlon + 1, e);
+    g.clon = dput(ctx, G.owned, clon.data(), nlon + 1, e);
+    g.slon = dput(ctx, G.owned, slon.data(), nlon + 1, e);
+    g.r_f = dput(ctx, G.owned, r_f.data(), nr + 1, e);
+    g.r2hi_f = dput(ctx, G.owned, r2hi.data(), nr + 1, e);
+    g.r2lo_f = dput(ctx, G.owned, r2lo.data(), nr + 1, e);
+    g.lat_f = dput(ctx, G.owned, lat_f.data(), nlat + 1, e);
+    g.slat_f = dput(ctx, G.owned, slat_f.data(), nlat + 1, e);
+    g.s2lat_f = dput(ctx, G.owned, s2lat_f.data(), nlat + 1, e);
+    g.lon_f = dput(ctx, G.owned, lon_f.data(), nlon + 1, e);
+    g.clon_f = dput(ctx, G.owned, clon_f.data(), nlon + 1, e);
+    g.slon_f = dput(ctx, G.owned, slon_f.data(), nlon + 1, e);
+    g.shA_f = dput(ctx, G.owned, shA.data(), nr, e);
+    g.T = dput(ctx, G.owned, d->T, ncell, e);
+    g.p = dput(ctx, G.owned, d->p, ncell, e);
+    g.rho = dput(ctx, G.owned, d->rho, ncell, e);
+    g.wind = d->wind ? dput(ctx, G.owned, d->wind, 3 * ncell, e) : nullptr;
+    g.vol = dput(ctx, G.owned, vol.data(), ncell, e);
+    if (e != cudaSuccess) {
+        for (void *q : G.owned) dfree(ctx, q);
+        return e == cudaErrorMemoryAllocation ? fail(ctx, GCMC_ERR_OOM, "grid allocation failed")
+                                              : cuda_fail(ctx, e, "grid upload");
+    }
+    const int id = (int)ctx->grids.size();
+    CK(cudaMemcpyAsync(ctx->d_grids + id, &G.dg, sizeof(DevGrid), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));   // host staging vectors go out of scope
+    ctx->grids.push_back(std::move(G));
+    *grid_id = id;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_upload_opacity(gcmc_ctx *ctx, int grid_id, const gcmc_opacity_desc *d, int *opac_id)
+{
+    if (!ctx || !d || !opac_id) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    if (grid_id < 0 || grid_id >= (int)ctx->grids.size()) return fail(ctx, GCMC_ERR_ARG, "bad grid_id");
+    cudaSetDevice(ctx->device);
+    const int64_t ncell = ctx->grids[grid_id].dg.ncell;
+    OpacH O;
+    O.kind = d->kind;
+    O.grid = grid_id;
+    cudaError_t e = cudaSuccess;
+    auto finite_nonneg = [](const std::vector<double> &v) {
+        for (double x : v)
+            if (!(x >= 0.0) || !std::isfinite(x)) return false;
+        return true;
+    };
+    if (d->kind == GCMC_OPAC_ALBEDO) {
+        if (d->nlam < 1) return fail(ctx, GCMC_ERR_ARG, "nlam must be >= 1");
+        std::vector<double> ka, kr, qc, wc, gc;
+        if (!fetch(ctx, d->kabs, d->nlam, d->memory, ka) || !fetch(ctx, d->kray, d->nlam, d->memory, kr) ||
+            !fetch(ctx, d->qcld, d->nlam, d->memory, qc) || !fetch(ctx, d->wcld, d->nlam, d->memory, wc) ||
+            !fetch(ctx, d->gcld, d->nlam, d->memory, gc))
+            return fail(ctx, GCMC_ERR_ARG, "albedo opacity arrays missing");
+        if (!finite_nonneg(ka) || !finite_nonneg(kr) || !finite_nonneg(qc) || !finite_nonneg(wc))
+            return fail(ctx, GCMC_ERR_NAN, "negative or non-finite opacity");
+        for (int l = 0; l < d->nlam; ++l)
+            if (!(wc[l] <= 1.0) || !(gc[l] > -1.0 && gc[l] < 1.0)) return fail(ctx, GCMC_ERR_ARG, "wcld in [0,1], |gcld| < 1");
+        if (d->acld) {
+            std::vector<float> ac;
+            if (!fetch(ctx, d->acld, ncell, d->memory, ac)) return fail(ctx, GCMC_ERR_CUDA, "reading acld failed");
+            for (float x : ac)
+                if (!(x >= 0.0f) || !std::isfinite(x)) return fail(ctx, GCMC_ERR_NAN, "negative or non-finite acld");
+        }
+        O.nlam = d->nlam;
+        O.alb.nlam = d->nlam;
+        O.alb.kabs = dput(ctx, O.owned, ka.data(), d->nlam, e);
+        O.alb.kray = dput(ctx, O.owned, kr.data(), d->nlam, e);
+        O.alb.qcld = dput(ctx, O.owned, qc.data(), d->nlam, e);
+        O.alb.wcld = dput(ctx, O.owned, wc.data(), d->nlam, e);
+        O.alb.gcld = dput(ctx, O.owned, gc.data(), d->nlam, e);
+        O.alb.acld = d->acld ? dput(ctx, O.owned, d->acld, ncell, e) : nullptr;
+    } else if (d->kind == GCMC_OPAC_KTABLE || d->kind == GCMC_OPAC_XSEC) {
+        if (d->nT < 2 || d->np < 2) return fail(ctx, GCMC_ERR_ARG, "table axes need >= 2 points");
+        std::vector<double> Tg, pg;
+        if (!fetch(ctx, d->Tg, d->nT, d->memory, Tg) || !fetch(ctx, d->pg, d->np, d->memory, pg))
+            return fail(ctx, GCMC_ERR_ARG, "table axes missing");
+        if (!strictly_increasing(Tg) || !strictly_increasing(pg) || !(Tg[0] > 0) || !(pg[0] > 0))
+            return fail(ctx, GCMC_ERR_ARG, "table axes must be positive and increasing");
+        if (d->kind == GCMC_OPAC_KTABLE) {
+            if (d->nb < 1 || d->ng < 1) return fail(ctx, GCMC_ERR_ARG, "nb, ng must be >= 1");
+            const size_t nk = (size_t)d->nb * d->ng * d->nT * d->np;
+            std::vector<float> k;
+            std::vector<double> lam;
+            if (!fetch(ctx, d->k, nk, d->memory, k) || !fetch(ctx, d->lam, d->nb, d->memory, lam))
+                return fail(ctx, GCMC_ERR_ARG, "k-table arrays missing");
+            std::vector<double> lnk(nk);
+            for (size_t i = 0; i < nk; ++i) {
+                if (!(k[i] > 0.0f) || !std::isfinite(k[i])) return fail(ctx, GCMC_ERR_NAN, "k must be positive, finite");
+                lnk[i] = std::log((double)k[i]);
+            }
+            for (double l : lam)
+                if (!(l > 0.0)) return fail(ctx, GCMC_ERR_ARG, "band wavelengths must be positive");
+            O.kt.nb = d->nb;
+            O.kt.ng = d->ng;
+            O.kt.nT = d->nT;
+            O.kt.np = d->np;
+            O.kt.lnk = dput(ctx, O.owned, lnk.data(), nk, e);
+            O.kt.Tg = dput(ctx, O.owned, Tg.data(), d->nT, e);
+            O.kt.pg = dput(ctx, O.owned, pg.data(), d->np, e);
+            O.lam = lam;
+            O.nlam = d->nb;
+        } else {
+            if (d->nl < 2) return fail(ctx, GCMC_ERR_ARG, "xsec table needs >= 2 wavelengths");
+            const size_t ns = (size_t)d->nl * d->nT * d->np;
+            std::vector<float> sg;
+            std::vector<double> xl;
+            if (!fetch(ctx, d->sigma, ns, d->memory, sg) || !fetch(ctx, d->xlam, d->nl, d->memory, xl))
+                return fail(ctx, GCMC_ERR_ARG, "xsec arrays missing");
+            if (!strictly_increasing(xl) || !(xl[0] > 0)) return fail(ctx, GCMC_ERR_ARG, "xlam must increase");
+            std::vector<double> ls(ns);
+            std::vector<float> lsf(ns);
+            for (size_t i = 0; i < ns; ++i) {
+                if (!(sg[i] > 0.0f) || !std::isfinite(sg[i])) return fail(ctx, GCMC_ERR_NAN, "sigma must be positive");
+                ls[i] = std::log((double)sg[i]);
+                lsf[i] = (float)ls[i];
+            }
+            O.xs.nl = d->nl;
+            O.xs.nT = d->nT;
+            O.xs.np = d->np;
+            O.xs.lam = dput(ctx, O.owned, xl.data(), d->nl, e);
+            O.xs.lnsig = dput(ctx, O.owned, ls.data(), ns, e);
+            O.xs.lnsig_f = dput(ctx, O.owned, lsf.data(), ns, e);
+            O.xs.Tg = dput(ctx, O.owned, Tg.data(), d->nT, e);
+            O.xs.pg = dput(ctx, O.owned, pg.data(), d->np, e);
+            O.xs.view_theta = d->view_theta;
+            O.xs.view_phi = d->view_phi;
+            O.xs.omega_rot = d->omega_rot;
+            O.lam = xl;
+            O.nlam = d->nl;
+        }
+    } else {
+        return fail(ctx, GCMC_ERR_ARG, "unknown opacity kind");
+    }
+    if (e != cudaSuccess) {
+        for (void *q : O.owned) dfree(ctx, q);
+        return e == cudaErrorMemoryAllocation ? fail(ctx, GCMC_ERR_OOM, "opacity allocation failed")
+                                              : cuda_fail(ctx, e, "opacity upload");
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    *opac_id = (int)ctx->opacs.size();
+    ctx->opacs.push_back(std::move(O));
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_set_source(gcmc_ctx *ctx, int grid_id, const gcmc_source_desc *d, int *source_id)
+{
+    if (!ctx || !d || !source_id) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    if (grid_id < 0 || grid_id >= (int)ctx->grids.size()) return fail(ctx, GCMC_ERR_ARG, "bad grid_id");
+    if (d->n_obs < 1 || d->n_obs > GCMC_MAX_OBS) return fail(ctx, GCMC_ERR_ARG, "n_obs must be in 1..GCMC_MAX_OBS");
+    auto unit = [](const double *v) { return std::fabs(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] - 1.0) < 1e-9; };
+    if (!unit(d->star)) return fail(ctx, GCMC_ERR_ARG, "star must be a unit vector");
+    for (int o = 0; o < d->n_obs; ++o)
+        if (!unit(d->obs[o])) return fail(ctx, GCMC_ERR_ARG, "observer directions must be unit vectors");
+    if (!(d->p_surv > 0.0 && d->p_surv <= 1.0) || !(d->w_rr >= 0.0) || !(d->tau_peel_cut > 0.0) ||
+        !(d->beta_emis >= 0.0 && d->beta_emis <= 1.0) || !(d->tau_vert_max > 0.0))
+        return fail(ctx, GCMC_ERR_ARG, "options out of range");
+    *source_id = (int)ctx->sources.size();
+    ctx->sources.push_back(*d);
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_run_packets(gcmc_ctx *ctx, const gcmc_job *job, double *tallies_out, int tallies_memory,
+                             gcmc_stats *stats_out)
+{
+    if (!ctx || !job) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    cudaSetDevice(ctx->device);
+    Plan P;
+    gcmc_status s = plan_run(ctx, job, 1, 128, P);
+    if (s) return s;
+    if ((s = ensure_arena(ctx, P.ws_bytes))) return s;
+    char *base = (char *)ctx->arena;
+    prof_mark(ctx);
+    if ((s = stage(ctx, P, base))) return s;
+    prof_mark(ctx);
+    const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
+    cudaError_t e = launch_plain(P.jobs[0].precision, P.scatter, ctx->d_grids, dj, 0, job->n_packets, nullptr, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "transport launch");
+    prof_mark(ctx);
+    return finish_run(ctx, P, base, tallies_out, tallies_memory, stats_out, 0);
+}
+
+gcmc_status gcmc_run_batch(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, const gcmc_launch_cfg *cfg,
+                           double *tallies_out, int tallies_memory, gcmc_stats *stats_out)
+{
+    if (!ctx || !jobs) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    cudaSetDevice(ctx->device);
+    const int chunk = cfg && cfg->chunk > 0 ? cfg->chunk : 1024;
+    Plan P;
+    gcmc_status s = plan_run(ctx, jobs, n_jobs, chunk, P);
+    if (s) return s;
+    if ((s = ensure_arena(ctx, P.ws_bytes))) return s;
+    char *base = (char *)ctx->arena;
+    int prec = P.jobs[0].precision;
+    for (const DevJob &d : P.jobs)
+        if (d.precision != prec) return fail(ctx, GCMC_ERR_ARG, "a batch runs in one precision");
+    prof_mark(ctx);
+    if ((s = stage(ctx, P, base))) return s;
+    prof_mark(ctx);
+    const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
+    cudaError_t e = launch_persistent(prec, P.scatter, ctx->d_grids, dj, n_jobs, P.total_items, chunk, cfg ? cfg->block : 0,
+                                      cfg ? cfg->blocks_per_sm : 0, cfg && cfg->interval > 0 ? cfg->interval : 1,
+                                      cfg && cfg->refill_min > 0 ? cfg->refill_min : 16,
+                                      reinterpret_cast<unsigned long long *>(base + P.off_work), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "transport launch");
+    prof_mark(ctx);
+    return finish_run(ctx, P, base, tallies_out, tallies_memory, stats_out, 1);
+}
+
+gcmc_status gcmc_submit(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, const gcmc_launch_cfg *cfg, uint64_t *ticket)
+{
+    if (!ctx || !jobs || !ticket) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    cudaSetDevice(ctx->device);
+    const int chunk = cfg && cfg->chunk > 0 ? cfg->chunk : 1024;
+    Plan P;
+    gcmc_status s = plan_run(ctx, jobs, n_jobs, chunk, P);
+    if (s) return s;
+    int prec = P.jobs[0].precision;
+    for (const DevJob &d : P.jobs)
+        if (d.precision != prec) return fail(ctx, GCMC_ERR_ARG, "a batch runs in one precision");
+    Ticket T;
+    T.n_jobs = n_jobs;
+    T.ws = dalloc(ctx, P.ws_bytes);
+    if (!T.ws) return fail(ctx, GCMC_ERR_OOM, "ticket workspace");
+    char *base = (char *)T.ws;
+    if ((s = stage(ctx, P, base))) {
+        dfree(ctx, T.ws);
+        return s;
+    }
+    const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
+    cudaError_t e = launch_persistent(prec, P.scatter, ctx->d_grids, dj, n_jobs, P.total_items, chunk, cfg ? cfg->block : 0,
+                                      cfg ? cfg->blocks_per_sm : 0, cfg && cfg->interval > 0 ? cfg->interval : 1,
+                                      cfg && cfg->refill_min > 0 ? cfg->refill_min : 16,
+                                      reinterpret_cast<unsigned long long *>(base + P.off_work), ctx->stream);
+    if (e != cudaSuccess) {
+        dfree(ctx, T.ws);
+        return cuda_fail(ctx, e, "transport launch");
+    }
+    CK(cudaMallocHost((void **)&T.h_acc, (size_t)n_jobs * ACC_SLOTS * 8));
+    CK(cudaMallocHost((void **)&T.h_info, (size_t)n_jobs * 4 * sizeof(double)));
+    if ((s = enqueue_readback(ctx, P, base, T.h_acc, T.h_info, reinterpret_cast<double *>(base + P.off_gather)))) return s;
+    CK(cudaEventCreateWithFlags(&T.done, cudaEventDisableTiming));
+    CK(cudaEventRecord(T.done, ctx->stream));
+    const uint64_t id = ctx->next_ticket++;
+    ctx->tickets[id] = T;
+    *ticket = id;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_poll(gcmc_ctx *ctx, uint64_t ticket, double *tallies_out, gcmc_stats *stats_out)
+{
+    if (!ctx) return GCMC_ERR_ARG;
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return fail(ctx, GCMC_ERR_ARG, "unknown ticket");
+    Ticket &T = it->second;
+    const cudaError_t q = cudaEventQuery(T.done);
+    if (q == cudaErrorNotReady) return GCMC_ERR_NOT_READY;
+    if (q != cudaSuccess) return cuda_fail(ctx, q, "ticket");
+    for (int j = 0; j < T.n_jobs; ++j) {
+        double t[MAX_OBS];
+        // n_obs is not kept with the ticket: unused observer slots are zero
+        unpack(T.h_acc + (size_t)j * ACC_SLOTS, T.h_info + 4 * j, MAX_OBS, t, stats_out ? stats_out + j : nullptr);
+        if (tallies_out) std::memcpy(tallies_out + (size_t)j * MAX_OBS, t, sizeof(t));
+    }
+    cudaEventDestroy(T.done);
+    cudaFreeHost(T.h_acc);
+    cudaFreeHost(T.h_info);
+    dfree(ctx, T.ws);
+    ctx->tickets.erase(it);
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_run_packets_debug(gcmc_ctx *ctx, const gcmc_job *job, int64_t packet0, int64_t n_run, double *pk_f,
+                                   int64_t *pk_steps, double *pk_tau, int32_t n_trace, int32_t max_trace, int32_t *tr_cell,
+                                   double *tr_len, int32_t *tr_n, double *tallies_out, gcmc_stats *stats_out)
+{
+    if (!ctx || !job) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    if (packet0 < 0 || n_run < 0 || packet0 + n_run > job->n_packets) return fail(ctx, GCMC_ERR_ARG, "packet range");
+    if (n_trace < 0 || max_trace < 0 || n_trace > n_run) return fail(ctx, GCMC_ERR_ARG, "trace sizes");
+    cudaSetDevice(ctx->device);
+    Plan P;
+    gcmc_status s = plan_run(ctx, job, 1, 128, P);
+    if (s) return s;
+    if ((s = ensure_arena(ctx, P.ws_bytes))) return s;
+    char *base = (char *)ctx->arena;
+    if ((s = stage(ctx, P, base))) return s;
+    const int nobs = P.jobs[0].n_obs;
+    HostLog hl{};
+    std::vector<void *> tmp;
+    cudaError_t e = cudaSuccess;
+    auto zalloc = [&](size_t bytes) -> void * {
+        void *p = dalloc(ctx, bytes);
+        if (p) {
+            tmp.push_back(p);
+            if (cudaMemsetAsync(p, 0, bytes, ctx->stream) != cudaSuccess) e = cudaErrorUnknown;
+        } else {
+            e = cudaErrorMemoryAllocation;
+        }
+        return p;
+    };
+    hl.pk_f = (double *)zalloc((size_t)n_run * nobs * sizeof(double));
+    hl.pk_steps = (int64_t *)zalloc((size_t)n_run * sizeof(int64_t));
+    hl.pk_tau = (double *)zalloc((size_t)n_run * sizeof(double));
+    hl.n_trace = n_trace;
+    hl.max_trace = max_trace;
+    if (n_trace > 0 && max_trace > 0) {
+        hl.tr_cell = (int32_t *)zalloc((size_t)n_trace * max_trace * sizeof(int32_t));
+        hl.tr_len = (double *)zalloc((size_t)n_trace * max_trace * sizeof(double));
+        hl.tr_n = (int32_t *)zalloc((size_t)n_trace * sizeof(int32_t));
+    }
+    if (e == cudaSuccess) {
+        const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
+        e = launch_plain(P.jobs[0].precision, P.scatter, ctx->d_grids, dj, packet0, n_run, &hl, ctx->stream);
+    }
+    if (e == cudaSuccess) {
+        if (pk_f) e = cudaMemcpyAsync(pk_f, hl.pk_f, (size_t)n_run * nobs * 8, cudaMemcpyDeviceToHost, ctx->stream);
+        if (pk_steps && e == cudaSuccess)
+            e = cudaMemcpyAsync(pk_steps, hl.pk_steps, (size_t)n_run * 8, cudaMemcpyDeviceToHost, ctx->stream);
+        if (pk_tau && e == cudaSuccess)
+            e = cudaMemcpyAsync(pk_tau, hl.pk_tau, (size_t)n_run * 8, cudaMemcpyDeviceToHost, ctx->stream);
+        if (hl.tr_cell && e == cudaSuccess) {
+            if (tr_cell) e = cudaMemcpyAsync(tr_cell, hl.tr_cell, (size_t)n_trace * max_trace * 4, cudaMemcpyDeviceToHost, ctx->stream);
+            if (tr_len && e == cudaSuccess)
+                e = cudaMemcpyAsync(tr_len, hl.tr_len, (size_t)n_trace * max_trace * 8, cudaMemcpyDeviceToHost, ctx->stream);
+            if (tr_n && e == cudaSuccess) e = cudaMemcpyAsync(tr_n, hl.tr_n, (size_t)n_trace * 4, cudaMemcpyDeviceToHost, ctx->stream);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    for (void *p : tmp) dfree(ctx, p);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "debug run");
+    return finish_run(ctx, P, base, tallies_out, GCMC_MEM_HOST, stats_out, 0);
+}
+
+gcmc_status gcmc_prep_cells(gcmc_ctx *ctx, const gcmc_job *job, double *alpha, double *omega, double *g, double *pgas,
+                            double *lum, double *cdf, double *wcell, gcmc_stats *stats_out)
+{
+    if (!ctx || !job) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    cudaSetDevice(ctx->device);
+    Plan P;
+    gcmc_status s = plan_run(ctx, job, 1, 128, P);
+    if (s) return s;
+    if ((s = ensure_arena(ctx, P.ws_bytes))) return s;
+    char *base = (char *)ctx->arena;
+    const int64_t ncell = ctx->grids[job->grid_id].dg.ncell;
+    double *dlum = nullptr;
+    if (lum && job->mode == GCMC_EMISSION) {
+        dlum = (double *)dalloc(ctx, ncell * 8);
+        if (!dlum) return fail(ctx, GCMC_ERR_OOM, "lum");
+    }
+    if ((s = stage(ctx, P, base, dlum))) {
+        dfree(ctx, dlum);
+        return s;
+    }
+    const bool f64 = P.jobs[0].precision == GCMC_FP64;
+    const size_t esz = f64 ? 8 : 4;
+    const int nrec = job->mode == GCMC_ALBEDO ? 4 : 1;
+    std::vector<char> raw(ncell * nrec * esz);
+    CK(cudaMemcpyAsync(raw.data(), base + P.off_rec[0], raw.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    if (job->mode == GCMC_EMISSION) {
+        if (cdf) CK(cudaMemcpyAsync(cdf, base + P.off_cdf[0], ncell * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        if (wcell) CK(cudaMemcpyAsync(wcell, base + P.off_w[0], ncell * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        if (dlum) CK(cudaMemcpyAsync(lum, dlum, ncell * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    s = finish_run(ctx, P, base, nullptr, GCMC_MEM_HOST, stats_out, 0);
+    dfree(ctx, dlum);
+    if (s) return s;
+    for (int64_t i = 0; i < ncell; ++i) {
+        double v[4] = {0, 0, 0, 0};
+        for (int c = 0; c < nrec; ++c)
+            v[c] = f64 ? reinterpret_cast<double *>(raw.data())[i * nrec + c] : reinterpret_cast<float *>(raw.data())[i * nrec + c];
+        if (alpha) alpha[i] = v[0];
+        if (nrec == 4) {
+            if (omega) omega[i] = v[1];
+            if (g) g[i] = v[2];
+            if (pgas) pgas[i] = v[3];
+        }
+    }
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_postscale(gcmc_ctx *ctx, int grid_id, int mode, double tally, int64_t n_packets, double l_tot,
+                           gcmc_observables *out)
+{
+    if (!ctx || !out) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    if (grid_id < 0 || grid_id >= (int)ctx->grids.size()) return fail(ctx, GCMC_ERR_ARG, "bad grid_id");
+    if (n_packets <= 0) return fail(ctx, GCMC_ERR_ARG, "n_packets must be positive");
+    std::memset(out, 0, sizeof(*out));
+    const double R0 = ctx->grids[grid_id].dg.R0, Rt = ctx->grids[grid_id].dg.Rtoa;
+    const double N = (double)n_packets;
+    if (mode == GCMC_ALBEDO) {
+        out->S = tally / N;
+        out->A_g = PI * out->S;
+        out->A_g_R0 = out->A_g * (Rt / R0) * (Rt / R0);
+    } else if (mode == GCMC_EMISSION) {
+        out->L_p = l_tot / N * tally;
+        out->I_p = out->L_p / (PI * Rt * Rt);
+        out->F_p = PI * out->I_p;
+    } else if (mode == GCMC_TRANSMISSION) {
+        out->I_p = (Rt - R0) / N * Rt * tally;
+        out->area = R0 * R0 + 2.0 * out->I_p;
+    } else {
+        return fail(ctx, GCMC_ERR_ARG, "bad mode");
+    }
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_release_grid(gcmc_ctx *ctx, int grid_id)
+{
+    if (!ctx || grid_id < 0 || grid_id >= (int)ctx->grids.size() || !ctx->grids[grid_id].dg.r)
+        return fail(ctx, GCMC_ERR_ARG, "unknown or released grid");
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (size_t o = 0; o < ctx->opacs.size(); ++o)
+        if (ctx->opacs[o].grid == grid_id && !ctx->opacs[o].owned.empty()) gcmc_release_opacity(ctx, (int)o);
+    GridH &G = ctx->grids[grid_id];
+    for (void *p : G.owned) dfree(ctx, p);
+    G.owned.clear();
+    std::memset(&G.dg, 0, sizeof(G.dg));
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_release_opacity(gcmc_ctx *ctx, int opac_id)
+{
+    if (!ctx || opac_id < 0 || opac_id >= (int)ctx->opacs.size() || ctx->opacs[opac_id].owned.empty())
+        return fail(ctx, GCMC_ERR_ARG, "unknown or released opacity");
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    OpacH &O = ctx->opacs[opac_id];
+    for (void *p : O.owned) dfree(ctx, p);
+    O.owned.clear();
+    O.grid = -1;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_set_profiling(gcmc_ctx *ctx, int on)
+{
+    if (!ctx) return GCMC_ERR_ARG;
+    for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+    ctx->prof_ev.clear();
+    ctx->prof = on != 0;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_get_profile(gcmc_ctx *ctx, double *prep_ms, double *transport_ms, int64_t *transport_launches)
+{
+    if (!ctx) return GCMC_ERR_ARG;
+    double a = 0.0, b = 0.0;
+    int64_t n = 0;
+    for (size_t q = 0; q + 3 <= ctx->prof_ev.size(); q += 3) {
+        float x = 0.0f, y = 0.0f;
+        if (cudaEventSynchronize(ctx->prof_ev[q + 2]) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "profile");
+        cudaEventElapsedTime(&x, ctx->prof_ev[q], ctx->prof_ev[q + 1]);
+        cudaEventElapsedTime(&y, ctx->prof_ev[q + 1], ctx->prof_ev[q + 2]);
+        a += x;
+        b += y;
+        ++n;
+    }
+    for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+    ctx->prof_ev.clear();
+    if (prep_ms) *prep_ms = a;
+    if (transport_ms) *transport_ms = b;
+    if (transport_launches) *transport_launches = n;
+    return GCMC_OK;
+}
+
+int64_t gcmc_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+gcmc_status gcmc_gather_bench(gcmc_ctx *ctx, int64_t n_records, int record_bytes, int64_t n_gathers, double *rate)
+{
+    if (!ctx || !rate || n_records < 1 || n_records > ((int64_t)1 << 32) - 1 || (record_bytes != 4 && record_bytes != 16) ||
+        n_gathers < 1)
+        return fail(ctx, GCMC_ERR_ARG, "gather bench arguments");
+    cudaSetDevice(ctx->device);
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    const int threads = 256, blocks = nsm * 8;
+    const int64_t per = std::max<int64_t>(1, n_gathers / ((int64_t)threads * blocks));
+    void *tab = dalloc(ctx, (size_t)n_records * record_bytes);
+    float *sink = (float *)dalloc(ctx, (size_t)threads * blocks * sizeof(float));
+    if (!tab || !sink) {
+        dfree(ctx, tab);
+        dfree(ctx, sink);
+        return fail(ctx, GCMC_ERR_OOM, "gather bench buffers");
+    }
+    cudaError_t e = cudaMemsetAsync(tab, 0x3c, (size_t)n_records * record_bytes, ctx->stream);
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    if (e == cudaSuccess) e = gather_bench(tab, n_records, record_bytes, std::max<int64_t>(1, per / 8), blocks, threads, sink, ctx->stream);
+    cudaEventRecord(a, ctx->stream);
+    if (e == cudaSuccess) e = gather_bench(tab, n_records, record_bytes, per, blocks, threads, sink, ctx->stream);
+    cudaEventRecord(b, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.0f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    dfree(ctx, tab);
+    dfree(ctx, sink);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gather bench");
+    *rate = (double)per * threads * blocks / (ms * 1e-3);
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_selftest_philox(gcmc_ctx *ctx, const uint32_t *ctr, const uint32_t *key, int n, uint32_t *out_lib,
+                                 uint32_t *out_curand)
+{
+    if (!ctx || n < 0 || (n > 0 && (!ctr || !key || !out_lib || !out_curand))) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    if (n == 0) return GCMC_OK;
+    cudaSetDevice(ctx->device);
+    uint32_t *d = (uint32_t *)dalloc(ctx, (size_t)n * 14 * sizeof(uint32_t));
+    if (!d) return fail(ctx, GCMC_ERR_OOM, "selftest");
+    uint32_t *dc = d, *dk = d + 4 * n, *dl = d + 6 * n, *du = d + 10 * n;
+    cudaError_t e = cudaMemcpyAsync(dc, ctr, (size_t)n * 16, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dk, key, (size_t)n * 8, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = selftest_philox(dc, dk, n, dl, du, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_lib, dl, (size_t)n * 16, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_curand, du, (size_t)n * 16, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, d);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "philox selftest");
+    return GCMC_OK;
+}
+
+}  // extern "C"

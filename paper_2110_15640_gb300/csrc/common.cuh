@@ -1,0 +1,170 @@
+// common.cuh -- device-side data layout and small primitives of libgcmc.
+//
+// Layout in HBM (one context):
+//   DevGrid   per uploaded grid: edge tables in FP64 and FP32 (r, r^2 as an FP32 hi+lo pair,
+//             sin(lat), sin^2(lat), cos/sin(lon)), per-cell T, p, rho, wind (FP32) and volume (FP64).
+//   DevJob    per job of a launch: mode, Philox key, packet count, pointers to the job's cell table
+//             (albedo: 16-byte {alpha, omega, g, P_gas} records in FP32, 32 bytes in FP64; absorber
+//             marches: 4/8-byte alpha), emission CDF and launch weights (FP64), source geometry and
+//             the job's 64-bit fixed-point accumulators.
+// Per-cell arrays are flattened [k][j][i] (longitude fastest), so a warp of packets launched from
+// neighbouring cells of one latitude row gathers neighbouring records.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gcmc.h"
+
+namespace gcmc {
+
+constexpr int MAX_OBS = GCMC_MAX_OBS;
+constexpr double PI = 3.14159265358979323846;
+constexpr double C_LIGHT = 2.99792458e8;
+constexpr double H_PLANCK = 6.62607015e-34;
+constexpr double K_BOLTZ = 1.380649e-23;
+// tally accumulator slots per job: [0, MAX_OBS) f sums, then 8 ledger sums, steps, packets, flags
+constexpr int ACC_LEDGER = MAX_OBS;
+constexpr int ACC_STEPS = MAX_OBS + 8;
+constexpr int ACC_PACKETS = MAX_OBS + 9;
+constexpr int ACC_FLAGS = MAX_OBS + 10;
+constexpr int ACC_SLOTS = 32;            // padded (256 bytes per job)
+constexpr double FIX_SCALE = 4294967296.0;   // 2^32: fixed-point resolution of tallies and ledger
+
+enum { K_FLIGHT = 0, K_PEEL = 1, K_CHORD = 2 };
+enum { E_CONT = -1, E_INTERACT = 0, E_ESCAPE = 1, E_BOTTOM = 2, E_CUTOFF = 3, E_CAP = 4, E_LOST = 5 };
+enum { F_RIN = 0, F_ROUT = 1, F_LATLO = 2, F_LATHI = 3, F_LONLO = 4, F_LONHI = 5, F_NONE = 6 };
+enum { FLAG_OVERFLOW = 1, FLAG_LOST = 2, FLAG_BAD = 4 };
+
+struct DevGrid {
+    int32_t nlon, nlat, nr, pad;
+    int64_t ncell;
+    double R0, Rtoa, lon0;
+    const double *r, *r2, *lat, *slat, *s2lat, *lon, *clon, *slon;     // FP64 edge tables
+    const float *r_f, *r2hi_f, *r2lo_f, *lat_f, *slat_f, *s2lat_f, *lon_f, *clon_f, *slon_f;
+    const float *shA_f;                                                 // [nr] (r_{k+1}/r_k)^3 - 1
+    const float *T, *p, *rho, *wind;                                    // per cell
+    const double *vol;                                                  // per cell
+};
+
+struct __align__(16) Rec64 {
+    double a, w, g, pg;
+};
+
+struct DevJob {
+    int32_t mode, n_obs, grid_slot, survival;
+    int32_t precision, pad0;
+    uint32_t key, pad1;
+    uint64_t seed;
+    int64_t n_packets;
+    int64_t chunk_begin;        // first work item of this job (batched launches)
+    int64_t max_steps;
+    const void *rec;            // albedo records, or alpha for absorber marches
+    const double *cdf;          // emission
+    const double *wcell;        // emission
+    const double *info;         // emission: [L_tot, n_incl, cdf_total] written by the cell-table kernels
+    double cdf_total, cdf_step; // emission: total and total / N
+    double star[3], e1[3], e2[3];
+    double obs[MAX_OBS][3];
+    double w_rr, p_surv, tau_cut, hg_eps;
+    unsigned long long *acc;    // [ACC_SLOTS]
+};
+
+// ------------------------------------------------------------------ Philox4x32-10 (Salmon et al. 2011)
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw_words(uint64_t seed, int64_t packet, uint32_t event, uint32_t key)
+{
+    return philox10(make_uint4((uint32_t)(uint64_t)packet, (uint32_t)((uint64_t)packet >> 32), event, key),
+                    make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// uniform in (0, 1): ((w >> 8) + 1/2) 2^-24, exact in FP64, correctly rounded in FP32
+template <typename real> __device__ __forceinline__ real u01(uint32_t w);
+template <> __device__ __forceinline__ double u01<double>(uint32_t w)
+{
+    return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0);
+}
+template <> __device__ __forceinline__ float u01<float>(uint32_t w)
+{
+    return __fmaf_rn((float)(w >> 8), 5.9604644775390625e-8f, 2.98023223876953125e-8f);
+}
+
+// ------------------------------------------------------------------ precision-dispatched helpers
+template <typename real> struct M;
+template <> struct M<float> {
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float exp_(float x) { return __expf(x); }
+    static __device__ __forceinline__ float log_(float x) { return __logf(x); }
+    static __device__ __forceinline__ float cbrt_(float x) { return cbrtf(x); }
+    static __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ void sincos_(float x, float *s, float *c) { sincosf(x, s, c); }
+    static __device__ __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
+    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+};
+template <> struct M<double> {
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
+    static __device__ __forceinline__ double exp_(double x) { return exp(x); }
+    static __device__ __forceinline__ double log_(double x) { return log(x); }
+    static __device__ __forceinline__ double cbrt_(double x) { return cbrt(x); }
+    static __device__ __forceinline__ double div_(double a, double b) { return a / b; }
+    static __device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
+    static __device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
+    static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+};
+
+template <typename real> __device__ __forceinline__ const real *tab_r(const DevGrid &g);
+template <> __device__ __forceinline__ const float *tab_r<float>(const DevGrid &g) { return g.r_f; }
+template <> __device__ __forceinline__ const double *tab_r<double>(const DevGrid &g) { return g.r; }
+template <typename real> __device__ __forceinline__ const real *tab_slat(const DevGrid &g);
+template <> __device__ __forceinline__ const float *tab_slat<float>(const DevGrid &g) { return g.slat_f; }
+template <> __device__ __forceinline__ const double *tab_slat<double>(const DevGrid &g) { return g.slat; }
+template <typename real> __device__ __forceinline__ const real *tab_s2lat(const DevGrid &g);
+template <> __device__ __forceinline__ const float *tab_s2lat<float>(const DevGrid &g) { return g.s2lat_f; }
+template <> __device__ __forceinline__ const double *tab_s2lat<double>(const DevGrid &g) { return g.s2lat; }
+template <typename real> __device__ __forceinline__ const real *tab_lat(const DevGrid &g);
+template <> __device__ __forceinline__ const float *tab_lat<float>(const DevGrid &g) { return g.lat_f; }
+template <> __device__ __forceinline__ const double *tab_lat<double>(const DevGrid &g) { return g.lat; }
+template <typename real> __device__ __forceinline__ const real *tab_lon(const DevGrid &g);
+template <> __device__ __forceinline__ const float *tab_lon<float>(const DevGrid &g) { return g.lon_f; }
+template <> __device__ __forceinline__ const double *tab_lon<double>(const DevGrid &g) { return g.lon; }
+template <typename real> __device__ __forceinline__ const real *tab_clon(const DevGrid &g);
+template <> __device__ __forceinline__ const float *tab_clon<float>(const DevGrid &g) { return g.clon_f; }
+template <> __device__ __forceinline__ const double *tab_clon<double>(const DevGrid &g) { return g.clon; }
+template <typename real> __device__ __forceinline__ const real *tab_slon(const DevGrid &g);
+template <> __device__ __forceinline__ const float *tab_slon<float>(const DevGrid &g) { return g.slon_f; }
+template <> __device__ __forceinline__ const double *tab_slon<double>(const DevGrid &g) { return g.slon; }
+
+// r_k^2 as an unevaluated sum hi + lo (exact r^2 in FP64; FP32 pair carries ~48 bits)
+template <typename real> __device__ __forceinline__ void r2_pair(const DevGrid &g, int k, real &hi, real &lo);
+template <> __device__ __forceinline__ void r2_pair<float>(const DevGrid &g, int k, float &hi, float &lo)
+{
+    hi = __ldg(g.r2hi_f + k);
+    lo = __ldg(g.r2lo_f + k);
+}
+template <> __device__ __forceinline__ void r2_pair<double>(const DevGrid &g, int k, double &hi, double &lo)
+{
+    hi = __ldg(g.r2 + k);
+    lo = 0.0;
+}
+
+// fixed-point conversion of a non-negative contribution
+template <typename real> __device__ __forceinline__ long long to_fix(real v);
+template <> __device__ __forceinline__ long long to_fix<float>(float v) { return __float2ll_rn(v * 4294967296.0f); }
+template <> __device__ __forceinline__ long long to_fix<double>(double v) { return __double2ll_rn(v * FIX_SCALE); }
+
+}  // namespace gcmc

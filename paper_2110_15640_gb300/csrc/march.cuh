@@ -1,0 +1,349 @@
+// march.cuh -- the cell-by-cell ray march through the spherical grid (hot loops 1-3), the packet
+// launch geometry and the scattering samplers, templated on the arithmetic type.
+//
+// Every straight ray is written x(s) = c0 + s d with c0 its point of closest approach to the planet
+// centre (c0 . d = 0, |c0| = p) and s the signed distance from c0.  In that frame
+//   radial shell r:          s = -/+ sqrt(r^2 - p^2)
+//   latitude cone sin(th)=S: (dz^2 - S^2) s^2 + 2 (zc dz) s + (zc^2 - S^2 p^2) = 0, disc = S^2 p^2 (Q - S^2),
+//                            Q = dz^2 + (zc/p)^2, valid on the nappe where z has the sign of S
+//   equator plane:           s = -zc / dz
+//   longitude half-plane:    s = -(n . c0) / (n . d), n = (-sin phi, cos phi, 0), on the phi side
+// Along a straight line the radius is convex in s, the azimuth is monotone (sign of (o x d)_z) and
+// the latitude has at most one extremum (sign of dz p^2 - zc s), so each step evaluates one shell,
+// usually one cone and one half-plane.  In FP32 the impact parameter p^2 is carried as an
+// unevaluated FP32 pair built with error-free products, so r^2 - p^2 keeps ~48 bits near grazing
+// incidence; cone roots within TAN_EPS of tangency are recomputed in FP64.
+#pragma once
+#include "common.cuh"
+
+namespace gcmc {
+
+template <typename real> struct Ray {
+    real cx, cy, cz;        // closest-approach point c0
+    real dx, dy, dz;        // unit direction
+    real s;                 // current position along the ray
+    real p2hi, p2lo;        // |c0|^2 = p^2 as hi + lo
+    real p, chz, Q;         // p, zc / p, dz^2 + chz^2
+    real crz;               // (o x d)_z: sign gives the direction of azimuthal motion
+    real tau, tau_target;   // accumulated optical depth; interaction target (< 0: none)
+    int i, j, k;            // current cell
+};
+
+// error-free product a*b = hi + lo
+// (the _rn intrinsics are never contracted into FMAs, which would break the error-free forms)
+__device__ __forceinline__ void two_prod(float a, float b, float &hi, float &lo)
+{
+    hi = __fmul_rn(a, b);
+    lo = __fmaf_rn(a, b, -hi);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (a*b - c*d) as an FP32 pair
+__device__ __forceinline__ void diff_prod(float a, float b, float c, float d, float &hi, float &lo)
+{
+    float p1, e1, p2, e2;
+    two_prod(a, b, p1, e1);
+    two_prod(c, d, p2, e2);
+    float s, e;
+    two_sum(p1, -p2, s, e);
+    e = __fadd_rn(e, __fsub_rn(e1, e2));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+// square of a pair, accumulated into (H, L)
+__device__ __forceinline__ void add_sq(float hi, float lo, float &H, float &L)
+{
+    float q, qe;
+    two_prod(hi, hi, q, qe);
+    qe = __fmaf_rn(2.0f * hi, lo, qe);
+    float s, e;
+    two_sum(H, q, s, e);
+    L = __fadd_rn(L, __fadd_rn(e, qe));
+    H = s;
+}
+
+template <typename real>
+__device__ __forceinline__ void ray_setup(Ray<real> &R, real ox, real oy, real oz, real dx, real dy, real dz)
+{
+    const real inv = M<real>::rsqrt_(dx * dx + dy * dy + dz * dz);
+    dx *= inv;
+    dy *= inv;
+    dz *= inv;
+    const real bo = ox * dx + oy * dy + oz * dz;
+    R.dx = dx;
+    R.dy = dy;
+    R.dz = dz;
+    R.cx = ox - bo * dx;
+    R.cy = oy - bo * dy;
+    R.cz = oz - bo * dz;
+    R.s = bo;
+    if constexpr (sizeof(real) == 4) {
+        // p^2 = |o x d|^2 as an FP32 pair
+        float ah, al, bh, bl, ch, cl;
+        diff_prod(oy, dz, oz, dy, ah, al);
+        diff_prod(oz, dx, ox, dz, bh, bl);
+        diff_prod(ox, dy, oy, dx, ch, cl);
+        float H = 0.0f, L = 0.0f;
+        add_sq(ah, al, H, L);
+        add_sq(bh, bl, H, L);
+        add_sq(ch, cl, H, L);
+        const float hi = __fadd_rn(H, L);
+        R.p2hi = hi;
+        R.p2lo = __fsub_rn(L, __fsub_rn(hi, H));
+        R.crz = ch;
+    } else {
+        const double ax = oy * dz - oz * dy, ay = oz * dx - ox * dz, az = ox * dy - oy * dx;
+        R.p2hi = ax * ax + ay * ay + az * az;
+        R.p2lo = 0.0;
+        R.crz = az;
+    }
+    R.p = M<real>::sqrt_(R.p2hi);
+    R.chz = R.p > (real)0 ? M<real>::div_(R.cz, R.p) : (real)0;
+    R.Q = dz * dz + R.chz * R.chz;
+}
+
+constexpr double TAN_EPS_CONE = 1e-5;
+
+// the cone roots on the valid nappe in FP64, recomputed from the FP32 ray near tangency;
+// returns the number of roots written to r[]
+__device__ __noinline__ int cone_roots64(double cx, double cy, double cz, double dx, double dy, double dz, double S,
+                                         double S2, double *r)
+{
+    const double p2 = cx * cx + cy * cy + cz * cz;
+    const double A = dz * dz - S2;
+    const double B = cz * dz;
+    const double C = cz * cz - S2 * p2;
+    const double disc = B * B - A * C;
+    if (disc < 0.0) return 0;
+    const double sq = sqrt(disc);
+    const double q = -(B + copysign(sq, B));
+    double t[2];
+    int m = 0, n = 0;
+    if (q != 0.0) {
+        t[m++] = q / A;
+        t[m++] = C / q;
+    } else {
+        t[m++] = 0.0;
+    }
+    for (int i = 0; i < m; ++i) {
+        const double z = cz + t[i] * dz;
+        if (S > 0 ? z > 0.0 : z < 0.0) r[n++] = t[i];
+    }
+    return n;
+}
+
+template <typename real>
+__device__ __forceinline__ real cone_root(const DevGrid &G, const Ray<real> &R, int e, real smin)
+{
+    const real S = __ldg(tab_slat<real>(G) + e);
+    const real inf = M<real>::inf();
+    if (S == (real)0) {
+        if (R.dz == (real)0) return inf;
+        const real sr = M<real>::div_(-R.cz, R.dz);
+        return sr > smin ? sr : inf;
+    }
+    const real S2 = __ldg(tab_s2lat<real>(G) + e);
+    const real A = R.dz * R.dz - S2;
+    const real dn = R.Q - S2;
+    if (dn < (real)0) return inf;
+    if constexpr (sizeof(real) == 4) {
+        if (dn < (real)TAN_EPS_CONE || fabsf(A) < (real)TAN_EPS_CONE) {
+            // validity is decided on the rounded root: the same test as every other face, so a face
+            // just crossed (root == s after rounding) is never taken again
+            double r[2];
+            const int m = cone_roots64(R.cx, R.cy, R.cz, R.dx, R.dy, R.dz, __ldg(G.slat + e), __ldg(G.s2lat + e), r);
+            real best = inf;
+            for (int i = 0; i < m; ++i) {
+                const real rf = (real)r[i];
+                if (rf > smin && rf < best) best = rf;
+            }
+            return best;
+        }
+    }
+    const real B = R.cz * R.dz;
+    const real C = R.p2hi * ((R.chz - S) * (R.chz + S));
+    const real sq = fabs(S) * R.p * M<real>::sqrt_(dn);
+    const real q = -(B + copysign(sq, B));
+    real best = inf;
+    if (q != (real)0) {
+        const real r1 = M<real>::div_(q, A);
+        const real r2 = M<real>::div_(C, q);
+        const real z1 = R.cz + r1 * R.dz, z2 = R.cz + r2 * R.dz;
+        const bool v1 = (S > (real)0 ? z1 > (real)0 : z1 < (real)0) && r1 > smin;
+        const bool v2 = (S > (real)0 ? z2 > (real)0 : z2 < (real)0) && r2 > smin;
+        if (v1) best = r1;
+        if (v2 && r2 < best) best = r2;
+    }
+    return best;
+}
+
+// Exit of the current cell: returns the s of the exit point and the face.
+template <typename real>
+__device__ __forceinline__ real cell_exit(const DevGrid &G, const Ray<real> &R, int &face)
+{
+    const real inf = M<real>::inf();
+    // radial shells
+    real best;
+    {
+        real hi, lo;
+        bool done = false;
+        if (R.s < (real)0) {
+            r2_pair<real>(G, R.k, hi, lo);
+            const real h = (hi - R.p2hi) + (lo - R.p2lo);
+            if (h > (real)0) {
+                best = -M<real>::sqrt_(h);
+                face = F_RIN;
+                done = true;
+            }
+        }
+        if (!done) {
+            r2_pair<real>(G, R.k + 1, hi, lo);
+            const real h = (hi - R.p2hi) + (lo - R.p2lo);
+            best = M<real>::sqrt_(h > (real)0 ? h : (real)0);
+            face = F_ROUT;
+        }
+    }
+    // latitude cones: the latitude along the line has one extremum (sign of dz p^2 - zc s)
+    if (G.nlat > 1) {
+        const bool has_lo = R.j > 0, has_hi = R.j + 1 < G.nlat;
+        const real D = R.dz * R.p2hi - R.cz * R.s;
+        const bool up = D > (real)0;
+        const bool both = fabs(D) < (real)1e-4 * R.p2hi;
+        real tlo = inf, thi = inf;
+        if (has_hi && (up || both)) thi = cone_root<real>(G, R, R.j + 1, R.s);
+        if (has_lo && (!up || both || thi == inf)) tlo = cone_root<real>(G, R, R.j, R.s);
+        if (has_hi && !up && !both && tlo == inf) thi = cone_root<real>(G, R, R.j + 1, R.s);
+        if (tlo < best) {
+            best = tlo;
+            face = F_LATLO;
+        }
+        if (thi < best) {
+            best = thi;
+            face = F_LATHI;
+        }
+    }
+    // longitude half-plane ahead in azimuth
+    if (G.nlon > 1 && R.crz != (real)0) {
+        const bool east = R.crz > (real)0;
+        const int e = east ? R.i + 1 : R.i;
+        const real c = __ldg(tab_clon<real>(G) + e), sn = __ldg(tab_slon<real>(G) + e);
+        const real nd = R.dy * c - R.dx * sn;
+        if (nd != (real)0) {
+            const real sr = M<real>::div_(-(R.cy * c - R.cx * sn), nd);
+            if (sr > R.s && c * (R.cx + sr * R.dx) + sn * (R.cy + sr * R.dy) > (real)0 && sr < best) {
+                best = sr;
+                face = east ? F_LONHI : F_LONLO;
+            }
+        }
+    }
+    return best;
+}
+
+// Cross `face`: update the cell; returns E_CONT, E_ESCAPE or E_BOTTOM.
+__device__ __forceinline__ int cross_face(const DevGrid &G, int face, int &i, int &j, int &k)
+{
+    switch (face) {
+    case F_RIN:
+        if (k == 0) return E_BOTTOM;
+        --k;
+        break;
+    case F_ROUT:
+        if (k == G.nr - 1) return E_ESCAPE;
+        ++k;
+        break;
+    case F_LATLO: --j; break;
+    case F_LATHI: ++j; break;
+    case F_LONLO: i = (i == 0) ? G.nlon - 1 : i - 1; break;
+    case F_LONHI: i = (i + 1 == G.nlon) ? 0 : i + 1; break;
+    default: break;
+    }
+    return E_CONT;
+}
+
+// ------------------------------------------------------------------ samplers (Sect. 3)
+template <typename real> __device__ __forceinline__ real sample_rayleigh(real z)
+{
+    // exact inverse CDF of 3/8 (1 + mu^2): mu^3 + 3 mu = 8 z - 4
+    const real q = (real)4 * z - (real)2;
+    const real u = M<real>::cbrt_(q + M<real>::sqrt_(q * q + (real)1));
+    return u - M<real>::div_((real)1, u);
+}
+
+template <typename real> __device__ __forceinline__ real sample_hg(real g, real z, real eps)
+{
+    if (fabs(g) < eps) return (real)2 * z - (real)1;
+    const real a = M<real>::div_((real)1 - g * g, (real)1 - g + (real)2 * g * z);
+    real mu = M<real>::div_((real)1 + g * g - a * a, (real)2 * g);
+    mu = mu > (real)1 ? (real)1 : mu;
+    mu = mu < (real)-1 ? (real)-1 : mu;
+    return mu;
+}
+
+// probability per steradian of scattering by angle acos(mu): (P_gas P_Ray + (1 - P_gas) P_HG) / (4 pi)
+template <typename real> __device__ __forceinline__ real theta_mix(real mu, real pg, real g)
+{
+    const real pr = (real)0.75 * ((real)1 + mu * mu);
+    const real den = (real)1 + g * g - (real)2 * g * mu;
+    const real ph = ((real)1 - g * g) * M<real>::rsqrt_(den) * M<real>::div_((real)1, den);
+    return (pg * pr + ((real)1 - pg) * ph) * (real)(1.0 / (4.0 * PI));
+}
+
+// direction at polar angle acos(mu), azimuth psi about d (azimuth origin as in the standard
+// e1 = (dx dz, dy dz, -(1 - dz^2)) / sqrt(1 - dz^2), e2 = (-dy, dx, 0) / sqrt(1 - dz^2) frame)
+template <typename real>
+__device__ __forceinline__ void turn(real &dx, real &dy, real &dz, real mu, real psi)
+{
+    real sp, cp;
+    M<real>::sincos_(psi, &sp, &cp);
+    const real s = M<real>::sqrt_(fmax((real)0, (real)1 - mu * mu));
+    real nx, ny, nz;
+    if (fabs(dz) < (real)0.99999) {
+        const real den = M<real>::sqrt_((real)1 - dz * dz);
+        const real id = M<real>::div_((real)1, den);
+        nx = mu * dx + s * (cp * dx * dz * id - sp * dy * id);
+        ny = mu * dy + s * (cp * dy * dz * id + sp * dx * id);
+        nz = mu * dz - s * cp * den;
+    } else {
+        nx = s * cp;
+        ny = s * sp;
+        nz = (dz > (real)0 ? (real)1 : (real)-1) * mu;
+    }
+    const real inv = M<real>::rsqrt_(nx * nx + ny * ny + nz * nz);
+    dx = nx * inv;
+    dy = ny * inv;
+    dz = nz * inv;
+}
+
+// latitude / longitude bins of a point (radial index known)
+template <typename real>
+__device__ __forceinline__ void locate_angles(const DevGrid &G, real x, real y, real z, int &i, int &j)
+{
+    const real lat = M<real>::atan2_(z, M<real>::sqrt_(x * x + y * y));
+    real lon = M<real>::atan2_(y, x);
+    const real lo0 = (real)G.lon0;
+    const real two_pi = (real)(2.0 * PI);
+    while (lon < lo0) lon += two_pi;
+    while (lon >= lo0 + two_pi) lon -= two_pi;
+    const real *lat_t = tab_lat<real>(G);
+    const real *lon_t = tab_lon<real>(G);
+    int jj = 0;
+    while (jj < G.nlat - 1 && lat >= __ldg(lat_t + jj + 1)) ++jj;
+    int ii = 0;
+    // binary search over longitude edges
+    int lo = 0, hi = G.nlon - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(lon_t + mid) <= lon) lo = mid; else hi = mid - 1;
+    }
+    ii = lo;
+    i = ii;
+    j = jj;
+}
+
+}  // namespace gcmc

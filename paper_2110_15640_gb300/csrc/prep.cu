@@ -1,0 +1,417 @@
+// prep.cu -- S1: per-job cell tables, computed on the device for every job of a launch.
+//
+//   albedo       alpha_ext = rho (k_abs + k_Ray) + a_cld q_cld, omega = alpha_sca / alpha_ext,
+//                P_gas = rho k_Ray / alpha_sca (Sect. 3.6), HG g; FP64 arithmetic, stored as one
+//                16-byte FP32 record per cell (32 bytes in FP64 runs).
+//   emission     alpha = rho k(T, p) from the correlated-k table (bilinear in ln T, ln p of ln k),
+//                L_i = 4 pi V_i alpha_i B_lambda(T_i) (Sect. 5.3), the tau_vert cut (Sect. 4.6),
+//                hybrid pdf q_i = (1 - beta) L_i/L_tot + beta/N'_c and launch weight (L_i/L_tot)/q_i
+//                (Sect. 4.3), and its cumulative sum.  All in FP64, because the cumulative pdf decides
+//                integers (the launch cell of every packet); the march table is alpha rounded to the
+//                march precision.
+//   transmission per-cell v_LOS (Sect. 7), lambda_eff = lambda_0 (1 - v_LOS / c), cross-section
+//                interpolated linearly in ln sigma between the bracketing table wavelengths and
+//                bilinearly in (ln T, ln p); FP32 in FP32 runs (no integer decision depends on it).
+#include <curand_philox4x32_x.h>
+
+#include "internal.h"
+
+namespace gcmc {
+
+__device__ __forceinline__ void interp_idx(const double *grid, int n, double v, int &a, double &w)
+{
+    if (v <= grid[0]) {
+        a = 0;
+        w = 0.0;
+        return;
+    }
+    if (v >= grid[n - 1]) {
+        a = n - 2;
+        w = 1.0;
+        return;
+    }
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (grid[mid] <= v) lo = mid; else hi = mid;
+    }
+    a = lo;
+    w = (log(v) - log(grid[lo])) / (log(grid[lo + 1]) - log(grid[lo]));
+}
+
+// ------------------------------------------------------------------ albedo
+template <typename real>
+__global__ void k_prep_albedo(DevGrid G, AlbDev op, const PrepJob *__restrict__ jobs)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= G.ncell) return;
+    const PrepJob pj = jobs[blockIdx.y];
+    const int l = pj.lam;
+    const double rho = (double)G.rho[idx];
+    const double ac = op.acld ? (double)op.acld[idx] * op.qcld[l] : 0.0;
+    const double ray = rho * op.kray[l];
+    const double ext = rho * (op.kabs[l] + op.kray[l]) + ac;
+    const double sca = ray + op.wcld[l] * ac;
+    const double om = ext > 0.0 ? sca / ext : 0.0;
+    const double pg = sca > 0.0 ? ray / sca : 1.0;
+    if constexpr (sizeof(real) == 4) {
+        reinterpret_cast<float4 *>(pj.rec)[idx] = make_float4((float)ext, (float)om, (float)op.gcld[l], (float)pg);
+    } else {
+        Rec64 r;
+        r.a = ext;
+        r.w = om;
+        r.g = op.gcld[l];
+        r.pg = pg;
+        reinterpret_cast<Rec64 *>(pj.rec)[idx] = r;
+    }
+}
+
+std::atomic<long long> g_launches{0};
+
+cudaError_t prep_albedo(int precision, const DevGrid *, const DevGrid &hg, const AlbDev &op, const PrepJob *djobs,
+                        int njobs, cudaStream_t st)
+{
+    count_launch(1);
+    dim3 grid((unsigned)((hg.ncell + PREP_BLOCK - 1) / PREP_BLOCK), (unsigned)njobs);
+    if (precision == GCMC_FP64) k_prep_albedo<double><<<grid, PREP_BLOCK, 0, st>>>(hg, op, djobs);
+    else k_prep_albedo<float><<<grid, PREP_BLOCK, 0, st>>>(hg, op, djobs);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ interpolation weights (T, p)
+__global__ void k_tp_weights(DevGrid G, const double *Tg, int nT, const double *pg, int np, int2 *ab, double2 *w)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= G.ncell) return;
+    int a, b;
+    double wT, wp;
+    interp_idx(Tg, nT, (double)G.T[idx], a, wT);
+    interp_idx(pg, np, (double)G.p[idx], b, wp);
+    ab[idx] = make_int2(a, b);
+    w[idx] = make_double2(wT, wp);
+}
+
+// ------------------------------------------------------------------ emission
+template <typename real>
+__global__ void k_emis_alpha(DevGrid G, KtabDev kt, const PrepJob *__restrict__ jobs, const int2 *__restrict__ ab,
+                             const double2 *__restrict__ w)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= G.ncell) return;
+    const PrepJob pj = jobs[blockIdx.y];
+    const int2 q = ab[idx];
+    const double wT = w[idx].x, wp = w[idx].y;
+    const double *base = kt.lnk + ((int64_t)pj.lam * kt.ng + pj.g) * kt.nT * kt.np;
+    const double l00 = base[q.x * kt.np + q.y], l10 = base[(q.x + 1) * kt.np + q.y];
+    const double l01 = base[q.x * kt.np + q.y + 1], l11 = base[(q.x + 1) * kt.np + q.y + 1];
+    const double lk = (1 - wT) * (1 - wp) * l00 + wT * (1 - wp) * l10 + (1 - wT) * wp * l01 + wT * wp * l11;
+    const double alpha = (double)G.rho[idx] * exp(lk);
+    const double x = H_PLANCK * C_LIGHT / (pj.lam_m * K_BOLTZ * (double)G.T[idx]);
+    const double B = pj.c1 / expm1(x);
+    const double L = 4.0 * PI * G.vol[idx] * alpha * B;
+    reinterpret_cast<real *>(pj.rec)[idx] = (real)alpha;
+    pj.cdf[idx] = L;
+    pj.wcell[idx] = alpha;
+    if (pj.lum) pj.lum[idx] = L;
+}
+
+// tau_vert cut along each column, from the top: a cell emits if the vertical optical depth above it
+// is below tau_vert_max; excluded cells are marked with L = -1
+__global__ void k_emis_cut(DevGrid G, const PrepJob *__restrict__ jobs, double tau_vert_max)
+{
+    const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t ncol = (int64_t)G.nlon * G.nlat;
+    if (col >= ncol) return;
+    const PrepJob pj = jobs[blockIdx.y];
+    double above = 0.0;
+    for (int k = G.nr - 1; k >= 0; --k) {
+        const int64_t idx = k * ncol + col;
+        const bool incl = above < tau_vert_max;
+        above += pj.wcell[idx] * (G.r[k + 1] - G.r[k]);
+        if (!incl) pj.cdf[idx] = -1.0;
+    }
+}
+
+__device__ __forceinline__ double warp_incl_scan(double v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// per-block sums of L over the emitting cells and their count (fixed tree order)
+__global__ void k_emis_reduce(int64_t ncell, const PrepJob *__restrict__ jobs)
+{
+    __shared__ double ss[EMIS_SCAN_BLOCK / 32], sc[EMIS_SCAN_BLOCK / 32];
+    const PrepJob pj = jobs[blockIdx.y];
+    const int64_t idx = (int64_t)blockIdx.x * EMIS_SCAN_BLOCK + threadIdx.x;
+    double L = idx < ncell ? pj.cdf[idx] : -1.0;
+    double v = L >= 0.0 ? L : 0.0, c = L >= 0.0 ? 1.0 : 0.0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        v += __shfl_down_sync(0xffffffffu, v, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ss[threadIdx.x >> 5] = v;
+        sc[threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = ss[threadIdx.x];
+        c = sc[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            v += __shfl_down_sync(0xffffffffu, v, o);
+            c += __shfl_down_sync(0xffffffffu, c, o);
+        }
+        if (threadIdx.x == 0) {
+            pj.bsum[blockIdx.x] = v;
+            pj.bcnt[blockIdx.x] = c;
+        }
+    }
+}
+
+__global__ void k_emis_total(int nblk, const PrepJob *__restrict__ jobs, int njobs)
+{
+    const int jb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (jb >= njobs) return;
+    const PrepJob pj = jobs[jb];
+    double s = 0.0, c = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        s += pj.bsum[b];
+        c += pj.bcnt[b];
+    }
+    pj.info[0] = s;
+    pj.info[1] = c;
+}
+
+// hybrid pdf, launch weights and the per-block inclusive scan of the pdf
+__global__ void k_emis_pdf(int64_t ncell, const PrepJob *__restrict__ jobs, double beta)
+{
+    __shared__ double ws[EMIS_SCAN_BLOCK / 32];
+    const PrepJob pj = jobs[blockIdx.y];
+    const int64_t idx = (int64_t)blockIdx.x * EMIS_SCAN_BLOCK + threadIdx.x;
+    const double Ltot = pj.info[0], nincl = pj.info[1];
+    double q = 0.0, wgt = 0.0;
+    if (idx < ncell) {
+        const double L = pj.cdf[idx];
+        if (L >= 0.0 && nincl > 0.0) {
+            if (Ltot > 0.0) {
+                q = (1.0 - beta) * L / Ltot + beta / nincl;
+                wgt = q > 0.0 ? (L / Ltot) / q : 0.0;
+            } else {
+                q = 1.0 / nincl;
+            }
+        }
+    }
+    double s = warp_incl_scan(q);
+    if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const double t = warp_incl_scan(ws[threadIdx.x]);
+        ws[threadIdx.x] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x >= 32) s += ws[(threadIdx.x >> 5) - 1];
+    if (idx < ncell) {
+        pj.cdf[idx] = s;
+        pj.wcell[idx] = wgt;
+    }
+    if (threadIdx.x == EMIS_SCAN_BLOCK - 1) pj.bsum[blockIdx.x] = s;
+}
+
+__global__ void k_emis_scan_blocks(int nblk, const PrepJob *__restrict__ jobs, int njobs)
+{
+    const int jb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (jb >= njobs) return;
+    const PrepJob pj = jobs[jb];
+    double run = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        const double t = pj.bsum[b];
+        pj.bcnt[b] = run;
+        run += t;
+    }
+    pj.info[2] = run;
+}
+
+__global__ void k_emis_cdf_add(int64_t ncell, const PrepJob *__restrict__ jobs)
+{
+    const PrepJob pj = jobs[blockIdx.y];
+    const int64_t idx = (int64_t)blockIdx.x * EMIS_SCAN_BLOCK + threadIdx.x;
+    if (idx < ncell && blockIdx.x > 0) pj.cdf[idx] += pj.bcnt[blockIdx.x];
+}
+
+cudaError_t prep_emission(int precision, const DevGrid *, const DevGrid &hg, const KtabDev &kt, const PrepJob *djobs,
+                          int njobs, double tau_vert_max, double beta, int2 *wk_ab, double2 *wk_w, cudaStream_t st)
+{
+    count_launch(8);
+    const unsigned nb = (unsigned)((hg.ncell + PREP_BLOCK - 1) / PREP_BLOCK);
+    k_tp_weights<<<nb, PREP_BLOCK, 0, st>>>(hg, kt.Tg, kt.nT, kt.pg, kt.np, wk_ab, wk_w);
+    dim3 g1(nb, (unsigned)njobs);
+    if (precision == GCMC_FP64) k_emis_alpha<double><<<g1, PREP_BLOCK, 0, st>>>(hg, kt, djobs, wk_ab, wk_w);
+    else k_emis_alpha<float><<<g1, PREP_BLOCK, 0, st>>>(hg, kt, djobs, wk_ab, wk_w);
+    const int64_t ncol = (int64_t)hg.nlon * hg.nlat;
+    dim3 g2((unsigned)((ncol + 127) / 128), (unsigned)njobs);
+    k_emis_cut<<<g2, 128, 0, st>>>(hg, djobs, tau_vert_max);
+    const int nblk = (int)((hg.ncell + EMIS_SCAN_BLOCK - 1) / EMIS_SCAN_BLOCK);
+    dim3 g3((unsigned)nblk, (unsigned)njobs);
+    k_emis_reduce<<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs);
+    k_emis_total<<<(njobs + 127) / 128, 128, 0, st>>>(nblk, djobs, njobs);
+    k_emis_pdf<<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
+    k_emis_scan_blocks<<<(njobs + 127) / 128, 128, 0, st>>>(nblk, djobs, njobs);
+    k_emis_cdf_add<<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ transmission (Doppler cross-sections)
+__global__ void k_xsec_cells(DevGrid G, XsecDev xs, int2 *ab, double2 *w, double *fac)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= G.ncell) return;
+    int a, b;
+    double wT, wp;
+    interp_idx(xs.Tg, xs.nT, (double)G.T[idx], a, wT);
+    interp_idx(xs.pg, xs.np, (double)G.p[idx], b, wp);
+    ab[idx] = make_int2(a, b);
+    w[idx] = make_double2(wT, wp);
+    double v = 0.0;
+    if (G.wind) {
+        const int i = (int)(idx % G.nlon), j = (int)((idx / G.nlon) % G.nlat), k = (int)(idx / ((int64_t)G.nlon * G.nlat));
+        const double lat = 0.5 * (G.lat[j] + G.lat[j + 1]);
+        const double th = 0.5 * PI - lat;     // polar angle of the cell
+        const double ph = 0.5 * (G.lon[i] + G.lon[i + 1]);
+        const double rmid = 0.5 * (G.r[k] + G.r[k + 1]);
+        const double u = G.wind[idx], vv = G.wind[G.ncell + idx], ww = G.wind[2 * G.ncell + idx];
+        const double dph = ph - xs.view_phi;
+        v = u * sin(xs.view_theta) * sin(dph) + (vv * cos(th) - ww * sin(th)) * sin(xs.view_theta) * cos(dph) -
+            (vv * sin(th) + ww * cos(th)) * cos(xs.view_theta) +
+            xs.omega_rot * rmid * sin(th) * sin(xs.view_theta) * sin(dph);
+    }
+    fac[idx] = 1.0 - v / C_LIGHT;
+}
+
+template <typename real>
+__global__ void k_prep_xsec(DevGrid G, XsecDev xs, const PrepJob *__restrict__ jobs, const int2 *__restrict__ ab,
+                            const double2 *__restrict__ w, const double *__restrict__ fac)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= G.ncell) return;
+    const PrepJob pj = jobs[blockIdx.y];
+    const double le = pj.lam_m * fac[idx];
+    int l;
+    const double *lam = xs.lam;
+    if (le <= lam[0]) l = -1;
+    else if (le >= lam[xs.nl - 1]) l = -2;
+    else {
+        l = pj.lam_hint;
+        if (l < 0) l = 0;
+        if (l > xs.nl - 2) l = xs.nl - 2;
+        while (lam[l + 1] <= le) ++l;
+        while (lam[l] > le) --l;
+    }
+    const int2 q = ab[idx];
+    const int np = xs.np, nTp = xs.nT * xs.np;
+    const int o00 = q.x * np + q.y, o10 = (q.x + 1) * np + q.y, o01 = q.x * np + q.y + 1, o11 = (q.x + 1) * np + q.y + 1;
+    if constexpr (sizeof(real) == 8) {
+        double wl;
+        int l0;
+        if (l == -1) { l0 = 0; wl = 0.0; }
+        else if (l == -2) { l0 = xs.nl - 2; wl = 1.0; }
+        else { l0 = l; wl = (le - lam[l0]) / (lam[l0 + 1] - lam[l0]); }
+        const double wT = w[idx].x, wp = w[idx].y;
+        double ls[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const double *s = xs.lnsig + (int64_t)(l0 + e) * nTp;
+            ls[e] = (1 - wT) * (1 - wp) * s[o00] + wT * (1 - wp) * s[o10] + (1 - wT) * wp * s[o01] + wT * wp * s[o11];
+        }
+        reinterpret_cast<double *>(pj.rec)[idx] = (double)G.rho[idx] * exp((1.0 - wl) * ls[0] + wl * ls[1]);
+    } else {
+        float wl;
+        int l0;
+        if (l == -1) { l0 = 0; wl = 0.0f; }
+        else if (l == -2) { l0 = xs.nl - 2; wl = 1.0f; }
+        else { l0 = l; wl = __fdividef((float)(le - lam[l0]), (float)(lam[l0 + 1] - lam[l0])); }
+        const float wT = (float)w[idx].x, wp = (float)w[idx].y;
+        float ls[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float *s = xs.lnsig_f + (int64_t)(l0 + e) * nTp;
+            ls[e] = (1 - wT) * (1 - wp) * __ldg(s + o00) + wT * (1 - wp) * __ldg(s + o10) + (1 - wT) * wp * __ldg(s + o01) +
+                    wT * wp * __ldg(s + o11);
+        }
+        reinterpret_cast<float *>(pj.rec)[idx] = G.rho[idx] * __expf((1.0f - wl) * ls[0] + wl * ls[1]);
+    }
+}
+
+cudaError_t prep_xsec(int precision, const DevGrid *, const DevGrid &hg, const XsecDev &xs, const PrepJob *djobs,
+                      int njobs, int2 *wk_ab, double2 *wk_w, double *wk_fac, cudaStream_t st)
+{
+    count_launch(2);
+    const unsigned nb = (unsigned)((hg.ncell + PREP_BLOCK - 1) / PREP_BLOCK);
+    k_xsec_cells<<<nb, PREP_BLOCK, 0, st>>>(hg, xs, wk_ab, wk_w, wk_fac);
+    dim3 g1(nb, (unsigned)njobs);
+    if (precision == GCMC_FP64) k_prep_xsec<double><<<g1, PREP_BLOCK, 0, st>>>(hg, xs, djobs, wk_ab, wk_w, wk_fac);
+    else k_prep_xsec<float><<<g1, PREP_BLOCK, 0, st>>>(hg, xs, djobs, wk_ab, wk_w, wk_fac);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Philox self test
+__global__ void k_philox_selftest(const uint32_t *ctr, const uint32_t *key, int n, uint32_t *out_lib, uint32_t *out_cur)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const uint4 c = make_uint4(ctr[4 * t], ctr[4 * t + 1], ctr[4 * t + 2], ctr[4 * t + 3]);
+    const uint2 k = make_uint2(key[2 * t], key[2 * t + 1]);
+    const uint4 a = philox10(c, k);
+    const uint4 b = curand_Philox4x32_10(c, k);
+    out_lib[4 * t] = a.x; out_lib[4 * t + 1] = a.y; out_lib[4 * t + 2] = a.z; out_lib[4 * t + 3] = a.w;
+    out_cur[4 * t] = b.x; out_cur[4 * t + 1] = b.y; out_cur[4 * t + 2] = b.z; out_cur[4 * t + 3] = b.w;
+}
+
+cudaError_t selftest_philox(const uint32_t *ctr, const uint32_t *key, int n, uint32_t *out_lib, uint32_t *out_cur,
+                            cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    count_launch(1);
+    k_philox_selftest<<<(n + 127) / 128, 128, 0, st>>>(ctr, key, n, out_lib, out_cur);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ random-gather microbenchmark
+template <int RB>
+__global__ void k_gather(const void *__restrict__ table, uint32_t n, int64_t iters, float *sink)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    float acc = 0.0f;
+    uint32_t h = t * 0x9E3779B9u + 0x7F4A7C15u;
+    for (int64_t it = 0; it < iters; ++it) {
+        h ^= h << 13;
+        h ^= h >> 17;
+        h ^= h << 5;
+        const uint32_t idx = __umulhi(h, n);
+        if constexpr (RB == 16) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(table) + idx);
+            acc += v.x + v.w;
+        } else {
+            acc += __ldg(reinterpret_cast<const float *>(table) + idx);
+        }
+    }
+    if (acc == 1.2345f) sink[t] = acc;
+}
+
+cudaError_t gather_bench(const void *table, int64_t n_records, int record_bytes, int64_t iters, int blocks, int threads,
+                         float *sink, cudaStream_t st)
+{
+    count_launch(1);
+    if (record_bytes == 16) k_gather<16><<<blocks, threads, 0, st>>>(table, (uint32_t)n_records, iters, sink);
+    else k_gather<4><<<blocks, threads, 0, st>>>(table, (uint32_t)n_records, iters, sink);
+    return cudaGetLastError();
+}
+
+}  // namespace gcmc

@@ -1,0 +1,602 @@
+// transport.cu -- photon-packet transport kernels (launch, tau sampling, cell march, interaction,
+// peel-off, limb chord, tally) in two launch forms:
+//   plain      one launch per job, one thread per packet (the straightforward GPU form)
+//   persistent one launch for a whole batch of jobs: resident warps pull (job, packet range) work
+//              items from a device counter; inside an item, lanes whose packets have finished are
+//              refilled together once at least `refill_min` of them are idle (ballot/popc), so the
+//              long launch code runs convergently instead of one lane at a time.
+// Each lane runs a small state machine whose every iteration is ONE cell step of whatever ray the
+// packet currently follows (flight with an optical-depth target, peel-off towards an observer, or
+// a chord), so lanes stay convergent on the same march code while their packets are in different
+// phases.  Kernels are instantiated without the scattering code (SCAT = false) for batches of
+// absorber-only marches (emission peel-offs, limb chords), which halves the live packet state.
+// Tallies and the energy ledger are 64-bit fixed point: per-thread slots in shared memory,
+// warp-reduced and added atomically to the job's accumulators, so sums are order independent.
+#include <climits>
+
+#include "internal.h"
+#include "march.cuh"
+
+namespace gcmc {
+
+template <typename real> struct Packet {
+    Ray<real> ray;
+    int kind, obs, stage, alive;
+    real W, W0;
+    real ix, iy, iz;       // interaction / emission point
+    real fx, fy, fz;       // flight direction before scattering
+    real om, gg, pg;       // cell record at the interaction
+    real bimp;             // chord impact parameter / R_TOA
+    int ci, cj, ck;
+    int steps;
+    int hint;              // launch cell of this lane's previous packet of the same work item (-1: none)
+    uint32_t ev;
+    int64_t n;
+};
+
+// per-job constants kept in registers for a work item
+template <typename real> struct JobC {
+    int max_steps;
+    real tau_cut;
+};
+
+struct LogOut {
+    int64_t packet0;
+    double *pk_f;
+    int64_t *pk_steps;
+    double *pk_tau;
+    int32_t *tr_cell;
+    double *tr_len;
+    int32_t *tr_n;
+    int32_t n_trace, max_trace;
+};
+
+constexpr int NSLOT = ACC_FLAGS + 1;
+
+template <typename real, bool LOG> struct Sink {
+    static constexpr bool is_log = LOG;
+    unsigned long long *sm;   // this thread's first slot; slots are blockDim apart
+    int stride;
+    LogOut lg;
+
+    __device__ __forceinline__ void add(int slot, unsigned long long v) { sm[slot * stride] += v; }
+    __device__ __forceinline__ void flag(unsigned long long v) { sm[ACC_FLAGS * stride] |= v; }
+    __device__ __forceinline__ void tally(int o, real f, int64_t n, int n_obs)
+    {
+        if (!(f < (real)1.0e9) || !(f >= (real)0)) {
+            flag(FLAG_OVERFLOW);
+            return;
+        }
+        add(o, (unsigned long long)to_fix<real>(f));
+        if constexpr (LOG) {
+            if (lg.pk_f) lg.pk_f[(n - lg.packet0) * n_obs + o] += (double)f;
+        }
+    }
+    __device__ __forceinline__ void ledger(int q, real w) { add(ACC_LEDGER + q, (unsigned long long)to_fix<real>(w)); }
+    __device__ __forceinline__ void trace(int64_t n, int cell, real len)
+    {
+        if constexpr (LOG) {
+            const int64_t q = n - lg.packet0;
+            if (lg.tr_cell && q < lg.n_trace) {
+                const int t = lg.tr_n[q];
+                if (t < lg.max_trace) {
+                    lg.tr_cell[q * lg.max_trace + t] = cell;
+                    lg.tr_len[q * lg.max_trace + t] = (double)len;
+                    lg.tr_n[q] = t + 1;
+                }
+            }
+        }
+    }
+};
+
+template <typename real>
+__device__ __forceinline__ void start_ray(Packet<real> &P, real ox, real oy, real oz, real dx, real dy, real dz, int i,
+                                          int j, int k, int kind, real tau_target)
+{
+    ray_setup<real>(P.ray, ox, oy, oz, dx, dy, dz);
+    P.ray.i = i;
+    P.ray.j = j;
+    P.ray.k = k;
+    P.ray.tau = (real)0;
+    P.ray.tau_target = tau_target;
+    P.kind = kind;
+}
+
+template <typename real, class SinkT>
+__device__ __forceinline__ void start_peel(Packet<real> &P, const DevJob &J, SinkT &S)
+{
+    S.trace(P.n, -2, (real)0);
+    start_ray<real>(P, P.ix, P.iy, P.iz, (real)J.obs[P.obs][0], (real)J.obs[P.obs][1], (real)J.obs[P.obs][2], P.ci,
+                    P.cj, P.ck, K_PEEL, (real)-1);
+}
+
+template <typename real, class SinkT>
+__device__ __forceinline__ void start_flight(Packet<real> &P, const DevJob &J, SinkT &S, real dx, real dy, real dz)
+{
+    const uint4 w = draw_words(J.seed, P.n, P.ev, J.key);
+    const real tau = -M<real>::log_(u01<real>(w.x));
+    S.trace(P.n, -1, (real)0);
+    start_ray<real>(P, P.ix, P.iy, P.iz, dx, dy, dz, P.ci, P.cj, P.ck, K_FLIGHT, tau);
+}
+
+template <typename real, class SinkT>
+__device__ __forceinline__ void finish(Packet<real> &P, SinkT &S)
+{
+    S.add(ACC_STEPS, (unsigned long long)P.steps);
+    S.add(ACC_PACKETS, 1ull);
+    if constexpr (SinkT::is_log) {
+        if (S.lg.pk_steps) S.lg.pk_steps[P.n - S.lg.packet0] = P.steps;
+    }
+    P.alive = 0;
+}
+
+// smallest cell index with cdf > target (stratified targets increase along a work item, so the
+// search gallops forward from the lane's previous launch cell; identical result to bisection)
+__device__ __forceinline__ int cdf_find(const long long *__restrict__ cb, int ncell, long long tbits, int hint)
+{
+    int lo = 0, hi = ncell - 1;
+    if (hint >= 0) {
+        if (__ldg(cb + hint) > tbits) return hint;
+        int step = 1, base = hint;
+        for (;;) {
+            const int probe = min(base + step, ncell - 1);
+            if (probe == ncell - 1 || __ldg(cb + probe) > tbits) {
+                lo = base + 1;
+                hi = probe;
+                break;
+            }
+            base = probe;
+            step <<= 1;
+        }
+    }
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(cb + mid) > tbits) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// S2: packet launch (Sect. 5: albedo disk, emission hybrid pdf, transmission annulus)
+template <typename real, bool SCAT, class SinkT>
+__device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64_t n, SinkT &S)
+{
+    P.n = n;
+    P.steps = 0;
+    P.alive = 1;
+    P.ev = 2;
+    if constexpr (SinkT::is_log) {
+        if (S.lg.pk_tau) S.lg.pk_tau[n - S.lg.packet0] = -1.0;
+        if (S.lg.pk_steps) S.lg.pk_steps[n - S.lg.packet0] = 0;
+    }
+    const uint4 w = draw_words(J.seed, n, 0u, J.key);
+    if (J.mode != GCMC_EMISSION) {
+        const real Rt = (real)G.Rtoa, R0 = (real)G.R0;
+        const real u0 = u01<real>(w.x), u1 = u01<real>(w.y);
+        real b, h;
+        if (SCAT && J.mode == GCMC_ALBEDO) b = Rt * M<real>::sqrt_(u0);
+        else b = R0 + u0 * (Rt - R0);
+        if constexpr (sizeof(real) == 8) h = sqrt(fmax(0.0, Rt * Rt - b * b));
+        else h = M<real>::sqrt_(fmaxf(0.0f, (Rt - b) * (Rt + b)));
+        real sp, cp;
+        M<real>::sincos_((real)(2.0 * PI) * u1, &sp, &cp);
+        real x[3], d[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            x[q] = b * (cp * (real)J.e1[q] + sp * (real)J.e2[q]) + h * (real)J.star[q];
+            d[q] = -(real)J.star[q];
+        }
+        int i, j;
+        locate_angles<real>(G, x[0], x[1], x[2], i, j);
+        P.W = P.W0 = (real)1;
+        S.ledger(0, P.W0);
+        P.ix = x[0];
+        P.iy = x[1];
+        P.iz = x[2];
+        P.ci = i;
+        P.cj = j;
+        P.ck = G.nr - 1;
+        if constexpr (SCAT) {
+            if (J.mode == GCMC_ALBEDO) {
+                start_flight<real>(P, J, S, d[0], d[1], d[2]);
+                return;
+            }
+        }
+        P.bimp = b / Rt;
+        S.trace(n, -3, (real)0);
+        start_ray<real>(P, x[0], x[1], x[2], d[0], d[1], d[2], i, j, G.nr - 1, K_CHORD, (real)-1);
+        return;
+    }
+    // emission: stratified inverse-CDF draw of the cell over the hybrid pdf
+    const double target = ((double)n + u01<double>(w.x)) * J.cdf_step;
+    const int idx = cdf_find(reinterpret_cast<const long long *>(J.cdf), (int)G.ncell, __double_as_longlong(target),
+                             P.hint);
+    P.hint = idx;
+    const int i = idx % G.nlon, j = (idx / G.nlon) % G.nlat, k = idx / (G.nlon * G.nlat);
+    const real u1 = u01<real>(w.y), u2 = u01<real>(w.z), u3 = u01<real>(w.w);
+    real r;
+    if constexpr (sizeof(real) == 8) {
+        const double r1 = G.r[k], r2 = G.r[k + 1];
+        r = cbrt(r1 * r1 * r1 + u1 * (r2 * r2 * r2 - r1 * r1 * r1));
+    } else {
+        // r = r1 (1 + u A)^(1/3), A = (r2/r1)^3 - 1, evaluated as r1 + r1 expm1(log1p(u A)/3): one rounding
+        const float r1 = __ldg(G.r_f + k);
+        const float t = expm1f(log1pf(u1 * __ldg(G.shA_f + k)) * (1.0f / 3.0f));
+        r = __fmaf_rn(r1, t, r1);
+    }
+    const real *sl_t = tab_slat<real>(G);
+    const real s1 = sl_t[j], s2 = sl_t[j + 1];
+    const real sl = s1 + u2 * (s2 - s1);
+    const real cl = M<real>::sqrt_(fmax((real)0, (real)1 - sl * sl));
+    const real *lon_t = tab_lon<real>(G);
+    const real ph = lon_t[i] + u3 * (lon_t[i + 1] - lon_t[i]);
+    real sp, cp;
+    M<real>::sincos_(ph, &sp, &cp);
+    P.ix = r * cl * cp;
+    P.iy = r * cl * sp;
+    P.iz = r * sl;
+    P.ci = i;
+    P.cj = j;
+    P.ck = k;
+    P.W = P.W0 = (real)J.wcell[idx];
+    S.ledger(0, P.W0);
+    P.stage = 0;
+    P.obs = 0;
+    start_peel<real>(P, J, S);
+}
+
+template <typename real, class SinkT>
+__device__ void after_peels_scatter(Packet<real> &P, const DevJob &J, SinkT &S)
+{
+    const real om = P.om;
+    if (P.W * om == (real)0) {
+        S.ledger(2, P.W);
+        finish<real>(P, S);
+        return;
+    }
+    if (J.survival) {
+        S.ledger(2, P.W * ((real)1 - om));
+        P.W *= om;
+        if (P.W < (real)J.w_rr * P.W0) {
+            const uint4 v = draw_words(J.seed, P.n, P.ev | 0x80000000u, J.key);
+            if (u01<real>(v.y) < (real)J.p_surv) {
+                const real Wn = P.W / (real)J.p_surv;
+                S.ledger(4, Wn - P.W);
+                P.W = Wn;
+            } else {
+                S.ledger(5, P.W);
+                finish<real>(P, S);
+                return;
+            }
+        }
+    } else {
+        const uint4 v = draw_words(J.seed, P.n, P.ev | 0x80000000u, J.key);
+        if (!(u01<real>(v.x) < om)) {
+            S.ledger(2, P.W);
+            finish<real>(P, S);
+            return;
+        }
+    }
+    const uint4 w = draw_words(J.seed, P.n, P.ev, J.key);
+    const real u1 = u01<real>(w.y), u2 = u01<real>(w.z), u3 = u01<real>(w.w);
+    const real mu = (u1 < P.pg) ? sample_rayleigh<real>(u2) : sample_hg<real>(P.gg, u2, (real)J.hg_eps);
+    real dx = P.fx, dy = P.fy, dz = P.fz;
+    turn<real>(dx, dy, dz, mu, (real)(2.0 * PI) * u3);
+    ++P.ev;
+    start_flight<real>(P, J, S, dx, dy, dz);
+}
+
+template <typename real, bool SCAT, class SinkT>
+__device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int idx)
+{
+    Ray<real> &R = P.ray;
+    if constexpr (SCAT) {
+        if (P.kind == K_FLIGHT) {
+            if (e != E_INTERACT) {
+                S.ledger(e == E_ESCAPE ? 1 : e == E_BOTTOM ? 3 : e == E_CAP ? 6 : 7, P.W);
+                finish<real>(P, S);
+                return;
+            }
+            P.fx = R.dx;
+            P.fy = R.dy;
+            P.fz = R.dz;
+            P.ix = R.cx + R.s * R.dx;
+            P.iy = R.cy + R.s * R.dy;
+            P.iz = R.cz + R.s * R.dz;
+            P.ci = R.i;
+            P.cj = R.j;
+            P.ck = R.k;
+            if constexpr (sizeof(real) == 4) {
+                const float4 rc = __ldg(reinterpret_cast<const float4 *>(J.rec) + idx);
+                P.om = rc.y;
+                P.gg = rc.z;
+                P.pg = rc.w;
+            } else {
+                const Rec64 rc = reinterpret_cast<const Rec64 *>(J.rec)[idx];
+                P.om = rc.w;
+                P.gg = rc.g;
+                P.pg = rc.pg;
+            }
+            P.stage = 1;
+            P.obs = 0;
+            start_peel<real>(P, J, S);
+            return;
+        }
+    }
+    if (P.kind == K_PEEL) {
+        if (e == E_CAP) {
+            S.ledger(6, P.W);
+            finish<real>(P, S);
+            return;
+        }
+        const real ex = (e == E_ESCAPE) ? M<real>::exp_(-R.tau) : (real)0;
+        real f;
+        if (!SCAT || P.stage == 0) {
+            if constexpr (SinkT::is_log) {
+                if (P.obs == 0 && S.lg.pk_tau) S.lg.pk_tau[P.n - S.lg.packet0] = (double)R.tau;
+            }
+            f = P.W * ex * (real)(1.0 / (4.0 * PI));
+        } else {
+            const real mu = P.fx * (real)J.obs[P.obs][0] + P.fy * (real)J.obs[P.obs][1] + P.fz * (real)J.obs[P.obs][2];
+            f = P.W * P.om * theta_mix<real>(mu, P.pg, P.gg) * ex;
+        }
+        S.tally(P.obs, f, P.n, J.n_obs);
+        ++P.obs;
+        if (P.obs < J.n_obs) {
+            start_peel<real>(P, J, S);
+            return;
+        }
+        if constexpr (SCAT) {
+            if (J.mode == GCMC_ALBEDO) {
+                after_peels_scatter<real>(P, J, S);
+                return;
+            }
+        }
+        finish<real>(P, S);
+        return;
+    }
+    // chord
+    real c;
+    if (e == E_ESCAPE) c = ((real)1 - M<real>::exp_(-R.tau)) * P.bimp;
+    else if (e == E_CUTOFF || e == E_BOTTOM) c = P.bimp;
+    else {
+        c = (real)0;
+        S.ledger(e == E_CAP ? 6 : 7, P.W);
+    }
+    if constexpr (SinkT::is_log) {
+        if (S.lg.pk_tau) S.lg.pk_tau[P.n - S.lg.packet0] = (double)R.tau;
+    }
+    S.tally(0, c, P.n, J.n_obs);
+    S.ledger(1, P.W);
+    finish<real>(P, S);
+}
+
+// one cell step (S3-S7) of the packet's current ray
+template <typename real, bool SCAT, class SinkT>
+__device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const DevGrid &G, const JobC<real> &jc, SinkT &S)
+{
+    Ray<real> &R = P.ray;
+    if (P.steps >= jc.max_steps) {
+        if (SCAT && P.kind == K_FLIGHT) {
+            S.ledger(6, P.W);
+            finish<real>(P, S);
+        } else {
+            on_end<real, SCAT>(P, J, S, E_CAP, 0);
+        }
+        return;
+    }
+    ++P.steps;
+    const int idx = (R.k * G.nlat + R.j) * G.nlon + R.i;
+    real a;
+    if (SCAT && J.mode == GCMC_ALBEDO) a = __ldg(reinterpret_cast<const real *>(J.rec) + 4 * idx);
+    else a = __ldg(reinterpret_cast<const real *>(J.rec) + idx);
+    int face = F_NONE;
+    const real sx = cell_exit<real>(G, R, face);
+    const real seg = sx - R.s;
+    if constexpr (SCAT) {
+        if (R.tau_target >= (real)0 && a > (real)0 && R.tau + a * seg >= R.tau_target) {
+            const real l = M<real>::div_(R.tau_target - R.tau, a);
+            S.trace(P.n, idx, l);
+            R.s += l;
+            R.tau = R.tau_target;
+            on_end<real, SCAT>(P, J, S, E_INTERACT, idx);
+            return;
+        }
+    }
+    R.tau += a * seg;
+    S.trace(P.n, idx, seg);
+    R.s = sx;
+    int e = cross_face(G, face, R.i, R.j, R.k);
+    if (e == E_CONT && R.tau_target < (real)0 && R.tau > jc.tau_cut) e = E_CUTOFF;
+    if (e != E_CONT) on_end<real, SCAT>(P, J, S, e, idx);
+}
+
+// warp-reduce the per-thread accumulators and add them to the job's totals
+__device__ __forceinline__ void flush(unsigned long long *sm, int stride, unsigned long long *acc)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll 1
+    for (int s = 0; s < NSLOT; ++s) {
+        unsigned long long v = sm[s * stride];
+        sm[s * stride] = 0ull;
+        if (s == ACC_FLAGS) {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && v) atomicOr(acc + s, v);
+        } else {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && v) atomicAdd(acc + s, v);
+        }
+    }
+}
+
+template <typename real> __device__ __forceinline__ JobC<real> job_consts(const DevJob &J)
+{
+    JobC<real> c;
+    c.max_steps = (int)min(J.max_steps, (int64_t)INT_MAX);
+    c.tau_cut = (real)J.tau_cut;
+    return c;
+}
+
+template <typename real, bool SCAT, bool LOG>
+__global__ void __launch_bounds__(256) k_transport_plain(const DevGrid *__restrict__ grids,
+                                                         const DevJob *__restrict__ jobp, int64_t packet0, int64_t n_run,
+                                                         LogOut lg)
+{
+    extern __shared__ unsigned long long sacc[];
+    Sink<real, LOG> S;
+    S.sm = sacc + threadIdx.x;
+    S.stride = blockDim.x;
+    S.lg = lg;
+    for (int s = 0; s < NSLOT; ++s) S.sm[s * S.stride] = 0ull;
+    const DevJob &J = *jobp;
+    const DevGrid &G = grids[J.grid_slot];
+    const JobC<real> jc = job_consts<real>(J);
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n_run) {
+        Packet<real> P;
+        P.hint = -1;
+        launch<real, SCAT>(P, J, G, packet0 + q, S);
+        while (P.alive) step<real, SCAT>(P, J, G, jc, S);
+    }
+    __syncwarp();
+    flush(S.sm, S.stride, J.acc);
+}
+
+template <typename real, bool SCAT>
+__global__ void __launch_bounds__(256) k_transport_persistent(const DevGrid *__restrict__ grids,
+                                                              const DevJob *__restrict__ jobs, int n_jobs,
+                                                              int64_t total_items, int chunk, int interval,
+                                                              int refill_min, unsigned long long *work)
+{
+    extern __shared__ unsigned long long sacc[];
+    Sink<real, false> S;
+    S.sm = sacc + threadIdx.x;
+    S.stride = blockDim.x;
+    for (int s = 0; s < NSLOT; ++s) S.sm[s * S.stride] = 0ull;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(work, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if ((int64_t)item >= total_items) break;
+        // job of this item: last job whose first item is <= item
+        int lo = 0, hi = n_jobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].chunk_begin <= (int64_t)item) lo = mid; else hi = mid - 1;
+        }
+        const DevJob &J = jobs[lo];
+        const DevGrid &G = grids[J.grid_slot];
+        const JobC<real> jc = job_consts<real>(J);
+        const int64_t p0 = ((int64_t)item - J.chunk_begin) * chunk;
+        const int64_t p1 = min(p0 + (int64_t)chunk, J.n_packets);
+        int64_t pool = p0;
+        Packet<real> P;
+        P.alive = 0;
+        P.hint = -1;
+        for (;;) {
+            const unsigned idle = __ballot_sync(0xffffffffu, !P.alive);
+            const int n_idle = __popc(idle);
+            const int64_t left = p1 - pool;
+            if (n_idle && left > 0 && (int64_t)n_idle >= min((int64_t)refill_min, left)) {
+                const int64_t mine = pool + __popc(idle & lt);
+                if (!P.alive && mine < p1) launch<real, SCAT>(P, J, G, mine, S);
+                pool += n_idle;
+            }
+            if (!__any_sync(0xffffffffu, P.alive)) break;
+            for (int t = 0; t < interval; ++t)
+                if (P.alive) step<real, SCAT>(P, J, G, jc, S);
+        }
+        __syncwarp();
+        flush(S.sm, S.stride, J.acc);
+    }
+}
+
+// ------------------------------------------------------------------ host launchers
+size_t transport_smem(int block) { return (size_t)NSLOT * block * sizeof(unsigned long long); }
+
+template <typename real, bool SCAT>
+static void plain_dispatch(unsigned nb, int block, size_t sm, cudaStream_t st, const DevGrid *grids, const DevJob *job,
+                           int64_t packet0, int64_t n_run, const LogOut &lg, bool log)
+{
+    if (log) k_transport_plain<real, SCAT, true><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
+    else k_transport_plain<real, SCAT, false><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
+}
+
+cudaError_t launch_plain(int precision, bool scatter, const DevGrid *grids, const DevJob *job, int64_t packet0,
+                         int64_t n_run, const HostLog *hl, cudaStream_t st)
+{
+    const int block = 128;
+    const int64_t nb = (n_run + block - 1) / block;
+    if (nb == 0) return cudaSuccess;
+    LogOut lg{};
+    if (hl) {
+        lg.packet0 = packet0;
+        lg.pk_f = hl->pk_f;
+        lg.pk_steps = hl->pk_steps;
+        lg.pk_tau = hl->pk_tau;
+        lg.tr_cell = hl->tr_cell;
+        lg.tr_len = hl->tr_len;
+        lg.tr_n = hl->tr_n;
+        lg.n_trace = hl->n_trace;
+        lg.max_trace = hl->max_trace;
+    }
+    const size_t sm = transport_smem(block);
+    count_launch(1);
+    const unsigned g = (unsigned)nb;
+    if (precision == GCMC_FP64) {
+        if (scatter) plain_dispatch<double, true>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr);
+        else plain_dispatch<double, false>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr);
+    } else {
+        if (scatter) plain_dispatch<float, true>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr);
+        else plain_dispatch<float, false>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr);
+    }
+    return cudaGetLastError();
+}
+
+template <typename real, bool SCAT>
+static cudaError_t persistent_dispatch(int block, int blocks_per_sm, int nsm, const DevGrid *grids, const DevJob *jobs,
+                                       int n_jobs, int64_t total_items, int chunk, int interval, int refill_min,
+                                       unsigned long long *work, cudaStream_t st)
+{
+    const size_t sm = transport_smem(block);
+    if (blocks_per_sm <= 0) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_persistent<real, SCAT>, block, sm);
+        blocks_per_sm = occ > 0 ? occ : 1;
+    }
+    const unsigned grid = (unsigned)(nsm * blocks_per_sm);
+    k_transport_persistent<real, SCAT><<<grid, block, sm, st>>>(grids, jobs, n_jobs, total_items, chunk, interval,
+                                                                refill_min, work);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_persistent(int precision, bool scatter, const DevGrid *grids, const DevJob *jobs, int n_jobs,
+                              int64_t total_items, int chunk, int block, int blocks_per_sm, int interval, int refill_min,
+                              unsigned long long *work, cudaStream_t st)
+{
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (block <= 0) block = 128;
+    if (block > 256 || block % 32) return cudaErrorInvalidValue;
+    if (interval < 1) interval = 1;
+    refill_min = refill_min < 1 ? 1 : refill_min > 32 ? 32 : refill_min;
+    count_launch(1);
+    if (precision == GCMC_FP64) {
+        if (scatter)
+            return persistent_dispatch<double, true>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+                                                     interval, refill_min, work, st);
+        return persistent_dispatch<double, false>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+                                                  interval, refill_min, work, st);
+    }
+    if (scatter)
+        return persistent_dispatch<float, true>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+                                                interval, refill_min, work, st);
+    return persistent_dispatch<float, false>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+                                             interval, refill_min, work, st);
+}
+
+}  // namespace gcmc

@@ -1,0 +1,48 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads without a GPU and exports every
+function include/gcmc.h declares; the binding's structs match the header's field order."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "gcmc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gcmc_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2110_15640_gb300 import build
+    return build.build()
+
+
+def test_library_exports_every_declared_function(built):
+    names = header_functions()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (gcmc_[a-z_0-9]+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_without_gpu(built):
+    from paper_2110_15640_gb300 import gcmc
+    L = gcmc.lib()
+    assert L.gcmc_version().startswith(b"gcmc")
+    assert set(gcmc.EXPORTED) == set(header_functions())
+
+
+def test_struct_layouts_match_header():
+    from paper_2110_15640_gb300 import gcmc
+    import ctypes as C
+    # sizes computed from the header's field lists (LP64)
+    assert C.sizeof(gcmc.gcmc_grid_desc) == 16 + 7 * 8
+    assert C.sizeof(gcmc.gcmc_job) == 8 * 4 + 16
+    assert C.sizeof(gcmc.gcmc_launch_cfg) == 24
+    assert C.sizeof(gcmc.gcmc_stats) == 16 + 64 + 16 + 8
+    assert C.sizeof(gcmc.gcmc_source_desc) == 24 + 8 + 8 * 3 * 8 + 6 * 8 + 8 + 8
