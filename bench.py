@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--interval", type=int, default=0)
+    ap.add_argument("--refill", type=int, default=0)
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
     return ap.parse_args()
 
 
@@ -178,10 +180,16 @@ def main():
     wl = workload(args, rank)
     stream = torch.cuda.Stream()
     ctx = gcmc.Context(local, stream=stream)
-    cfg = gcmc.gcmc_launch_cfg(args.block, 0, args.chunk, args.interval)
+    from paper_2110_15640_gb300 import autotune
     with torch.cuda.stream(stream):
         gid, oid, sid, jobs = gcmc.load_workload(ctx, wl, gcmc.FP32, device_inputs=True)
         tall = torch.zeros((len(jobs), gcmc.MAX_OBS), dtype=torch.float64, device="cuda")
+        if args.no_tune or args.block or args.chunk or args.interval or args.refill:
+            cfg = gcmc.gcmc_launch_cfg(args.block, 0, args.chunk, args.interval, args.refill, 0)
+            tuned = {"block": args.block or 128, "chunk": args.chunk or 1024, "interval": args.interval or 1,
+                     "refill_min": args.refill or 16}
+        else:   # untimed search on 16 of the jobs (tallies do not depend on the launch parameters)
+            cfg, tuned, _ = autotune.tune(ctx, jobs[:16], stream, reps=1)
         _, sts = ctx.run_batch(jobs, cfg=cfg)                       # untimed: exact packet-step count
     steps_per_step = int(sum(s.steps for s in sts))
     packets_per_step = int(sum(s.packets for s in sts))
@@ -261,9 +269,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = os.cpu_count() or 1
-        rate, dt, _ = cpu_oracle_rate(wl, 4, min(args.packets, 1_000_000), cores)
+        rate, dt, _ = cpu_oracle_rate(wl, 48, min(args.packets, 1_000_000), cores)
         cpu = {"value": rate, "unit": "packet-steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"4 of {len(jobs)} (band, g) jobs x {min(args.packets, 1_000_000)} packets, S1 + transport, "
+               "sample": f"48 of {len(jobs)} (band, g) jobs x {min(args.packets, 1_000_000)} packets, S1 + transport, "
                          f"{dt:.1f} s"}
     if rank == 0:
         line = {
@@ -276,8 +284,7 @@ def main():
                        "packets_per_step": packets_per_step, "capped_weight": capped,
                        "l2": "inputs larger than L2 (per-step cell tables ~2 GB)",
                        "precision": "FP32 march, FP64 emission pdf, 64-bit fixed-point tallies",
-                       "launch": {"block": args.block or 128, "chunk": args.chunk or 1024,
-                                  "interval": args.interval or 1}},
+                       "launch": tuned},
             "plain_form": {"value": plain_value, "unit": "packet-steps/s", "ms_per_step": 1e3 * t_plain / args.plain_steps,
                            "launches_per_step": len(jobs)},
             "batched_over_plain": value / plain_value,

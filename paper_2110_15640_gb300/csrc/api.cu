@@ -612,7 +612,7 @@ gcmc_status gcmc_upload_grid(gcmc_ctx *ctx, const gcmc_grid_desc *d, int *grid_i
     std::vector<double> r2(nr + 1), slat(nlat + 1), s2lat(nlat + 1), clon(nlon + 1), slon(nlon + 1);
     std::vector<float> r_f(nr + 1), r2hi(nr + 1), r2lo(nr + 1), lat_f(nlat + 1), slat_f(nlat + 1), s2lat_f(nlat + 1),
         lon_f(nlon + 1), clon_f(nlon + 1), slon_f(nlon + 1);
-    std::vector<float> shA(nr);
+    std::vector<float> shA(nr), r_lo(nr + 1), slat_lo(nlat + 1), lon_lo(nlon + 1), dslat(nlat), dlon(nlon);
     for (int k = 0; k < nr; ++k) {
         const double q = G.r[k + 1] / G.r[k];
         shA[k] = (float)(q * q * q - 1.0);
@@ -637,6 +637,11 @@ gcmc_status gcmc_upload_grid(gcmc_ctx *ctx, const gcmc_grid_desc *d, int *grid_i
         clon_f[i] = (float)clon[i];
         slon_f[i] = (float)slon[i];
     }
+    for (int k = 0; k <= nr; ++k) r_lo[k] = (float)(G.r[k] - (double)r_f[k]);
+    for (int j = 0; j <= nlat; ++j) slat_lo[j] = (float)(slat[j] - (double)slat_f[j]);
+    for (int i = 0; i <= nlon; ++i) lon_lo[i] = (float)(G.lon[i] - (double)lon_f[i]);
+    for (int j = 0; j < nlat; ++j) dslat[j] = (float)(slat[j + 1] - slat[j]);
+    for (int i = 0; i < nlon; ++i) dlon[i] = (float)(G.lon[i + 1] - G.lon[i]);
     std::vector<double> vol(ncell);
     for (int64_t idx = 0; idx < ncell; ++idx) {
         const int64_t i = idx % nlon, j = (idx / nlon) % nlat, k = idx / ((int64_t)nlon * nlat);
@@ -672,6 +677,11 @@ gcmc_status gcmc_upload_grid(gcmc_ctx *ctx, const gcmc_grid_desc *d, int *grid_i
     g.clon_f = dput(ctx, G.owned, clon_f.data(), nlon + 1, e);
     g.slon_f = dput(ctx, G.owned, slon_f.data(), nlon + 1, e);
     g.shA_f = dput(ctx, G.owned, shA.data(), nr, e);
+    g.r_lo_f = dput(ctx, G.owned, r_lo.data(), nr + 1, e);
+    g.slat_lo_f = dput(ctx, G.owned, slat_lo.data(), nlat + 1, e);
+    g.lon_lo_f = dput(ctx, G.owned, lon_lo.data(), nlon + 1, e);
+    g.dslat_f = dput(ctx, G.owned, dslat.data(), nlat, e);
+    g.dlon_f = dput(ctx, G.owned, dlon.data(), nlon, e);
     g.T = dput(ctx, G.owned, d->T, ncell, e);
     g.p = dput(ctx, G.owned, d->p, ncell, e);
     g.rho = dput(ctx, G.owned, d->rho, ncell, e);

@@ -42,6 +42,9 @@ struct DevGrid {
     const double *r, *r2, *lat, *slat, *s2lat, *lon, *clon, *slon;     // FP64 edge tables
     const float *r_f, *r2hi_f, *r2lo_f, *lat_f, *slat_f, *s2lat_f, *lon_f, *clon_f, *slon_f;
     const float *shA_f;                                                 // [nr] (r_{k+1}/r_k)^3 - 1
+    // low parts of the FP32 edges (edge = hi + lo to ~48 bits) and FP32 cell widths, so that
+    // positions sampled inside a cell carry no edge rounding that repeats for every packet
+    const float *r_lo_f, *slat_lo_f, *lon_lo_f, *dslat_f, *dlon_f;
     const float *T, *p, *rho, *wind;                                    // per cell
     const double *vol;                                                  // per cell
 };

@@ -213,22 +213,24 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
     P.hint = idx;
     const int i = idx % G.nlon, j = (idx / G.nlon) % G.nlat, k = idx / (G.nlon * G.nlat);
     const real u1 = u01<real>(w.y), u2 = u01<real>(w.z), u3 = u01<real>(w.w);
-    real r;
+    real r, sl, ph;
     if constexpr (sizeof(real) == 8) {
         const double r1 = G.r[k], r2 = G.r[k + 1];
         r = cbrt(r1 * r1 * r1 + u1 * (r2 * r2 * r2 - r1 * r1 * r1));
+        const double s1 = G.slat[j], s2 = G.slat[j + 1];
+        sl = s1 + u2 * (s2 - s1);
+        ph = G.lon[i] + u3 * (G.lon[i + 1] - G.lon[i]);
     } else {
-        // r = r1 (1 + u A)^(1/3), A = (r2/r1)^3 - 1, evaluated as r1 + r1 expm1(log1p(u A)/3): one rounding
+        // r = r1 (1 + u A)^(1/3), A = (r2/r1)^3 - 1, as r1 + (r1_lo + r1 expm1(log1p(u A)/3)); sin(lat) and
+        // lon likewise from hi + lo edges: each coordinate is rounded once, so no edge rounding is
+        // shared by all packets of a cell
         const float r1 = __ldg(G.r_f + k);
         const float t = expm1f(log1pf(u1 * __ldg(G.shA_f + k)) * (1.0f / 3.0f));
-        r = __fmaf_rn(r1, t, r1);
+        r = r1 + __fmaf_rn(r1, t, __ldg(G.r_lo_f + k));
+        sl = __ldg(G.slat_f + j) + __fmaf_rn(u2, __ldg(G.dslat_f + j), __ldg(G.slat_lo_f + j));
+        ph = __ldg(G.lon_f + i) + __fmaf_rn(u3, __ldg(G.dlon_f + i), __ldg(G.lon_lo_f + i));
     }
-    const real *sl_t = tab_slat<real>(G);
-    const real s1 = sl_t[j], s2 = sl_t[j + 1];
-    const real sl = s1 + u2 * (s2 - s1);
     const real cl = M<real>::sqrt_(fmax((real)0, (real)1 - sl * sl));
-    const real *lon_t = tab_lon<real>(G);
-    const real ph = lon_t[i] + u3 * (lon_t[i + 1] - lon_t[i]);
     real sp, cp;
     M<real>::sincos_(ph, &sp, &cp);
     P.ix = r * cl * cp;
