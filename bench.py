@@ -59,7 +59,8 @@ def workload(args, rank):
     from paper_2110_15640_gb300 import synth
     wl = synth.config2_emission(n_packets=args.packets, nb=30, ng=8, bands=range(args.bands),
                                 gpoints=range(args.gpoints))
-    wl.seed = 2 + 7919 * rank          # distinct packets per rank (weak scaling)
+    from paper_2110_15640_gb300 import shard
+    wl.seed = shard.rank_seed(2, rank)   # distinct packets per rank (weak scaling)
     return wl
 
 

@@ -15,9 +15,10 @@ from . import gcmc
 
 DEFAULT_SPACE = {
     "block": [64, 128, 256],
-    "chunk": [512, 1024, 2048],
+    "blocks_per_sm": [0, 6, 8],
+    "chunk": [256, 512, 1024, 2048],
     "refill_min": [8, 16, 24, 32],
-    "interval": [1, 2],
+    "interval": [1, 2, 4],
 }
 
 
@@ -39,11 +40,11 @@ def tune(ctx, jobs, stream, space=None, reps=2, coordinate=True, log=None):
     """Return (best gcmc_launch_cfg, table of (cfg dict, ms)).  coordinate=True searches one axis at a
     time from the defaults (about a dozen runs) instead of the full product."""
     space = space or DEFAULT_SPACE
-    best = {"block": 128, "chunk": 1024, "refill_min": 16, "interval": 1}
+    best = {"block": 128, "blocks_per_sm": 0, "chunk": 512, "refill_min": 32, "interval": 2}
     table = []
 
     def run(c):
-        cfg = gcmc.gcmc_launch_cfg(c["block"], 0, c["chunk"], c["interval"], c["refill_min"], 0)
+        cfg = gcmc.gcmc_launch_cfg(c["block"], c["blocks_per_sm"], c["chunk"], c["interval"], c["refill_min"], 0)
         ms = _time_cfg(ctx, jobs, cfg, reps, stream)
         table.append((dict(c), ms))
         if log:
@@ -69,7 +70,7 @@ def tune(ctx, jobs, stream, space=None, reps=2, coordinate=True, log=None):
             ms = run(c)
             if ms < best_ms:
                 best, best_ms = c, ms
-    cfg = gcmc.gcmc_launch_cfg(best["block"], 0, best["chunk"], best["interval"], best["refill_min"], 0)
+    cfg = gcmc.gcmc_launch_cfg(best["block"], best["blocks_per_sm"], best["chunk"], best["interval"], best["refill_min"], 0)
     return cfg, best, table
 
 
@@ -83,4 +84,4 @@ def load(path):
         return None
     with open(path) as f:
         b = json.load(f)["best"]
-    return gcmc.gcmc_launch_cfg(b["block"], 0, b["chunk"], b["interval"], b["refill_min"], 0), b
+    return gcmc.gcmc_launch_cfg(b["block"], b.get("blocks_per_sm", 0), b["chunk"], b["interval"], b["refill_min"], 0), b

@@ -167,6 +167,8 @@ struct Plan {
     size_t off_jobs = 0, off_prep = 0, off_acc = 0, off_work = 0, off_gather = 0, ws_bytes = 0;
     int64_t total_items = 0;
     bool scatter = false;               // some job follows scattered packets (albedo)
+    int one_grid = 1;                   // every job uses the same grid
+    int tab_n = 0;                      // largest march-table size (pair entries) of the jobs' grids
 };
 
 gcmc_status check_job(gcmc_ctx *ctx, const gcmc_job &j)
@@ -328,6 +330,11 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
         items += (j.n_packets + chunk - 1) / chunk;
     }
     P.total_items = items;
+    for (int q = 0; q < n; ++q) {
+        const DevGrid &g = ctx->grids[jobs[q].grid_id].dg;
+        P.tab_n = std::max(P.tab_n, tab_entries(g.nlon, g.nlat, g.nr));
+        if (jobs[q].grid_id != jobs[0].grid_id) P.one_grid = 0;
+    }
     return GCMC_OK;
 }
 
@@ -589,6 +596,11 @@ gcmc_status gcmc_upload_grid(gcmc_ctx *ctx, const gcmc_grid_desc *d, int *grid_i
     if ((int)ctx->grids.size() >= ctx->grid_cap) return fail(ctx, GCMC_ERR_RANGE, "too many grids in one context");
     const int64_t ncell = (int64_t)d->nlon * d->nlat * d->nr;
     if (ncell > ((int64_t)1 << 31) - 1) return fail(ctx, GCMC_ERR_RANGE, "more than 2^31 - 1 cells");
+    // cell indices are divided by nlon and nlon * nlat with 40-bit multipliers: exact while
+    // ncell * nlon * nlat < 2^40; the march tables (nr + nlat + nlon + 3 pairs) live in shared memory
+    if ((double)ncell * (double)d->nlon * (double)d->nlat >= 1099511627776.0 ||
+        tab_entries(d->nlon, d->nlat, d->nr) > 4096)
+        return fail(ctx, GCMC_ERR_RANGE, "grid too large for this build (ncell * nlon * nlat < 2^40, nr + nlat + nlon < 4093)");
     if (!d->T || !d->p || !d->rho) return fail(ctx, GCMC_ERR_ARG, "T, p and rho are required");
     GridH G;
     if (!fetch(ctx, d->r_edges, d->nr + 1, d->memory, G.r) || !fetch(ctx, d->lat_edges, d->nlat + 1, d->memory, G.lat) ||
@@ -642,6 +654,20 @@ gcmc_status gcmc_upload_grid(gcmc_ctx *ctx, const gcmc_grid_desc *d, int *grid_i
     for (int i = 0; i <= nlon; ++i) lon_lo[i] = (float)(G.lon[i] - (double)lon_f[i]);
     for (int j = 0; j < nlat; ++j) dslat[j] = (float)(slat[j + 1] - slat[j]);
     for (int i = 0; i < nlon; ++i) dlon[i] = (float)(G.lon[i + 1] - G.lon[i]);
+    std::vector<float2> r2p_f(nr + 1), slp_f(nlat + 1), csp_f(nlon + 1);
+    std::vector<double2> r2p(nr + 1), slp(nlat + 1), csp(nlon + 1);
+    for (int k = 0; k <= nr; ++k) {
+        r2p_f[k] = make_float2(r2hi[k], r2lo[k]);
+        r2p[k] = make_double2(r2[k], 0.0);
+    }
+    for (int j = 0; j <= nlat; ++j) {
+        slp_f[j] = make_float2(slat_f[j], s2lat_f[j]);
+        slp[j] = make_double2(slat[j], s2lat[j]);
+    }
+    for (int i = 0; i <= nlon; ++i) {
+        csp_f[i] = make_float2(clon_f[i], slon_f[i]);
+        csp[i] = make_double2(clon[i], slon[i]);
+    }
     std::vector<double> vol(ncell);
     for (int64_t idx = 0; idx < ncell; ++idx) {
         const int64_t i = idx % nlon, j = (idx / nlon) % nlat, k = idx / ((int64_t)nlon * nlat);
@@ -682,6 +708,14 @@ gcmc_status gcmc_upload_grid(gcmc_ctx *ctx, const gcmc_grid_desc *d, int *grid_i
     g.lon_lo_f = dput(ctx, G.owned, lon_lo.data(), nlon + 1, e);
     g.dslat_f = dput(ctx, G.owned, dslat.data(), nlat, e);
     g.dlon_f = dput(ctx, G.owned, dlon.data(), nlon, e);
+    g.r2p_f = dput(ctx, G.owned, r2p_f.data(), nr + 1, e);
+    g.slp_f = dput(ctx, G.owned, slp_f.data(), nlat + 1, e);
+    g.csp_f = dput(ctx, G.owned, csp_f.data(), nlon + 1, e);
+    g.r2p = dput(ctx, G.owned, r2p.data(), nr + 1, e);
+    g.slp = dput(ctx, G.owned, slp.data(), nlat + 1, e);
+    g.csp = dput(ctx, G.owned, csp.data(), nlon + 1, e);
+    g.mag_lon = (((uint64_t)1 << 40) + (uint64_t)nlon - 1) / (uint64_t)nlon;
+    g.mag_ll = (((uint64_t)1 << 40) + (uint64_t)nlon * nlat - 1) / ((uint64_t)nlon * nlat);
     g.T = dput(ctx, G.owned, d->T, ncell, e);
     g.p = dput(ctx, G.owned, d->p, ncell, e);
     g.rho = dput(ctx, G.owned, d->rho, ncell, e);
@@ -844,7 +878,8 @@ gcmc_status gcmc_run_packets(gcmc_ctx *ctx, const gcmc_job *job, double *tallies
     if ((s = stage(ctx, P, base))) return s;
     prof_mark(ctx);
     const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
-    cudaError_t e = launch_plain(P.jobs[0].precision, P.scatter, ctx->d_grids, dj, 0, job->n_packets, nullptr, ctx->stream);
+    cudaError_t e = launch_plain(P.jobs[0].precision, P.scatter, ctx->d_grids, dj, 0, job->n_packets, nullptr, P.tab_n,
+                                 ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "transport launch");
     prof_mark(ctx);
     return finish_run(ctx, P, base, tallies_out, tallies_memory, stats_out, 0);
@@ -870,7 +905,7 @@ gcmc_status gcmc_run_batch(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, cons
     const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
     cudaError_t e = launch_persistent(prec, P.scatter, ctx->d_grids, dj, n_jobs, P.total_items, chunk, cfg ? cfg->block : 0,
                                       cfg ? cfg->blocks_per_sm : 0, cfg && cfg->interval > 0 ? cfg->interval : 1,
-                                      cfg && cfg->refill_min > 0 ? cfg->refill_min : 16,
+                                      cfg && cfg->refill_min > 0 ? cfg->refill_min : 16, P.one_grid, P.tab_n,
                                       reinterpret_cast<unsigned long long *>(base + P.off_work), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "transport launch");
     prof_mark(ctx);
@@ -900,7 +935,7 @@ gcmc_status gcmc_submit(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, const g
     const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
     cudaError_t e = launch_persistent(prec, P.scatter, ctx->d_grids, dj, n_jobs, P.total_items, chunk, cfg ? cfg->block : 0,
                                       cfg ? cfg->blocks_per_sm : 0, cfg && cfg->interval > 0 ? cfg->interval : 1,
-                                      cfg && cfg->refill_min > 0 ? cfg->refill_min : 16,
+                                      cfg && cfg->refill_min > 0 ? cfg->refill_min : 16, P.one_grid, P.tab_n,
                                       reinterpret_cast<unsigned long long *>(base + P.off_work), ctx->stream);
     if (e != cudaSuccess) {
         dfree(ctx, T.ws);
@@ -980,7 +1015,7 @@ gcmc_status gcmc_run_packets_debug(gcmc_ctx *ctx, const gcmc_job *job, int64_t p
     }
     if (e == cudaSuccess) {
         const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
-        e = launch_plain(P.jobs[0].precision, P.scatter, ctx->d_grids, dj, packet0, n_run, &hl, ctx->stream);
+        e = launch_plain(P.jobs[0].precision, P.scatter, ctx->d_grids, dj, packet0, n_run, &hl, P.tab_n, ctx->stream);
     }
     if (e == cudaSuccess) {
         if (pk_f) e = cudaMemcpyAsync(pk_f, hl.pk_f, (size_t)n_run * nobs * 8, cudaMemcpyDeviceToHost, ctx->stream);

@@ -45,6 +45,11 @@ struct DevGrid {
     // low parts of the FP32 edges (edge = hi + lo to ~48 bits) and FP32 cell widths, so that
     // positions sampled inside a cell carry no edge rounding that repeats for every packet
     const float *r_lo_f, *slat_lo_f, *lon_lo_f, *dslat_f, *dlon_f;
+    // the march's edge tables as pairs (one 8/16-byte load each), staged in shared memory by the kernels:
+    // r2p = (r^2 hi, r^2 lo) [nr+1], slp = (sin lat, sin^2 lat) [nlat+1], csp = (cos lon, sin lon) [nlon+1]
+    const float2 *r2p_f, *slp_f, *csp_f;
+    const double2 *r2p, *slp, *csp;
+    uint64_t mag_lon, mag_ll;   // ceil(2^40 / nlon), ceil(2^40 / (nlon nlat)): exact division of cell indices
     const float *T, *p, *rho, *wind;                                    // per cell
     const double *vol;                                                  // per cell
 };
@@ -163,6 +168,48 @@ template <> __device__ __forceinline__ void r2_pair<double>(const DevGrid &g, in
 {
     hi = __ldg(g.r2 + k);
     lo = 0.0;
+}
+
+template <typename real> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+
+template <typename real> __device__ __forceinline__ const typename Pair<real>::type *pair_r2(const DevGrid &g);
+template <> __device__ __forceinline__ const float2 *pair_r2<float>(const DevGrid &g) { return g.r2p_f; }
+template <> __device__ __forceinline__ const double2 *pair_r2<double>(const DevGrid &g) { return g.r2p; }
+template <typename real> __device__ __forceinline__ const typename Pair<real>::type *pair_sl(const DevGrid &g);
+template <> __device__ __forceinline__ const float2 *pair_sl<float>(const DevGrid &g) { return g.slp_f; }
+template <> __device__ __forceinline__ const double2 *pair_sl<double>(const DevGrid &g) { return g.slp; }
+template <typename real> __device__ __forceinline__ const typename Pair<real>::type *pair_cs(const DevGrid &g);
+template <> __device__ __forceinline__ const float2 *pair_cs<float>(const DevGrid &g) { return g.csp_f; }
+template <> __device__ __forceinline__ const double2 *pair_cs<double>(const DevGrid &g) { return g.csp; }
+
+// the march's view of a grid: sizes and edge tables (in shared memory inside the kernels)
+template <typename real> struct Tabs {
+    const typename Pair<real>::type *r2, *sl, *cs;
+    int nlon, nlat, nr;
+};
+
+// number of pair entries the march tables of a grid take
+__host__ __device__ inline int tab_entries(int nlon, int nlat, int nr) { return (nr + 1) + (nlat + 1) + (nlon + 1); }
+
+// copy a grid's march tables into `dst` (lanes lane0 .. lane0 + nthreads - 1 cooperate)
+template <typename real>
+__device__ __forceinline__ Tabs<real> stage_tabs(const DevGrid &G, typename Pair<real>::type *dst, int t, int nthreads)
+{
+    using P = typename Pair<real>::type;
+    const int a = G.nr + 1, b = G.nlat + 1, c = G.nlon + 1;
+    const P *r2 = pair_r2<real>(G), *sl = pair_sl<real>(G), *cs = pair_cs<real>(G);
+    for (int q = t; q < a + b + c; q += nthreads)
+        dst[q] = q < a ? r2[q] : q < a + b ? sl[q - a] : cs[q - a - b];
+    Tabs<real> T;
+    T.r2 = dst;
+    T.sl = dst + a;
+    T.cs = dst + a + b;
+    T.nlon = G.nlon;
+    T.nlat = G.nlat;
+    T.nr = G.nr;
+    return T;
 }
 
 // fixed-point conversion of a non-negative contribution

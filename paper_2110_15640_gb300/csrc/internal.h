@@ -69,10 +69,10 @@ cudaError_t prep_xsec(int precision, const DevGrid *dgrid, const DevGrid &hgrid,
 // transport
 size_t transport_smem(int block);
 cudaError_t launch_plain(int precision, bool scatter, const DevGrid *grids, const DevJob *job, int64_t packet0,
-                         int64_t n_run, const HostLog *hl, cudaStream_t st);
+                         int64_t n_run, const HostLog *hl, int tab_entries_n, cudaStream_t st);
 cudaError_t launch_persistent(int precision, bool scatter, const DevGrid *grids, const DevJob *jobs, int n_jobs,
                               int64_t total_items, int chunk, int block, int blocks_per_sm, int interval, int refill_min,
-                              unsigned long long *work, cudaStream_t st);
+                              int one_grid, int tab_n, unsigned long long *work, cudaStream_t st);
 
 // process-wide kernel launch counter
 extern std::atomic<long long> g_launches;

@@ -25,6 +25,7 @@ template <typename real> struct Ray {
     real p2hi, p2lo;        // |c0|^2 = p^2 as hi + lo
     real p, chz, Q;         // p, zc / p, dz^2 + chz^2
     real crz;               // (o x d)_z: sign gives the direction of azimuthal motion
+    real B, dz2;            // zc dz and dz^2 (cone coefficients that depend on the ray only)
     real tau, tau_target;   // accumulated optical depth; interaction target (< 0: none)
     int i, j, k;            // current cell
 };
@@ -106,6 +107,8 @@ __device__ __forceinline__ void ray_setup(Ray<real> &R, real ox, real oy, real o
     R.p = M<real>::sqrt_(R.p2hi);
     R.chz = R.p > (real)0 ? M<real>::div_(R.cz, R.p) : (real)0;
     R.Q = dz * dz + R.chz * R.chz;
+    R.B = R.cz * dz;
+    R.dz2 = dz * dz;
 }
 
 constexpr double TAN_EPS_CONE = 1e-5;
@@ -115,6 +118,11 @@ constexpr double TAN_EPS_CONE = 1e-5;
 __device__ __noinline__ int cone_roots64(double cx, double cy, double cz, double dx, double dy, double dz, double S,
                                          double S2, double *r)
 {
+    if (S == 0.0) {   // equator plane z = 0
+        if (dz == 0.0) return 0;
+        r[0] = -cz / dz;
+        return 1;
+    }
     const double p2 = cx * cx + cy * cy + cz * cz;
     const double A = dz * dz - S2;
     const double B = cz * dz;
@@ -138,24 +146,20 @@ __device__ __noinline__ int cone_roots64(double cx, double cy, double cz, double
     return n;
 }
 
+// smallest root > smin of latitude edge e on its valid nappe (the equator edge is the plane z = 0);
+// +inf if none.  Straight-line code: every lane of a warp runs the same instructions.
 template <typename real>
-__device__ __forceinline__ real cone_root(const DevGrid &G, const Ray<real> &R, int e, real smin)
+__device__ __forceinline__ real cone_root(const DevGrid &G, const Tabs<real> &T, const Ray<real> &R, int e, real smin)
 {
-    const real S = __ldg(tab_slat<real>(G) + e);
     const real inf = M<real>::inf();
-    if (S == (real)0) {
-        if (R.dz == (real)0) return inf;
-        const real sr = M<real>::div_(-R.cz, R.dz);
-        return sr > smin ? sr : inf;
-    }
-    const real S2 = __ldg(tab_s2lat<real>(G) + e);
-    const real A = R.dz * R.dz - S2;
-    const real dn = R.Q - S2;
-    if (dn < (real)0) return inf;
+    const auto sp = T.sl[e];
+    const real S = sp.x, S2 = sp.y;
+    const real A = R.dz2 - S2;
+    const real dn = R.Q - S2;                       // disc = S^2 p^2 (Q - S^2)
     if constexpr (sizeof(real) == 4) {
-        if (dn < (real)TAN_EPS_CONE || fabsf(A) < (real)TAN_EPS_CONE) {
-            // validity is decided on the rounded root: the same test as every other face, so a face
-            // just crossed (root == s after rounding) is never taken again
+        if (dn >= (real)0 && (dn < (real)TAN_EPS_CONE || fabsf(A) < (real)TAN_EPS_CONE)) {
+            // near tangency: roots in FP64 from the FP32 ray; validity is decided on the rounded
+            // root, the same test as every other face, so a face just crossed is never taken again
             double r[2];
             const int m = cone_roots64(R.cx, R.cy, R.cz, R.dx, R.dy, R.dz, __ldg(G.slat + e), __ldg(G.s2lat + e), r);
             real best = inf;
@@ -166,103 +170,74 @@ __device__ __forceinline__ real cone_root(const DevGrid &G, const Ray<real> &R, 
             return best;
         }
     }
-    const real B = R.cz * R.dz;
+    const real B = R.B;
     const real C = R.p2hi * ((R.chz - S) * (R.chz + S));
-    const real sq = fabs(S) * R.p * M<real>::sqrt_(dn);
+    const real sq = fabs(S) * R.p * M<real>::sqrt_(fmax(dn, (real)0));
     const real q = -(B + copysign(sq, B));
-    real best = inf;
-    if (q != (real)0) {
-        const real r1 = M<real>::div_(q, A);
-        const real r2 = M<real>::div_(C, q);
-        const real z1 = R.cz + r1 * R.dz, z2 = R.cz + r2 * R.dz;
-        const bool v1 = (S > (real)0 ? z1 > (real)0 : z1 < (real)0) && r1 > smin;
-        const bool v2 = (S > (real)0 ? z2 > (real)0 : z2 < (real)0) && r2 > smin;
-        if (v1) best = r1;
-        if (v2 && r2 < best) best = r2;
-    }
-    return best;
+    // the equator edge is the plane z = 0 with the single root -zc/dz (two rounded copies of one root
+    // could otherwise re-cross the plane at zero length)
+    const bool eq = S == (real)0;
+    const real r1 = eq ? M<real>::div_(-R.cz, R.dz) : M<real>::div_(q, A);
+    const real r2 = M<real>::div_(C, q);
+    const real z1 = R.cz + r1 * R.dz, z2 = R.cz + r2 * R.dz;
+    // a root counts on the nappe whose z has the sign of S
+    const bool ok = dn >= (real)0 && q != (real)0;
+    const bool v1 = (eq ? R.dz != (real)0 : ok && z1 * S > (real)0) && r1 > smin;
+    const bool v2 = !eq && ok && z2 * S > (real)0 && r2 > smin;
+    const real a1 = v1 ? r1 : inf, a2 = v2 ? r2 : inf;
+    return a1 < a2 ? a1 : a2;
 }
 
-// Exit of the current cell: returns the s of the exit point and the face.
+// Exit of the current cell: returns the s of the exit point and the face.  Every candidate face is
+// evaluated with selects (both shells' discriminants, both cones, the half-plane ahead in azimuth),
+// so the lanes of a warp stay converged; ties go to the first face in the order r-, r+, lat-, lat+, lon.
 template <typename real>
-__device__ __forceinline__ real cell_exit(const DevGrid &G, const Ray<real> &R, int &face)
+__device__ __forceinline__ real cell_exit(const DevGrid &G, const Tabs<real> &T, const Ray<real> &R, int &face)
 {
     const real inf = M<real>::inf();
-    // radial shells
-    real best;
-    {
-        real hi, lo;
-        bool done = false;
-        if (R.s < (real)0) {
-            r2_pair<real>(G, R.k, hi, lo);
-            const real h = (hi - R.p2hi) + (lo - R.p2lo);
-            if (h > (real)0) {
-                best = -M<real>::sqrt_(h);
-                face = F_RIN;
-                done = true;
-            }
-        }
-        if (!done) {
-            r2_pair<real>(G, R.k + 1, hi, lo);
-            const real h = (hi - R.p2hi) + (lo - R.p2lo);
-            best = M<real>::sqrt_(h > (real)0 ? h : (real)0);
-            face = F_ROUT;
-        }
+    // radial shells: inward (s < 0) and still outside the inner shell -> inner root, else outer root
+    const auto ri = T.r2[R.k], ro = T.r2[R.k + 1];
+    const real hin = (ri.x - R.p2hi) + (ri.y - R.p2lo);
+    const real hout = (ro.x - R.p2hi) + (ro.y - R.p2lo);
+    const bool inward = R.s < (real)0 && hin > (real)0;
+    const real h = inward ? hin : fmax(hout, (real)0);
+    const real rt = M<real>::sqrt_(h);
+    real best = inward ? -rt : rt;
+    face = inward ? F_RIN : F_ROUT;
+    // latitude cones (edges j and j+1; the poles are not surfaces)
+    const real tlo = R.j > 0 ? cone_root<real>(G, T, R, R.j, R.s) : inf;
+    const real thi = R.j + 1 < T.nlat ? cone_root<real>(G, T, R, R.j + 1, R.s) : inf;
+    if (tlo < best) {
+        best = tlo;
+        face = F_LATLO;
     }
-    // latitude cones: the latitude along the line has one extremum (sign of dz p^2 - zc s)
-    if (G.nlat > 1) {
-        const bool has_lo = R.j > 0, has_hi = R.j + 1 < G.nlat;
-        const real D = R.dz * R.p2hi - R.cz * R.s;
-        const bool up = D > (real)0;
-        const bool both = fabs(D) < (real)1e-4 * R.p2hi;
-        real tlo = inf, thi = inf;
-        if (has_hi && (up || both)) thi = cone_root<real>(G, R, R.j + 1, R.s);
-        if (has_lo && (!up || both || thi == inf)) tlo = cone_root<real>(G, R, R.j, R.s);
-        if (has_hi && !up && !both && tlo == inf) thi = cone_root<real>(G, R, R.j + 1, R.s);
-        if (tlo < best) {
-            best = tlo;
-            face = F_LATLO;
-        }
-        if (thi < best) {
-            best = thi;
-            face = F_LATHI;
-        }
+    if (thi < best) {
+        best = thi;
+        face = F_LATHI;
     }
-    // longitude half-plane ahead in azimuth
-    if (G.nlon > 1 && R.crz != (real)0) {
-        const bool east = R.crz > (real)0;
-        const int e = east ? R.i + 1 : R.i;
-        const real c = __ldg(tab_clon<real>(G) + e), sn = __ldg(tab_slon<real>(G) + e);
-        const real nd = R.dy * c - R.dx * sn;
-        if (nd != (real)0) {
-            const real sr = M<real>::div_(-(R.cy * c - R.cx * sn), nd);
-            if (sr > R.s && c * (R.cx + sr * R.dx) + sn * (R.cy + sr * R.dy) > (real)0 && sr < best) {
-                best = sr;
-                face = east ? F_LONHI : F_LONLO;
-            }
-        }
+    // longitude: the azimuth along a line is monotone (sign of (o x d)_z), so only the edge ahead counts
+    const bool east = R.crz > (real)0;
+    const auto cs = T.cs[east ? R.i + 1 : R.i];
+    const real nd = R.dy * cs.x - R.dx * cs.y;
+    const real sr = M<real>::div_(-(R.cy * cs.x - R.cx * cs.y), nd);
+    const bool lon_ok = T.nlon > 1 && R.crz != (real)0 && nd != (real)0 && sr > R.s &&
+                        cs.x * (R.cx + sr * R.dx) + cs.y * (R.cy + sr * R.dy) > (real)0;
+    if (lon_ok && sr < best) {
+        best = sr;
+        face = east ? F_LONHI : F_LONLO;
     }
     return best;
 }
 
 // Cross `face`: update the cell; returns E_CONT, E_ESCAPE or E_BOTTOM.
-__device__ __forceinline__ int cross_face(const DevGrid &G, int face, int &i, int &j, int &k)
+template <class GT> __device__ __forceinline__ int cross_face(const GT &G, int face, int &i, int &j, int &k)
 {
-    switch (face) {
-    case F_RIN:
-        if (k == 0) return E_BOTTOM;
-        --k;
-        break;
-    case F_ROUT:
-        if (k == G.nr - 1) return E_ESCAPE;
-        ++k;
-        break;
-    case F_LATLO: --j; break;
-    case F_LATHI: ++j; break;
-    case F_LONLO: i = (i == 0) ? G.nlon - 1 : i - 1; break;
-    case F_LONHI: i = (i + 1 == G.nlon) ? 0 : i + 1; break;
-    default: break;
-    }
+    if (face == F_RIN && k == 0) return E_BOTTOM;
+    if (face == F_ROUT && k == G.nr - 1) return E_ESCAPE;
+    k += (face == F_ROUT) - (face == F_RIN);
+    j += (face == F_LATHI) - (face == F_LATLO);
+    const int ni = i + (face == F_LONHI) - (face == F_LONLO);
+    i = ni < 0 ? G.nlon - 1 : ni == G.nlon ? 0 : ni;
     return E_CONT;
 }
 

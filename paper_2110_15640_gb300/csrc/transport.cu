@@ -30,6 +30,7 @@ template <typename real> struct Packet {
     int ci, cj, ck;
     int steps;
     int hint;              // launch cell of this lane's previous packet of the same work item (-1: none)
+    int ended, end_e, end_idx;   // the current ray has ended (persistent kernel: processed at the refill point)
     uint32_t ev;
     int64_t n;
 };
@@ -163,6 +164,7 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
     P.n = n;
     P.steps = 0;
     P.alive = 1;
+    P.ended = 0;
     P.ev = 2;
     if constexpr (SinkT::is_log) {
         if (S.lg.pk_tau) S.lg.pk_tau[n - S.lg.packet0] = -1.0;
@@ -211,7 +213,11 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
     const int idx = cdf_find(reinterpret_cast<const long long *>(J.cdf), (int)G.ncell, __double_as_longlong(target),
                              P.hint);
     P.hint = idx;
-    const int i = idx % G.nlon, j = (idx / G.nlon) % G.nlat, k = idx / (G.nlon * G.nlat);
+    const int nll = G.nlon * G.nlat;
+    const int k = (int)(((uint64_t)idx * G.mag_ll) >> 40);
+    const int rem = idx - k * nll;
+    const int j = (int)(((uint64_t)rem * G.mag_lon) >> 40);
+    const int i = rem - j * G.nlon;
     const real u1 = u01<real>(w.y), u2 = u01<real>(w.z), u3 = u01<real>(w.w);
     real r, sl, ph;
     if constexpr (sizeof(real) == 8) {
@@ -225,7 +231,11 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
         // lon likewise from hi + lo edges: each coordinate is rounded once, so no edge rounding is
         // shared by all packets of a cell
         const float r1 = __ldg(G.r_f + k);
-        const float t = expm1f(log1pf(u1 * __ldg(G.shA_f + k)) * (1.0f / 3.0f));
+        const float x = u1 * __ldg(G.shA_f + k);
+        // (1 + x)^(1/3) - 1: binomial series for thin shells (truncation < 3e-8 relative at x < 0.05)
+        const float t = x < 0.05f ? x * (1.0f / 3.0f + x * (-1.0f / 9.0f + x * (5.0f / 81.0f + x * (-10.0f / 243.0f +
+                                                                                                 x * (22.0f / 729.0f)))))
+                                  : expm1f(log1pf(x) * (1.0f / 3.0f));
         r = r1 + __fmaf_rn(r1, t, __ldg(G.r_lo_f + k));
         sl = __ldg(G.slat_f + j) + __fmaf_rn(u2, __ldg(G.dslat_f + j), __ldg(G.slat_lo_f + j));
         ph = __ldg(G.lon_f + i) + __fmaf_rn(u3, __ldg(G.dlon_f + i), __ldg(G.lon_lo_f + i));
@@ -374,25 +384,23 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
 
 // one cell step (S3-S7) of the packet's current ray
 template <typename real, bool SCAT, class SinkT>
-__device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const DevGrid &G, const JobC<real> &jc, SinkT &S)
+__device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const DevGrid &G, const Tabs<real> &T,
+                                     const JobC<real> &jc, SinkT &S)
 {
     Ray<real> &R = P.ray;
     if (P.steps >= jc.max_steps) {
-        if (SCAT && P.kind == K_FLIGHT) {
-            S.ledger(6, P.W);
-            finish<real>(P, S);
-        } else {
-            on_end<real, SCAT>(P, J, S, E_CAP, 0);
-        }
+        P.ended = 1;
+        P.end_e = E_CAP;
+        P.end_idx = 0;
         return;
     }
     ++P.steps;
-    const int idx = (R.k * G.nlat + R.j) * G.nlon + R.i;
+    const int idx = (R.k * T.nlat + R.j) * T.nlon + R.i;
     real a;
     if (SCAT && J.mode == GCMC_ALBEDO) a = __ldg(reinterpret_cast<const real *>(J.rec) + 4 * idx);
     else a = __ldg(reinterpret_cast<const real *>(J.rec) + idx);
     int face = F_NONE;
-    const real sx = cell_exit<real>(G, R, face);
+    const real sx = cell_exit<real>(G, T, R, face);
     const real seg = sx - R.s;
     if constexpr (SCAT) {
         if (R.tau_target >= (real)0 && a > (real)0 && R.tau + a * seg >= R.tau_target) {
@@ -400,16 +408,30 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
             S.trace(P.n, idx, l);
             R.s += l;
             R.tau = R.tau_target;
-            on_end<real, SCAT>(P, J, S, E_INTERACT, idx);
+            P.ended = 1;
+            P.end_e = E_INTERACT;
+            P.end_idx = idx;
             return;
         }
     }
     R.tau += a * seg;
     S.trace(P.n, idx, seg);
     R.s = sx;
-    int e = cross_face(G, face, R.i, R.j, R.k);
+    int e = cross_face(T, face, R.i, R.j, R.k);
     if (e == E_CONT && R.tau_target < (real)0 && R.tau > jc.tau_cut) e = E_CUTOFF;
-    if (e != E_CONT) on_end<real, SCAT>(P, J, S, e, idx);
+    if (e != E_CONT) {
+        P.ended = 1;
+        P.end_e = e;
+        P.end_idx = idx;
+    }
+}
+
+// the end of the packet's current ray: tally, next ray, interaction or finish
+template <typename real, bool SCAT, class SinkT>
+__device__ __forceinline__ void settle(Packet<real> &P, const DevJob &J, SinkT &S)
+{
+    P.ended = 0;
+    on_end<real, SCAT>(P, J, S, P.end_e, P.end_idx);
 }
 
 // warp-reduce the per-thread accumulators and add them to the job's totals
@@ -445,7 +467,7 @@ __global__ void __launch_bounds__(256) k_transport_plain(const DevGrid *__restri
                                                          const DevJob *__restrict__ jobp, int64_t packet0, int64_t n_run,
                                                          LogOut lg)
 {
-    extern __shared__ unsigned long long sacc[];
+    extern __shared__ __align__(16) unsigned long long sacc[];
     Sink<real, LOG> S;
     S.sm = sacc + threadIdx.x;
     S.stride = blockDim.x;
@@ -453,31 +475,49 @@ __global__ void __launch_bounds__(256) k_transport_plain(const DevGrid *__restri
     for (int s = 0; s < NSLOT; ++s) S.sm[s * S.stride] = 0ull;
     const DevJob &J = *jobp;
     const DevGrid &G = grids[J.grid_slot];
+    auto *tab = reinterpret_cast<typename Pair<real>::type *>(sacc + NSLOT * blockDim.x);
+    const Tabs<real> T = stage_tabs<real>(G, tab, threadIdx.x, blockDim.x);
+    __syncthreads();
     const JobC<real> jc = job_consts<real>(J);
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q < n_run) {
         Packet<real> P;
         P.hint = -1;
         launch<real, SCAT>(P, J, G, packet0 + q, S);
-        while (P.alive) step<real, SCAT>(P, J, G, jc, S);
+        while (P.alive) {
+            if (P.ended) settle<real, SCAT>(P, J, S);
+            else step<real, SCAT>(P, J, G, T, jc, S);
+        }
     }
     __syncwarp();
     flush(S.sm, S.stride, J.acc);
 }
 
-template <typename real, bool SCAT>
-__global__ void __launch_bounds__(256) k_transport_persistent(const DevGrid *__restrict__ grids,
+// MINB > 0: compiled for MINB resident 128-thread blocks per SM (register cap 65536 / (128 MINB))
+template <typename real, bool SCAT, int MINB>
+__global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) k_transport_persistent(const DevGrid *__restrict__ grids,
                                                               const DevJob *__restrict__ jobs, int n_jobs,
                                                               int64_t total_items, int chunk, int interval,
-                                                              int refill_min, unsigned long long *work)
+                                                              int refill_min, int one_grid, int tab_n,
+                                                              unsigned long long *work)
 {
-    extern __shared__ unsigned long long sacc[];
+    extern __shared__ __align__(16) unsigned long long sacc[];
     Sink<real, false> S;
     S.sm = sacc + threadIdx.x;
     S.stride = blockDim.x;
     for (int s = 0; s < NSLOT; ++s) S.sm[s * S.stride] = 0ull;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
+    // march tables in shared memory: one copy per block when every job uses the same grid, else one
+    // per warp, restaged when the warp's work item comes from another grid
+    auto *tab0 = reinterpret_cast<typename Pair<real>::type *>(sacc + NSLOT * blockDim.x);
+    Tabs<real> T;
+    int cur_grid = -1;
+    if (one_grid) {
+        cur_grid = jobs[0].grid_slot;
+        T = stage_tabs<real>(grids[cur_grid], tab0, threadIdx.x, blockDim.x);
+        __syncthreads();
+    }
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(work, 1ull);
@@ -491,6 +531,12 @@ __global__ void __launch_bounds__(256) k_transport_persistent(const DevGrid *__r
         }
         const DevJob &J = jobs[lo];
         const DevGrid &G = grids[J.grid_slot];
+        if (J.grid_slot != cur_grid) {
+            __syncwarp();
+            cur_grid = J.grid_slot;
+            T = stage_tabs<real>(G, tab0 + (threadIdx.x >> 5) * tab_n, lane, 32);
+            __syncwarp();
+        }
         const JobC<real> jc = job_consts<real>(J);
         const int64_t p0 = ((int64_t)item - J.chunk_begin) * chunk;
         const int64_t p1 = min(p0 + (int64_t)chunk, J.n_packets);
@@ -498,7 +544,10 @@ __global__ void __launch_bounds__(256) k_transport_persistent(const DevGrid *__r
         Packet<real> P;
         P.alive = 0;
         P.hint = -1;
+        P.ended = 0;
         for (;;) {
+            // rays that ended since the last check are settled together (tally, next ray or finish)
+            if (P.alive && P.ended) settle<real, SCAT>(P, J, S);
             const unsigned idle = __ballot_sync(0xffffffffu, !P.alive);
             const int n_idle = __popc(idle);
             const int64_t left = p1 - pool;
@@ -509,7 +558,7 @@ __global__ void __launch_bounds__(256) k_transport_persistent(const DevGrid *__r
             }
             if (!__any_sync(0xffffffffu, P.alive)) break;
             for (int t = 0; t < interval; ++t)
-                if (P.alive) step<real, SCAT>(P, J, G, jc, S);
+                if (P.alive && !P.ended) step<real, SCAT>(P, J, G, T, jc, S);
         }
         __syncwarp();
         flush(S.sm, S.stride, J.acc);
@@ -518,6 +567,8 @@ __global__ void __launch_bounds__(256) k_transport_persistent(const DevGrid *__r
 
 // ------------------------------------------------------------------ host launchers
 size_t transport_smem(int block) { return (size_t)NSLOT * block * sizeof(unsigned long long); }
+
+static size_t tab_bytes(int precision, int entries) { return (size_t)entries * (precision == GCMC_FP64 ? 16 : 8); }
 
 template <typename real, bool SCAT>
 static void plain_dispatch(unsigned nb, int block, size_t sm, cudaStream_t st, const DevGrid *grids, const DevJob *job,
@@ -528,7 +579,7 @@ static void plain_dispatch(unsigned nb, int block, size_t sm, cudaStream_t st, c
 }
 
 cudaError_t launch_plain(int precision, bool scatter, const DevGrid *grids, const DevJob *job, int64_t packet0,
-                         int64_t n_run, const HostLog *hl, cudaStream_t st)
+                         int64_t n_run, const HostLog *hl, int tab_entries_n, cudaStream_t st)
 {
     const int block = 128;
     const int64_t nb = (n_run + block - 1) / block;
@@ -545,7 +596,7 @@ cudaError_t launch_plain(int precision, bool scatter, const DevGrid *grids, cons
         lg.n_trace = hl->n_trace;
         lg.max_trace = hl->max_trace;
     }
-    const size_t sm = transport_smem(block);
+    const size_t sm = transport_smem(block) + tab_bytes(precision, tab_entries_n);
     count_launch(1);
     const unsigned g = (unsigned)nb;
     if (precision == GCMC_FP64) {
@@ -558,26 +609,45 @@ cudaError_t launch_plain(int precision, bool scatter, const DevGrid *grids, cons
     return cudaGetLastError();
 }
 
+template <typename real, bool SCAT, int MINB>
+static cudaError_t persistent_run(int block, int blocks_per_sm, int nsm, const DevGrid *grids, const DevJob *jobs,
+                                  int n_jobs, int64_t total_items, int chunk, int interval, int refill_min, int one_grid,
+                                  int tab_n, unsigned long long *work, cudaStream_t st)
+{
+    auto kern = k_transport_persistent<real, SCAT, MINB>;
+    const size_t sm = transport_smem(block) + (size_t)tab_n * sizeof(typename Pair<real>::type) * (one_grid ? 1 : block / 32);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, sm);
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    if (blocks_per_sm <= 0 || blocks_per_sm > occ) blocks_per_sm = occ;
+    const unsigned grid = (unsigned)(nsm * blocks_per_sm);
+    kern<<<grid, block, sm, st>>>(grids, jobs, n_jobs, total_items, chunk, interval, refill_min, one_grid, tab_n, work);
+    return cudaGetLastError();
+}
+
 template <typename real, bool SCAT>
 static cudaError_t persistent_dispatch(int block, int blocks_per_sm, int nsm, const DevGrid *grids, const DevJob *jobs,
                                        int n_jobs, int64_t total_items, int chunk, int interval, int refill_min,
-                                       unsigned long long *work, cudaStream_t st)
+                                       int one_grid, int tab_n, unsigned long long *work, cudaStream_t st)
 {
-    const size_t sm = transport_smem(block);
-    if (blocks_per_sm <= 0) {
-        int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_persistent<real, SCAT>, block, sm);
-        blocks_per_sm = occ > 0 ? occ : 1;
+    // FP32 absorber-only batches (the emission and limb-chord hot path) have variants compiled for
+    // 6 and 8 resident 128-thread blocks per SM; blocks_per_sm selects them
+    if constexpr (sizeof(real) == 4 && !SCAT) {
+        if (block <= 128 && blocks_per_sm >= 8)
+            return persistent_run<real, SCAT, 8>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+                                                 interval, refill_min, one_grid, tab_n, work, st);
+        if (block <= 128 && blocks_per_sm >= 6)
+            return persistent_run<real, SCAT, 6>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+                                                 interval, refill_min, one_grid, tab_n, work, st);
     }
-    const unsigned grid = (unsigned)(nsm * blocks_per_sm);
-    k_transport_persistent<real, SCAT><<<grid, block, sm, st>>>(grids, jobs, n_jobs, total_items, chunk, interval,
-                                                                refill_min, work);
-    return cudaGetLastError();
+    return persistent_run<real, SCAT, 0>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk, interval,
+                                         refill_min, one_grid, tab_n, work, st);
 }
 
 cudaError_t launch_persistent(int precision, bool scatter, const DevGrid *grids, const DevJob *jobs, int n_jobs,
                               int64_t total_items, int chunk, int block, int blocks_per_sm, int interval, int refill_min,
-                              unsigned long long *work, cudaStream_t st)
+                              int one_grid, int tab_n, unsigned long long *work, cudaStream_t st)
 {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
@@ -590,15 +660,15 @@ cudaError_t launch_persistent(int precision, bool scatter, const DevGrid *grids,
     if (precision == GCMC_FP64) {
         if (scatter)
             return persistent_dispatch<double, true>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
-                                                     interval, refill_min, work, st);
+                                                     interval, refill_min, one_grid, tab_n, work, st);
         return persistent_dispatch<double, false>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
-                                                  interval, refill_min, work, st);
+                                                  interval, refill_min, one_grid, tab_n, work, st);
     }
     if (scatter)
         return persistent_dispatch<float, true>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
-                                                interval, refill_min, work, st);
+                                                interval, refill_min, one_grid, tab_n, work, st);
     return persistent_dispatch<float, false>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
-                                             interval, refill_min, work, st);
+                                             interval, refill_min, one_grid, tab_n, work, st);
 }
 
 }  // namespace gcmc
