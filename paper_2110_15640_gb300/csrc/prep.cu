@@ -132,17 +132,6 @@ __global__ void k_emis_cut(DevGrid G, const PrepJob *__restrict__ jobs, double t
     }
 }
 
-__device__ __forceinline__ double warp_incl_scan(double v)
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
-    }
-    return v;
-}
-
 // per-block sums of L over the emitting cells and their count (fixed tree order)
 __global__ void k_emis_reduce(int64_t ncell, const PrepJob *__restrict__ jobs)
 {
@@ -190,10 +179,26 @@ __global__ void k_emis_total(int nblk, const PrepJob *__restrict__ jobs, int njo
     pj.info[1] = c;
 }
 
-// hybrid pdf, launch weights and the per-block inclusive scan of the pdf
+// The cumulative pdf is accumulated in 64-bit fixed point, Q_i = round(q_i 2^62) (sum <= 2^62 (1 + eps)):
+// integer prefix sums are exact in any order, so the cumulative sum is monotone and exactly flat over
+// cells with zero pdf, whatever the block and warp structure of the scan.
+constexpr double CDF_FIX = 4611686018427387904.0;   // 2^62
+
+__device__ __forceinline__ long long warp_incl_scan_ll(long long v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// hybrid pdf, launch weights and the per-block inclusive scan of the fixed-point pdf
 __global__ void k_emis_pdf(int64_t ncell, const PrepJob *__restrict__ jobs, double beta)
 {
-    __shared__ double ws[EMIS_SCAN_BLOCK / 32];
+    __shared__ long long ws[EMIS_SCAN_BLOCK / 32];
     const PrepJob pj = jobs[blockIdx.y];
     const int64_t idx = (int64_t)blockIdx.x * EMIS_SCAN_BLOCK + threadIdx.x;
     const double Ltot = pj.info[0], nincl = pj.info[1];
@@ -209,20 +214,18 @@ __global__ void k_emis_pdf(int64_t ncell, const PrepJob *__restrict__ jobs, doub
             }
         }
     }
-    double s = warp_incl_scan(q);
+    long long s = warp_incl_scan_ll(__double2ll_rn(q * CDF_FIX));
     if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = s;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        const double t = warp_incl_scan(ws[threadIdx.x]);
-        ws[threadIdx.x] = t;
-    }
+    if (threadIdx.x < 32) ws[threadIdx.x] = warp_incl_scan_ll(ws[threadIdx.x]);
     __syncthreads();
     if (threadIdx.x >= 32) s += ws[(threadIdx.x >> 5) - 1];
+    long long *cq = reinterpret_cast<long long *>(pj.cdf);   // within-block prefix, as integers until cdf_add
     if (idx < ncell) {
-        pj.cdf[idx] = s;
+        cq[idx] = s;
         pj.wcell[idx] = wgt;
     }
-    if (threadIdx.x == EMIS_SCAN_BLOCK - 1) pj.bsum[blockIdx.x] = s;
+    if (threadIdx.x == EMIS_SCAN_BLOCK - 1) reinterpret_cast<long long *>(pj.bsum)[blockIdx.x] = s;
 }
 
 __global__ void k_emis_scan_blocks(int nblk, const PrepJob *__restrict__ jobs, int njobs)
@@ -230,20 +233,25 @@ __global__ void k_emis_scan_blocks(int nblk, const PrepJob *__restrict__ jobs, i
     const int jb = blockIdx.x * blockDim.x + threadIdx.x;
     if (jb >= njobs) return;
     const PrepJob pj = jobs[jb];
-    double run = 0.0;
+    const long long *bt = reinterpret_cast<const long long *>(pj.bsum);
+    long long *off = reinterpret_cast<long long *>(pj.bcnt);
+    long long run = 0;
     for (int b = 0; b < nblk; ++b) {
-        const double t = pj.bsum[b];
-        pj.bcnt[b] = run;
+        const long long t = bt[b];
+        off[b] = run;
         run += t;
     }
-    pj.info[2] = run;
+    pj.info[2] = (double)run / CDF_FIX;
 }
 
 __global__ void k_emis_cdf_add(int64_t ncell, const PrepJob *__restrict__ jobs)
 {
     const PrepJob pj = jobs[blockIdx.y];
     const int64_t idx = (int64_t)blockIdx.x * EMIS_SCAN_BLOCK + threadIdx.x;
-    if (idx < ncell && blockIdx.x > 0) pj.cdf[idx] += pj.bcnt[blockIdx.x];
+    if (idx >= ncell) return;
+    long long *cq = reinterpret_cast<long long *>(pj.cdf);
+    const long long v = cq[idx] + reinterpret_cast<const long long *>(pj.bcnt)[blockIdx.x];
+    pj.cdf[idx] = (double)v / CDF_FIX;
 }
 
 cudaError_t prep_emission(int precision, const DevGrid *, const DevGrid &hg, const KtabDev &kt, const PrepJob *djobs,

@@ -101,6 +101,11 @@ def test_cell_tables_emission(G):
             st = got["stats"]
             np.testing.assert_allclose(got["lum"], ref["L"], rtol=1e-13)
             np.testing.assert_allclose(got["cdf"], ref["cdf"], rtol=1e-12, atol=1e-15)
+            # monotone, and exactly flat over the cells the tau_vert cut excludes
+            dq = np.diff(np.concatenate([[0.0], got["cdf"]]))
+            q_ref = np.diff(np.concatenate([[0.0], ref["cdf"]]))
+            assert np.all(dq >= 0)
+            assert np.array_equal(dq == 0, q_ref == 0)
             np.testing.assert_allclose(got["wcell"], ref["wcell"], rtol=1e-12)
             assert st.n_emit_cells == ref["n_incl"]
             assert abs(st.l_tot / ref["L_tot"] - 1) < 1e-13
