@@ -254,6 +254,31 @@ int64_t gcmc_kernel_launches(void);
 gcmc_status gcmc_gather_bench(gcmc_ctx *ctx, int64_t n_records, int record_bytes, int64_t n_gathers,
                               double *gathers_per_s);
 
+/* ---------------------------------------------------------------- allocation-free variant */
+
+/* Largest cell count gcmc_emission_pdf_noalloc accepts (its scratch: 64 KiB per GPU). */
+#define GCMC_NOALLOC_MAX_CELLS 4194304
+
+/* The emission pdf stage (hybrid pdf q_i, cumulative sum and launch weights) without any device
+   allocation, for callers that cannot call cudaMalloc/cudaFree: code that must not trigger their
+   implicit device-wide synchronisation, or hosts that hand a library only pre-allocated device
+   memory.  The paper has no counterpart: this is a calling convention of the library.
+   All pointers are DEVICE memory owned by the caller:
+     lum     [ncell]  luminosity L_i of each cell, W/m; a negative value marks a cell excluded by the
+                      tau_vert cut (as the library's own cell-table kernels mark them)
+     cdf     [ncell]  out: cumulative hybrid pdf (the pdf of cell i is cdf[i] - cdf[i-1])
+     wcell   [ncell]  out: launch weight (L_i / L_tot) / q_i, 0 for excluded cells
+     totals  [3]      out: L_tot, number of emitting cells, cdf total
+   beta is the hybrid biasing fraction (0..1).  Work is queued on `stream` (a cudaStream_t, NULL =
+   default stream); the call returns without waiting.  Scratch lives in a fixed array in the
+   library's device memory, one per GPU, held until the process exits; the first call on a device
+   looks up its address (do that first call before any stream capture).  Every call shares that
+   array, so calls that overlap on the GPU (e.g. on two streams) race: order them on one stream.
+   Errors: GCMC_ERR_ARG (NULL pointer, ncell < 1, beta outside [0, 1]), GCMC_ERR_RANGE (ncell >
+   GCMC_NOALLOC_MAX_CELLS), GCMC_ERR_CUDA. */
+gcmc_status gcmc_emission_pdf_noalloc(const double *lum, int64_t ncell, double beta, double *cdf, double *wcell,
+                                      double *totals, void *stream);
+
 /* ---------------------------------------------------------------- self tests */
 
 /* Philox4x32-10 of the library and cuRAND's curand_Philox4x32_10 on the device for n

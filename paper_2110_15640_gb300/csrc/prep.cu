@@ -14,6 +14,9 @@
 //                bilinearly in (ln T, ln p); FP32 in FP32 runs (no integer decision depends on it).
 #include <curand_philox4x32_x.h>
 
+#include <algorithm>
+#include <cstring>
+
 #include "internal.h"
 
 namespace gcmc {
@@ -423,3 +426,70 @@ cudaError_t gather_bench(const void *table, int64_t n_records, int record_bytes,
 }
 
 }  // namespace gcmc
+
+// ------------------------------------------------------------------ allocation-free emission pdf
+// Scratch of gcmc_emission_pdf_noalloc: per-block partial sums and counts (EMIS_SCAN_BLOCK cells per
+// block) and the job record the pdf kernels read.  File-scope device memory: one copy per GPU that
+// loads the library, kept until exit.  Every slot read by a kernel is written earlier in the same
+// call (partial sums by k_emis_reduce, offsets by k_emis_scan_blocks, the record by k_noalloc_job),
+// so nothing needs clearing between calls; overlapping calls race on it.
+namespace {
+constexpr int NOALLOC_BLOCKS = GCMC_NOALLOC_MAX_CELLS / gcmc::EMIS_SCAN_BLOCK;
+struct __align__(256) NoallocScratch {
+    double bsum[NOALLOC_BLOCKS];
+    double bcnt[NOALLOC_BLOCKS];
+    gcmc::PrepJob job;
+};
+static __device__ __align__(256) NoallocScratch g_noalloc;
+
+__global__ void k_noalloc_job(NoallocScratch *sc, double *cdf, double *wcell, double *totals)
+{
+    gcmc::PrepJob j;
+    memset(&j, 0, sizeof(j));
+    j.cdf = cdf;
+    j.wcell = wcell;
+    j.info = totals;
+    j.bsum = sc->bsum;
+    j.bcnt = sc->bcnt;
+    sc->job = j;
+}
+
+__global__ void k_noalloc_copy(const double *__restrict__ src, double *__restrict__ dst, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+std::atomic<NoallocScratch *> g_noalloc_addr[64];   // per device: address of g_noalloc (host-side lookup)
+}  // namespace
+
+extern "C" gcmc_status gcmc_emission_pdf_noalloc(const double *lum, int64_t ncell, double beta, double *cdf,
+                                                 double *wcell, double *totals, void *stream)
+{
+    using namespace gcmc;
+    if (!lum || !cdf || !wcell || !totals || ncell < 1 || !(beta >= 0.0 && beta <= 1.0)) return GCMC_ERR_ARG;
+    if (ncell > GCMC_NOALLOC_MAX_CELLS) return GCMC_ERR_RANGE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GCMC_ERR_CUDA;
+    // set-up once per device, with that device current: the device address of the scratch array
+    NoallocScratch *sc = g_noalloc_addr[dev].load();
+    if (!sc) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc) != cudaSuccess || !p) return GCMC_ERR_CUDA;
+        sc = static_cast<NoallocScratch *>(p);
+        g_noalloc_addr[dev].store(sc);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nblk = (int)((ncell + EMIS_SCAN_BLOCK - 1) / EMIS_SCAN_BLOCK);
+    count_launch(7);
+    k_noalloc_job<<<1, 1, 0, st>>>(sc, cdf, wcell, totals);
+    k_noalloc_copy<<<(unsigned)std::min<int64_t>((ncell + 255) / 256, 4096), 256, 0, st>>>(lum, cdf, ncell);
+    const PrepJob *pj = &sc->job;
+    dim3 g3((unsigned)nblk, 1u);
+    k_emis_reduce<<<g3, EMIS_SCAN_BLOCK, 0, st>>>(ncell, pj);
+    k_emis_total<<<1, 128, 0, st>>>(nblk, pj, 1);
+    k_emis_pdf<<<g3, EMIS_SCAN_BLOCK, 0, st>>>(ncell, pj, beta);
+    k_emis_scan_blocks<<<1, 128, 0, st>>>(nblk, pj, 1);
+    k_emis_cdf_add<<<g3, EMIS_SCAN_BLOCK, 0, st>>>(ncell, pj);
+    return cudaGetLastError() == cudaSuccess ? GCMC_OK : GCMC_ERR_CUDA;
+}

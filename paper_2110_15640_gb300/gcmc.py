@@ -111,6 +111,8 @@ def lib():
             "gcmc_get_profile": ([C.c_void_p, P(C.c_double), P(C.c_double), P(C.c_int64)], C.c_int),
             "gcmc_kernel_launches": ([], C.c_int64),
             "gcmc_gather_bench": ([C.c_void_p, C.c_int64, C.c_int, C.c_int64, P(C.c_double)], C.c_int),
+            "gcmc_emission_pdf_noalloc": ([C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_void_p], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -124,7 +126,9 @@ EXPORTED = ["gcmc_create", "gcmc_destroy", "gcmc_set_stream", "gcmc_set_allocato
             "gcmc_upload_grid", "gcmc_upload_opacity", "gcmc_set_source", "gcmc_run_packets", "gcmc_run_batch",
             "gcmc_submit", "gcmc_poll", "gcmc_run_packets_debug", "gcmc_prep_cells", "gcmc_postscale",
             "gcmc_selftest_philox", "gcmc_version", "gcmc_release_grid", "gcmc_release_opacity",
-            "gcmc_set_profiling", "gcmc_get_profile", "gcmc_kernel_launches", "gcmc_gather_bench"]
+            "gcmc_set_profiling", "gcmc_get_profile", "gcmc_kernel_launches", "gcmc_gather_bench",
+            "gcmc_emission_pdf_noalloc"]
+NOALLOC_MAX_CELLS = 4194304
 
 
 class GcmcError(RuntimeError):
@@ -377,6 +381,14 @@ class Context:
         b = np.zeros((n, 4), np.uint32)
         self._check(lib().gcmc_selftest_philox(self.h, _ptr(ctr), _ptr(key), n, _ptr(a), _ptr(b)), "gcmc_selftest_philox")
         return a, b
+
+
+def emission_pdf_noalloc(lum, ncell, beta, cdf, wcell, totals, stream=None):
+    """Allocation-free emission pdf stage: every argument array is caller-owned device memory (torch
+    CUDA tensors of float64).  Returns the gcmc status code; the work is queued on `stream`."""
+    handle = getattr(stream, "cuda_stream", stream)
+    return int(lib().gcmc_emission_pdf_noalloc(_ptr(lum), int(ncell), float(beta), _ptr(cdf), _ptr(wcell),
+                                               _ptr(totals), C.c_void_p(int(handle) if handle else 0)))
 
 
 def kernel_launches():
