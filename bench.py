@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--interval", type=int, default=0)
     ap.add_argument("--refill", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
     return ap.parse_args()
 
@@ -185,10 +186,10 @@ def main():
     with torch.cuda.stream(stream):
         gid, oid, sid, jobs = gcmc.load_workload(ctx, wl, gcmc.FP32, device_inputs=True)
         tall = torch.zeros((len(jobs), gcmc.MAX_OBS), dtype=torch.float64, device="cuda")
-        if args.no_tune or args.block or args.chunk or args.interval or args.refill:
-            cfg = gcmc.gcmc_launch_cfg(args.block, 0, args.chunk, args.interval, args.refill, 0)
-            tuned = {"block": args.block or 128, "chunk": args.chunk or 1024, "interval": args.interval or 1,
-                     "refill_min": args.refill or 16}
+        if args.no_tune or args.block or args.chunk or args.interval or args.refill or args.blocks_per_sm:
+            cfg = gcmc.gcmc_launch_cfg(args.block, args.blocks_per_sm, args.chunk, args.interval, args.refill, 0)
+            tuned = {"block": args.block or 128, "blocks_per_sm": args.blocks_per_sm, "chunk": args.chunk or 1024,
+                     "interval": args.interval or 1, "refill_min": args.refill or 16}
         else:   # untimed search on 16 of the jobs (tallies do not depend on the launch parameters)
             cfg, tuned, _ = autotune.tune(ctx, jobs[:16], stream, reps=1)
         _, sts = ctx.run_batch(jobs, cfg=cfg)                       # untimed: exact packet-step count
@@ -236,7 +237,7 @@ def main():
     p1.record(stream)
     torch.cuda.synchronize()
     t_plain = p0.elapsed_time(p1) / 1e3
-    plain_value = steps_per_step * args.plain_steps / t_plain
+    plain_value = steps_per_step * args.plain_steps / t_plain if args.plain_steps else None
 
     # ---------------- end to end through the C ABI from pinned host buffers
     ga, oa = gcmc.workload_arrays(wl, "pinned")
@@ -258,8 +259,8 @@ def main():
         F_band = F @ wl.opac.wg[:args.gpoints]
         ctx.release_grid(g2)
     torch.cuda.synchronize()
-    t_e2e = (time.perf_counter() - te) / args.e2e_steps
-    e2e_value = steps_per_step / t_e2e
+    t_e2e = (time.perf_counter() - te) / max(args.e2e_steps, 1)
+    e2e_value = steps_per_step / t_e2e if args.e2e_steps else None
 
     # ---------------- roofline of the transport kernel and the gather roofline
     tr_avg = tr_ms / max(ntr, 1) / 1e3
@@ -284,11 +285,12 @@ def main():
                        "grid": "128x64x50", "packet_steps_per_step": steps_per_step,
                        "packets_per_step": packets_per_step, "capped_weight": capped,
                        "l2": "inputs larger than L2 (per-step cell tables ~2 GB)",
-                       "precision": "FP32 march, FP64 emission pdf, 64-bit fixed-point tallies",
+                       "precision": "FP32 march and opacities, FP64 luminosities, 64-bit fixed-point pdf and tallies",
                        "launch": tuned},
-            "plain_form": {"value": plain_value, "unit": "packet-steps/s", "ms_per_step": 1e3 * t_plain / args.plain_steps,
+            "plain_form": {"value": plain_value, "unit": "packet-steps/s",
+                           "ms_per_step": 1e3 * t_plain / args.plain_steps if args.plain_steps else None,
                            "launches_per_step": len(jobs)},
-            "batched_over_plain": value / plain_value,
+            "batched_over_plain": value / plain_value if plain_value else None,
             "e2e": {"value": e2e_value, "unit": "packet-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * t_e2e},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_OPS / 1e12, "unit": "TFLOP/s",

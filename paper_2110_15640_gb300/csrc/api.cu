@@ -151,6 +151,9 @@ void perp_basis(const double s[3], double e1[3], double e2[3])
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Planck prefactor 2 h c^2 / lambda^5 of B_lambda (SI)
+double planck_c1(double lam) { return 2.0 * 6.62607015e-34 * 2.99792458e8 * 2.99792458e8 / std::pow(lam, 5.0); }
+
 // ------------------------------------------------------------------ run planning
 struct Group {
     int grid, opac, mode, precision, source;
@@ -161,9 +164,11 @@ struct Plan {
     std::vector<DevJob> jobs;
     std::vector<PrepJob> prep;          // in group order (members of a group are contiguous)
     std::vector<int> prep_pos;          // position of job q in `prep`
+    std::vector<int> job_group;         // group of job q
     std::vector<Group> groups;
     std::vector<size_t> off_rec, off_cdf, off_w, off_info, off_bsum, off_bcnt;
-    std::vector<size_t> g_off_ab, g_off_w, g_off_fac, g_first;
+    std::vector<size_t> g_off_ab, g_off_w, g_off_fac, g_off_vb, g_first;
+    std::vector<int> g_nslots;          // emission: distinct band wavelengths of the group
     size_t off_jobs = 0, off_prep = 0, off_acc = 0, off_work = 0, off_gather = 0, ws_bytes = 0;
     int64_t total_items = 0;
     bool scatter = false;               // some job follows scattered packets (albedo)
@@ -205,6 +210,7 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
     }
     P.jobs.resize(n);
     P.prep_pos.resize(n);
+    P.job_group.assign(n, 0);
     P.off_rec.assign(n, 0);
     P.off_cdf.assign(n, 0);
     P.off_w.assign(n, 0);
@@ -227,6 +233,7 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
             gi = (int)P.groups.size() - 1;
         }
         P.groups[gi].members.push_back(q);
+        P.job_group[q] = gi;
     }
     size_t ws = 0;
     for (int q = 0; q < n; ++q) {
@@ -237,11 +244,12 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
         P.off_rec[q] = ws;
         ws += align256((size_t)ncell * (j.mode == GCMC_ALBEDO ? 4 * esz : esz));
         if (j.mode == GCMC_EMISSION) {
-            const int64_t nblk = (ncell + EMIS_SCAN_BLOCK - 1) / EMIS_SCAN_BLOCK;
+            const int64_t nblk = std::max<int64_t>((ncell + EMIS_SCAN_BLOCK - 1) / EMIS_SCAN_BLOCK,
+                                                   emis_col_blocks(ctx->grids[j.grid_id].dg));
             P.off_cdf[q] = ws;
             ws += align256(ncell * 8);
             P.off_w[q] = ws;
-            ws += align256(ncell * 8);
+            ws += align256(ncell * esz);
             P.off_info[q] = ws;
             ws += 256;
             P.off_bsum[q] = ws;
@@ -254,9 +262,20 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
     P.g_off_ab.resize(ng);
     P.g_off_w.resize(ng);
     P.g_off_fac.resize(ng);
+    P.g_off_vb.assign(ng, 0);
+    P.g_nslots.assign(ng, 0);
     P.g_first.resize(ng);
+    std::vector<std::vector<int>> slot_lams(ng);
     for (size_t g = 0; g < ng; ++g) {
         const int64_t ncell = ctx->grids[P.groups[g].grid].dg.ncell;
+        if (P.groups[g].mode == GCMC_EMISSION) {
+            for (int q : P.groups[g].members)
+                if (std::find(slot_lams[g].begin(), slot_lams[g].end(), jobs[q].lam_idx) == slot_lams[g].end())
+                    slot_lams[g].push_back(jobs[q].lam_idx);
+            P.g_nslots[g] = (int)slot_lams[g].size();
+            P.g_off_vb[g] = ws;
+            ws += align256((size_t)P.g_nslots[g] * ncell * 8);
+        }
         P.g_off_ab[g] = ws;
         ws += align256(ncell * sizeof(int2));
         P.g_off_w[g] = ws;
@@ -291,7 +310,14 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
             pj.lam_hint = j.lam_idx;
             if (o.kind == GCMC_OPAC_KTABLE) {
                 pj.lam_m = o.lam[j.lam_idx];
-                pj.c1 = 2.0 * 6.62607015e-34 * 2.99792458e8 * 2.99792458e8 / std::pow(pj.lam_m, 5.0);
+                pj.c1 = planck_c1(pj.lam_m);
+                pj.bslot = (int)(std::find(slot_lams[g].begin(), slot_lams[g].end(), j.lam_idx) - slot_lams[g].begin());
+                // entry s of the group carries the Planck parameters of band slot s
+                const int s = (int)(P.prep.size() - P.g_first[g]);
+                if (s < P.g_nslots[g]) {
+                    pj.pl_lam = o.lam[slot_lams[g][s]];
+                    pj.pl_c1 = planck_c1(pj.pl_lam);
+                }
             } else if (o.kind == GCMC_OPAC_XSEC) {
                 pj.lam_m = o.lam[j.lam_idx];
             }
@@ -326,6 +352,16 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
         d.p_surv = s.p_surv;
         d.tau_cut = s.tau_peel_cut;
         d.hg_eps = s.hg_iso_eps;
+        for (int a = 0; a < 3; ++a) {
+            d.star_f[a] = (float)d.star[a];
+            d.e1_f[a] = (float)d.e1[a];
+            d.e2_f[a] = (float)d.e2[a];
+        }
+        for (int o = 0; o < MAX_OBS; ++o)
+            for (int a = 0; a < 3; ++a) d.obs_f[o][a] = (float)d.obs[o][a];
+        d.w_rr_f = (float)d.w_rr;
+        d.p_surv_f = (float)d.p_surv;
+        d.hg_eps_f = (float)d.hg_eps;
         d.chunk_begin = items;
         items += (j.n_packets + chunk - 1) / chunk;
     }
@@ -343,9 +379,8 @@ __global__ void k_finalize_jobs(DevJob *jobs, int n)
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     if (jobs[q].mode == GCMC_EMISSION) {
-        const double tot = jobs[q].info[2];
-        jobs[q].cdf_total = tot;
-        jobs[q].cdf_step = jobs[q].n_packets > 0 ? tot / (double)jobs[q].n_packets : 0.0;
+        const long long qtot = reinterpret_cast<const long long *>(jobs[q].info)[INFO_QTOT];
+        jobs[q].cdf_step_fix = jobs[q].n_packets > 0 ? qtot / jobs[q].n_packets : 0;
     }
 }
 
@@ -360,12 +395,13 @@ gcmc_status stage(gcmc_ctx *ctx, Plan &P, char *base, double *lum = nullptr)
         d.rec = pj.rec;
         d.acc = reinterpret_cast<unsigned long long *>(base + P.off_acc) + (size_t)q * ACC_SLOTS;
         if (d.mode == GCMC_EMISSION) {
-            pj.cdf = reinterpret_cast<double *>(base + P.off_cdf[q]);
-            pj.wcell = reinterpret_cast<double *>(base + P.off_w[q]);
+            pj.cdf = reinterpret_cast<long long *>(base + P.off_cdf[q]);
+            pj.wcell = base + P.off_w[q];
             pj.info = reinterpret_cast<double *>(base + P.off_info[q]);
             pj.bsum = reinterpret_cast<double *>(base + P.off_bsum[q]);
             pj.bcnt = reinterpret_cast<double *>(base + P.off_bcnt[q]);
             pj.lum = lum;
+            pj.vb = reinterpret_cast<const double *>(base + P.g_off_vb[P.job_group[q]]);
             d.cdf = pj.cdf;
             d.wcell = pj.wcell;
             d.info = pj.info;
@@ -388,8 +424,8 @@ gcmc_status stage(gcmc_ctx *ctx, Plan &P, char *base, double *lum = nullptr)
             e = prep_albedo(G.precision, ctx->d_grids + G.grid, gh.dg, oh.alb, gp, m, ctx->stream);
         } else if (G.mode == GCMC_EMISSION) {
             const gcmc_source_desc &s = ctx->sources[G.source];
-            e = prep_emission(G.precision, ctx->d_grids + G.grid, gh.dg, oh.kt, gp, m, s.tau_vert_max, s.beta_emis, ab,
-                              ww, ctx->stream);
+            e = prep_emission(G.precision, ctx->d_grids + G.grid, gh.dg, oh.kt, gp, m, P.g_nslots[g], s.tau_vert_max,
+                              s.beta_emis, ab, ww, ctx->stream);
         } else {
             e = prep_xsec(G.precision, ctx->d_grids + G.grid, gh.dg, oh.xs, gp, m, ab, ww, fac, ctx->stream);
         }
@@ -799,7 +835,21 @@ gcmc_status gcmc_upload_opacity(gcmc_ctx *ctx, int grid_id, const gcmc_opacity_d
             O.kt.ng = d->ng;
             O.kt.nT = d->nT;
             O.kt.np = d->np;
+            // FP32 node records for FP32 marches: {k_ab, d1, d2, d3} with the differences of ln k taken in FP64
+            std::vector<float4> node(nk);
+            const int nT = d->nT, np = d->np;
+            for (size_t sl = 0; sl < (size_t)d->nb * d->ng; ++sl)
+                for (int a = 0; a < nT; ++a)
+                    for (int b = 0; b < np; ++b) {
+                        const size_t i = sl * nT * np + (size_t)a * np + b;
+                        const int a1 = a + 1 < nT ? a + 1 : a, b1 = b + 1 < np ? b + 1 : b;
+                        const double l00 = lnk[i], l10 = lnk[sl * nT * np + (size_t)a1 * np + b];
+                        const double l01 = lnk[sl * nT * np + (size_t)a * np + b1];
+                        const double l11 = lnk[sl * nT * np + (size_t)a1 * np + b1];
+                        node[i] = make_float4(k[i], (float)(l10 - l00), (float)(l01 - l00), (float)(l11 - l10 - l01 + l00));
+                    }
             O.kt.lnk = dput(ctx, O.owned, lnk.data(), nk, e);
+            O.kt.node_f = dput(ctx, O.owned, node.data(), nk, e);
             O.kt.Tg = dput(ctx, O.owned, Tg.data(), d->nT, e);
             O.kt.pg = dput(ctx, O.owned, pg.data(), d->np, e);
             O.lam = lam;
@@ -1061,14 +1111,28 @@ gcmc_status gcmc_prep_cells(gcmc_ctx *ctx, const gcmc_job *job, double *alpha, d
     const int nrec = job->mode == GCMC_ALBEDO ? 4 : 1;
     std::vector<char> raw(ncell * nrec * esz);
     CK(cudaMemcpyAsync(raw.data(), base + P.off_rec[0], raw.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<long long> cq;
+    std::vector<char> wraw;
     if (job->mode == GCMC_EMISSION) {
-        if (cdf) CK(cudaMemcpyAsync(cdf, base + P.off_cdf[0], ncell * 8, cudaMemcpyDeviceToHost, ctx->stream));
-        if (wcell) CK(cudaMemcpyAsync(wcell, base + P.off_w[0], ncell * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        if (cdf) {
+            cq.resize(ncell);
+            CK(cudaMemcpyAsync(cq.data(), base + P.off_cdf[0], ncell * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        if (wcell) {
+            wraw.resize(ncell * esz);
+            CK(cudaMemcpyAsync(wraw.data(), base + P.off_w[0], wraw.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        }
         if (dlum) CK(cudaMemcpyAsync(lum, dlum, ncell * 8, cudaMemcpyDeviceToHost, ctx->stream));
     }
     s = finish_run(ctx, P, base, nullptr, GCMC_MEM_HOST, stats_out, 0);
     dfree(ctx, dlum);
     if (s) return s;
+    // the cumulative pdf as the fraction-scaled value Q / 2^62, the weights widened to FP64
+    for (size_t i = 0; i < cq.size(); ++i) cdf[i] = (double)cq[i] / 4611686018427387904.0;
+    if (!wraw.empty())
+        for (int64_t i = 0; i < ncell; ++i)
+            wcell[i] = f64 ? reinterpret_cast<const double *>(wraw.data())[i]
+                           : (double)reinterpret_cast<const float *>(wraw.data())[i];
     for (int64_t i = 0; i < ncell; ++i) {
         double v[4] = {0, 0, 0, 0};
         for (int c = 0; c < nrec; ++c)

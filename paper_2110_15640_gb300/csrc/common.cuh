@@ -67,14 +67,39 @@ struct DevJob {
     int64_t chunk_begin;        // first work item of this job (batched launches)
     int64_t max_steps;
     const void *rec;            // albedo records, or alpha for absorber marches
-    const double *cdf;          // emission
-    const double *wcell;        // emission
-    const double *info;         // emission: [L_tot, n_incl, cdf_total] written by the cell-table kernels
-    double cdf_total, cdf_step; // emission: total and total / N
+    const long long *cdf;       // emission: cumulative hybrid pdf, 2^62 fixed point
+    const void *wcell;          // emission: launch weights (march precision)
+    const double *info;         // emission: [L_tot, n_incl, cdf_total, ...] written by the cell-table kernels
+    long long cdf_step_fix;     // emission: floor(Q_tot / N), the stratum width in fixed point
     double star[3], e1[3], e2[3];
     double obs[MAX_OBS][3];
     double w_rr, p_surv, tau_cut, hg_eps;
+    // the same vectors and constants rounded once to FP32, for FP32 marches
+    float star_f[3], e1_f[3], e2_f[3];
+    float obs_f[MAX_OBS][3];
+    float w_rr_f, p_surv_f, hg_eps_f, pad2;
     unsigned long long *acc;    // [ACC_SLOTS]
+};
+
+// job constants in the march precision (FP32 marches read the copies rounded on the host)
+template <typename real> struct JV;
+template <> struct JV<double> {
+    static __device__ __forceinline__ double star(const DevJob &J, int q) { return J.star[q]; }
+    static __device__ __forceinline__ double e1(const DevJob &J, int q) { return J.e1[q]; }
+    static __device__ __forceinline__ double e2(const DevJob &J, int q) { return J.e2[q]; }
+    static __device__ __forceinline__ double obs(const DevJob &J, int o, int q) { return J.obs[o][q]; }
+    static __device__ __forceinline__ double w_rr(const DevJob &J) { return J.w_rr; }
+    static __device__ __forceinline__ double p_surv(const DevJob &J) { return J.p_surv; }
+    static __device__ __forceinline__ double hg_eps(const DevJob &J) { return J.hg_eps; }
+};
+template <> struct JV<float> {
+    static __device__ __forceinline__ float star(const DevJob &J, int q) { return J.star_f[q]; }
+    static __device__ __forceinline__ float e1(const DevJob &J, int q) { return J.e1_f[q]; }
+    static __device__ __forceinline__ float e2(const DevJob &J, int q) { return J.e2_f[q]; }
+    static __device__ __forceinline__ float obs(const DevJob &J, int o, int q) { return J.obs_f[o][q]; }
+    static __device__ __forceinline__ float w_rr(const DevJob &J) { return J.w_rr_f; }
+    static __device__ __forceinline__ float p_surv(const DevJob &J) { return J.p_surv_f; }
+    static __device__ __forceinline__ float hg_eps(const DevJob &J) { return J.hg_eps_f; }
 };
 
 // ------------------------------------------------------------------ Philox4x32-10 (Salmon et al. 2011)

@@ -21,21 +21,36 @@ struct HostLog {               // device pointers of the per-packet debug output
 // per-job parameters of the cell-table kernels
 struct PrepJob {
     int32_t lam, g;            // wavelength / band index, g-ordinate
-    int32_t lam_hint, pad;
+    int32_t lam_hint;
+    int32_t bslot;             // emission: row of this job's band in the group's 4 pi V B(T) table
     double lam_m;              // wavelength (m) for the Planck function (k-table) or rest wavelength (xsec)
     double c1;                 // Planck prefactor 2 h c^2 / lambda^5 (k-table)
     void *rec;                 // output: albedo records or alpha (march precision)
-    double *cdf;               // emission: cumulative pdf (also scratch for L)
-    double *wcell;             // emission: launch weight (also scratch for FP64 alpha)
-    double *info;              // emission: [L_tot, n_incl, cdf_total] (device)
+    long long *cdf;            // emission: cumulative pdf in 2^62 fixed point (first scratch for L_i as FP64)
+    void *wcell;               // emission: launch weight (march precision)
+    double *info;              // emission: [L_tot, n_incl, cdf_total, Q_tot bits, constants of the pdf] (device)
     double *bsum;              // emission: per-block partial sums [nblk]
     double *bcnt;              // emission: per-block included counts [nblk]
     double *lum;               // emission: optional copy of L_i (debug), or NULL
+    const double *vb;          // emission: the group's 4 pi V_i B(T_i) table, [band slot][cell]
+    // emission, entry s < number of band slots of the group: wavelength, Planck prefactor of slot s
+    double pl_lam, pl_c1;
+};
+
+// slots of PrepJob::info
+enum : int {
+    INFO_LTOT = 0, INFO_NINCL = 1, INFO_CDFTOT = 2, INFO_QTOT = 3,   // QTOT: int64 bits
+    INFO_QA = 4, INFO_QB = 5,                                        // Q_i = rint(QA L_i + QB)
+    INFO_INVL = 6, INFO_BN = 7,                                      // 1 / L_tot, beta / n_incl
 };
 
 struct KtabDev {               // device k-table (natural logs in FP64)
     int nb, ng, nT, np;
     const double *lnk;         // [nb][ng][nT][np]
+    // FP32 node records {k_ab, ln k_(a+1)b - ln k_ab, ln k_a(b+1) - ln k_ab, mixed second difference}:
+    // k = k_ab exp(wT d1 + wp d2 + wT wp d3) is the bilinear interpolation of ln k with an argument of
+    // order one, so FP32 keeps ~1e-7 relative accuracy (ln k itself would lose ~ulp(10))
+    const float4 *node_f;      // [nb][ng][nT][np]
     const double *Tg, *pg;     // axes
 };
 
@@ -61,8 +76,9 @@ constexpr int EMIS_SCAN_BLOCK = 1024;
 cudaError_t prep_albedo(int precision, const DevGrid *dgrid, const DevGrid &hgrid, const AlbDev &op,
                         const PrepJob *djobs, int njobs, cudaStream_t st);
 cudaError_t prep_emission(int precision, const DevGrid *dgrid, const DevGrid &hgrid, const KtabDev &kt,
-                          const PrepJob *djobs, int njobs, double tau_vert_max, double beta, int2 *wk_ab,
-                          double2 *wk_w, cudaStream_t st);
+                          const PrepJob *djobs, int njobs, int nslots, double tau_vert_max, double beta, int2 *wk_ab,
+                          void *wk_w, cudaStream_t st);
+int emis_col_blocks(const DevGrid &g);     // partial-sum blocks of the column kernel
 cudaError_t prep_xsec(int precision, const DevGrid *dgrid, const DevGrid &hgrid, const XsecDev &xs,
                       const PrepJob *djobs, int njobs, int2 *wk_ab, double2 *wk_w, double *wk_fac, cudaStream_t st);
 

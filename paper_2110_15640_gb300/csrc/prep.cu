@@ -6,9 +6,11 @@
 //   emission     alpha = rho k(T, p) from the correlated-k table (bilinear in ln T, ln p of ln k),
 //                L_i = 4 pi V_i alpha_i B_lambda(T_i) (Sect. 5.3), the tau_vert cut (Sect. 4.6),
 //                hybrid pdf q_i = (1 - beta) L_i/L_tot + beta/N'_c and launch weight (L_i/L_tot)/q_i
-//                (Sect. 4.3), and its cumulative sum.  All in FP64, because the cumulative pdf decides
-//                integers (the launch cell of every packet); the march table is alpha rounded to the
-//                march precision.
+//                (Sect. 4.3), and its cumulative sum in 64-bit fixed point (exact, monotone, flat
+//                over excluded cells).  4 pi V B(T) is computed once per band (FP64); L_i, L_tot and
+//                the fixed-point pdf are FP64.  FP64 runs compute alpha and the weights in FP64 term
+//                by term; FP32 runs compute alpha in FP32 (~3e-7 relative) and FP32 weights, which is
+//                what their march and tallies consume.
 //   transmission per-cell v_LOS (Sect. 7), lambda_eff = lambda_0 (1 - v_LOS / c), cross-section
 //                interpolated linearly in ln sigma between the bracketing table wavelengths and
 //                bilinearly in (ln T, ln p); FP32 in FP32 runs (no integer decision depends on it).
@@ -16,6 +18,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -82,7 +85,13 @@ cudaError_t prep_albedo(int precision, const DevGrid *, const DevGrid &hg, const
 }
 
 // ------------------------------------------------------------------ interpolation weights (T, p)
-__global__ void k_tp_weights(DevGrid G, const double *Tg, int nT, const double *pg, int np, int2 *ab, double2 *w)
+template <typename real> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+template <typename real>
+__global__ void k_tp_weights(DevGrid G, const double *Tg, int nT, const double *pg, int np, int2 *ab,
+                             typename Vec2<real>::type *w)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= G.ncell) return;
@@ -91,57 +100,117 @@ __global__ void k_tp_weights(DevGrid G, const double *Tg, int nT, const double *
     interp_idx(Tg, nT, (double)G.T[idx], a, wT);
     interp_idx(pg, np, (double)G.p[idx], b, wp);
     ab[idx] = make_int2(a, b);
-    w[idx] = make_double2(wT, wp);
+    w[idx] = {(real)wT, (real)wp};
 }
 
 // ------------------------------------------------------------------ emission
-template <typename real>
-__global__ void k_emis_alpha(DevGrid G, KtabDev kt, const PrepJob *__restrict__ jobs, const int2 *__restrict__ ab,
-                             const double2 *__restrict__ w)
+// 4 pi V_i B_lambda(T_i) once per distinct band wavelength of the group (the g-ordinates of a band
+// share it); row s of the table belongs to the wavelength carried by entry s of the job array
+__global__ void k_emis_planck(DevGrid G, const PrepJob *__restrict__ jobs)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= G.ncell) return;
-    const PrepJob pj = jobs[blockIdx.y];
-    const int2 q = ab[idx];
-    const double wT = w[idx].x, wp = w[idx].y;
-    const double *base = kt.lnk + ((int64_t)pj.lam * kt.ng + pj.g) * kt.nT * kt.np;
-    const double l00 = base[q.x * kt.np + q.y], l10 = base[(q.x + 1) * kt.np + q.y];
-    const double l01 = base[q.x * kt.np + q.y + 1], l11 = base[(q.x + 1) * kt.np + q.y + 1];
-    const double lk = (1 - wT) * (1 - wp) * l00 + wT * (1 - wp) * l10 + (1 - wT) * wp * l01 + wT * wp * l11;
-    const double alpha = (double)G.rho[idx] * exp(lk);
-    const double x = H_PLANCK * C_LIGHT / (pj.lam_m * K_BOLTZ * (double)G.T[idx]);
-    const double B = pj.c1 / expm1(x);
-    const double L = 4.0 * PI * G.vol[idx] * alpha * B;
-    reinterpret_cast<real *>(pj.rec)[idx] = (real)alpha;
-    pj.cdf[idx] = L;
-    pj.wcell[idx] = alpha;
-    if (pj.lum) pj.lum[idx] = L;
+    const double lam = jobs[blockIdx.y].pl_lam, c1 = jobs[blockIdx.y].pl_c1;
+    const double x = H_PLANCK * C_LIGHT / (lam * K_BOLTZ * (double)G.T[idx]);
+    double *vb = const_cast<double *>(jobs[0].vb);
+    vb[(int64_t)blockIdx.y * G.ncell + idx] = 4.0 * PI * G.vol[idx] * (c1 / expm1(x));
 }
 
-// tau_vert cut along each column, from the top: a cell emits if the vertical optical depth above it
-// is below tau_vert_max; excluded cells are marked with L = -1
-__global__ void k_emis_cut(DevGrid G, const PrepJob *__restrict__ jobs, double tau_vert_max)
+constexpr int COL_BLOCK = 128;
+
+int emis_col_blocks(const DevGrid &g) { return (int)(((int64_t)g.nlon * g.nlat + COL_BLOCK - 1) / COL_BLOCK); }
+
+// One thread per (job, column), walking the column from the top: alpha = rho k(T, p), the tau_vert
+// cut (a cell emits if the vertical optical depth above it is below tau_vert_max), L_i = 4 pi V_i
+// B(T_i) alpha_i, and per-block partial sums of L and of the emitting-cell count (fixed order).
+// Excluded cells get L = -1 in the scratch copy that the pdf kernel reads.
+template <typename real>
+__global__ void __launch_bounds__(COL_BLOCK) k_emis_column(DevGrid G, KtabDev kt, const PrepJob *__restrict__ jobs,
+                                                           const int2 *__restrict__ ab,
+                                                           const typename Vec2<real>::type *__restrict__ w,
+                                                           double tau_vert_max)
 {
-    const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    extern __shared__ __align__(16) unsigned char col_smem[];
+    real *s_dr = reinterpret_cast<real *>(col_smem);     // layer thicknesses [nr]
+    __shared__ double red_s[COL_BLOCK / 32];
+    __shared__ int red_c[COL_BLOCK / 32];
+    for (int k = threadIdx.x; k < G.nr; k += blockDim.x) s_dr[k] = (real)(G.r[k + 1] - G.r[k]);
+    __syncthreads();
+    const PrepJob &pj = jobs[blockIdx.y];
     const int64_t ncol = (int64_t)G.nlon * G.nlat;
-    if (col >= ncol) return;
-    const PrepJob pj = jobs[blockIdx.y];
-    double above = 0.0;
-    for (int k = G.nr - 1; k >= 0; --k) {
-        const int64_t idx = k * ncol + col;
-        const bool incl = above < tau_vert_max;
-        above += pj.wcell[idx] * (G.r[k + 1] - G.r[k]);
-        if (!incl) pj.cdf[idx] = -1.0;
+    const int64_t col = (int64_t)blockIdx.x * COL_BLOCK + threadIdx.x;
+    double lsum = 0.0;
+    int cnt = 0;
+    if (col < ncol) {
+        const double *__restrict__ vb = pj.vb + (int64_t)pj.bslot * G.ncell;
+        real *__restrict__ rec = reinterpret_cast<real *>(pj.rec);
+        double *__restrict__ lb = reinterpret_cast<double *>(pj.cdf);
+        double *__restrict__ lum = pj.lum;
+        const int64_t slice = ((int64_t)pj.lam * kt.ng + pj.g) * kt.nT * kt.np;
+        const real tmax = (real)tau_vert_max;
+        real above = (real)0;
+        for (int k = G.nr - 1; k >= 0; --k) {
+            const int64_t idx = k * ncol + col;
+            const int2 q = ab[idx];
+            real alpha;
+            if constexpr (sizeof(real) == 8) {
+                const double2 ww = w[idx];
+                const double wT = ww.x, wp = ww.y;
+                const double *base = kt.lnk + slice;
+                const double l00 = base[q.x * kt.np + q.y], l10 = base[(q.x + 1) * kt.np + q.y];
+                const double l01 = base[q.x * kt.np + q.y + 1], l11 = base[(q.x + 1) * kt.np + q.y + 1];
+                const double lk = (1 - wT) * (1 - wp) * l00 + wT * (1 - wp) * l10 + (1 - wT) * wp * l01 + wT * wp * l11;
+                alpha = (double)G.rho[idx] * exp(lk);
+            } else {
+                const float2 ww = w[idx];
+                const float4 nd = __ldg(kt.node_f + slice + q.x * kt.np + q.y);
+                alpha = (G.rho[idx] * nd.x) * expf(fmaf(ww.x, fmaf(ww.y, nd.w, nd.y), ww.y * nd.z));
+            }
+            rec[idx] = alpha;
+            const bool incl = above < tmax;
+            above += alpha * s_dr[k];
+            const double L = vb[idx] * (double)alpha;
+            if (lum) lum[idx] = L;
+            if (incl) {
+                lb[idx] = L;
+                lsum += L;
+                ++cnt;
+            } else {
+                lb[idx] = -1.0;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+        cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red_s[threadIdx.x >> 5] = lsum;
+        red_c[threadIdx.x >> 5] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        int c = 0;
+        for (int q = 0; q < COL_BLOCK / 32; ++q) {
+            s += red_s[q];
+            c += red_c[q];
+        }
+        pj.bsum[blockIdx.x] = s;
+        pj.bcnt[blockIdx.x] = (double)c;
     }
 }
 
-// per-block sums of L over the emitting cells and their count (fixed tree order)
+// per-block sums of L over the emitting cells (L >= 0) and their count, for an L array given directly
+// (the allocation-free entry point)
 __global__ void k_emis_reduce(int64_t ncell, const PrepJob *__restrict__ jobs)
 {
     __shared__ double ss[EMIS_SCAN_BLOCK / 32], sc[EMIS_SCAN_BLOCK / 32];
     const PrepJob pj = jobs[blockIdx.y];
     const int64_t idx = (int64_t)blockIdx.x * EMIS_SCAN_BLOCK + threadIdx.x;
-    double L = idx < ncell ? pj.cdf[idx] : -1.0;
+    const double *lb = reinterpret_cast<const double *>(pj.cdf);
+    double L = idx < ncell ? lb[idx] : -1.0;
     double v = L >= 0.0 ? L : 0.0, c = L >= 0.0 ? 1.0 : 0.0;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -168,24 +237,41 @@ __global__ void k_emis_reduce(int64_t ncell, const PrepJob *__restrict__ jobs)
     }
 }
 
-__global__ void k_emis_total(int nblk, const PrepJob *__restrict__ jobs, int njobs)
+// The cumulative pdf is accumulated in 64-bit fixed point, Q_i = round(q_i 2^62) (sum <= 2^62 (1 + eps)):
+// integer prefix sums are exact in any order, so the cumulative sum is monotone and exactly flat over
+// cells with zero pdf, whatever the block and warp structure of the scan.
+constexpr double CDF_FIX = 4611686018427387904.0;   // 2^62
+
+// totals of the partial sums (fixed order) and the per-job constants of the hybrid pdf
+// q_i = (1 - beta) L_i / L_tot + beta / n_incl (Sect. 4.3)
+__global__ void k_emis_total(int nparts, const PrepJob *__restrict__ jobs, int njobs, double beta)
 {
     const int jb = blockIdx.x * blockDim.x + threadIdx.x;
     if (jb >= njobs) return;
     const PrepJob pj = jobs[jb];
     double s = 0.0, c = 0.0;
-    for (int b = 0; b < nblk; ++b) {
+    for (int b = 0; b < nparts; ++b) {
         s += pj.bsum[b];
         c += pj.bcnt[b];
     }
-    pj.info[0] = s;
-    pj.info[1] = c;
+    double qa = 0.0, qb = 0.0, invl = 0.0, bn = 0.0;
+    if (c > 0.0) {
+        if (s > 0.0) {
+            qa = (1.0 - beta) / s * CDF_FIX;
+            qb = beta / c * CDF_FIX;
+            invl = 1.0 / s;
+            bn = beta / c;
+        } else {
+            qb = CDF_FIX / c;
+        }
+    }
+    pj.info[INFO_LTOT] = s;
+    pj.info[INFO_NINCL] = c;
+    pj.info[INFO_QA] = qa;
+    pj.info[INFO_QB] = qb;
+    pj.info[INFO_INVL] = invl;
+    pj.info[INFO_BN] = bn;
 }
-
-// The cumulative pdf is accumulated in 64-bit fixed point, Q_i = round(q_i 2^62) (sum <= 2^62 (1 + eps)):
-// integer prefix sums are exact in any order, so the cumulative sum is monotone and exactly flat over
-// cells with zero pdf, whatever the block and warp structure of the scan.
-constexpr double CDF_FIX = 4611686018427387904.0;   // 2^62
 
 __device__ __forceinline__ long long warp_incl_scan_ll(long long v)
 {
@@ -198,35 +284,49 @@ __device__ __forceinline__ long long warp_incl_scan_ll(long long v)
     return v;
 }
 
-// hybrid pdf, launch weights and the per-block inclusive scan of the fixed-point pdf
+// hybrid pdf, launch weight (L_i / L_tot) / q_i and the per-block inclusive scan of the fixed-point pdf.
+// FP64 weights follow the definition term by term; FP32 weights are p / ((1 - beta) p + beta / n) with
+// p = L_i / L_tot rounded to FP32, and the fixed-point pdf is rint(QA L_i + QB) (one FP64 FMA).
+template <typename WT>
 __global__ void k_emis_pdf(int64_t ncell, const PrepJob *__restrict__ jobs, double beta)
 {
     __shared__ long long ws[EMIS_SCAN_BLOCK / 32];
-    const PrepJob pj = jobs[blockIdx.y];
+    const PrepJob &pj = jobs[blockIdx.y];
     const int64_t idx = (int64_t)blockIdx.x * EMIS_SCAN_BLOCK + threadIdx.x;
-    const double Ltot = pj.info[0], nincl = pj.info[1];
-    double q = 0.0, wgt = 0.0;
+    long long Q = 0;
+    WT wgt = (WT)0;
     if (idx < ncell) {
-        const double L = pj.cdf[idx];
-        if (L >= 0.0 && nincl > 0.0) {
-            if (Ltot > 0.0) {
-                q = (1.0 - beta) * L / Ltot + beta / nincl;
-                wgt = q > 0.0 ? (L / Ltot) / q : 0.0;
-            } else {
-                q = 1.0 / nincl;
+        const double L = reinterpret_cast<const double *>(pj.cdf)[idx];
+        if constexpr (sizeof(WT) == 8) {
+            const double Ltot = pj.info[INFO_LTOT], nincl = pj.info[INFO_NINCL];
+            if (L >= 0.0 && nincl > 0.0) {
+                double q;
+                if (Ltot > 0.0) {
+                    q = (1.0 - beta) * L / Ltot + beta / nincl;
+                    wgt = q > 0.0 ? (L / Ltot) / q : 0.0;
+                } else {
+                    q = 1.0 / nincl;
+                }
+                Q = __double2ll_rn(q * CDF_FIX);
+            }
+        } else {
+            if (L >= 0.0) {
+                Q = __double2ll_rn(fma(pj.info[INFO_QA], L, pj.info[INFO_QB]));
+                const float p = (float)(L * pj.info[INFO_INVL]);
+                const float qf = fmaf((float)(1.0 - beta), p, (float)pj.info[INFO_BN]);
+                wgt = qf > 0.0f ? p / qf : 0.0f;
             }
         }
     }
-    long long s = warp_incl_scan_ll(__double2ll_rn(q * CDF_FIX));
+    long long s = warp_incl_scan_ll(Q);
     if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x < 32) ws[threadIdx.x] = warp_incl_scan_ll(ws[threadIdx.x]);
     __syncthreads();
     if (threadIdx.x >= 32) s += ws[(threadIdx.x >> 5) - 1];
-    long long *cq = reinterpret_cast<long long *>(pj.cdf);   // within-block prefix, as integers until cdf_add
     if (idx < ncell) {
-        cq[idx] = s;
-        pj.wcell[idx] = wgt;
+        pj.cdf[idx] = s;     // within-block prefix until cdf_add
+        reinterpret_cast<WT *>(pj.wcell)[idx] = wgt;
     }
     if (threadIdx.x == EMIS_SCAN_BLOCK - 1) reinterpret_cast<long long *>(pj.bsum)[blockIdx.x] = s;
 }
@@ -244,38 +344,48 @@ __global__ void k_emis_scan_blocks(int nblk, const PrepJob *__restrict__ jobs, i
         off[b] = run;
         run += t;
     }
-    pj.info[2] = (double)run / CDF_FIX;
+    pj.info[INFO_CDFTOT] = (double)run / CDF_FIX;
+    reinterpret_cast<long long *>(pj.info)[INFO_QTOT] = run;
 }
 
+// block offsets added to the within-block prefixes: the fixed-point cumulative pdf itself (OUT =
+// long long, what the launch searches) or its value as FP64 (OUT = double)
+template <typename OUT>
 __global__ void k_emis_cdf_add(int64_t ncell, const PrepJob *__restrict__ jobs)
 {
-    const PrepJob pj = jobs[blockIdx.y];
+    const PrepJob &pj = jobs[blockIdx.y];
     const int64_t idx = (int64_t)blockIdx.x * EMIS_SCAN_BLOCK + threadIdx.x;
     if (idx >= ncell) return;
-    long long *cq = reinterpret_cast<long long *>(pj.cdf);
-    const long long v = cq[idx] + reinterpret_cast<const long long *>(pj.bcnt)[blockIdx.x];
-    pj.cdf[idx] = (double)v / CDF_FIX;
+    const long long v = pj.cdf[idx] + reinterpret_cast<const long long *>(pj.bcnt)[blockIdx.x];
+    if constexpr (std::is_same<OUT, double>::value) reinterpret_cast<double *>(pj.cdf)[idx] = (double)v / CDF_FIX;
+    else pj.cdf[idx] = v;
 }
 
 cudaError_t prep_emission(int precision, const DevGrid *, const DevGrid &hg, const KtabDev &kt, const PrepJob *djobs,
-                          int njobs, double tau_vert_max, double beta, int2 *wk_ab, double2 *wk_w, cudaStream_t st)
+                          int njobs, int nslots, double tau_vert_max, double beta, int2 *wk_ab, void *wk_w,
+                          cudaStream_t st)
 {
-    count_launch(8);
+    count_launch(7);
+    const bool f64 = precision == GCMC_FP64;
     const unsigned nb = (unsigned)((hg.ncell + PREP_BLOCK - 1) / PREP_BLOCK);
-    k_tp_weights<<<nb, PREP_BLOCK, 0, st>>>(hg, kt.Tg, kt.nT, kt.pg, kt.np, wk_ab, wk_w);
-    dim3 g1(nb, (unsigned)njobs);
-    if (precision == GCMC_FP64) k_emis_alpha<double><<<g1, PREP_BLOCK, 0, st>>>(hg, kt, djobs, wk_ab, wk_w);
-    else k_emis_alpha<float><<<g1, PREP_BLOCK, 0, st>>>(hg, kt, djobs, wk_ab, wk_w);
-    const int64_t ncol = (int64_t)hg.nlon * hg.nlat;
-    dim3 g2((unsigned)((ncol + 127) / 128), (unsigned)njobs);
-    k_emis_cut<<<g2, 128, 0, st>>>(hg, djobs, tau_vert_max);
+    if (f64) k_tp_weights<double><<<nb, PREP_BLOCK, 0, st>>>(hg, kt.Tg, kt.nT, kt.pg, kt.np, wk_ab, (double2 *)wk_w);
+    else k_tp_weights<float><<<nb, PREP_BLOCK, 0, st>>>(hg, kt.Tg, kt.nT, kt.pg, kt.np, wk_ab, (float2 *)wk_w);
+    k_emis_planck<<<dim3(nb, (unsigned)nslots), PREP_BLOCK, 0, st>>>(hg, djobs);
+    const int ncolb = emis_col_blocks(hg);
+    const dim3 gc((unsigned)ncolb, (unsigned)njobs);
+    if (f64)
+        k_emis_column<double><<<gc, COL_BLOCK, hg.nr * sizeof(double), st>>>(hg, kt, djobs, wk_ab, (const double2 *)wk_w,
+                                                                             tau_vert_max);
+    else
+        k_emis_column<float><<<gc, COL_BLOCK, hg.nr * sizeof(float), st>>>(hg, kt, djobs, wk_ab, (const float2 *)wk_w,
+                                                                           tau_vert_max);
+    k_emis_total<<<(njobs + 127) / 128, 128, 0, st>>>(ncolb, djobs, njobs, beta);
     const int nblk = (int)((hg.ncell + EMIS_SCAN_BLOCK - 1) / EMIS_SCAN_BLOCK);
-    dim3 g3((unsigned)nblk, (unsigned)njobs);
-    k_emis_reduce<<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs);
-    k_emis_total<<<(njobs + 127) / 128, 128, 0, st>>>(nblk, djobs, njobs);
-    k_emis_pdf<<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
+    const dim3 g3((unsigned)nblk, (unsigned)njobs);
+    if (f64) k_emis_pdf<double><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
+    else k_emis_pdf<float><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
     k_emis_scan_blocks<<<(njobs + 127) / 128, 128, 0, st>>>(nblk, djobs, njobs);
-    k_emis_cdf_add<<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs);
+    k_emis_cdf_add<long long><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs);
     return cudaGetLastError();
 }
 
@@ -446,7 +556,7 @@ __global__ void k_noalloc_job(NoallocScratch *sc, double *cdf, double *wcell, do
 {
     gcmc::PrepJob j;
     memset(&j, 0, sizeof(j));
-    j.cdf = cdf;
+    j.cdf = reinterpret_cast<long long *>(cdf);
     j.wcell = wcell;
     j.info = totals;
     j.bsum = sc->bsum;
@@ -487,9 +597,9 @@ extern "C" gcmc_status gcmc_emission_pdf_noalloc(const double *lum, int64_t ncel
     const PrepJob *pj = &sc->job;
     dim3 g3((unsigned)nblk, 1u);
     k_emis_reduce<<<g3, EMIS_SCAN_BLOCK, 0, st>>>(ncell, pj);
-    k_emis_total<<<1, 128, 0, st>>>(nblk, pj, 1);
-    k_emis_pdf<<<g3, EMIS_SCAN_BLOCK, 0, st>>>(ncell, pj, beta);
+    k_emis_total<<<1, 128, 0, st>>>(nblk, pj, 1, beta);
+    k_emis_pdf<double><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(ncell, pj, beta);
     k_emis_scan_blocks<<<1, 128, 0, st>>>(nblk, pj, 1);
-    k_emis_cdf_add<<<g3, EMIS_SCAN_BLOCK, 0, st>>>(ncell, pj);
+    k_emis_cdf_add<double><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(ncell, pj);
     return cudaGetLastError() == cudaSuccess ? GCMC_OK : GCMC_ERR_CUDA;
 }

@@ -107,7 +107,7 @@ template <typename real, class SinkT>
 __device__ __forceinline__ void start_peel(Packet<real> &P, const DevJob &J, SinkT &S)
 {
     S.trace(P.n, -2, (real)0);
-    start_ray<real>(P, P.ix, P.iy, P.iz, (real)J.obs[P.obs][0], (real)J.obs[P.obs][1], (real)J.obs[P.obs][2], P.ci,
+    start_ray<real>(P, P.ix, P.iy, P.iz, JV<real>::obs(J, P.obs, 0), JV<real>::obs(J, P.obs, 1), JV<real>::obs(J, P.obs, 2), P.ci,
                     P.cj, P.ck, K_PEEL, (real)-1);
 }
 
@@ -184,8 +184,8 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
         real x[3], d[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            x[q] = b * (cp * (real)J.e1[q] + sp * (real)J.e2[q]) + h * (real)J.star[q];
-            d[q] = -(real)J.star[q];
+            x[q] = b * (cp * JV<real>::e1(J, q) + sp * JV<real>::e2(J, q)) + h * JV<real>::star(J, q);
+            d[q] = -JV<real>::star(J, q);
         }
         int i, j;
         locate_angles<real>(G, x[0], x[1], x[2], i, j);
@@ -209,9 +209,12 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
         return;
     }
     // emission: stratified inverse-CDF draw of the cell over the hybrid pdf
-    const double target = ((double)n + u01<double>(w.x)) * J.cdf_step;
-    const int idx = cdf_find(reinterpret_cast<const long long *>(J.cdf), (int)G.ncell, __double_as_longlong(target),
-                             P.hint);
+    // stratified target (n + u) Q_tot / N in 2^62 fixed point with u = (m + 1/2) 2^-24, m the top 24
+    // bits of the word: n step + floor((2m + 1) step / 2^25), exact integer arithmetic (< Q_tot)
+    const unsigned long long step = (unsigned long long)J.cdf_step_fix;
+    const long long target = (long long)((unsigned long long)n * step +
+                                         __umul64hi((unsigned long long)(2u * (w.x >> 8) + 1u) << 39, step));
+    const int idx = cdf_find(J.cdf, (int)G.ncell, target, P.hint);
     P.hint = idx;
     const int nll = G.nlon * G.nlat;
     const int k = (int)(((uint64_t)idx * G.mag_ll) >> 40);
@@ -249,7 +252,7 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
     P.ci = i;
     P.cj = j;
     P.ck = k;
-    P.W = P.W0 = (real)J.wcell[idx];
+    P.W = P.W0 = reinterpret_cast<const real *>(J.wcell)[idx];
     S.ledger(0, P.W0);
     P.stage = 0;
     P.obs = 0;
@@ -268,10 +271,10 @@ __device__ void after_peels_scatter(Packet<real> &P, const DevJob &J, SinkT &S)
     if (J.survival) {
         S.ledger(2, P.W * ((real)1 - om));
         P.W *= om;
-        if (P.W < (real)J.w_rr * P.W0) {
+        if (P.W < JV<real>::w_rr(J) * P.W0) {
             const uint4 v = draw_words(J.seed, P.n, P.ev | 0x80000000u, J.key);
-            if (u01<real>(v.y) < (real)J.p_surv) {
-                const real Wn = P.W / (real)J.p_surv;
+            if (u01<real>(v.y) < JV<real>::p_surv(J)) {
+                const real Wn = P.W / JV<real>::p_surv(J);
                 S.ledger(4, Wn - P.W);
                 P.W = Wn;
             } else {
@@ -290,7 +293,7 @@ __device__ void after_peels_scatter(Packet<real> &P, const DevJob &J, SinkT &S)
     }
     const uint4 w = draw_words(J.seed, P.n, P.ev, J.key);
     const real u1 = u01<real>(w.y), u2 = u01<real>(w.z), u3 = u01<real>(w.w);
-    const real mu = (u1 < P.pg) ? sample_rayleigh<real>(u2) : sample_hg<real>(P.gg, u2, (real)J.hg_eps);
+    const real mu = (u1 < P.pg) ? sample_rayleigh<real>(u2) : sample_hg<real>(P.gg, u2, JV<real>::hg_eps(J));
     real dx = P.fx, dy = P.fy, dz = P.fz;
     turn<real>(dx, dy, dz, mu, (real)(2.0 * PI) * u3);
     ++P.ev;
@@ -348,7 +351,7 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
             }
             f = P.W * ex * (real)(1.0 / (4.0 * PI));
         } else {
-            const real mu = P.fx * (real)J.obs[P.obs][0] + P.fy * (real)J.obs[P.obs][1] + P.fz * (real)J.obs[P.obs][2];
+            const real mu = P.fx * JV<real>::obs(J, P.obs, 0) + P.fy * JV<real>::obs(J, P.obs, 1) + P.fz * JV<real>::obs(J, P.obs, 2);
             f = P.W * P.om * theta_mix<real>(mu, P.pg, P.gg) * ex;
         }
         S.tally(P.obs, f, P.n, J.n_obs);

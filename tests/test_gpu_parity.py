@@ -92,24 +92,28 @@ def test_cell_tables_albedo(G):
 
 
 def test_cell_tables_emission(G):
+    """Emission cell tables against the oracle.  FP64 runs follow the definitions term by term (1e-13).
+    FP32 runs compute alpha = rho k_ab exp(wT d1 + wp d2 + wT wp d3) in FP32 from the k-table node
+    records: expf (<= 2 ulp), FP32 weights and differences (<= 1 ulp of an O(1) argument) and three
+    roundings bound alpha, L_i, the pdf and the FP32 weights to ~5e-7 relative; 2e-6 is asserted."""
     wl = S.config2_emission(n_packets=1000, nlon=16, nlat=8, nr=12, nb=3, ng=3)
     for prec in ("FP64", "FP32"):
         gid, oid, sid, jobs = _load(G, wl, _fp(prec))
+        rt = 1e-13 if prec == "FP64" else 2e-6
         for j, job in list(zip(wl.jobs, jobs))[::4]:
             ref = O.prep_cells(wl, j)
             got = G.prep_cells(job, wl.grid.ncell)
             st = got["stats"]
-            np.testing.assert_allclose(got["lum"], ref["L"], rtol=1e-13)
-            np.testing.assert_allclose(got["cdf"], ref["cdf"], rtol=1e-12, atol=1e-15)
+            np.testing.assert_allclose(got["lum"], ref["L"], rtol=rt)
+            np.testing.assert_allclose(got["cdf"], ref["cdf"], rtol=max(rt, 1e-12), atol=1e-15)
             # monotone, and exactly flat over the cells the tau_vert cut excludes
             dq = np.diff(np.concatenate([[0.0], got["cdf"]]))
             q_ref = np.diff(np.concatenate([[0.0], ref["cdf"]]))
             assert np.all(dq >= 0)
             assert np.array_equal(dq == 0, q_ref == 0)
-            np.testing.assert_allclose(got["wcell"], ref["wcell"], rtol=1e-12)
+            np.testing.assert_allclose(got["wcell"], ref["wcell"], rtol=max(rt, 1e-12))
             assert st.n_emit_cells == ref["n_incl"]
-            assert abs(st.l_tot / ref["L_tot"] - 1) < 1e-13
-            rt = 1e-13 if prec == "FP64" else 6e-8
+            assert abs(st.l_tot / ref["L_tot"] - 1) < rt
             np.testing.assert_allclose(got["alpha"], ref["alpha"], rtol=rt)
 
 

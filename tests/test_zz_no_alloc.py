@@ -18,7 +18,7 @@ def test_noalloc_pdf_matches_prep_cells_twice():
     ctx = gcmc.Context(0)
     try:
         wl = synth.config2_emission(n_packets=1000, bands=[3], gpoints=[5])      # 128 x 64 x 50 cells
-        _, _, _, jobs = gcmc.load_workload(ctx, wl, gcmc.FP32)
+        _, _, _, jobs = gcmc.load_workload(ctx, wl, gcmc.FP64)   # FP64 tables, as the entry point computes
         n = wl.grid.ncell
         ref = ctx.prep_cells(jobs[0], n)
         st = ref["stats"]
