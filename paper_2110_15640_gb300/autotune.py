@@ -17,7 +17,7 @@ DEFAULT_SPACE = {
     "block": [64, 128, 256],
     "blocks_per_sm": [0, 6, 8],
     "chunk": [256, 512, 1024, 2048],
-    "refill_min": [8, 16, 24, 32],
+    "refill_min": [4, 8, 16, 32],
     "interval": [1, 2, 4],
 }
 
@@ -40,7 +40,7 @@ def tune(ctx, jobs, stream, space=None, reps=2, coordinate=True, log=None):
     """Return (best gcmc_launch_cfg, table of (cfg dict, ms)).  coordinate=True searches one axis at a
     time from the defaults (about a dozen runs) instead of the full product."""
     space = space or DEFAULT_SPACE
-    best = {"block": 128, "blocks_per_sm": 0, "chunk": 512, "refill_min": 32, "interval": 2}
+    best = {"block": 128, "blocks_per_sm": 6, "chunk": 512, "refill_min": 8, "interval": 4}
     table = []
 
     def run(c):

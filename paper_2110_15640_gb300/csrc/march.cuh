@@ -188,6 +188,48 @@ __device__ __forceinline__ real cone_root(const DevGrid &G, const Tabs<real> &T,
     return a1 < a2 ? a1 : a2;
 }
 
+// Latitude exit of the current cell.  Along the line, f(s) = sin(lat) = (zc + s dz) / sqrt(p^2 + s^2)
+// has f' of the sign of g(s) = dz p^2 - s zc, so a single extremum, f = sign(zc) sqrt(Q), at
+// g = 0, and the limits -dz, +dz at s -> -inf, +inf.  Moving up (g > 0) the ray crosses the upper
+// edge S_hi iff the supremum of f ahead exceeds it (sqrt(Q) if the maximum lies ahead, i.e. zc > 0,
+// else dz); failing that, after the maximum it crosses the lower edge iff dz < S_lo; the upper
+// crossing always comes first.  Moving down mirrors this.  So one cone is evaluated per step, with
+// the same root and validity rules as before; when Q or dz lies within TAN_EPS of an edge's S^2 or S
+// (the boundaries of the choice, which are also the tangency cases) both cones are evaluated.
+template <typename real>
+__device__ __forceinline__ real lat_exit(const DevGrid &G, const Tabs<real> &T, const Ray<real> &R, int &face)
+{
+    const real inf = M<real>::inf();
+    const bool has_lo = R.j > 0, has_hi = R.j + 1 < T.nlat;
+    // the poles are not surfaces: sentinels outside [-1, 1] make them unreachable below
+    const real Slo = has_lo ? T.sl[R.j].x : (real)-2;
+    const real Shi = has_hi ? T.sl[R.j + 1].x : (real)2;
+    const real dz = R.dz, Q = R.Q;
+    const real eps = sizeof(real) == 4 ? (real)TAN_EPS_CONE : (real)1e-12;
+    const bool amb = fabs(Q - Shi * Shi) < eps || fabs(Q - Slo * Slo) < eps || fabs(dz - Shi) < eps ||
+                     fabs(dz - Slo) < eps;
+    if (amb) {
+        const real tlo = has_lo ? cone_root<real>(G, T, R, R.j, R.s) : inf;
+        const real thi = has_hi ? cone_root<real>(G, T, R, R.j + 1, R.s) : inf;
+        face = thi < tlo ? F_LATHI : F_LATLO;
+        return thi < tlo ? thi : tlo;
+    }
+    const real g = dz * R.p2hi - R.s * R.cz;
+    const bool up = g > (real)0 || (g == (real)0 && R.cz < (real)0);
+    const bool ext_ahead = up ? R.cz > (real)0 : R.cz < (real)0;
+    bool to_hi, to_lo;
+    if (up) {
+        to_hi = ext_ahead ? (Shi <= (real)0 || Q > Shi * Shi) : dz > Shi;
+        to_lo = !to_hi && ext_ahead && dz < Slo;
+    } else {
+        to_lo = ext_ahead ? (Slo >= (real)0 || Q > Slo * Slo) : dz < Slo;
+        to_hi = !to_lo && ext_ahead && dz > Shi;
+    }
+    const real t = cone_root<real>(G, T, R, to_hi ? R.j + 1 : R.j, R.s);
+    face = to_hi ? F_LATHI : F_LATLO;
+    return (to_hi || to_lo) ? t : inf;
+}
+
 // Exit of the current cell: returns the s of the exit point and the face.  Every candidate face is
 // evaluated with selects (both shells' discriminants, both cones, the half-plane ahead in azimuth),
 // so the lanes of a warp stay converged; ties go to the first face in the order r-, r+, lat-, lat+, lon.
@@ -204,16 +246,12 @@ __device__ __forceinline__ real cell_exit(const DevGrid &G, const Tabs<real> &T,
     const real rt = M<real>::sqrt_(h);
     real best = inward ? -rt : rt;
     face = inward ? F_RIN : F_ROUT;
-    // latitude cones (edges j and j+1; the poles are not surfaces)
-    const real tlo = R.j > 0 ? cone_root<real>(G, T, R, R.j, R.s) : inf;
-    const real thi = R.j + 1 < T.nlat ? cone_root<real>(G, T, R, R.j + 1, R.s) : inf;
-    if (tlo < best) {
-        best = tlo;
-        face = F_LATLO;
-    }
-    if (thi < best) {
-        best = thi;
-        face = F_LATHI;
+    // latitude: the one cone the ray reaches first (both near the thresholds of that choice)
+    int flat = F_NONE;
+    const real tlat = lat_exit<real>(G, T, R, flat);
+    if (tlat < best) {
+        best = tlat;
+        face = flat;
     }
     // longitude: the azimuth along a line is monotone (sign of (o x d)_z), so only the edge ahead counts
     const bool east = R.crz > (real)0;

@@ -39,6 +39,8 @@ template <typename real> struct Packet {
 template <typename real> struct JobC {
     int max_steps;
     real tau_cut;
+    const real *rec;       // march table: alpha, or the first component of the albedo records
+    int rec_stride;        // 4 for albedo records, else 1
 };
 
 struct LogOut {
@@ -400,8 +402,8 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
     ++P.steps;
     const int idx = (R.k * T.nlat + R.j) * T.nlon + R.i;
     real a;
-    if (SCAT && J.mode == GCMC_ALBEDO) a = __ldg(reinterpret_cast<const real *>(J.rec) + 4 * idx);
-    else a = __ldg(reinterpret_cast<const real *>(J.rec) + idx);
+    if constexpr (SCAT) a = __ldg(jc.rec + jc.rec_stride * idx);
+    else a = __ldg(jc.rec + idx);
     int face = F_NONE;
     const real sx = cell_exit<real>(G, T, R, face);
     const real seg = sx - R.s;
@@ -462,6 +464,8 @@ template <typename real> __device__ __forceinline__ JobC<real> job_consts(const 
     JobC<real> c;
     c.max_steps = (int)min(J.max_steps, (int64_t)INT_MAX);
     c.tau_cut = (real)J.tau_cut;
+    c.rec = reinterpret_cast<const real *>(J.rec);
+    c.rec_stride = J.mode == GCMC_ALBEDO ? 4 : 1;
     return c;
 }
 
@@ -496,9 +500,10 @@ __global__ void __launch_bounds__(256) k_transport_plain(const DevGrid *__restri
     flush(S.sm, S.stride, J.acc);
 }
 
-// MINB > 0: compiled for MINB resident 128-thread blocks per SM (register cap 65536 / (128 MINB))
+// MINB > 0: compiled for MINB resident 128-thread blocks per SM (register cap 65536 / (128 MINB));
+// MINB = 0: any block size up to 256, at most 128 registers (two 256-thread blocks per SM)
 template <typename real, bool SCAT, int MINB>
-__global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) k_transport_persistent(const DevGrid *__restrict__ grids,
+__global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 2) k_transport_persistent(const DevGrid *__restrict__ grids,
                                                               const DevJob *__restrict__ jobs, int n_jobs,
                                                               int64_t total_items, int chunk, int interval,
                                                               int refill_min, int one_grid, int tab_n,
