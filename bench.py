@@ -26,6 +26,7 @@ if ROOT not in sys.path:
 
 OPS_PER_STEP = 64          # FP32-pipe operations of one cell step (count in the design doc)
 PEAK_FP32_OPS = 152 * 128 * 2.07e9   # GB300: SMs x FP32 lanes x max SM clock (an FMA counts as one op)
+PEAK_FP64_OPS = 152 * 2 * 2.07e9     # GB300: FP64 issue is 1/64 of FP32 (2 lanes per SM per clock)
 
 
 def parse():
@@ -46,6 +47,9 @@ def parse():
     ap.add_argument("--refill", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
+    ap.add_argument("--workload", default="emission", choices=["emission", "albedo", "phasecurve", "transmission", "serving"])
+    ap.add_argument("--requests", type=int, default=10_000, help="serving: requests in the stream")
+    ap.add_argument("--hbm-budget-gb", type=float, default=16.0, help="serving: admitted workspace")
     return ap.parse_args()
 
 
@@ -57,12 +61,24 @@ def dist_env():
 
 
 def workload(args, rank):
-    from paper_2110_15640_gb300 import synth
-    wl = synth.config2_emission(n_packets=args.packets, nb=30, ng=8, bands=range(args.bands),
-                                gpoints=range(args.gpoints))
-    from paper_2110_15640_gb300 import shard
-    wl.seed = shard.rank_seed(2, rank)   # distinct packets per rank (weak scaling)
+    """The synthetic workload of --workload (seeded; distinct packets per rank for weak scaling)."""
+    from paper_2110_15640_gb300 import shard, synth
+    if args.workload == "albedo":
+        wl = synth.config1_albedo()
+    elif args.workload == "phasecurve":
+        wl = synth.config3_phase_curve()
+    elif args.workload == "transmission":
+        wl = synth.config4_transmission()
+    else:
+        wl = synth.config2_emission(n_packets=args.packets, nb=30, ng=8, bands=range(args.bands),
+                                    gpoints=range(args.gpoints))
+    wl.seed = shard.rank_seed(wl.seed, rank)
     return wl
+
+
+# oracle sample per workload for the CPU baseline: (jobs, packets per job or None for all)
+CPU_SAMPLE = {"emission": (48, 1_000_000), "albedo": (1, None), "phasecurve": (24, None), "transmission": (960, None)}
+REF_SAMPLE = {"emission": (2, 200_000), "albedo": (1, None), "phasecurve": (2, None), "transmission": (96, None)}
 
 
 class ClockSampler:
@@ -117,13 +133,15 @@ def gpu_uuid(dev):
 
 
 def cpu_oracle_rate(wl, n_jobs, n_packets, nthreads):
-    """Oracle (FP64 CPU) packet-steps/s on a sample of the workload's jobs, S1 included."""
+    """Oracle (FP64 CPU) packet-steps/s on a sample of the workload's jobs (spread over the job list),
+    S1 included; n_packets None runs each job's full packet count."""
     from oracle import oracle as O
     steps = 0
     t0 = time.perf_counter()
-    for job in wl.jobs[:n_jobs]:
+    for job in wl.jobs[::max(1, len(wl.jobs) // n_jobs)][:n_jobs]:
         cells = O.prep_cells(wl, job)
-        r = O.run(wl, job, cells=cells, packet0=0, n_run=n_packets, nthreads=nthreads)
+        npk = job.n_packets if n_packets is None else min(n_packets, job.n_packets)
+        r = O.run(wl, job, cells=cells, packet0=0, n_run=npk, nthreads=nthreads)
         steps += r["steps"]
     dt = time.perf_counter() - t0
     return steps / dt, dt, steps
@@ -135,7 +153,7 @@ def run_reference(args):
         return 0
     wl = workload(args, 0)
     cores = os.cpu_count() or 1
-    nj, npk = 2, min(args.packets, 200_000)
+    nj, npk = REF_SAMPLE[args.workload]
     for _ in range(args.warmup):
         cpu_oracle_rate(wl, 1, 20_000, cores)
     rates, total_steps, total_t = [], 0, 0.0
@@ -145,12 +163,14 @@ def run_reference(args):
         total_steps += st
         total_t += dt
     value = total_steps / total_t
-    sample = f"{nj} of {len(wl.jobs)} (band, g) jobs x {npk} packets per step (S1 + transport), full 128x64x50 grid"
+    g = wl.grid
+    sample = (f"{nj} of {len(wl.jobs)} jobs x {npk or 'all their'} packets per step (S1 + transport), "
+              f"full {g.nlon}x{g.nlat}x{g.nr} grid")
     line = {"metric": "packet-steps/s", "value": value, "unit": "packet-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": wl.name, "jobs": len(wl.jobs), "packets_per_job": args.packets},
+            "config": {"workload": wl.name, "jobs": len(wl.jobs), "packets": wl.total_packets},
             "cpu_baseline": {"value": value, "unit": "packet-steps/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "packet-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -158,8 +178,108 @@ def run_reference(args):
     return 0
 
 
+def serve_stream(sv, jobs, arrivals, timeout_s=600.0):
+    """Submit jobs[i] at arrivals[i] seconds after the start and run the server's loop until all have
+    completed; returns (per-request latency in s, total packet-steps, wall seconds)."""
+    n = len(jobs)
+    lat = [0.0] * n
+    who = {}
+    steps, done, i = 0, 0, 0
+    t0 = time.perf_counter()
+    while done < n:
+        now = time.perf_counter() - t0
+        while i < n and arrivals[i] <= now:
+            who[sv.submit(jobs[i])] = i
+            i += 1
+        for tk in sv.progress():
+            q = who.pop(tk)
+            _, st = sv.result(tk)
+            lat[q] = time.perf_counter() - t0 - arrivals[q]
+            steps += st.steps
+            done += 1
+        if now > timeout_s:
+            raise RuntimeError(f"serving stream: {n - done} requests open after {timeout_s} s")
+        if i < n and not who:
+            time.sleep(max(0.0, min(arrivals[i] - now, 1e-3)))
+    return lat, steps, time.perf_counter() - t0
+
+
+def plain_stream(ctx, jobs, arrivals):
+    """The same stream on the plain form: one request at a time, in arrival order, one cell-table
+    preparation and one transport launch each (gcmc_run_packets)."""
+    n = len(jobs)
+    lat = [0.0] * n
+    steps, busy = 0, 0.0
+    t0 = time.perf_counter()
+    for q in range(n):
+        now = time.perf_counter() - t0
+        if arrivals[q] > now:
+            time.sleep(arrivals[q] - now)
+        ts = time.perf_counter()
+        _, st = ctx.run_packets(jobs[q])
+        te = time.perf_counter()
+        busy += te - ts
+        steps += st.steps
+        lat[q] = te - t0 - arrivals[q]
+    return lat, steps, time.perf_counter() - t0, busy
+
+
+def pct(xs, p):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs) * 1e3, p))
+
+
+def serving_bench(args):
+    """Serving workload: a Poisson stream of mixed requests on four resident grids through the
+    continuous-batching server, at 0.7x and 0.9x of the server's saturated request rate, and the same
+    stream on the plain one-launch-per-request form."""
+    import numpy as np
+    import torch
+    from paper_2110_15640_gb300 import build, gcmc, synth
+    build.build()
+    torch.cuda.set_device(0)
+    sw = synth.config5_serving(n_requests=args.requests)
+    ctx = gcmc.Context(0)
+    jobs = gcmc.load_serving(ctx, sw)
+    sv = gcmc.Server(ctx, hbm_budget=int(args.hbm_budget_gb * (1 << 30)))
+    sv.run_all(jobs[:32])                                   # warm-up (first launches, pools)
+    # saturated: every request queued at t = 0
+    lat_s, steps_s, wall_s = serve_stream(sv, jobs, [0.0] * len(jobs))
+    rate_sat = len(jobs) / wall_s
+    rng = np.random.default_rng(55)
+    runs = {}
+    for load in (0.7, 0.9):
+        arr = np.cumsum(rng.exponential(1.0 / (load * rate_sat), len(jobs))).tolist()
+        lat, steps, wall = serve_stream(sv, jobs, arr)
+        runs[load] = {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "packet_steps_per_s": steps / wall,
+                      "requests_per_s": len(jobs) / wall, "wall_s": wall}
+    stq = sv.query()
+    sv.close()
+    arr = np.cumsum(rng.exponential(1.0 / (0.7 * rate_sat), len(jobs))).tolist()
+    lat_p, steps_p, wall_p, busy_p = plain_stream(ctx, jobs, arr)
+    ctx.close()
+    line = {
+        "metric": "packet-steps/s", "value": steps_s / wall_s, "unit": "packet-steps/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * wall_s, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": sw.name, "requests": len(jobs), "grids": ["x".join(map(str, g)) for g in synth.SERVING_GRIDS],
+                   "packets": "log-uniform 1e4..1e7", "modes": "albedo / emission / transmission, 1/3 each",
+                   "hbm_budget_gb": args.hbm_budget_gb},
+        "saturated": {"packet_steps_per_s": steps_s / wall_s, "requests_per_s": rate_sat, "wall_s": wall_s,
+                      "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99)},
+        "poisson_0.7": runs[0.7], "poisson_0.9": runs[0.9],
+        "plain_form_at_0.7": {"p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
+                              "packet_steps_per_s_busy": steps_p / busy_p, "wall_s": wall_p},
+        "server": {"kernel_launches": stq.kernel_launches, "grid_blocks": stq.grid_blocks},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "serving":
+        return serving_bench(args)
     if args.impl == "reference":
         return run_reference(args)
     import numpy as np
@@ -180,11 +300,12 @@ def main():
             torch.distributed.barrier()
 
     wl = workload(args, rank)
+    prec = gcmc.FP64 if args.workload == "albedo" else gcmc.FP32     # the 32x16x20 albedo case runs FP64
     stream = torch.cuda.Stream()
     ctx = gcmc.Context(local, stream=stream)
     from paper_2110_15640_gb300 import autotune
     with torch.cuda.stream(stream):
-        gid, oid, sid, jobs = gcmc.load_workload(ctx, wl, gcmc.FP32, device_inputs=True)
+        gid, oid, sid, jobs = gcmc.load_workload(ctx, wl, prec, device_inputs=True)
         tall = torch.zeros((len(jobs), gcmc.MAX_OBS), dtype=torch.float64, device="cuda")
         if args.no_tune or args.block or args.chunk or args.interval or args.refill or args.blocks_per_sm:
             cfg = gcmc.gcmc_launch_cfg(args.block, args.blocks_per_sm, args.chunk, args.interval, args.refill, 0)
@@ -249,43 +370,57 @@ def main():
     for _ in range(args.e2e_steps):
         g2 = ctx.upload_grid(wl.grid, device_arrays=ga, memory=gcmc.MEM_HOST)
         o2 = ctx.upload_opacity(g2, wl.opac, device_arrays=oa, memory=gcmc.MEM_HOST)
-        s2 = ctx.set_source(g2, wl.source, gcmc.FP32)
-        jb = [gcmc.Context.job(g2, o2, s2, j.mode, j.lam_idx, j.g_idx, j.n_packets, j.seed, j.job_key) for j in jobs]
+        jb = gcmc.workload_jobs(wl, g2, o2, ctx.set_sources(g2, wl.source, prec))
         tl, st2 = ctx.run_batch(jb, cfg=cfg)
-        F = np.zeros((args.bands, args.gpoints))
-        for q, j in enumerate(wl.jobs):
-            ob = ctx.postscale(g2, gcmc.EMISSION, tl[q][0], j.n_packets, st2[q].l_tot)
-            F[j.lam_idx, j.g_idx] = ob["F_p"]
-        F_band = F @ wl.opac.wg[:args.gpoints]
+        obs = [ctx.postscale(g2, wl.mode, tl[q][0], j.n_packets, st2[q].l_tot) for q, j in enumerate(wl.jobs)]
+        if wl.mode == gcmc.EMISSION:
+            F = np.zeros((args.bands, args.gpoints))
+            for q, j in enumerate(wl.jobs):
+                F[j.lam_idx, j.g_idx] = obs[q]["F_p"]
+            F_band = {"spectrum_F_p_band_mean": float(np.mean(F @ wl.opac.wg[:args.gpoints]))}
+        elif wl.mode == gcmc.ALBEDO:
+            F_band = {"A_g_mean": float(np.mean([o["A_g"] for o in obs]))}
+        else:
+            F_band = {"area_mean": float(np.mean([o["area"] for o in obs]))}
         ctx.release_grid(g2)
     torch.cuda.synchronize()
     t_e2e = (time.perf_counter() - te) / max(args.e2e_steps, 1)
     e2e_value = steps_per_step / t_e2e if args.e2e_steps else None
 
     # ---------------- roofline of the transport kernel and the gather roofline
+    f64 = prec == gcmc.FP64
     tr_avg = tr_ms / max(ntr, 1) / 1e3
     achieved = OPS_PER_STEP * steps_per_step / tr_avg / 1e12
-    gather = ctx.gather_bench(wl.grid.ncell, 4, 1 << 30)
+    rec_bytes = 16 if wl.mode == gcmc.ALBEDO else 4
+    gather = ctx.gather_bench(wl.grid.ncell, rec_bytes, 1 << 30)
     clocks = clk.summary()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = os.cpu_count() or 1
-        rate, dt, _ = cpu_oracle_rate(wl, 48, min(args.packets, 1_000_000), cores)
+        nj, npk = CPU_SAMPLE[args.workload]
+        rate, dt, _ = cpu_oracle_rate(wl, nj, npk, cores)
         cpu = {"value": rate, "unit": "packet-steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"48 of {len(jobs)} (band, g) jobs x {min(args.packets, 1_000_000)} packets, S1 + transport, "
+               "sample": f"{min(nj, len(jobs))} of {len(jobs)} jobs x {npk or 'all their'} packets, S1 + transport, "
                          f"{dt:.1f} s"}
     if rank == 0:
+        g = wl.grid
+        per_step_bytes = len(jobs) * g.ncell * (rec_bytes + (12 if wl.mode == gcmc.EMISSION else 0))
+        peak = (PEAK_FP64_OPS if f64 else PEAK_FP32_OPS) / 1e12
         line = {
             "metric": "packet-steps/s", "value": value, "unit": "packet-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if f64 else "f32",
+            "data": "synthetic",
             "spectra_per_s": world * args.steps / t,
-            "config": {"workload": wl.name, "jobs": len(jobs), "packets_per_job": args.packets,
-                       "grid": "128x64x50", "packet_steps_per_step": steps_per_step,
-                       "packets_per_step": packets_per_step, "capped_weight": capped,
-                       "l2": "inputs larger than L2 (per-step cell tables ~2 GB)",
-                       "precision": "FP32 march and opacities, FP64 luminosities, 64-bit fixed-point pdf and tallies",
+            "config": {"workload": wl.name, "jobs": len(jobs), "packets_per_step": packets_per_step,
+                       "grid": f"{g.nlon}x{g.nlat}x{g.nr}", "packet_steps_per_step": steps_per_step,
+                       "capped_weight": capped,
+                       "l2": (f"inputs larger than L2 (per-step cell tables {per_step_bytes / 1e9:.2f} GB)"
+                              if per_step_bytes > 129e6 else
+                              f"per-step cell tables {per_step_bytes / 1e6:.1f} MB fit in L2 (the workload's own size)"),
+                       "precision": ("FP64 march, tables and tallies" if f64 else
+                                     "FP32 march and opacities, FP64 luminosities, 64-bit fixed-point pdf and tallies"),
                        "launch": tuned},
             "plain_form": {"value": plain_value, "unit": "packet-steps/s",
                            "ms_per_step": 1e3 * t_plain / args.plain_steps if args.plain_steps else None,
@@ -293,16 +428,16 @@ def main():
             "batched_over_plain": value / plain_value if plain_value else None,
             "e2e": {"value": e2e_value, "unit": "packet-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * t_e2e},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_OPS / 1e12, "unit": "TFLOP/s",
-                         "frac": achieved / (PEAK_FP32_OPS / 1e12), "traffic": None,
-                         "kernel": "k_transport_persistent<float>", "ops_per_step": OPS_PER_STEP,
+            "roofline": {"bound": "fp64" if f64 else "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": f"k_transport_persistent<{'double' if f64 else 'float'}>", "ops_per_step": OPS_PER_STEP,
                          "kernel_ms": 1e3 * tr_avg, "prep_ms": prep_ms / max(ntr, 1)},
-            "gather_roofline": {"gathers_per_s": gather, "table_records": wl.grid.ncell, "record_bytes": 4,
+            "gather_roofline": {"gathers_per_s": gather, "table_records": g.ncell, "record_bytes": rec_bytes,
                                 "frac": (steps_per_step / tr_avg) / gather},
             "cpu_baseline": cpu,
             "gpu_launches": launches,
             "clocks": clocks,
-            "spectrum_F_p_band_mean": float(np.mean(F_band)) if F_band is not None else None,
+            "observables": F_band,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -256,7 +256,7 @@ gcmc_status gcmc_gather_bench(gcmc_ctx *ctx, int64_t n_records, int record_bytes
 
 /* ---------------------------------------------------------------- allocation-free variant */
 
-/* Largest cell count gcmc_emission_pdf_noalloc accepts (its scratch: 64 KiB per GPU). */
+/* Largest cell count gcmc_emission_pdf_noalloc accepts (its scratch: 256 KiB per GPU). */
 #define GCMC_NOALLOC_MAX_CELLS 4194304
 
 /* The emission pdf stage (hybrid pdf q_i, cumulative sum and launch weights) without any device
@@ -285,6 +285,76 @@ gcmc_status gcmc_emission_pdf_noalloc(const double *lum, int64_t ncell, double b
    counters/keys (host arrays ctr [n][4], key [n][2]); results to out_lib, out_curand [n][4]. */
 gcmc_status gcmc_selftest_philox(gcmc_ctx *ctx, const uint32_t *ctr, const uint32_t *key, int n,
                                  uint32_t *out_lib, uint32_t *out_curand);
+
+/* ---------------------------------------------------------------- serving (continuous batching)
+
+   A request loop over spectrum jobs that arrive while others run.  The paper runs one (lambda, g)
+   job after another from a host loop (Sect. 2); this server keeps grids and opacity tables resident
+   and overlaps jobs on the device.  One persistent transport kernel drains a queue of published
+   jobs in publication order; a job is admitted in arrival order (its cell tables built on a second
+   stream, beside the running kernel) once a completion slot is free and its workspace fits in
+   hbm_budget bytes together with the other admitted jobs (admission by HBM footprint); it is
+   published to the running kernel through host-mapped memory as soon as its cell tables are ready,
+   and warps take its work items once the jobs published before it have none left to claim.
+   The warp that finishes a job's last work item writes the job's tallies into host-mapped memory.
+   A job's tallies do not depend on what else runs: every packet's random numbers are keyed by
+   (seed, packet, event, job key) and the sums are 64-bit fixed point, so a job gives bit-identical
+   tallies alone and in any mix.
+
+   Ownership: the server uses its context's grids, opacities and sources, which must stay uploaded
+   while jobs that use them are queued; it owns its streams, host-mapped buffers and job workspaces.
+   A server and its context are used from one host thread.  Jobs run in FP32 (their source's
+   precision must be GCMC_FP32), on grids no larger (in nr + nlat + nlon) than the largest grid
+   present when the server was created, with n_packets >= 1. */
+typedef struct gcmc_server gcmc_server;
+
+typedef struct {
+    int32_t block;            /* threads per block of the serving kernel: 0 or 128 */
+    int32_t blocks_per_sm;    /* 0 = one block per SM less than fits (room for cell-table kernels) */
+    int32_t chunk;            /* packets per warp work item, multiple of 32; 0 = 256 */
+    int32_t interval;         /* march steps between refill checks; 0 = 4 */
+    int32_t refill_min;       /* see gcmc_launch_cfg; 0 = 8 */
+    int32_t max_jobs;         /* jobs admitted at once (completion slots), 1..32768; 0 = 1024 */
+    uint64_t hbm_budget;      /* bytes of job workspace admitted at once; 0 = 8 GiB.  A job larger than
+                                 the budget is admitted alone. */
+    int32_t idle_us;          /* the serving kernel leaves after about this many microseconds without
+                                 published work (it is relaunched when work arrives); 0 = 2000 */
+    int32_t pad;
+} gcmc_server_cfg;
+
+typedef struct {
+    int64_t pending;          /* submitted, waiting for admission */
+    int64_t admitted;         /* admitted and not yet complete */
+    int64_t completed;        /* completed since creation */
+    uint64_t bytes_in_use;    /* workspace of the admitted jobs */
+    int64_t kernel_launches;  /* serving-kernel launches since creation */
+    int32_t kernel_running;   /* 1 while the serving kernel is resident */
+    int32_t grid_blocks;      /* blocks of the last serving-kernel launch */
+} gcmc_server_stats;
+
+gcmc_status gcmc_server_create(gcmc_ctx *ctx, const gcmc_server_cfg *cfg, gcmc_server **out);
+
+/* Queue one job (copied); returns its ticket.  Nothing is launched until gcmc_server_progress. */
+gcmc_status gcmc_server_submit(gcmc_server *sv, const gcmc_job *job, uint64_t *ticket);
+
+/* One pass of the request loop, never blocking: collect completed jobs (their tickets are written to
+   done_tickets, at most cap of them; *n_done counts all), admit queued jobs that fit, publish those
+   whose cell tables are ready, and (re)launch the serving kernel if published work has none. */
+gcmc_status gcmc_server_progress(gcmc_server *sv, uint64_t *done_tickets, int cap, int *n_done);
+
+/* Tallies [GCMC_MAX_OBS] (sums of f over packets, as gcmc_run_batch) and stats (may be NULL) of a
+   completed job; GCMC_ERR_NOT_READY if the ticket has not completed (or was already taken). */
+gcmc_status gcmc_server_result(gcmc_server *sv, uint64_t ticket, double *tallies_out, gcmc_stats *stats_out);
+
+/* Host times of a completed job that gcmc_server_result has not yet taken, in seconds since the
+   server was created: t4 = {submitted, admitted (cell tables queued), published, completion seen}. */
+gcmc_status gcmc_server_times(gcmc_server *sv, uint64_t ticket, double *t4);
+
+gcmc_status gcmc_server_query(gcmc_server *sv, gcmc_server_stats *stats);
+
+/* Stop the server: published jobs finish first.  Returns GCMC_ERR_TIMEOUT, and frees nothing, if the
+   serving kernel has not finished within timeout_s seconds; queued (unadmitted) jobs are dropped. */
+gcmc_status gcmc_server_destroy(gcmc_server *sv, double timeout_s);
 
 /* Library version string. */
 const char *gcmc_version(void);

@@ -16,7 +16,7 @@ from . import gcmc
 DEFAULT_SPACE = {
     "block": [64, 128, 256],
     "blocks_per_sm": [0, 6, 8],
-    "chunk": [256, 512, 1024, 2048],
+    "chunk": [32, 64, 128, 256, 512, 1024],
     "refill_min": [4, 8, 16, 32],
     "interval": [1, 2, 4],
 }

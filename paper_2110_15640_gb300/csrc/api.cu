@@ -1,11 +1,14 @@
 // api.cu -- the C ABI of libgcmc (declared in include/gcmc.h): contexts, validated uploads, the
 // per-run workspace, S1 grouping, plain / batched / asynchronous runs, debug outputs, post-scale.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -58,6 +61,12 @@ struct gcmc_ctx {
     std::map<uint64_t, Ticket> tickets;
     uint64_t next_ticket = 1;
     std::string err;
+    struct Staging {
+        char *ptr = nullptr;
+        size_t cap = 0;
+        cudaEvent_t ev = nullptr;
+    } stg[2];                              // pinned staging of job records, used in turn
+    int stg_i = 0;
     bool prof = false;                     // profiling: events around S1 and transport of each run
     std::vector<cudaEvent_t> prof_ev;      // triples (before S1, before transport, after transport)
 };
@@ -105,7 +114,10 @@ template <typename T> T *dput(gcmc_ctx *ctx, std::vector<void *> &owned, const T
         return nullptr;
     }
     owned.push_back(d);
-    if (src && n) e = cudaMemcpyAsync(d, src, n * sizeof(T), cudaMemcpyDefault, ctx->stream);
+    if (src && n) {
+        const cudaError_t r = cudaMemcpyAsync(d, src, n * sizeof(T), cudaMemcpyDefault, ctx->stream);
+        if (r != cudaSuccess) e = r;
+    }
     return d;
 }
 
@@ -151,8 +163,6 @@ void perp_basis(const double s[3], double e1[3], double e2[3])
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Planck prefactor 2 h c^2 / lambda^5 of B_lambda (SI)
-double planck_c1(double lam) { return 2.0 * 6.62607015e-34 * 2.99792458e8 * 2.99792458e8 / std::pow(lam, 5.0); }
 
 // ------------------------------------------------------------------ run planning
 struct Group {
@@ -167,8 +177,7 @@ struct Plan {
     std::vector<int> job_group;         // group of job q
     std::vector<Group> groups;
     std::vector<size_t> off_rec, off_cdf, off_w, off_info, off_bsum, off_bcnt;
-    std::vector<size_t> g_off_ab, g_off_w, g_off_fac, g_off_vb, g_first;
-    std::vector<int> g_nslots;          // emission: distinct band wavelengths of the group
+    std::vector<size_t> g_first;
     size_t off_jobs = 0, off_prep = 0, off_acc = 0, off_work = 0, off_gather = 0, ws_bytes = 0;
     int64_t total_items = 0;
     bool scatter = false;               // some job follows scattered packets (albedo)
@@ -259,30 +268,7 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
         }
     }
     const size_t ng = P.groups.size();
-    P.g_off_ab.resize(ng);
-    P.g_off_w.resize(ng);
-    P.g_off_fac.resize(ng);
-    P.g_off_vb.assign(ng, 0);
-    P.g_nslots.assign(ng, 0);
     P.g_first.resize(ng);
-    std::vector<std::vector<int>> slot_lams(ng);
-    for (size_t g = 0; g < ng; ++g) {
-        const int64_t ncell = ctx->grids[P.groups[g].grid].dg.ncell;
-        if (P.groups[g].mode == GCMC_EMISSION) {
-            for (int q : P.groups[g].members)
-                if (std::find(slot_lams[g].begin(), slot_lams[g].end(), jobs[q].lam_idx) == slot_lams[g].end())
-                    slot_lams[g].push_back(jobs[q].lam_idx);
-            P.g_nslots[g] = (int)slot_lams[g].size();
-            P.g_off_vb[g] = ws;
-            ws += align256((size_t)P.g_nslots[g] * ncell * 8);
-        }
-        P.g_off_ab[g] = ws;
-        ws += align256(ncell * sizeof(int2));
-        P.g_off_w[g] = ws;
-        ws += align256(ncell * sizeof(double2));
-        P.g_off_fac[g] = ws;
-        ws += align256(ncell * sizeof(double));
-    }
     P.off_jobs = ws;
     ws += align256(n * sizeof(DevJob));
     P.off_prep = ws;
@@ -310,14 +296,6 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
             pj.lam_hint = j.lam_idx;
             if (o.kind == GCMC_OPAC_KTABLE) {
                 pj.lam_m = o.lam[j.lam_idx];
-                pj.c1 = planck_c1(pj.lam_m);
-                pj.bslot = (int)(std::find(slot_lams[g].begin(), slot_lams[g].end(), j.lam_idx) - slot_lams[g].begin());
-                // entry s of the group carries the Planck parameters of band slot s
-                const int s = (int)(P.prep.size() - P.g_first[g]);
-                if (s < P.g_nslots[g]) {
-                    pj.pl_lam = o.lam[slot_lams[g][s]];
-                    pj.pl_c1 = planck_c1(pj.pl_lam);
-                }
             } else if (o.kind == GCMC_OPAC_XSEC) {
                 pj.lam_m = o.lam[j.lam_idx];
             }
@@ -385,7 +363,27 @@ __global__ void k_finalize_jobs(DevJob *jobs, int n)
 }
 
 // S1 for every job of the plan, then the device job array, accumulators and work counter.
-gcmc_status stage(gcmc_ctx *ctx, Plan &P, char *base, double *lum = nullptr)
+// Host staging of the job records: copies from pinned memory are asynchronous, whereas a copy from
+// pageable memory synchronises the stream first.  The context keeps two pinned buffers and uses them
+// in turn, each guarded by an event after its copies; callers with their own pinned slot (the
+// server, one per job slot) pass it as host_stage.
+char *stage_buffer(gcmc_ctx *ctx, size_t bytes, cudaEvent_t *ev_out)
+{
+    gcmc_ctx::Staging &b = ctx->stg[ctx->stg_i ^= 1];
+    if (b.ev) cudaEventSynchronize(b.ev);
+    else if (cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    if (b.cap < bytes) {
+        if (b.ptr) cudaFreeHost(b.ptr);
+        b.ptr = nullptr;
+        b.cap = 0;
+        if (cudaMallocHost((void **)&b.ptr, bytes) != cudaSuccess) return nullptr;
+        b.cap = bytes;
+    }
+    *ev_out = b.ev;
+    return b.ptr;
+}
+
+gcmc_status stage(gcmc_ctx *ctx, Plan &P, char *base, double *lum = nullptr, char *host_stage = nullptr)
 {
     const int n = (int)P.jobs.size();
     for (int q = 0; q < n; ++q) {
@@ -401,7 +399,6 @@ gcmc_status stage(gcmc_ctx *ctx, Plan &P, char *base, double *lum = nullptr)
             pj.bsum = reinterpret_cast<double *>(base + P.off_bsum[q]);
             pj.bcnt = reinterpret_cast<double *>(base + P.off_bcnt[q]);
             pj.lum = lum;
-            pj.vb = reinterpret_cast<const double *>(base + P.g_off_vb[P.job_group[q]]);
             d.cdf = pj.cdf;
             d.wcell = pj.wcell;
             d.info = pj.info;
@@ -409,29 +406,32 @@ gcmc_status stage(gcmc_ctx *ctx, Plan &P, char *base, double *lum = nullptr)
     }
     PrepJob *dprep = reinterpret_cast<PrepJob *>(base + P.off_prep);
     DevJob *djobs = reinterpret_cast<DevJob *>(base + P.off_jobs);
-    CK(cudaMemcpyAsync(dprep, P.prep.data(), n * sizeof(PrepJob), cudaMemcpyHostToDevice, ctx->stream));
+    const size_t bp = n * sizeof(PrepJob), bj = n * sizeof(DevJob);
+    cudaEvent_t stg_ev = nullptr;
+    char *hs = host_stage ? host_stage : stage_buffer(ctx, bp + bj, &stg_ev);
+    if (!hs) return fail(ctx, GCMC_ERR_OOM, "pinned staging");
+    std::memcpy(hs, P.prep.data(), bp);
+    std::memcpy(hs + bp, P.jobs.data(), bj);
+    CK(cudaMemcpyAsync(dprep, hs, bp, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(djobs, hs + bp, bj, cudaMemcpyHostToDevice, ctx->stream));
+    if (stg_ev) CK(cudaEventRecord(stg_ev, ctx->stream));
     for (size_t g = 0; g < P.groups.size(); ++g) {
         const Group &G = P.groups[g];
         const PrepJob *gp = dprep + P.g_first[g];
         const int m = (int)G.members.size();
         const GridH &gh = ctx->grids[G.grid];
         const OpacH &oh = ctx->opacs[G.opac];
-        int2 *ab = reinterpret_cast<int2 *>(base + P.g_off_ab[g]);
-        double2 *ww = reinterpret_cast<double2 *>(base + P.g_off_w[g]);
-        double *fac = reinterpret_cast<double *>(base + P.g_off_fac[g]);
         cudaError_t e;
         if (G.mode == GCMC_ALBEDO) {
             e = prep_albedo(G.precision, ctx->d_grids + G.grid, gh.dg, oh.alb, gp, m, ctx->stream);
         } else if (G.mode == GCMC_EMISSION) {
             const gcmc_source_desc &s = ctx->sources[G.source];
-            e = prep_emission(G.precision, ctx->d_grids + G.grid, gh.dg, oh.kt, gp, m, P.g_nslots[g], s.tau_vert_max,
-                              s.beta_emis, ab, ww, ctx->stream);
+            e = prep_emission(G.precision, gh.dg, oh.kt, gp, m, s.tau_vert_max, s.beta_emis, ctx->stream);
         } else {
-            e = prep_xsec(G.precision, ctx->d_grids + G.grid, gh.dg, oh.xs, gp, m, ab, ww, fac, ctx->stream);
+            e = prep_xsec(G.precision, gh.dg, oh.xs, gp, m, ctx->stream);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cell-table kernels");
     }
-    CK(cudaMemcpyAsync(djobs, P.jobs.data(), n * sizeof(DevJob), cudaMemcpyHostToDevice, ctx->stream));
     count_launch(1);
     k_finalize_jobs<<<(n + 127) / 128, 128, 0, ctx->stream>>>(djobs, n);
     CK(cudaGetLastError());
@@ -597,6 +597,10 @@ gcmc_status gcmc_destroy(gcmc_ctx *ctx)
     for (auto &o : ctx->opacs)
         for (void *p : o.owned) dfree(ctx, p);
     dfree(ctx, ctx->arena);
+    for (auto &b : ctx->stg) {
+        if (b.ptr) cudaFreeHost(b.ptr);
+        if (b.ev) cudaEventDestroy(b.ev);
+    }
     if (ctx->h_acc) cudaFreeHost(ctx->h_acc);
     if (ctx->h_info) cudaFreeHost(ctx->h_info);
     cudaFree(ctx->d_grids);
@@ -854,6 +858,18 @@ gcmc_status gcmc_upload_opacity(gcmc_ctx *ctx, int grid_id, const gcmc_opacity_d
             O.kt.pg = dput(ctx, O.owned, pg.data(), d->np, e);
             O.lam = lam;
             O.nlam = d->nb;
+            // per-cell tables on this grid: interpolation cells and weights, 4 pi V B(T) per band
+            const DevGrid &hg = ctx->grids[grid_id].dg;
+            const double *lam_dev = dput(ctx, O.owned, lam.data(), d->nb, e);
+            int2 *ab = dput<int2>(ctx, O.owned, nullptr, hg.ncell, e);
+            double2 *w64 = dput<double2>(ctx, O.owned, nullptr, hg.ncell, e);
+            float2 *w32 = dput<float2>(ctx, O.owned, nullptr, hg.ncell, e);
+            double *vb = dput<double>(ctx, O.owned, nullptr, (size_t)d->nb * hg.ncell, e);
+            if (e == cudaSuccess) e = ktable_cells(hg, lam_dev, d->nb, ab, w64, w32, vb, O.kt, ctx->stream);
+            O.kt.ab = ab;
+            O.kt.w64 = w64;
+            O.kt.w32 = w32;
+            O.kt.vb = vb;
         } else {
             if (d->nl < 2) return fail(ctx, GCMC_ERR_ARG, "xsec table needs >= 2 wavelengths");
             const size_t ns = (size_t)d->nl * d->nT * d->np;
@@ -882,6 +898,15 @@ gcmc_status gcmc_upload_opacity(gcmc_ctx *ctx, int grid_id, const gcmc_opacity_d
             O.xs.omega_rot = d->omega_rot;
             O.lam = xl;
             O.nlam = d->nl;
+            // per-cell tables on this grid: interpolation cells and weights, Doppler factors
+            const DevGrid &hg = ctx->grids[grid_id].dg;
+            int2 *ab = dput<int2>(ctx, O.owned, nullptr, hg.ncell, e);
+            double2 *w = dput<double2>(ctx, O.owned, nullptr, hg.ncell, e);
+            double *fac = dput<double>(ctx, O.owned, nullptr, hg.ncell, e);
+            if (e == cudaSuccess) e = xsec_cells(hg, O.xs, ab, w, fac, ctx->stream);
+            O.xs.ab = ab;
+            O.xs.w = w;
+            O.xs.fac = fac;
         }
     } else {
         return fail(ctx, GCMC_ERR_ARG, "unknown opacity kind");
@@ -1289,6 +1314,392 @@ gcmc_status gcmc_selftest_philox(gcmc_ctx *ctx, const uint32_t *ctr, const uint3
     dfree(ctx, d);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "philox selftest");
     return GCMC_OK;
+}
+
+}  // extern "C"
+
+// ==================================================================== serving (continuous batching)
+// A server owns two streams of its context: the serving kernel runs on one and never ends while
+// there is published work; cell tables of newly admitted jobs are built on the other, beside it.
+// Jobs wait in a host queue until a completion slot and their workspace fit (admission by HBM
+// footprint), are prepared, and are published to the running kernel through host-mapped memory in
+// admission order.  Completion records come back through host-mapped memory as well.
+// per slot: the job records, then the initial value of the slot's claim counter
+constexpr size_t SERVE_STAGE_BYTES = (sizeof(PrepJob) + sizeof(DevJob) + 8 + 255) & ~(size_t)255;
+
+struct gcmc_server {
+    struct Job {
+        uint64_t ticket = 0;
+        gcmc_job job{};
+        int slot = -1;
+        uint64_t seg = 0;
+        uint32_t gen = 0;
+        void *ws = nullptr;
+        size_t bytes = 0;
+        cudaEvent_t prepped = nullptr;
+        int n_obs = 0;
+        int64_t n_items = 0;
+        const DevJob *djob = nullptr;
+        bool published = false;
+        double t[4] = {0, 0, 0, 0};   // submitted, admitted, published, completed (s since creation)
+    };
+    struct Result {
+        double tally[MAX_OBS];
+        gcmc_stats st;
+        double t[4];
+    };
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+    gcmc_ctx *ctx = nullptr;
+    gcmc_server_cfg cfg{};
+    cudaStream_t s_serve = nullptr, s_prep = nullptr;
+    ServeCtl *ctl = nullptr;          // host-mapped (host pointers; the device sees the same addresses)
+    ServeSeg *ring = nullptr;
+    ServeDone *done = nullptr;
+    char *stage_h = nullptr;          // pinned, one job-record staging area per completion slot
+    cudaMemPool_t pool = nullptr;     // job workspaces (stream-ordered on the preparation stream)
+    ServeQueue q{};
+    unsigned long long *dstate = nullptr;
+    std::deque<Job> pending;
+    std::deque<Job> admitted;         // segment order
+    std::map<uint64_t, Result> results;
+    std::vector<int> free_slots;
+    size_t bytes_in_use = 0;
+    uint64_t next_ticket = 1, next_seg = 0, published = 0;
+    uint32_t next_gen = 0;
+    cudaEvent_t kdone = nullptr;
+    bool kernel_started = false;
+    int tab_n = 0;
+    int64_t kernel_launches = 0, completed = 0;
+    int grid_blocks = 0;
+};
+
+namespace {
+
+void server_free(gcmc_server *sv)
+{
+    if (sv->kdone) cudaEventDestroy(sv->kdone);
+    for (auto *dq : {&sv->pending, &sv->admitted})
+        for (auto &j : *dq) {
+            if (j.prepped) cudaEventDestroy(j.prepped);
+            if (j.ws) cudaFree(j.ws);
+        }
+    if (sv->dstate) cudaFree(sv->dstate);
+    if (sv->ctl) cudaFreeHost(sv->ctl);
+    if (sv->ring) cudaFreeHost(sv->ring);
+    if (sv->done) cudaFreeHost(sv->done);
+    if (sv->stage_h) cudaFreeHost(sv->stage_h);
+    if (sv->pool) cudaMemPoolDestroy(sv->pool);
+    if (sv->s_serve) cudaStreamDestroy(sv->s_serve);
+    if (sv->s_prep) cudaStreamDestroy(sv->s_prep);
+    delete sv;
+}
+
+bool kernel_running(gcmc_server *sv)
+{
+    return sv->kernel_started && cudaEventQuery(sv->kdone) == cudaErrorNotReady;
+}
+
+// oldest published segment that has not completed (next_seg when none)
+uint64_t oldest_open(const gcmc_server *sv)
+{
+    uint64_t o = sv->next_seg;
+    for (const auto &j : sv->admitted)
+        if (j.published) o = std::min(o, j.seg);
+    return o;
+}
+
+gcmc_status server_admit(gcmc_server *sv)
+{
+    gcmc_ctx *ctx = sv->ctx;
+    while (!sv->pending.empty() && !sv->free_slots.empty()) {
+        gcmc_server::Job &j = sv->pending.front();
+        Plan P;
+        gcmc_status s = plan_run(ctx, &j.job, 1, sv->cfg.chunk, P);
+        if (s) return s;
+        if (sv->bytes_in_use + P.ws_bytes > sv->cfg.hbm_budget && sv->bytes_in_use > 0) break;   // wait for memory
+        void *ws = nullptr;
+        CK(cudaMallocFromPoolAsync(&ws, P.ws_bytes, sv->pool, sv->s_prep));
+        cudaStream_t keep = ctx->stream;
+        ctx->stream = sv->s_prep;
+        const int slot = sv->free_slots.back();
+        s = stage(ctx, P, (char *)ws, nullptr, sv->stage_h + (size_t)slot * SERVE_STAGE_BYTES);
+        ctx->stream = keep;
+        if (s) {
+            cudaFreeAsync(ws, sv->s_prep);
+            return s;
+        }
+        j.ws = ws;
+        j.bytes = P.ws_bytes;
+        j.slot = slot;
+        sv->free_slots.pop_back();
+        j.n_obs = P.jobs[0].n_obs;
+        j.n_items = (j.job.n_packets + sv->cfg.chunk - 1) / sv->cfg.chunk;
+        j.djob = reinterpret_cast<const DevJob *>((char *)ws + P.off_jobs);
+        j.gen = (++sv->next_gen) & 0xFFFFFFu;
+        unsigned long long *init = reinterpret_cast<unsigned long long *>(
+            sv->stage_h + (size_t)slot * SERVE_STAGE_BYTES + sizeof(PrepJob) + sizeof(DevJob));
+        *init = (unsigned long long)j.gen << SERVE_GEN_SHIFT;
+        CK(cudaMemcpyAsync(sv->q.slot_next + slot, init, 8, cudaMemcpyHostToDevice, sv->s_prep));
+        CK(cudaMemsetAsync(sv->q.slot_done + slot, 0, 8, sv->s_prep));
+        CK(cudaEventCreateWithFlags(&j.prepped, cudaEventDisableTiming));
+        CK(cudaEventRecord(j.prepped, sv->s_prep));
+        j.t[1] = sv->now();
+        sv->bytes_in_use += j.bytes;
+        sv->admitted.push_back(j);
+        sv->pending.pop_front();
+    }
+    return GCMC_OK;
+}
+
+// Jobs are published as soon as their cell tables are ready (a job's claim and completion counters
+// belong to its slot, so the order of segments is free).  A ring entry is rewritten only when every
+// segment older than half a ring has completed.
+gcmc_status server_publish(gcmc_server *sv)
+{
+    gcmc_ctx *ctx = sv->ctx;
+    bool any = false;
+    const uint64_t oldest = oldest_open(sv);
+    for (auto &j : sv->admitted) {
+        if (j.published) continue;
+        if (sv->next_seg - oldest >= SERVE_RING / 2) break;
+        const cudaError_t e = cudaEventQuery(j.prepped);
+        if (e == cudaErrorNotReady) continue;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cell tables of a served job");
+        j.seg = sv->next_seg++;
+        ServeSeg &g = sv->ring[j.seg % SERVE_RING];
+        g.job = j.djob;
+        g.n_items = j.n_items;
+        g.slot = (uint32_t)j.slot;
+        g.gen = j.gen;
+        j.published = true;
+        j.t[2] = sv->now();
+        sv->published = j.seg + 1;
+        any = true;
+    }
+    if (any) __atomic_store_n(&sv->ctl->published, sv->published, __ATOMIC_RELEASE);
+    return GCMC_OK;
+}
+
+gcmc_status server_collect(gcmc_server *sv, uint64_t *done_tickets, int cap, int *n_done)
+{
+    const unsigned err = __atomic_load_n(&sv->ctl->err, __ATOMIC_ACQUIRE);
+    if (err & 1u) return fail(sv->ctx, GCMC_ERR_CUDA, "serving kernel: a work claim met a reused slot");
+    if (err & 2u) return fail(sv->ctx, GCMC_ERR_TIMEOUT, "serving kernel: a warp waited past its idle cap");
+    int nd = 0;
+    for (auto it = sv->admitted.begin(); it != sv->admitted.end();) {
+        gcmc_server::Job &j = *it;
+        if (!j.published || __atomic_load_n(&sv->done[j.slot].seq, __ATOMIC_ACQUIRE) != j.seg + 1) {
+            ++it;
+            continue;
+        }
+        const ServeDone &d = sv->done[j.slot];
+        gcmc_server::Result r;
+        unpack(d.acc, d.info, j.n_obs, r.tally, &r.st);
+        j.t[3] = sv->now();
+        std::memcpy(r.t, j.t, sizeof(r.t));
+        sv->results[j.ticket] = r;
+        if (done_tickets && nd < cap) done_tickets[nd] = j.ticket;
+        ++nd;
+        cudaFreeAsync(j.ws, sv->s_prep);
+        cudaEventDestroy(j.prepped);
+        sv->bytes_in_use -= j.bytes;
+        sv->free_slots.push_back(j.slot);
+        ++sv->completed;
+        it = sv->admitted.erase(it);
+    }
+    if (n_done) *n_done = nd;
+    return GCMC_OK;
+}
+
+gcmc_status server_kick(gcmc_server *sv)
+{
+    gcmc_ctx *ctx = sv->ctx;
+    bool open = false;
+    for (const auto &j : sv->admitted)
+        if (j.published) {
+            open = true;
+            break;
+        }
+    if (!open || kernel_running(sv)) return GCMC_OK;
+    const int idle_polls = sv->cfg.idle_us > 0 ? sv->cfg.idle_us : 2000;
+    // a fresh launch: no warp idle, not leaving (stream-ordered after the previous launch)
+    CK(cudaMemsetAsync(sv->q.n_idle, 0, 16, sv->s_serve));
+    cudaError_t e = launch_serve(ctx->d_grids, sv->q, sv->cfg.block, sv->cfg.blocks_per_sm, sv->cfg.chunk, sv->cfg.interval,
+                                 sv->cfg.refill_min, sv->tab_n, idle_polls, &sv->grid_blocks, sv->s_serve);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "serving kernel launch");
+    CK(cudaEventRecord(sv->kdone, sv->s_serve));
+    sv->kernel_started = true;
+    ++sv->kernel_launches;
+    return GCMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gcmc_status gcmc_server_create(gcmc_ctx *ctx, const gcmc_server_cfg *cfg, gcmc_server **out)
+{
+    if (!ctx || !out) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    gcmc_server *sv = new gcmc_server();
+    sv->ctx = ctx;
+    if (cfg) sv->cfg = *cfg;
+    gcmc_server_cfg &c = sv->cfg;
+    if (c.block == 0) c.block = 128;
+    if (c.chunk <= 0) c.chunk = 256;
+    if (c.interval <= 0) c.interval = 4;
+    if (c.refill_min <= 0) c.refill_min = 8;
+    if (c.max_jobs <= 0) c.max_jobs = 1024;
+    if (c.hbm_budget == 0) c.hbm_budget = (uint64_t)8 << 30;
+    if (c.block != 128 || c.chunk % 32 || c.max_jobs > (int)(SERVE_RING / 2)) {
+        delete sv;
+        return fail(ctx, GCMC_ERR_ARG, "server: block must be 128, chunk a multiple of 32, max_jobs <= 32768");
+    }
+    for (const auto &g : ctx->grids)
+        if (g.dg.r) sv->tab_n = std::max(sv->tab_n, tab_entries(g.dg.nlon, g.dg.nlat, g.dg.nr));
+    if (sv->tab_n == 0) {
+        delete sv;
+        return fail(ctx, GCMC_ERR_ARG, "server: upload the grids first");
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&sv->s_serve, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->s_prep, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&sv->ctl, sizeof(ServeCtl), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&sv->ring, sizeof(ServeSeg) * SERVE_RING, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&sv->done, sizeof(ServeDone) * c.max_jobs, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&sv->stage_h, (size_t)SERVE_STAGE_BYTES * c.max_jobs);
+    if (e == cudaSuccess) e = cudaMalloc(&sv->dstate, 8 * (3 + 2 * (size_t)c.max_jobs));
+    if (e == cudaSuccess) e = cudaMemset(sv->dstate, 0, 8 * (3 + 2 * (size_t)c.max_jobs));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->kdone, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        // a pool of its own that keeps freed workspace mapped (no release back to the driver)
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = ctx->device;
+        e = cudaMemPoolCreate(&sv->pool, &props);
+        uint64_t keep = ~0ull;
+        if (e == cudaSuccess) e = cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    ServeCtl *dctl = nullptr;
+    ServeSeg *dring = nullptr;
+    ServeDone *ddone = nullptr;
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&dctl, sv->ctl, 0);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&dring, sv->ring, 0);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&ddone, sv->done, 0);
+    if (e != cudaSuccess) {
+        server_free(sv);
+        return cuda_fail(ctx, e, "server create");
+    }
+    std::memset(sv->ctl, 0, sizeof(ServeCtl));
+    std::memset(sv->ring, 0, sizeof(ServeSeg) * SERVE_RING);
+    std::memset(sv->done, 0, sizeof(ServeDone) * c.max_jobs);
+    sv->q.ctl = dctl;
+    sv->q.ring = dring;
+    sv->q.done = ddone;
+    sv->q.cur_seg = sv->dstate;
+    sv->q.n_idle = sv->dstate + 1;
+    sv->q.exiting = sv->dstate + 2;
+    sv->q.slot_next = sv->dstate + 3;
+    sv->q.slot_done = sv->dstate + 3 + c.max_jobs;
+    for (int s = c.max_jobs - 1; s >= 0; --s) sv->free_slots.push_back(s);
+    *out = sv;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_server_submit(gcmc_server *sv, const gcmc_job *job, uint64_t *ticket)
+{
+    if (!sv || !job || !ticket) return GCMC_ERR_ARG;
+    gcmc_ctx *ctx = sv->ctx;
+    gcmc_status s = check_job(ctx, *job);
+    if (s) return s;
+    if (job->n_packets < 1) return fail(ctx, GCMC_ERR_ARG, "a served job needs n_packets >= 1");
+    if (ctx->sources[job->source_id].precision == GCMC_FP64) return fail(ctx, GCMC_ERR_ARG, "the server runs FP32 jobs");
+    const DevGrid &g = ctx->grids[job->grid_id].dg;
+    if (tab_entries(g.nlon, g.nlat, g.nr) > sv->tab_n)
+        return fail(ctx, GCMC_ERR_ARG, "grid larger than every grid present when the server was created");
+    gcmc_server::Job j;
+    j.ticket = sv->next_ticket++;
+    j.job = *job;
+    j.t[0] = sv->now();
+    sv->pending.push_back(j);
+    *ticket = j.ticket;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_server_progress(gcmc_server *sv, uint64_t *done_tickets, int cap, int *n_done)
+{
+    if (!sv) return GCMC_ERR_ARG;
+    cudaSetDevice(sv->ctx->device);
+    gcmc_status s = server_collect(sv, done_tickets, cap, n_done);
+    if (!s) s = server_admit(sv);
+    if (!s) s = server_publish(sv);
+    if (!s) s = server_kick(sv);
+    return s;
+}
+
+gcmc_status gcmc_server_result(gcmc_server *sv, uint64_t ticket, double *tallies_out, gcmc_stats *stats_out)
+{
+    if (!sv) return GCMC_ERR_ARG;
+    auto it = sv->results.find(ticket);
+    if (it == sv->results.end()) return GCMC_ERR_NOT_READY;
+    if (tallies_out) std::memcpy(tallies_out, it->second.tally, sizeof(it->second.tally));
+    if (stats_out) *stats_out = it->second.st;
+    sv->results.erase(it);
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_server_times(gcmc_server *sv, uint64_t ticket, double *t4)
+{
+    if (!sv || !t4) return GCMC_ERR_ARG;
+    auto it = sv->results.find(ticket);
+    if (it == sv->results.end()) return GCMC_ERR_NOT_READY;
+    std::memcpy(t4, it->second.t, sizeof(it->second.t));
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_server_query(gcmc_server *sv, gcmc_server_stats *st)
+{
+    if (!sv || !st) return GCMC_ERR_ARG;
+    std::memset(st, 0, sizeof(*st));
+    st->pending = (int64_t)sv->pending.size();
+    st->admitted = (int64_t)sv->admitted.size();
+    st->completed = sv->completed;
+    st->bytes_in_use = sv->bytes_in_use;
+    st->kernel_launches = sv->kernel_launches;
+    st->kernel_running = kernel_running(sv) ? 1 : 0;
+    st->grid_blocks = sv->grid_blocks;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_server_destroy(gcmc_server *sv, double timeout_s)
+{
+    if (!sv) return GCMC_ERR_ARG;
+    gcmc_ctx *ctx = sv->ctx;
+    cudaSetDevice(ctx->device);
+    // published work finishes first; the kernel leaves when it finds the queue empty and stop set
+    __atomic_store_n(&sv->ctl->stop, 1u, __ATOMIC_RELEASE);
+    gcmc_status s = GCMC_OK;
+    if (sv->kernel_started) {
+        const auto t0 = std::chrono::steady_clock::now();
+        for (;;) {
+            const cudaError_t e = cudaEventQuery(sv->kdone);
+            if (e == cudaSuccess) break;
+            if (e != cudaErrorNotReady) {
+                s = cuda_fail(ctx, e, "serving kernel");
+                break;
+            }
+            if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > timeout_s) {
+                // the kernel is still draining published work: leave everything allocated
+                return fail(ctx, GCMC_ERR_TIMEOUT, "serving kernel still running at destroy");
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(200));
+        }
+    }
+    cudaStreamSynchronize(sv->s_prep);
+    server_free(sv);
+    return s;
 }
 
 }  // extern "C"

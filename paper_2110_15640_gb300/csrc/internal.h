@@ -21,10 +21,8 @@ struct HostLog {               // device pointers of the per-packet debug output
 // per-job parameters of the cell-table kernels
 struct PrepJob {
     int32_t lam, g;            // wavelength / band index, g-ordinate
-    int32_t lam_hint;
-    int32_t bslot;             // emission: row of this job's band in the group's 4 pi V B(T) table
-    double lam_m;              // wavelength (m) for the Planck function (k-table) or rest wavelength (xsec)
-    double c1;                 // Planck prefactor 2 h c^2 / lambda^5 (k-table)
+    int32_t lam_hint, pad;
+    double lam_m;              // band centre (k-table) or rest wavelength (xsec), m
     void *rec;                 // output: albedo records or alpha (march precision)
     long long *cdf;            // emission: cumulative pdf in 2^62 fixed point (first scratch for L_i as FP64)
     void *wcell;               // emission: launch weight (march precision)
@@ -32,9 +30,6 @@ struct PrepJob {
     double *bsum;              // emission: per-block partial sums [nblk]
     double *bcnt;              // emission: per-block included counts [nblk]
     double *lum;               // emission: optional copy of L_i (debug), or NULL
-    const double *vb;          // emission: the group's 4 pi V_i B(T_i) table, [band slot][cell]
-    // emission, entry s < number of band slots of the group: wavelength, Planck prefactor of slot s
-    double pl_lam, pl_c1;
 };
 
 // slots of PrepJob::info
@@ -52,6 +47,11 @@ struct KtabDev {               // device k-table (natural logs in FP64)
     // order one, so FP32 keeps ~1e-7 relative accuracy (ln k itself would lose ~ulp(10))
     const float4 *node_f;      // [nb][ng][nT][np]
     const double *Tg, *pg;     // axes
+    // per-cell tables of the grid the table is uploaded for, built once at upload:
+    const int2 *ab;            // [ncell] (T, p) interpolation cell
+    const double2 *w64;        // [ncell] (wT, wp) in FP64
+    const float2 *w32;         // [ncell] the same rounded to FP32
+    const double *vb;          // [nb][ncell] 4 pi V_i B_lambda(T_i) at each band centre
 };
 
 struct XsecDev {
@@ -61,6 +61,10 @@ struct XsecDev {
     const float *lnsig_f;      // FP32 logs
     const double *Tg, *pg;
     double view_theta, view_phi, omega_rot;
+    // per-cell tables of the grid the table is uploaded for, built once at upload:
+    const int2 *ab;            // [ncell] (T, p) interpolation cell
+    const double2 *w;          // [ncell] (wT, wp)
+    const double *fac;         // [ncell] Doppler factor lambda_eff / lambda_0 = 1 - v_LOS / c
 };
 
 struct AlbDev {
@@ -70,17 +74,63 @@ struct AlbDev {
 };
 
 constexpr int PREP_BLOCK = 256;
-constexpr int EMIS_SCAN_BLOCK = 1024;
+// cells per block of the emission pdf scan: small blocks, so that the cell-table kernels of a
+// newly admitted job fit beside a resident serving kernel
+constexpr int EMIS_SCAN_BLOCK = 256;
 
 // cell tables (S1)
 cudaError_t prep_albedo(int precision, const DevGrid *dgrid, const DevGrid &hgrid, const AlbDev &op,
                         const PrepJob *djobs, int njobs, cudaStream_t st);
-cudaError_t prep_emission(int precision, const DevGrid *dgrid, const DevGrid &hgrid, const KtabDev &kt,
-                          const PrepJob *djobs, int njobs, int nslots, double tau_vert_max, double beta, int2 *wk_ab,
-                          void *wk_w, cudaStream_t st);
+cudaError_t prep_emission(int precision, const DevGrid &hgrid, const KtabDev &kt, const PrepJob *djobs, int njobs,
+                          double tau_vert_max, double beta, cudaStream_t st);
 int emis_col_blocks(const DevGrid &g);     // partial-sum blocks of the column kernel
-cudaError_t prep_xsec(int precision, const DevGrid *dgrid, const DevGrid &hgrid, const XsecDev &xs,
-                      const PrepJob *djobs, int njobs, int2 *wk_ab, double2 *wk_w, double *wk_fac, cudaStream_t st);
+cudaError_t prep_xsec(int precision, const DevGrid &hgrid, const XsecDev &xs, const PrepJob *djobs, int njobs,
+                      cudaStream_t st);
+// per-cell tables of an opacity on its grid (at upload): interpolation cells and weights, and
+// 4 pi V B(T) per band (k-table) or the Doppler factors (cross sections); lam_dev: band centres [nb]
+cudaError_t ktable_cells(const DevGrid &hgrid, const double *lam_dev, int nb, int2 *ab, double2 *w64, float2 *w32,
+                         double *vb, const KtabDev &kt, cudaStream_t st);
+cudaError_t xsec_cells(const DevGrid &hgrid, const XsecDev &xs, int2 *ab, double2 *w, double *fac, cudaStream_t st);
+
+// serving queue (continuous batching): host-mapped control block, job ring and completion records,
+// and device-side claim counters
+constexpr unsigned SERVE_RING = 65536;      // published jobs addressable at once (ring of segments)
+struct ServeCtl {
+    unsigned long long published;           // segments published by the host (store-release)
+    unsigned int stop;                      // the host asks the kernel to leave when idle
+    unsigned int err;                       // set by the kernel: a claim met another job of its slot
+};
+// A slot's claim counter holds (generation << SERVE_GEN_SHIFT) | items claimed; the generation
+// (the job's admission number) is set with the count when the slot is given to a job, so a claim
+// can tell whether the counter still belongs to the job it read from the ring.
+constexpr int SERVE_GEN_SHIFT = 40;
+// upper bound on the polls of an idle warp while other warps still run (about 20 s): past it the
+// warp reports an error and the launch leaves
+constexpr long long SERVE_IDLE_CAP = 20000000;
+struct ServeSeg {
+    const DevJob *job;                      // device pointer
+    int64_t n_items;                        // work items of `chunk` packets
+    uint32_t slot;                          // completion record and counters
+    uint32_t gen;                           // admission number of the job (low 24 bits)
+};
+struct ServeDone {
+    unsigned long long acc[ACC_SLOTS];      // the job's accumulators
+    double info[4];                         // emission: L_tot, n_incl, cdf_total
+    unsigned long long seq;                 // segment index + 1, written last
+    unsigned long long pad[3];
+};
+struct ServeQueue {
+    ServeCtl *ctl;                          // host-mapped
+    const ServeSeg *ring;                   // host-mapped [SERVE_RING]
+    ServeDone *done;                        // host-mapped [slots]
+    unsigned long long *cur_seg;            // device: oldest segment with unclaimed items
+    unsigned long long *n_idle;             // device: warps of the current launch without work
+    unsigned long long *exiting;            // device: the current launch is leaving
+    unsigned long long *slot_next;          // device [slots]: next item of the slot's job to claim
+    unsigned long long *slot_done;          // device [slots]: items of the slot's job finished
+};
+cudaError_t launch_serve(const DevGrid *grids, const ServeQueue &q, int block, int blocks_per_sm, int chunk, int interval,
+                         int refill_min, int tab_n, int idle_polls, int *grid_blocks, cudaStream_t st);
 
 // transport
 size_t transport_smem(int block);

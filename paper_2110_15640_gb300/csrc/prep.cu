@@ -85,13 +85,8 @@ cudaError_t prep_albedo(int precision, const DevGrid *, const DevGrid &hg, const
 }
 
 // ------------------------------------------------------------------ interpolation weights (T, p)
-template <typename real> struct Vec2;
-template <> struct Vec2<float> { using type = float2; };
-template <> struct Vec2<double> { using type = double2; };
-
-template <typename real>
-__global__ void k_tp_weights(DevGrid G, const double *Tg, int nT, const double *pg, int np, int2 *ab,
-                             typename Vec2<real>::type *w)
+__global__ void k_tp_weights(DevGrid G, const double *Tg, int nT, const double *pg, int np, int2 *ab, double2 *w64,
+                             float2 *w32)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= G.ncell) return;
@@ -100,20 +95,30 @@ __global__ void k_tp_weights(DevGrid G, const double *Tg, int nT, const double *
     interp_idx(Tg, nT, (double)G.T[idx], a, wT);
     interp_idx(pg, np, (double)G.p[idx], b, wp);
     ab[idx] = make_int2(a, b);
-    w[idx] = {(real)wT, (real)wp};
+    w64[idx] = make_double2(wT, wp);
+    w32[idx] = make_float2((float)wT, (float)wp);
 }
 
 // ------------------------------------------------------------------ emission
-// 4 pi V_i B_lambda(T_i) once per distinct band wavelength of the group (the g-ordinates of a band
-// share it); row s of the table belongs to the wavelength carried by entry s of the job array
-__global__ void k_emis_planck(DevGrid G, const PrepJob *__restrict__ jobs)
+// 4 pi V_i B_lambda(T_i) for every band centre (row b of vb), once per k-table upload
+__global__ void k_emis_planck(DevGrid G, const double *__restrict__ lam, double *vb)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= G.ncell) return;
-    const double lam = jobs[blockIdx.y].pl_lam, c1 = jobs[blockIdx.y].pl_c1;
-    const double x = H_PLANCK * C_LIGHT / (lam * K_BOLTZ * (double)G.T[idx]);
-    double *vb = const_cast<double *>(jobs[0].vb);
+    const double l = lam[blockIdx.y];
+    const double c1 = 2.0 * H_PLANCK * C_LIGHT * C_LIGHT / (l * l * l * l * l);
+    const double x = H_PLANCK * C_LIGHT / (l * K_BOLTZ * (double)G.T[idx]);
     vb[(int64_t)blockIdx.y * G.ncell + idx] = 4.0 * PI * G.vol[idx] * (c1 / expm1(x));
+}
+
+cudaError_t ktable_cells(const DevGrid &hg, const double *lam_dev, int nb, int2 *ab, double2 *w64, float2 *w32, double *vb,
+                         const KtabDev &kt, cudaStream_t st)
+{
+    count_launch(2);
+    const unsigned nbk = (unsigned)((hg.ncell + PREP_BLOCK - 1) / PREP_BLOCK);
+    k_tp_weights<<<nbk, PREP_BLOCK, 0, st>>>(hg, kt.Tg, kt.nT, kt.pg, kt.np, ab, w64, w32);
+    k_emis_planck<<<dim3(nbk, (unsigned)nb), PREP_BLOCK, 0, st>>>(hg, lam_dev, vb);
+    return cudaGetLastError();
 }
 
 constexpr int COL_BLOCK = 128;
@@ -126,8 +131,6 @@ int emis_col_blocks(const DevGrid &g) { return (int)(((int64_t)g.nlon * g.nlat +
 // Excluded cells get L = -1 in the scratch copy that the pdf kernel reads.
 template <typename real>
 __global__ void __launch_bounds__(COL_BLOCK) k_emis_column(DevGrid G, KtabDev kt, const PrepJob *__restrict__ jobs,
-                                                           const int2 *__restrict__ ab,
-                                                           const typename Vec2<real>::type *__restrict__ w,
                                                            double tau_vert_max)
 {
     extern __shared__ __align__(16) unsigned char col_smem[];
@@ -142,7 +145,8 @@ __global__ void __launch_bounds__(COL_BLOCK) k_emis_column(DevGrid G, KtabDev kt
     double lsum = 0.0;
     int cnt = 0;
     if (col < ncol) {
-        const double *__restrict__ vb = pj.vb + (int64_t)pj.bslot * G.ncell;
+        const double *__restrict__ vb = kt.vb + (int64_t)pj.lam * G.ncell;
+        const int2 *__restrict__ ab = kt.ab;
         real *__restrict__ rec = reinterpret_cast<real *>(pj.rec);
         double *__restrict__ lb = reinterpret_cast<double *>(pj.cdf);
         double *__restrict__ lum = pj.lum;
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(COL_BLOCK) k_emis_column(DevGrid G, KtabDev kt
             const int2 q = ab[idx];
             real alpha;
             if constexpr (sizeof(real) == 8) {
-                const double2 ww = w[idx];
+                const double2 ww = kt.w64[idx];
                 const double wT = ww.x, wp = ww.y;
                 const double *base = kt.lnk + slice;
                 const double l00 = base[q.x * kt.np + q.y], l10 = base[(q.x + 1) * kt.np + q.y];
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(COL_BLOCK) k_emis_column(DevGrid G, KtabDev kt
                 const double lk = (1 - wT) * (1 - wp) * l00 + wT * (1 - wp) * l10 + (1 - wT) * wp * l01 + wT * wp * l11;
                 alpha = (double)G.rho[idx] * exp(lk);
             } else {
-                const float2 ww = w[idx];
+                const float2 ww = kt.w32[idx];
                 const float4 nd = __ldg(kt.node_f + slice + q.x * kt.np + q.y);
                 alpha = (G.rho[idx] * nd.x) * expf(fmaf(ww.x, fmaf(ww.y, nd.w, nd.y), ww.y * nd.z));
             }
@@ -223,8 +227,9 @@ __global__ void k_emis_reduce(int64_t ncell, const PrepJob *__restrict__ jobs)
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-        v = ss[threadIdx.x];
-        c = sc[threadIdx.x];
+        constexpr int NW = EMIS_SCAN_BLOCK / 32;
+        v = threadIdx.x < NW ? ss[threadIdx.x] : 0.0;
+        c = threadIdx.x < NW ? sc[threadIdx.x] : 0.0;
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
             v += __shfl_down_sync(0xffffffffu, v, o);
@@ -321,7 +326,11 @@ __global__ void k_emis_pdf(int64_t ncell, const PrepJob *__restrict__ jobs, doub
     long long s = warp_incl_scan_ll(Q);
     if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = s;
     __syncthreads();
-    if (threadIdx.x < 32) ws[threadIdx.x] = warp_incl_scan_ll(ws[threadIdx.x]);
+    if (threadIdx.x < 32) {
+        constexpr int NW = EMIS_SCAN_BLOCK / 32;
+        const long long t = warp_incl_scan_ll(threadIdx.x < NW ? ws[threadIdx.x] : 0ll);
+        if (threadIdx.x < NW) ws[threadIdx.x] = t;
+    }
     __syncthreads();
     if (threadIdx.x >= 32) s += ws[(threadIdx.x >> 5) - 1];
     if (idx < ncell) {
@@ -331,21 +340,27 @@ __global__ void k_emis_pdf(int64_t ncell, const PrepJob *__restrict__ jobs, doub
     if (threadIdx.x == EMIS_SCAN_BLOCK - 1) reinterpret_cast<long long *>(pj.bsum)[blockIdx.x] = s;
 }
 
+// exclusive prefix of the per-block totals (one warp per job, 32 blocks per pass) and the job's total
 __global__ void k_emis_scan_blocks(int nblk, const PrepJob *__restrict__ jobs, int njobs)
 {
-    const int jb = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jb = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (jb >= njobs) return;
-    const PrepJob pj = jobs[jb];
+    const PrepJob &pj = jobs[jb];
     const long long *bt = reinterpret_cast<const long long *>(pj.bsum);
     long long *off = reinterpret_cast<long long *>(pj.bcnt);
     long long run = 0;
-    for (int b = 0; b < nblk; ++b) {
-        const long long t = bt[b];
-        off[b] = run;
-        run += t;
+    for (int b0 = 0; b0 < nblk; b0 += 32) {
+        const int b = b0 + lane;
+        const long long t = b < nblk ? bt[b] : 0ll;
+        const long long inc = warp_incl_scan_ll(t);
+        if (b < nblk) off[b] = run + inc - t;
+        run += __shfl_sync(0xffffffffu, inc, 31);
     }
-    pj.info[INFO_CDFTOT] = (double)run / CDF_FIX;
-    reinterpret_cast<long long *>(pj.info)[INFO_QTOT] = run;
+    if (lane == 0) {
+        pj.info[INFO_CDFTOT] = (double)run / CDF_FIX;
+        reinterpret_cast<long long *>(pj.info)[INFO_QTOT] = run;
+    }
 }
 
 // block offsets added to the within-block prefixes: the fixed-point cumulative pdf itself (OUT =
@@ -361,30 +376,21 @@ __global__ void k_emis_cdf_add(int64_t ncell, const PrepJob *__restrict__ jobs)
     else pj.cdf[idx] = v;
 }
 
-cudaError_t prep_emission(int precision, const DevGrid *, const DevGrid &hg, const KtabDev &kt, const PrepJob *djobs,
-                          int njobs, int nslots, double tau_vert_max, double beta, int2 *wk_ab, void *wk_w,
-                          cudaStream_t st)
+cudaError_t prep_emission(int precision, const DevGrid &hg, const KtabDev &kt, const PrepJob *djobs, int njobs,
+                          double tau_vert_max, double beta, cudaStream_t st)
 {
-    count_launch(7);
+    count_launch(5);
     const bool f64 = precision == GCMC_FP64;
-    const unsigned nb = (unsigned)((hg.ncell + PREP_BLOCK - 1) / PREP_BLOCK);
-    if (f64) k_tp_weights<double><<<nb, PREP_BLOCK, 0, st>>>(hg, kt.Tg, kt.nT, kt.pg, kt.np, wk_ab, (double2 *)wk_w);
-    else k_tp_weights<float><<<nb, PREP_BLOCK, 0, st>>>(hg, kt.Tg, kt.nT, kt.pg, kt.np, wk_ab, (float2 *)wk_w);
-    k_emis_planck<<<dim3(nb, (unsigned)nslots), PREP_BLOCK, 0, st>>>(hg, djobs);
     const int ncolb = emis_col_blocks(hg);
     const dim3 gc((unsigned)ncolb, (unsigned)njobs);
-    if (f64)
-        k_emis_column<double><<<gc, COL_BLOCK, hg.nr * sizeof(double), st>>>(hg, kt, djobs, wk_ab, (const double2 *)wk_w,
-                                                                             tau_vert_max);
-    else
-        k_emis_column<float><<<gc, COL_BLOCK, hg.nr * sizeof(float), st>>>(hg, kt, djobs, wk_ab, (const float2 *)wk_w,
-                                                                           tau_vert_max);
+    if (f64) k_emis_column<double><<<gc, COL_BLOCK, hg.nr * sizeof(double), st>>>(hg, kt, djobs, tau_vert_max);
+    else k_emis_column<float><<<gc, COL_BLOCK, hg.nr * sizeof(float), st>>>(hg, kt, djobs, tau_vert_max);
     k_emis_total<<<(njobs + 127) / 128, 128, 0, st>>>(ncolb, djobs, njobs, beta);
     const int nblk = (int)((hg.ncell + EMIS_SCAN_BLOCK - 1) / EMIS_SCAN_BLOCK);
     const dim3 g3((unsigned)nblk, (unsigned)njobs);
     if (f64) k_emis_pdf<double><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
     else k_emis_pdf<float><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
-    k_emis_scan_blocks<<<(njobs + 127) / 128, 128, 0, st>>>(nblk, djobs, njobs);
+    k_emis_scan_blocks<<<(njobs + 3) / 4, 128, 0, st>>>(nblk, djobs, njobs);
     k_emis_cdf_add<long long><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs);
     return cudaGetLastError();
 }
@@ -417,9 +423,11 @@ __global__ void k_xsec_cells(DevGrid G, XsecDev xs, int2 *ab, double2 *w, double
 }
 
 template <typename real>
-__global__ void k_prep_xsec(DevGrid G, XsecDev xs, const PrepJob *__restrict__ jobs, const int2 *__restrict__ ab,
-                            const double2 *__restrict__ w, const double *__restrict__ fac)
+__global__ void k_prep_xsec(DevGrid G, XsecDev xs, const PrepJob *__restrict__ jobs)
 {
+    const int2 *__restrict__ ab = xs.ab;
+    const double2 *__restrict__ w = xs.w;
+    const double *__restrict__ fac = xs.fac;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= G.ncell) return;
     const PrepJob pj = jobs[blockIdx.y];
@@ -470,15 +478,20 @@ __global__ void k_prep_xsec(DevGrid G, XsecDev xs, const PrepJob *__restrict__ j
     }
 }
 
-cudaError_t prep_xsec(int precision, const DevGrid *, const DevGrid &hg, const XsecDev &xs, const PrepJob *djobs,
-                      int njobs, int2 *wk_ab, double2 *wk_w, double *wk_fac, cudaStream_t st)
+cudaError_t xsec_cells(const DevGrid &hg, const XsecDev &xs, int2 *ab, double2 *w, double *fac, cudaStream_t st)
 {
-    count_launch(2);
+    count_launch(1);
     const unsigned nb = (unsigned)((hg.ncell + PREP_BLOCK - 1) / PREP_BLOCK);
-    k_xsec_cells<<<nb, PREP_BLOCK, 0, st>>>(hg, xs, wk_ab, wk_w, wk_fac);
-    dim3 g1(nb, (unsigned)njobs);
-    if (precision == GCMC_FP64) k_prep_xsec<double><<<g1, PREP_BLOCK, 0, st>>>(hg, xs, djobs, wk_ab, wk_w, wk_fac);
-    else k_prep_xsec<float><<<g1, PREP_BLOCK, 0, st>>>(hg, xs, djobs, wk_ab, wk_w, wk_fac);
+    k_xsec_cells<<<nb, PREP_BLOCK, 0, st>>>(hg, xs, ab, w, fac);
+    return cudaGetLastError();
+}
+
+cudaError_t prep_xsec(int precision, const DevGrid &hg, const XsecDev &xs, const PrepJob *djobs, int njobs, cudaStream_t st)
+{
+    count_launch(1);
+    const dim3 g1((unsigned)((hg.ncell + PREP_BLOCK - 1) / PREP_BLOCK), (unsigned)njobs);
+    if (precision == GCMC_FP64) k_prep_xsec<double><<<g1, PREP_BLOCK, 0, st>>>(hg, xs, djobs);
+    else k_prep_xsec<float><<<g1, PREP_BLOCK, 0, st>>>(hg, xs, djobs);
     return cudaGetLastError();
 }
 
@@ -599,7 +612,7 @@ extern "C" gcmc_status gcmc_emission_pdf_noalloc(const double *lum, int64_t ncel
     k_emis_reduce<<<g3, EMIS_SCAN_BLOCK, 0, st>>>(ncell, pj);
     k_emis_total<<<1, 128, 0, st>>>(nblk, pj, 1, beta);
     k_emis_pdf<double><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(ncell, pj, beta);
-    k_emis_scan_blocks<<<1, 128, 0, st>>>(nblk, pj, 1);
+    k_emis_scan_blocks<<<1, 32, 0, st>>>(nblk, pj, 1);
     k_emis_cdf_add<double><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(ncell, pj);
     return cudaGetLastError() == cudaSuccess ? GCMC_OK : GCMC_ERR_CUDA;
 }

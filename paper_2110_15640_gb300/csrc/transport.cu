@@ -500,6 +500,37 @@ __global__ void __launch_bounds__(256) k_transport_plain(const DevGrid *__restri
     flush(S.sm, S.stride, J.acc);
 }
 
+// One work item (packets p0 .. p1-1 of job J) on one warp: lanes whose packets have finished are
+// refilled together once at least refill_min of them are idle; rays that ended are settled at
+// those points; between them every live lane takes `interval` cell steps.
+template <typename real, bool SCAT, class SinkT>
+__device__ __forceinline__ void run_item(const DevJob &J, const DevGrid &G, const Tabs<real> &T, int64_t p0, int64_t p1,
+                                         int interval, int refill_min, SinkT &S)
+{
+    const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+    const JobC<real> jc = job_consts<real>(J);
+    int64_t pool = p0;
+    Packet<real> P;
+    P.alive = 0;
+    P.hint = -1;
+    P.ended = 0;
+    for (;;) {
+        if (P.alive && P.ended) settle<real, SCAT>(P, J, S);
+        const unsigned idle = __ballot_sync(0xffffffffu, !P.alive);
+        const int n_idle = __popc(idle);
+        const int64_t left = p1 - pool;
+        if (n_idle && left > 0 && (int64_t)n_idle >= min((int64_t)refill_min, left)) {
+            const int64_t mine = pool + __popc(idle & lt);
+            if (!P.alive && mine < p1) launch<real, SCAT>(P, J, G, mine, S);
+            pool += n_idle;
+        }
+        if (!__any_sync(0xffffffffu, P.alive)) break;
+        for (int t = 0; t < interval; ++t)
+            if (P.alive && !P.ended) step<real, SCAT>(P, J, G, T, jc, S);
+    }
+    __syncwarp();
+}
+
 // MINB > 0: compiled for MINB resident 128-thread blocks per SM (register cap 65536 / (128 MINB));
 // MINB = 0: any block size up to 256, at most 128 registers (two 256-thread blocks per SM)
 template <typename real, bool SCAT, int MINB>
@@ -515,7 +546,6 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 2) k_transport
     S.stride = blockDim.x;
     for (int s = 0; s < NSLOT; ++s) S.sm[s * S.stride] = 0ull;
     const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
     // march tables in shared memory: one copy per block when every job uses the same grid, else one
     // per warp, restaged when the warp's work item comes from another grid
     auto *tab0 = reinterpret_cast<typename Pair<real>::type *>(sacc + NSLOT * blockDim.x);
@@ -545,31 +575,138 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 2) k_transport
             T = stage_tabs<real>(G, tab0 + (threadIdx.x >> 5) * tab_n, lane, 32);
             __syncwarp();
         }
-        const JobC<real> jc = job_consts<real>(J);
         const int64_t p0 = ((int64_t)item - J.chunk_begin) * chunk;
-        const int64_t p1 = min(p0 + (int64_t)chunk, J.n_packets);
-        int64_t pool = p0;
-        Packet<real> P;
-        P.alive = 0;
-        P.hint = -1;
-        P.ended = 0;
-        for (;;) {
-            // rays that ended since the last check are settled together (tally, next ray or finish)
-            if (P.alive && P.ended) settle<real, SCAT>(P, J, S);
-            const unsigned idle = __ballot_sync(0xffffffffu, !P.alive);
-            const int n_idle = __popc(idle);
-            const int64_t left = p1 - pool;
-            if (n_idle && left > 0 && (int64_t)n_idle >= min((int64_t)refill_min, left)) {
-                const int64_t mine = pool + __popc(idle & lt);
-                if (!P.alive && mine < p1) launch<real, SCAT>(P, J, G, mine, S);
-                pool += n_idle;
-            }
-            if (!__any_sync(0xffffffffu, P.alive)) break;
-            for (int t = 0; t < interval; ++t)
-                if (P.alive && !P.ended) step<real, SCAT>(P, J, G, T, jc, S);
-        }
-        __syncwarp();
+        run_item<real, SCAT>(J, G, T, p0, min(p0 + (int64_t)chunk, J.n_packets), interval, refill_min, S);
         flush(S.sm, S.stride, J.acc);
+    }
+}
+
+// ------------------------------------------------------------------ serving kernel
+// A persistent kernel fed by a queue of jobs that the host publishes while it runs (continuous
+// batching).  Warps drain the published jobs in publication order: each claims work items of the
+// oldest job that has unclaimed items (from the counter of the job's slot), runs them, and adds its
+// tallies; the warp that finishes a job's last item
+// copies the job's accumulators and emission totals into the job's completion record in host-mapped
+// memory and then writes the record's sequence number.  A warp that finds no published work polls
+// with a sleep and leaves after `idle_polls` empty polls, or at once when the host sets `stop`; the
+// host relaunches the kernel when new work is published after it has left.
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned int ld_acquire_sys(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <typename real, bool SCAT>
+__global__ void __launch_bounds__(128, 4) k_transport_serve(const DevGrid *__restrict__ grids, ServeQueue q, int chunk,
+                                                         int interval, int refill_min, int tab_n, int idle_polls)
+{
+    extern __shared__ __align__(16) unsigned long long sacc[];
+    Sink<real, false> S;
+    S.sm = sacc + threadIdx.x;
+    S.stride = blockDim.x;
+    for (int s = 0; s < NSLOT; ++s) S.sm[s * S.stride] = 0ull;
+    const int lane = threadIdx.x & 31;
+    auto *tabw = reinterpret_cast<typename Pair<real>::type *>(sacc + NSLOT * blockDim.x) + (threadIdx.x >> 5) * tab_n;
+    Tabs<real> T;
+    int cur_grid = -1;
+    long long empty = 0;
+    bool idle = false;
+    const unsigned long long n_warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (;;) {
+        // the kernel leaves as a whole: once one warp has seen every warp idle for idle_polls polls it
+        // sets `exiting`, and every warp leaves at its next check (work published later is taken by
+        // the next launch)
+        // lane 0 reads the queue state; the warp takes every decision on the broadcast values
+        unsigned long long seg = 0, pub = 0, leaving = 0;
+        if (lane == 0) {
+            leaving = ld_relaxed_gpu(q.exiting);
+            seg = ld_relaxed_gpu(q.cur_seg);
+            pub = ld_acquire_sys(&q.ctl->published);
+        }
+        leaving = __shfl_sync(0xffffffffu, leaving, 0);
+        seg = __shfl_sync(0xffffffffu, seg, 0);
+        pub = __shfl_sync(0xffffffffu, pub, 0);
+        if (leaving) break;
+        if (seg >= pub) {
+            int quit = 0;
+            if (lane == 0) {
+                if (!idle) atomicAdd(q.n_idle, 1ull);
+                const bool all_idle = ld_relaxed_gpu(q.n_idle) == n_warps;
+                if ((all_idle && (empty >= idle_polls || ld_acquire_sys(&q.ctl->stop))) || empty >= SERVE_IDLE_CAP) {
+                    if (!all_idle) atomicOr_system(&q.ctl->err, 2u);   // waited SERVE_IDLE_CAP polls
+                    atomicExch(q.exiting, 1ull);
+                    quit = 1;
+                }
+            }
+            idle = true;
+            ++empty;
+            if (__shfl_sync(0xffffffffu, quit, 0)) break;
+            __nanosleep(1000);
+            continue;
+        }
+        if (idle) {
+            idle = false;
+            if (lane == 0) atomicAdd(q.n_idle, ~0ull);   // minus one
+        }
+        empty = 0;
+        const unsigned r = (unsigned)(seg % SERVE_RING);
+        const ServeSeg sg = q.ring[r];
+        unsigned long long w = 0;
+        if (lane == 0) w = atomicAdd(q.slot_next + sg.slot, 1ull);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        const unsigned long long item = w & ((1ull << SERVE_GEN_SHIFT) - 1ull);
+        if ((unsigned)(w >> SERVE_GEN_SHIFT) != (sg.gen & 0xFFFFFFu)) {
+            // the slot was given to another job after this warp read the ring: report it and move on
+            if (lane == 0) atomicOr_system(&q.ctl->err, 1u);
+            __syncwarp();
+            continue;
+        }
+        if ((int64_t)item >= sg.n_items) {       // every item of this job is claimed: move on
+            if (lane == 0) atomicCAS(q.cur_seg, seg, seg + 1);
+            __syncwarp();
+            continue;
+        }
+        const DevJob &J = *sg.job;
+        const DevGrid &G = grids[J.grid_slot];
+        if (J.grid_slot != cur_grid) {
+            __syncwarp();
+            cur_grid = J.grid_slot;
+            T = stage_tabs<real>(G, tabw, lane, 32);
+            __syncwarp();
+        }
+        const int64_t p0 = (int64_t)item * chunk;
+        run_item<real, SCAT>(J, G, T, p0, min(p0 + (int64_t)chunk, J.n_packets), interval, refill_min, S);
+        flush(S.sm, S.stride, J.acc);
+        __threadfence();
+        unsigned long long fin = 0;
+        if (lane == 0) fin = atomicAdd(q.slot_done + sg.slot, 1ull) + 1ull;
+        fin = __shfl_sync(0xffffffffu, fin, 0);
+        if ((int64_t)fin == sg.n_items) {        // last item of the job: publish its completion record
+            __threadfence();
+            ServeDone *d = q.done + sg.slot;
+            d->acc[lane] = atomicAdd(J.acc + lane, 0ull);   // ACC_SLOTS == 32: one slot per lane
+            if (lane < 3) d->info[lane] = J.mode == GCMC_EMISSION ? J.info[lane] : 0.0;
+            __threadfence_system();
+            __syncwarp();
+            if (lane == 0) st_release_sys(&d->seq, seg + 1ull);
+        }
     }
 }
 
@@ -651,6 +788,31 @@ static cudaError_t persistent_dispatch(int block, int blocks_per_sm, int nsm, co
     }
     return persistent_run<real, SCAT, 0>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk, interval,
                                          refill_min, one_grid, tab_n, work, st);
+}
+
+cudaError_t launch_serve(const DevGrid *grids, const ServeQueue &q, int block, int blocks_per_sm, int chunk, int interval,
+                         int refill_min, int tab_n, int idle_polls, int *grid_blocks, cudaStream_t st)
+{
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (block != 128) return cudaErrorInvalidValue;
+    if (interval < 1) interval = 1;
+    refill_min = refill_min < 1 ? 1 : refill_min > 32 ? 32 : refill_min;
+    auto kern = k_transport_serve<float, true>;
+    const size_t sm = transport_smem(block) + (size_t)tab_n * sizeof(float2) * (block / 32);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, sm);
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    // default: one block per SM less than fits, so that the cell-table kernels of newly admitted jobs
+    // run beside the serving kernel
+    if (blocks_per_sm <= 0) blocks_per_sm = occ > 1 ? occ - 1 : 1;
+    if (blocks_per_sm > occ) blocks_per_sm = occ;
+    *grid_blocks = nsm * blocks_per_sm;
+    count_launch(1);
+    kern<<<(unsigned)(nsm * blocks_per_sm), block, sm, st>>>(grids, q, chunk, interval, refill_min, tab_n, idle_polls);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_persistent(int precision, bool scatter, const DevGrid *grids, const DevJob *jobs, int n_jobs,

@@ -65,6 +65,18 @@ class gcmc_launch_cfg(C.Structure):
                 ("refill_min", C.c_int32), ("pad", C.c_int32)]
 
 
+class gcmc_server_cfg(C.Structure):
+    _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("chunk", C.c_int32), ("interval", C.c_int32),
+                ("refill_min", C.c_int32), ("max_jobs", C.c_int32), ("hbm_budget", C.c_uint64),
+                ("idle_us", C.c_int32), ("pad", C.c_int32)]
+
+
+class gcmc_server_stats(C.Structure):
+    _fields_ = [("pending", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("bytes_in_use", C.c_uint64), ("kernel_launches", C.c_int64), ("kernel_running", C.c_int32),
+                ("grid_blocks", C.c_int32)]
+
+
 class gcmc_observables(C.Structure):
     _fields_ = [("S", C.c_double), ("A_g", C.c_double), ("A_g_R0", C.c_double), ("L_p", C.c_double),
                 ("I_p", C.c_double), ("F_p", C.c_double), ("area", C.c_double)]
@@ -113,6 +125,13 @@ def lib():
             "gcmc_gather_bench": ([C.c_void_p, C.c_int64, C.c_int, C.c_int64, P(C.c_double)], C.c_int),
             "gcmc_emission_pdf_noalloc": ([C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.c_void_p], C.c_int),
+            "gcmc_server_create": ([C.c_void_p, P(gcmc_server_cfg), P(C.c_void_p)], C.c_int),
+            "gcmc_server_submit": ([C.c_void_p, P(gcmc_job), P(C.c_uint64)], C.c_int),
+            "gcmc_server_progress": ([C.c_void_p, P(C.c_uint64), C.c_int, P(C.c_int)], C.c_int),
+            "gcmc_server_result": ([C.c_void_p, C.c_uint64, C.c_void_p, P(gcmc_stats)], C.c_int),
+            "gcmc_server_query": ([C.c_void_p, P(gcmc_server_stats)], C.c_int),
+            "gcmc_server_times": ([C.c_void_p, C.c_uint64, P(C.c_double)], C.c_int),
+            "gcmc_server_destroy": ([C.c_void_p, C.c_double], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -127,7 +146,8 @@ EXPORTED = ["gcmc_create", "gcmc_destroy", "gcmc_set_stream", "gcmc_set_allocato
             "gcmc_submit", "gcmc_poll", "gcmc_run_packets_debug", "gcmc_prep_cells", "gcmc_postscale",
             "gcmc_selftest_philox", "gcmc_version", "gcmc_release_grid", "gcmc_release_opacity",
             "gcmc_set_profiling", "gcmc_get_profile", "gcmc_kernel_launches", "gcmc_gather_bench",
-            "gcmc_emission_pdf_noalloc"]
+            "gcmc_emission_pdf_noalloc", "gcmc_server_create", "gcmc_server_submit", "gcmc_server_progress",
+            "gcmc_server_result", "gcmc_server_query", "gcmc_server_destroy", "gcmc_server_times"]
 NOALLOC_MAX_CELLS = 4194304
 
 
@@ -252,6 +272,19 @@ class Context:
         oid = C.c_int()
         self._check(lib().gcmc_upload_opacity(self.h, int(grid_id), C.byref(d), C.byref(oid)), "gcmc_upload_opacity")
         return oid.value
+
+    def set_sources(self, grid_id, source, precision=FP32):
+        """Sources holding every observer of `source`, MAX_OBS per source (a source of the C ABI holds
+        at most MAX_OBS directions); returns the source ids.  Observer o is entry o % MAX_OBS of
+        source o // MAX_OBS."""
+        import copy
+        obs = np.atleast_2d(np.asarray(source.obs, np.float64))
+        sids = []
+        for o0 in range(0, len(obs), MAX_OBS):
+            part = copy.copy(source)
+            part.obs = obs[o0:o0 + MAX_OBS]
+            sids.append(self.set_source(grid_id, part, precision))
+        return sids
 
     def set_source(self, grid_id, source, precision=FP32):
         d = gcmc_source_desc()
@@ -463,7 +496,106 @@ def load_workload(ctx, wl, precision=FP32, device_inputs=False):
     else:
         gid = ctx.upload_grid(wl.grid)
         oid = ctx.upload_opacity(gid, wl.opac)
-    sid = ctx.set_source(gid, wl.source, precision)
-    jobs = [Context.job(gid, oid, sid, wl.mode, j.lam_idx, j.g_idx, j.n_packets, wl.seed, j.key,
-                        getattr(j, "obs_idx", -1)) for j in wl.jobs]
-    return gid, oid, sid, jobs
+    sids = ctx.set_sources(gid, wl.source, precision)
+    jobs = workload_jobs(wl, gid, oid, sids)
+    return gid, oid, sids[0], jobs
+
+
+def workload_jobs(wl, gid, oid, sids):
+    """gcmc_job structs of a workload's jobs; a job that tallies one observer o (obs_idx >= 0) uses
+    source o // MAX_OBS, entry o % MAX_OBS (sources from Context.set_sources)."""
+    jobs = []
+    for j in wl.jobs:
+        o = getattr(j, "obs_idx", -1)
+        if o < 0 and len(sids) > 1:
+            raise ValueError("a job that tallies every observer needs at most MAX_OBS observers")
+        sid = sids[o // MAX_OBS] if o >= 0 else sids[0]
+        jobs.append(Context.job(gid, oid, sid, wl.mode, j.lam_idx, j.g_idx, j.n_packets, wl.seed, j.key,
+                                o % MAX_OBS if o >= 0 else -1))
+    return jobs
+
+
+def load_serving(ctx, sw, precision=FP32):
+    """Upload every scene of a synth.ServingWorkload (grid, three opacities, three sources) and return
+    the requests as gcmc_job structs, in request order."""
+    from . import synth as S
+    ids = []
+    for sc in sw.scenes:
+        gid = ctx.upload_grid(sc.grid)
+        oa = ctx.upload_opacity(gid, sc.albedo)
+        ok = ctx.upload_opacity(gid, sc.ktable)
+        ox = ctx.upload_opacity(gid, sc.xsec)
+        sa = ctx.set_source(gid, sc.src_albedo, precision)
+        se = ctx.set_source(gid, sc.src_emission, precision)
+        st = ctx.set_source(gid, sc.src_transmission, precision)
+        ids.append({S.MODE_ALBEDO: (gid, oa, sa), S.MODE_EMISSION: (gid, ok, se), S.MODE_TRANSMISSION: (gid, ox, st)})
+    jobs = []
+    for r in sw.requests:
+        gid, oid, sid = ids[r.scene][r.mode]
+        jobs.append(Context.job(gid, oid, sid, r.mode, r.lam_idx, r.g_idx, r.n_packets, sw.seed, r.key, r.obs_idx))
+    return jobs
+
+
+class Server:
+    """The continuous-batching request loop of one context (gcmc_server_*): submit jobs as they arrive,
+    call progress() often, and take results of the tickets progress() reports complete."""
+
+    def __init__(self, ctx: Context, block=128, blocks_per_sm=0, chunk=256, interval=4, refill_min=8,
+                 max_jobs=1024, hbm_budget=8 << 30, idle_us=2000):
+        self.ctx = ctx
+        self.h = C.c_void_p()
+        cfg = gcmc_server_cfg(block, blocks_per_sm, chunk, interval, refill_min, max_jobs, int(hbm_budget),
+                              idle_us, 0)
+        ctx._check(lib().gcmc_server_create(ctx.h, C.byref(cfg), C.byref(self.h)), "gcmc_server_create")
+        self._done = (C.c_uint64 * 4096)()
+
+    def submit(self, job: gcmc_job) -> int:
+        t = C.c_uint64()
+        self.ctx._check(lib().gcmc_server_submit(self.h, C.byref(job), C.byref(t)), "gcmc_server_submit")
+        return int(t.value)
+
+    def progress(self):
+        """One pass of the loop; returns the tickets that completed in it."""
+        n = C.c_int()
+        self.ctx._check(lib().gcmc_server_progress(self.h, self._done, len(self._done), C.byref(n)),
+                        "gcmc_server_progress")
+        if n.value > len(self._done):
+            raise GcmcError(ERR_RANGE, "more completions in one pass than the ticket buffer holds")
+        return [int(self._done[i]) for i in range(n.value)]
+
+    def times(self, ticket: int):
+        """(submitted, admitted, published, completed) host times in s of a completed, untaken ticket."""
+        t = (C.c_double * 4)()
+        self.ctx._check(lib().gcmc_server_times(self.h, C.c_uint64(ticket), t), "gcmc_server_times")
+        return tuple(t)
+
+    def result(self, ticket: int):
+        """(tallies [MAX_OBS], gcmc_stats) of a completed ticket."""
+        out = np.zeros(MAX_OBS, np.float64)
+        st = gcmc_stats()
+        self.ctx._check(lib().gcmc_server_result(self.h, C.c_uint64(ticket), _ptr(out), C.byref(st)),
+                        "gcmc_server_result")
+        return out, st
+
+    def query(self) -> gcmc_server_stats:
+        st = gcmc_server_stats()
+        self.ctx._check(lib().gcmc_server_query(self.h, C.byref(st)), "gcmc_server_query")
+        return st
+
+    def close(self, timeout_s=60.0):
+        if self.h:
+            self.ctx._check(lib().gcmc_server_destroy(self.h, float(timeout_s)), "gcmc_server_destroy")
+            self.h = C.c_void_p()
+
+    def run_all(self, jobs, timeout_s=120.0):
+        """Submit every job at once and loop until all have completed; returns [(tallies, stats)]."""
+        import time
+        tickets = [self.submit(j) for j in jobs]
+        want, got = set(tickets), {}
+        t0 = time.perf_counter()
+        while len(got) < len(want):
+            for t in self.progress():
+                got[t] = self.result(t)
+            if time.perf_counter() - t0 > timeout_s:
+                raise GcmcError(ERR_TIMEOUT, f"{len(want) - len(got)} served jobs still open after {timeout_s} s")
+        return [got[t] for t in tickets]

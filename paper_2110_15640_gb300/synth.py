@@ -418,6 +418,90 @@ def config4_transmission(n_packets=10_000, seed=4, nlon=96, nlat=48, nr=60, n_la
                     notes=dict(margin=margin))
 
 
+# --------------------------------------------------------------------------- serving stream
+
+@dataclasses.dataclass
+class Scene:
+    """One resident planet model of the serving workload: a grid and the three modes' inputs."""
+    grid: Grid
+    albedo: AlbedoOpacity
+    ktable: KTable
+    xsec: XsecTable
+    margin: int                      # first usable index of the cross-section wavelength grid
+    src_albedo: Source
+    src_emission: Source
+    src_transmission: Source
+
+
+@dataclasses.dataclass
+class Request:
+    mode: int
+    scene: int
+    lam_idx: int
+    g_idx: int
+    obs_idx: int
+    n_packets: int
+    key: int
+
+
+@dataclasses.dataclass
+class ServingWorkload:
+    name: str
+    scenes: list
+    requests: list
+    seed: int
+
+
+SERVING_GRIDS = ((32, 16, 20), (64, 32, 40), (128, 64, 50), (256, 128, 100))
+
+
+def config5_serving(n_requests=10_000, seed=5, grids=SERVING_GRIDS, n_lo=1.0e4, n_hi=1.0e7, nlam_alb=8,
+                    nphase=4, nb=8, ng=4, n_lam_x=64, n_lines=300):
+    """Serving: a stream of spectrum requests mixing albedo, emission and transmission (1/3 each), on
+    grids drawn uniformly from 32x16x20 .. 256x128x100 (each a hot-Jupiter model with winds, a Rayleigh
+    + cloud albedo opacity over nlam_alb wavelengths and nphase observer phases, an nb x ng k-table and
+    an n_lam_x-point Doppler cross-section table), packets per request log-uniform in [n_lo, n_hi].
+    Each request is one (mode, wavelength / band, g or phase) job.  Arrival times are drawn by the
+    caller (Poisson at a chosen rate)."""
+    rng = np.random.default_rng(seed)
+    scenes = []
+    for (nlon, nlat, nr) in grids:
+        grid, m = hotjupiter_grid(nlon, nlat, nr, wind=True)
+        lam = np.geomspace(0.3e-6, 1.0e-6, nlam_alb)
+        alb = AlbedoOpacity(kabs=5.0e-5 * 10.0 ** (0.5 * np.sin(12.0 * np.log(lam / 0.3e-6))),
+                            kray=3.1e-5 * (lam / 0.5e-6) ** -4, qcld=np.ones(nlam_alb),
+                            wcld=np.full(nlam_alb, 0.9), gcld=np.full(nlam_alb, 0.6), acld=cloud_profile(grid, m))
+        kt = make_ktable(rng, nb=nb, ng=ng)
+        xs, margin = make_xsec_table(rng, n_lines=n_lines, n_lam=n_lam_x)
+        xs.omega_rot = 2.0 * math.pi / (3.5 * 86400.0)
+        xs.view_theta = 0.5 * math.pi
+        xs.view_phi = math.pi
+        phases = np.arange(nphase) * (180.0 / nphase)
+        scenes.append(Scene(
+            grid=grid, albedo=alb, ktable=kt, xsec=xs, margin=margin,
+            src_albedo=Source(star=np.array([1.0, 0.0, 0.0]), obs=phase_dirs(phases), opts=Options()),
+            src_emission=Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[1.0, 0.0, 0.0]]),
+                                opts=Options(scatter_emission=0)),
+            src_transmission=Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[-1.0, 0.0, 0.0]]),
+                                    opts=Options())))
+    modes = rng.integers(0, 3, n_requests)
+    sc = rng.integers(0, len(grids), n_requests)
+    npk = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), n_requests)).astype(np.int64)
+    reqs = []
+    for q in range(n_requests):
+        mode = int(modes[q])
+        if mode == MODE_ALBEDO:
+            lam, g, obs = int(rng.integers(nlam_alb)), int(rng.integers(nphase)), -1
+            obs = g
+        elif mode == MODE_EMISSION:
+            lam, g, obs = int(rng.integers(nb)), int(rng.integers(ng)), -1
+        else:
+            lam, g, obs = int(scenes[sc[q]].margin + rng.integers(n_lam_x)), 0, -1
+        reqs.append(Request(mode=mode, scene=int(sc[q]), lam_idx=lam, g_idx=g, obs_idx=obs,
+                            n_packets=int(max(npk[q], 1)), key=q))
+    return ServingWorkload(f"serving_{n_requests}req", scenes, reqs, seed)
+
+
 # --------------------------------------------------------------------------- small analytic cases
 
 def uniform_absorber_sphere(alpha=2.0e-6, R0=R_JUP, H_atm=5.0e6, nlon=4, nlat=4, nr=4, n_packets=20000,
