@@ -8,8 +8,12 @@ jobs: cell tables (S1) and one persistent transport launch (S2-S8) with device t
 
 Prints ONE JSON line (rank 0): packet-steps/s of the batched form (value), the plain one-launch-
 per-job form beside it, spectra/s, the end-to-end number through the C ABI from pinned host
-buffers, the roofline of the transport kernel, the oracle's CPU baseline and the clocks seen.
+buffers, the roofline of the transport kernel, the oracle's CPU baseline, the clocks seen, and a
+request-latency summary (p50/p99) of a 1000-request sample of the serving stream.
 `--impl reference` times the FP64 CPU oracle on the same workload instead.
+
+Other workloads (--workload): albedo (32x16x20, FP64), phasecurve (40 wavelengths x 24 phases),
+transmission (9532 wavelengths, Doppler cross sections), serving (the full request stream).
 """
 import argparse
 import json
@@ -24,7 +28,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-OPS_PER_STEP = 64          # FP32-pipe operations of one cell step (count in the design doc)
+OPS_PER_STEP = 64          # FP32-pipe operations of one cell step (counted from the formulas)
+# DRAM bytes (read + write) of the persistent transport kernel per emission job of the 128x64x50 grid,
+# from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 8-job band-0 launch: the traffic
+# grows with the number of job tables the launch touches
+TRAFFIC_PER_EMISSION_JOB = 48.4e6 / 8
 PEAK_FP32_OPS = 152 * 128 * 2.07e9   # GB300: SMs x FP32 lanes x max SM clock (an FMA counts as one op)
 PEAK_FP64_OPS = 152 * 2 * 2.07e9     # GB300: FP64 issue is 1/64 of FP32 (2 lanes per SM per clock)
 
@@ -50,6 +58,8 @@ def parse():
     ap.add_argument("--workload", default="emission", choices=["emission", "albedo", "phasecurve", "transmission", "serving"])
     ap.add_argument("--requests", type=int, default=10_000, help="serving: requests in the stream")
     ap.add_argument("--hbm-budget-gb", type=float, default=16.0, help="serving: admitted workspace")
+    ap.add_argument("--serving-requests", type=int, default=1000,
+                    help="emission bench: requests of the serving sample in its JSON line (0: none)")
     return ap.parse_args()
 
 
@@ -229,48 +239,60 @@ def pct(xs, p):
     return float(np.percentile(np.asarray(xs) * 1e3, p))
 
 
-def serving_bench(args):
+def serving_run(n_requests, hbm_budget_gb, loads=(0.7, 0.9)):
     """Serving workload: a Poisson stream of mixed requests on four resident grids through the
-    continuous-batching server, at 0.7x and 0.9x of the server's saturated request rate, and the same
-    stream on the plain one-launch-per-request form."""
+    continuous-batching server, at the given fractions of the server's saturated request rate, and the
+    same stream (at the first load) on the plain one-launch-per-request form.  Returns a dict."""
     import numpy as np
-    import torch
-    from paper_2110_15640_gb300 import build, gcmc, synth
-    build.build()
-    torch.cuda.set_device(0)
-    sw = synth.config5_serving(n_requests=args.requests)
+    from paper_2110_15640_gb300 import gcmc, synth
+    sw = synth.config5_serving(n_requests=n_requests)
     ctx = gcmc.Context(0)
     jobs = gcmc.load_serving(ctx, sw)
-    sv = gcmc.Server(ctx, hbm_budget=int(args.hbm_budget_gb * (1 << 30)))
+    sv = gcmc.Server(ctx, hbm_budget=int(hbm_budget_gb * (1 << 30)))
     sv.run_all(jobs[:32])                                   # warm-up (first launches, pools)
     # saturated: every request queued at t = 0
     lat_s, steps_s, wall_s = serve_stream(sv, jobs, [0.0] * len(jobs))
     rate_sat = len(jobs) / wall_s
     rng = np.random.default_rng(55)
     runs = {}
-    for load in (0.7, 0.9):
+    for load in loads:
         arr = np.cumsum(rng.exponential(1.0 / (load * rate_sat), len(jobs))).tolist()
         lat, steps, wall = serve_stream(sv, jobs, arr)
         runs[load] = {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "packet_steps_per_s": steps / wall,
                       "requests_per_s": len(jobs) / wall, "wall_s": wall}
     stq = sv.query()
     sv.close()
-    arr = np.cumsum(rng.exponential(1.0 / (0.7 * rate_sat), len(jobs))).tolist()
+    arr = np.cumsum(rng.exponential(1.0 / (loads[0] * rate_sat), len(jobs))).tolist()
     lat_p, steps_p, wall_p, busy_p = plain_stream(ctx, jobs, arr)
     ctx.close()
+    out = {"workload": sw.name, "requests": len(jobs),
+           "grids": ["x".join(map(str, g)) for g in synth.SERVING_GRIDS],
+           "packets": "log-uniform 1e4..1e7", "modes": "albedo / emission / transmission, 1/3 each",
+           "hbm_budget_gb": hbm_budget_gb,
+           "saturated": {"packet_steps_per_s": steps_s / wall_s, "requests_per_s": rate_sat, "wall_s": wall_s,
+                         "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99)},
+           f"plain_form_at_{loads[0]}": {"p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
+                                         "packet_steps_per_s": steps_p / wall_p,
+                                         "packet_steps_per_s_busy": steps_p / busy_p, "wall_s": wall_p},
+           "server": {"kernel_launches": stq.kernel_launches, "grid_blocks": stq.grid_blocks}}
+    for load in loads:
+        out[f"poisson_{load}"] = runs[load]
+    return out
+
+
+def serving_bench(args):
+    import torch
+    from paper_2110_15640_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    sv = serving_run(args.requests, args.hbm_budget_gb)
     line = {
-        "metric": "packet-steps/s", "value": steps_s / wall_s, "unit": "packet-steps/s", "n_gpus": 1,
-        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * wall_s, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": sw.name, "requests": len(jobs), "grids": ["x".join(map(str, g)) for g in synth.SERVING_GRIDS],
-                   "packets": "log-uniform 1e4..1e7", "modes": "albedo / emission / transmission, 1/3 each",
-                   "hbm_budget_gb": args.hbm_budget_gb},
-        "saturated": {"packet_steps_per_s": steps_s / wall_s, "requests_per_s": rate_sat, "wall_s": wall_s,
-                      "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99)},
-        "poisson_0.7": runs[0.7], "poisson_0.9": runs[0.9],
-        "plain_form_at_0.7": {"p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
-                              "packet_steps_per_s_busy": steps_p / busy_p, "wall_s": wall_p},
-        "server": {"kernel_launches": stq.kernel_launches, "grid_blocks": stq.grid_blocks},
+        "metric": "packet-steps/s", "value": sv["saturated"]["packet_steps_per_s"], "unit": "packet-steps/s",
+        "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * sv["saturated"]["wall_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": sv["workload"], "requests": sv["requests"], "grids": sv["grids"],
+                   "packets": sv["packets"], "modes": sv["modes"], "hbm_budget_gb": sv["hbm_budget_gb"]},
+        "serving": sv,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -395,6 +417,12 @@ def main():
     gather = ctx.gather_bench(wl.grid.ncell, rec_bytes, 1 << 30)
     clocks = clk.summary()
 
+    serving = None
+    if rank == 0 and world == 1 and args.workload == "emission" and args.serving_requests > 0:
+        # request-latency summary on a sample of the serving stream (the full stream: --workload serving)
+        serving = serving_run(args.serving_requests, args.hbm_budget_gb)
+        del serving["grids"]
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = os.cpu_count() or 1
@@ -429,7 +457,9 @@ def main():
             "e2e": {"value": e2e_value, "unit": "packet-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * t_e2e},
             "roofline": {"bound": "fp64" if f64 else "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (TRAFFIC_PER_EMISSION_JOB * len(jobs)
+                                     if args.workload == "emission" and g.nlon * g.nlat * g.nr == 409600 else None),
                          "kernel": f"k_transport_persistent<{'double' if f64 else 'float'}>", "ops_per_step": OPS_PER_STEP,
                          "kernel_ms": 1e3 * tr_avg, "prep_ms": prep_ms / max(ntr, 1)},
             "gather_roofline": {"gathers_per_s": gather, "table_records": g.ncell, "record_bytes": rec_bytes,
@@ -438,6 +468,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks,
             "observables": F_band,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
