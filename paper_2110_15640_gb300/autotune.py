@@ -18,7 +18,7 @@ DEFAULT_SPACE = {
     "blocks_per_sm": [0, 6, 8],
     "chunk": [32, 64, 128, 256, 512, 1024],
     "refill_min": [4, 8, 16, 32],
-    "interval": [1, 2, 4],
+    "interval": [2, 4, 8, 16],
 }
 
 

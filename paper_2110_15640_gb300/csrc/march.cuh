@@ -270,11 +270,12 @@ __device__ __forceinline__ real cell_exit(const DevGrid &G, const Tabs<real> &T,
 // Cross `face`: update the cell; returns E_CONT, E_ESCAPE or E_BOTTOM.
 template <class GT> __device__ __forceinline__ int cross_face(const GT &G, int face, int &i, int &j, int &k)
 {
-    if (face == F_RIN && k == 0) return E_BOTTOM;
-    if (face == F_ROUT && k == G.nr - 1) return E_ESCAPE;
-    k += (face == F_ROUT) - (face == F_RIN);
-    j += (face == F_LATHI) - (face == F_LATLO);
-    const int ni = i + (face == F_LONHI) - (face == F_LONLO);
+    const int nk = k + (face & 3) - 1;
+    if (nk < 0) return E_BOTTOM;
+    if (nk >= G.nr) return E_ESCAPE;
+    k = nk;
+    j += ((face >> 2) & 3) - 1;
+    const int ni = i + ((face >> 4) & 3) - 1;
     i = ni < 0 ? G.nlon - 1 : ni == G.nlon ? 0 : ni;
     return E_CONT;
 }

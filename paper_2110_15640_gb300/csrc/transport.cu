@@ -423,7 +423,9 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
     S.trace(P.n, idx, seg);
     R.s = sx;
     int e = cross_face(T, face, R.i, R.j, R.k);
-    if (e == E_CONT && R.tau_target < (real)0 && R.tau > jc.tau_cut) e = E_CUTOFF;
+    // the optical-depth cut-off applies to marches without an interaction target (peel-offs, chords;
+    // every march of an absorber-only kernel)
+    if (e == E_CONT && (!SCAT || R.tau_target < (real)0) && R.tau > jc.tau_cut) e = E_CUTOFF;
     if (e != E_CONT) {
         P.ended = 1;
         P.end_e = e;
@@ -509,7 +511,8 @@ __device__ __forceinline__ void run_item(const DevJob &J, const DevGrid &G, cons
 {
     const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
     const JobC<real> jc = job_consts<real>(J);
-    int64_t pool = p0;
+    const int count = (int)(p1 - p0);          // packets of the item (at most chunk)
+    int next = 0;                              // packets of the item started so far
     Packet<real> P;
     P.alive = 0;
     P.hint = -1;
@@ -517,12 +520,14 @@ __device__ __forceinline__ void run_item(const DevJob &J, const DevGrid &G, cons
     for (;;) {
         if (P.alive && P.ended) settle<real, SCAT>(P, J, S);
         const unsigned idle = __ballot_sync(0xffffffffu, !P.alive);
-        const int n_idle = __popc(idle);
-        const int64_t left = p1 - pool;
-        if (n_idle && left > 0 && (int64_t)n_idle >= min((int64_t)refill_min, left)) {
-            const int64_t mine = pool + __popc(idle & lt);
-            if (!P.alive && mine < p1) launch<real, SCAT>(P, J, G, mine, S);
-            pool += n_idle;
+        const int left = count - next;
+        if (idle && left > 0) {
+            const int n_idle = __popc(idle);
+            if (n_idle >= min(refill_min, left)) {
+                const int mine = next + __popc(idle & lt);
+                if (!P.alive && mine < count) launch<real, SCAT>(P, J, G, p0 + mine, S);
+                next += n_idle;
+            }
         }
         if (!__any_sync(0xffffffffu, P.alive)) break;
         for (int t = 0; t < interval; ++t)
