@@ -101,6 +101,9 @@ typedef struct {
     int32_t *tr_cell;      /* [n_trace][max_trace] flat cell index, or -1 - kind at a march start */
     double *tr_len;        /* [n_trace][max_trace] */
     int32_t *tr_n;         /* [n_trace] entries written */
+    double *cf;            /* contribution functions (Sect. 6), or NULL: [2][n_obs][ncell] sums of the
+                              peel-off contributions f by the cell they leave from; [0] thermal (the
+                              emission launch peel-off), [1] scattered (peel-offs at scattering events) */
 } orc_run_args;
 
 /* ------------------------------------------------------------------ Philox4x32-10 */
@@ -540,11 +543,37 @@ void orc_prep_xsec(const orc_grid *G, const double *T, const double *p, const do
 }
 
 /* ------------------------------------------------------------------ packets */
+/* one peel-off contribution attributed to the cell it leaves from (contribution functions) */
+typedef struct {
+    int64_t idx;
+    int32_t kind, obs;
+    double f;
+} cf_rec;
+
 typedef struct {
     double tally[ORC_MAX_OBS], tally_c[ORC_MAX_OBS];
     double ledger[8], ledger_c[8];
     int64_t steps;
+    cf_rec *cf;            /* this chunk's contributions in packet order (when requested) */
+    int64_t n_cf, cap_cf;
+    int cf_oom;
 } acc_t;
+
+static void cf_put(acc_t *acc, int64_t idx, int kind, int obs, double f)
+{
+    if (acc->n_cf == acc->cap_cf) {
+        int64_t cap = acc->cap_cf ? 2 * acc->cap_cf : 1024;
+        cf_rec *q = (cf_rec *)realloc(acc->cf, (size_t)cap * sizeof(cf_rec));
+        if (!q) {
+            acc->cf_oom = 1;
+            return;
+        }
+        acc->cf = q;
+        acc->cap_cf = cap;
+    }
+    cf_rec r = {idx, kind, obs, f};
+    acc->cf[acc->n_cf++] = r;
+}
 
 static inline void kahan(double *s, double *c, double v)
 {
@@ -673,6 +702,7 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
             if (first_tau < 0) first_tau = tau;
             if (st == END_CAP) break;
             f_obs[o] += W * e / (4.0 * ORC_PI);
+            if (A->cf) cf_put(acc, idx, 0, o, W * e / (4.0 * ORC_PI));
         }
         if (S->scatter_emission && M.steps < M.max_steps) {
             double v[4];
@@ -711,6 +741,7 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
             double e = peel(&M, x, c, S->obs[o], S->tau_peel_cut, &tau_o, &so);
             if (so == END_CAP) { capped = 1; break; }
             f_obs[o] += W * om * orc_theta(dot3(d, S->obs[o]), pg, gg) * e;
+            if (A->cf) cf_put(acc, idx, 1, o, W * om * orc_theta(dot3(d, S->obs[o]), pg, gg) * e);
         }
         if (capped) { kahan(&acc->ledger[6], &acc->ledger_c[6], W); break; }
         if (W * om == 0.0) { kahan(&acc->ledger[2], &acc->ledger_c[2], W); break; }
@@ -765,7 +796,6 @@ typedef struct {
 static void run_chunk(const job_t *J, int64_t ch, acc_t *acc)
 {
     const orc_run_args *A = J->A;
-    memset(acc, 0, sizeof(*acc));
     int64_t b = ch * CHUNK, e = b + CHUNK;
     if (e > A->n_run) e = A->n_run;
     for (int64_t q = b; q < e; ++q) {
@@ -823,16 +853,25 @@ int orc_run(const orc_grid *G, const orc_cells *C, const orc_source *S, orc_run_
     pthread_mutex_destroy(&P.mu);
     double ts[ORC_MAX_OBS] = {0}, tc[ORC_MAX_OBS] = {0}, ls[8] = {0}, lc[8] = {0};
     int64_t steps = 0;
+    int cf_oom = 0;
     for (int64_t ch = 0; ch < nch; ++ch) {
         for (int o = 0; o < S->n_obs; ++o) kahan(&ts[o], &tc[o], chunks[ch].tally[o]);
         for (int q = 0; q < 8; ++q) kahan(&ls[q], &lc[q], chunks[ch].ledger[q]);
         steps += chunks[ch].steps;
+        /* contributions in packet order: the sums do not depend on the thread count */
+        const int64_t ncell = (int64_t)G->nlon * G->nlat * G->nr;
+        for (int64_t q = 0; q < chunks[ch].n_cf; ++q) {
+            const cf_rec *r = &chunks[ch].cf[q];
+            A->cf[((int64_t)r->kind * S->n_obs + r->obs) * ncell + r->idx] += r->f;
+        }
+        cf_oom |= chunks[ch].cf_oom;
+        free(chunks[ch].cf);
     }
     for (int o = 0; o < S->n_obs; ++o) A->tally[o] = ts[o];
     if (A->ledger) for (int q = 0; q < 8; ++q) A->ledger[q] = ls[q];
     if (A->steps) A->steps[0] = steps;
     free(chunks);
-    return 0;
+    return cf_oom ? -3 : 0;
 }
 
 int orc_max_obs(void) { return ORC_MAX_OBS; }
