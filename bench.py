@@ -87,7 +87,7 @@ def workload(args, rank):
 
 
 # oracle sample per workload for the CPU baseline: (jobs, packets per job or None for all)
-CPU_SAMPLE = {"emission": (48, 1_000_000), "albedo": (1, None), "phasecurve": (24, None), "transmission": (960, None)}
+CPU_SAMPLE = {"emission": (48, 1_000_000), "albedo": (1, None), "phasecurve": (24, None), "transmission": (480, None)}
 REF_SAMPLE = {"emission": (2, 200_000), "albedo": (1, None), "phasecurve": (2, None), "transmission": (96, None)}
 
 

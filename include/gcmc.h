@@ -192,6 +192,16 @@ typedef struct {
 gcmc_status gcmc_run_batch(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, const gcmc_launch_cfg *cfg,
                            double *tallies_out, int tallies_memory, gcmc_stats *stats_out);
 
+/* Contribution functions (Sect. 6): one albedo or emission job run with per-cell counters of the
+   peel-off contributions, attributed to the cell each peel-off leaves from.  cf_out (host,
+   [2][n_obs][ncell], n_obs the job's observer count) receives the sums of f over packets, in the
+   units of tallies_out: [0] thermal (emission launch peel-offs), [1] scattered (peel-offs at
+   scattering events).  They add up, over cells and both kinds, to the job's tally; the paper's
+   contribution function of a cell is its share, CF = cf / tally.  tallies_out [GCMC_MAX_OBS] and
+   stats_out may be NULL.  Transmission jobs are refused (GCMC_ERR_ARG).  Synchronises the stream. */
+gcmc_status gcmc_run_contrib(gcmc_ctx *ctx, const gcmc_job *job, double *tallies_out, double *cf_out,
+                             gcmc_stats *stats_out);
+
 /* Asynchronous batched form for request loops: enqueue the work on the context's stream and
    return a ticket at once; gcmc_poll returns GCMC_ERR_NOT_READY until the ticket's work has
    finished, then fills tallies_out [n_jobs][GCMC_MAX_OBS] (host) and stats_out (may be NULL). */

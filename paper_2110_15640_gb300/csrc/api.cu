@@ -185,6 +185,25 @@ struct Plan {
     int tab_n = 0;                      // largest march-table size (pair entries) of the jobs' grids
 };
 
+// FP32 cross-section jobs: the table wavelengths that bracket every Doppler-shifted wavelength of the
+// grid, lambda_0 (1 + d) for d in [dmin, dmax], as FP32 offsets lambda_l / lambda_0 - 1 (xs_n = -1 when
+// the window reaches a table edge or is longer than XS_LOCAL: the kernel then brackets in FP64)
+void xsec_window(const OpacH &o, PrepJob &pj)
+{
+    const std::vector<double> &lam = o.lam;
+    const double a = pj.lam_m * (1.0 + o.xs.dmin), b = pj.lam_m * (1.0 + o.xs.dmax);
+    pj.xs_lo = 0;
+    pj.xs_n = -1;
+    if (!(a > lam.front() && b < lam.back())) return;
+    const int lo = (int)(std::upper_bound(lam.begin(), lam.end(), a) - lam.begin()) - 1;   // last lam <= a
+    const int hi = (int)(std::upper_bound(lam.begin(), lam.end(), b) - lam.begin());       // first lam > b
+    const int n = hi - lo + 1;
+    if (lo < 0 || n > XS_LOCAL) return;
+    for (int t = 0; t < n; ++t) pj.xs_d[t] = (float)((lam[lo + t] - pj.lam_m) / pj.lam_m);
+    pj.xs_lo = lo;
+    pj.xs_n = n;
+}
+
 gcmc_status check_job(gcmc_ctx *ctx, const gcmc_job &j)
 {
     if (j.grid_id < 0 || j.grid_id >= (int)ctx->grids.size()) return fail(ctx, GCMC_ERR_ARG, "bad grid_id");
@@ -298,6 +317,7 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
                 pj.lam_m = o.lam[j.lam_idx];
             } else if (o.kind == GCMC_OPAC_XSEC) {
                 pj.lam_m = o.lam[j.lam_idx];
+                xsec_window(o, pj);
             }
             P.prep.push_back(pj);
         }
@@ -903,10 +923,20 @@ gcmc_status gcmc_upload_opacity(gcmc_ctx *ctx, int grid_id, const gcmc_opacity_d
             int2 *ab = dput<int2>(ctx, O.owned, nullptr, hg.ncell, e);
             double2 *w = dput<double2>(ctx, O.owned, nullptr, hg.ncell, e);
             double *fac = dput<double>(ctx, O.owned, nullptr, hg.ncell, e);
-            if (e == cudaSuccess) e = xsec_cells(hg, O.xs, ab, w, fac, ctx->stream);
+            float2 *w32 = dput<float2>(ctx, O.owned, nullptr, hg.ncell, e);
+            float *dlt = dput<float>(ctx, O.owned, nullptr, hg.ncell, e);
+            float *mm = dput<float>(ctx, O.owned, nullptr, 2, e);
+            if (e == cudaSuccess) e = xsec_cells(hg, O.xs, ab, w, fac, w32, dlt, mm, ctx->stream);
+            float hmm[2] = {0.0f, 0.0f};
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hmm, mm, sizeof(hmm), cudaMemcpyDeviceToHost, ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
             O.xs.ab = ab;
             O.xs.w = w;
             O.xs.fac = fac;
+            O.xs.w32 = w32;
+            O.xs.dlt_f = dlt;
+            O.xs.dmin = hmm[0];
+            O.xs.dmax = hmm[1];
         }
     } else {
         return fail(ctx, GCMC_ERR_ARG, "unknown opacity kind");
@@ -985,6 +1015,42 @@ gcmc_status gcmc_run_batch(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, cons
     if (e != cudaSuccess) return cuda_fail(ctx, e, "transport launch");
     prof_mark(ctx);
     return finish_run(ctx, P, base, tallies_out, tallies_memory, stats_out, 1);
+}
+
+gcmc_status gcmc_run_contrib(gcmc_ctx *ctx, const gcmc_job *job, double *tallies_out, double *cf_out,
+                             gcmc_stats *stats_out)
+{
+    if (!ctx || !job || !cf_out) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    if (job->mode == GCMC_TRANSMISSION)
+        return fail(ctx, GCMC_ERR_ARG, "contribution functions are defined for albedo and emission jobs");
+    cudaSetDevice(ctx->device);
+    const int chunk = 256;
+    Plan P;
+    gcmc_status s = plan_run(ctx, job, 1, chunk, P);
+    if (s) return s;
+    if ((s = ensure_arena(ctx, P.ws_bytes))) return s;
+    char *base = (char *)ctx->arena;
+    const int64_t ncell = ctx->grids[job->grid_id].dg.ncell;
+    const size_t ncf = (size_t)2 * P.jobs[0].n_obs * ncell;
+    unsigned long long *dcf = (unsigned long long *)dalloc(ctx, ncf * 8);
+    if (!dcf) return fail(ctx, GCMC_ERR_OOM, "contribution-function counters");
+    cudaError_t e = cudaMemsetAsync(dcf, 0, ncf * 8, ctx->stream);
+    P.jobs[0].cf = dcf;
+    P.jobs[0].cf_ncell = ncell;
+    if (e == cudaSuccess && (s = stage(ctx, P, base)) == GCMC_OK) {
+        const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
+        e = launch_persistent(P.jobs[0].precision, P.scatter, ctx->d_grids, dj, 1, P.total_items, chunk, 128, 0, 4, 8,
+                              P.one_grid, P.tab_n, reinterpret_cast<unsigned long long *>(base + P.off_work), ctx->stream);
+    }
+    std::vector<unsigned long long> h(ncf);
+    if (!s && e == cudaSuccess) e = cudaMemcpyAsync(h.data(), dcf, ncf * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (!s && e == cudaSuccess) s = finish_run(ctx, P, base, tallies_out, GCMC_MEM_HOST, stats_out, 0);
+    if (e != cudaSuccess && !s) s = cuda_fail(ctx, e, "contribution-function run");
+    cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, dcf);
+    if (s) return s;
+    for (size_t i = 0; i < ncf; ++i) cf_out[i] = (double)(long long)h[i] / FIX_SCALE;
+    return GCMC_OK;
 }
 
 gcmc_status gcmc_submit(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, const gcmc_launch_cfg *cfg, uint64_t *ticket)

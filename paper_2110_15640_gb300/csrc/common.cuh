@@ -85,6 +85,10 @@ struct DevJob {
     float obs_f[MAX_OBS][3];
     float w_rr_f, p_surv_f, hg_eps_f, pad2;
     unsigned long long *acc;    // [ACC_SLOTS]
+    // contribution functions (Sect. 6), or NULL: [2][n_obs][cf_ncell] fixed-point sums of the peel-off
+    // contributions by the cell they leave from, [0] thermal (emission launch), [1] scattered
+    unsigned long long *cf;
+    int64_t cf_ncell;
 };
 
 // job constants in the march precision (FP32 marches read the copies rounded on the host)

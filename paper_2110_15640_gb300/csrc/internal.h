@@ -18,6 +18,8 @@ struct HostLog {               // device pointers of the per-packet debug output
     int32_t n_trace, max_trace;
 };
 
+constexpr int XS_LOCAL = 64;   // most table wavelengths an FP32 cross-section job brackets in
+
 // per-job parameters of the cell-table kernels
 struct PrepJob {
     int32_t lam, g;            // wavelength / band index, g-ordinate
@@ -30,6 +32,11 @@ struct PrepJob {
     double *bsum;              // emission: per-block partial sums [nblk]
     double *bcnt;              // emission: per-block included counts [nblk]
     double *lum;               // emission: optional copy of L_i (debug), or NULL
+    // cross sections, FP32 runs: the table wavelengths lambda_l, l = xs_lo .. xs_lo + xs_n - 1, that
+    // bracket every Doppler-shifted wavelength of the grid, as FP32 offsets lambda_l / lambda_0 - 1
+    // (xs_n = -1: bracket in FP64 instead)
+    int32_t xs_lo, xs_n;
+    float xs_d[XS_LOCAL];
 };
 
 // slots of PrepJob::info
@@ -65,6 +72,9 @@ struct XsecDev {
     const int2 *ab;            // [ncell] (T, p) interpolation cell
     const double2 *w;          // [ncell] (wT, wp)
     const double *fac;         // [ncell] Doppler factor lambda_eff / lambda_0 = 1 - v_LOS / c
+    const float2 *w32;         // [ncell] (wT, wp) in FP32
+    const float *dlt_f;        // [ncell] lambda_eff / lambda_0 - 1 in FP32
+    double dmin, dmax;         // range of dlt_f over the grid
 };
 
 struct AlbDev {
@@ -90,7 +100,8 @@ cudaError_t prep_xsec(int precision, const DevGrid &hgrid, const XsecDev &xs, co
 // 4 pi V B(T) per band (k-table) or the Doppler factors (cross sections); lam_dev: band centres [nb]
 cudaError_t ktable_cells(const DevGrid &hgrid, const double *lam_dev, int nb, int2 *ab, double2 *w64, float2 *w32,
                          double *vb, const KtabDev &kt, cudaStream_t st);
-cudaError_t xsec_cells(const DevGrid &hgrid, const XsecDev &xs, int2 *ab, double2 *w, double *fac, cudaStream_t st);
+cudaError_t xsec_cells(const DevGrid &hgrid, const XsecDev &xs, int2 *ab, double2 *w, double *fac, float2 *w32,
+                       float *dlt, float *minmax, cudaStream_t st);
 
 // serving queue (continuous batching): host-mapped control block, job ring and completion records,
 // and device-side claim counters

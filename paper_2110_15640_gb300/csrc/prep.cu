@@ -396,7 +396,7 @@ cudaError_t prep_emission(int precision, const DevGrid &hg, const KtabDev &kt, c
 }
 
 // ------------------------------------------------------------------ transmission (Doppler cross-sections)
-__global__ void k_xsec_cells(DevGrid G, XsecDev xs, int2 *ab, double2 *w, double *fac)
+__global__ void k_xsec_cells(DevGrid G, XsecDev xs, int2 *ab, double2 *w, double *fac, float2 *w32, float *dlt)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= G.ncell) return;
@@ -406,6 +406,7 @@ __global__ void k_xsec_cells(DevGrid G, XsecDev xs, int2 *ab, double2 *w, double
     interp_idx(xs.pg, xs.np, (double)G.p[idx], b, wp);
     ab[idx] = make_int2(a, b);
     w[idx] = make_double2(wT, wp);
+    w32[idx] = make_float2((float)wT, (float)wp);
     double v = 0.0;
     if (G.wind) {
         const int i = (int)(idx % G.nlon), j = (int)((idx / G.nlon) % G.nlat), k = (int)(idx / ((int64_t)G.nlon * G.nlat));
@@ -420,9 +421,39 @@ __global__ void k_xsec_cells(DevGrid G, XsecDev xs, int2 *ab, double2 *w, double
             xs.omega_rot * rmid * sin(th) * sin(xs.view_theta) * sin(dph);
     }
     fac[idx] = 1.0 - v / C_LIGHT;
+    dlt[idx] = (float)(-v / C_LIGHT);   // lambda_eff / lambda_0 - 1, |.| ~ 1e-5: FP32 keeps ~1e-12 absolute
 }
 
-template <typename real>
+// min and max of an FP32 array (one block)
+__global__ void k_minmax_f(const float *__restrict__ x, int64_t n, float *out)
+{
+    __shared__ float smin[32], smax[32];
+    float lo = 3.0e38f, hi = -3.0e38f;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        lo = fminf(lo, x[i]);
+        hi = fmaxf(hi, x[i]);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        smin[threadIdx.x >> 5] = lo;
+        smax[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+            lo = fminf(lo, smin[q]);
+            hi = fmaxf(hi, smax[q]);
+        }
+        out[0] = lo;
+        out[1] = hi;
+    }
+}
+
+// FP64 cross-section tables: lambda_eff bracketed and interpolated in FP64
 __global__ void k_prep_xsec(DevGrid G, XsecDev xs, const PrepJob *__restrict__ jobs)
 {
     const int2 *__restrict__ ab = xs.ab;
@@ -446,43 +477,84 @@ __global__ void k_prep_xsec(DevGrid G, XsecDev xs, const PrepJob *__restrict__ j
     const int2 q = ab[idx];
     const int np = xs.np, nTp = xs.nT * xs.np;
     const int o00 = q.x * np + q.y, o10 = (q.x + 1) * np + q.y, o01 = q.x * np + q.y + 1, o11 = (q.x + 1) * np + q.y + 1;
-    if constexpr (sizeof(real) == 8) {
-        double wl;
-        int l0;
-        if (l == -1) { l0 = 0; wl = 0.0; }
-        else if (l == -2) { l0 = xs.nl - 2; wl = 1.0; }
-        else { l0 = l; wl = (le - lam[l0]) / (lam[l0 + 1] - lam[l0]); }
-        const double wT = w[idx].x, wp = w[idx].y;
-        double ls[2];
+    double wl;
+    int l0;
+    if (l == -1) { l0 = 0; wl = 0.0; }
+    else if (l == -2) { l0 = xs.nl - 2; wl = 1.0; }
+    else { l0 = l; wl = (le - lam[l0]) / (lam[l0 + 1] - lam[l0]); }
+    const double wT = w[idx].x, wp = w[idx].y;
+    double ls[2];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const double *s = xs.lnsig + (int64_t)(l0 + e) * nTp;
-            ls[e] = (1 - wT) * (1 - wp) * s[o00] + wT * (1 - wp) * s[o10] + (1 - wT) * wp * s[o01] + wT * wp * s[o11];
-        }
-        reinterpret_cast<double *>(pj.rec)[idx] = (double)G.rho[idx] * exp((1.0 - wl) * ls[0] + wl * ls[1]);
-    } else {
-        float wl;
-        int l0;
-        if (l == -1) { l0 = 0; wl = 0.0f; }
-        else if (l == -2) { l0 = xs.nl - 2; wl = 1.0f; }
-        else { l0 = l; wl = __fdividef((float)(le - lam[l0]), (float)(lam[l0 + 1] - lam[l0])); }
-        const float wT = (float)w[idx].x, wp = (float)w[idx].y;
-        float ls[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const float *s = xs.lnsig_f + (int64_t)(l0 + e) * nTp;
-            ls[e] = (1 - wT) * (1 - wp) * __ldg(s + o00) + wT * (1 - wp) * __ldg(s + o10) + (1 - wT) * wp * __ldg(s + o01) +
-                    wT * wp * __ldg(s + o11);
-        }
-        reinterpret_cast<float *>(pj.rec)[idx] = G.rho[idx] * __expf((1.0f - wl) * ls[0] + wl * ls[1]);
+    for (int e = 0; e < 2; ++e) {
+        const double *s = xs.lnsig + (int64_t)(l0 + e) * nTp;
+        ls[e] = (1 - wT) * (1 - wp) * s[o00] + wT * (1 - wp) * s[o10] + (1 - wT) * wp * s[o01] + wT * wp * s[o11];
     }
+    reinterpret_cast<double *>(pj.rec)[idx] = (double)G.rho[idx] * exp((1.0 - wl) * ls[0] + wl * ls[1]);
 }
 
-cudaError_t xsec_cells(const DevGrid &hg, const XsecDev &xs, int2 *ab, double2 *w, double *fac, cudaStream_t st)
+// FP32 cross-section tables.  The Doppler shift moves lambda_eff by |v_LOS|/c ~ 1e-5 around the job's
+// rest wavelength, so the host gives each job the table wavelengths that can bracket any of the grid's
+// shifts, as FP32 offsets relative to the rest wavelength (d_l = lambda_l / lambda_0 - 1, from FP64);
+// each cell brackets its own shift d (FP32) among them and interpolates in FP32.  Jobs whose window
+// reaches a table edge, or needs more than XS_LOCAL wavelengths, bracket lambda_eff in FP64 as the FP64
+// kernel does.
+__global__ void k_prep_xsec_f32(DevGrid G, XsecDev xs, const PrepJob *__restrict__ jobs)
 {
-    count_launch(1);
+    __shared__ float s_d[XS_LOCAL];
+    const PrepJob &pj = jobs[blockIdx.y];
+    const int n = pj.xs_n, lo = pj.xs_lo;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) s_d[t] = pj.xs_d[t];
+    __syncthreads();
+    const double *lam = xs.lam;
+    const int nl = xs.nl;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= G.ncell) return;
+    int l0;
+    float wl;
+    if (n > 0) {
+        const float d = xs.dlt_f[idx];
+        int t = 0;
+        while (t + 2 < n && s_d[t + 1] <= d) ++t;
+        l0 = lo + t;
+        wl = __fdividef(d - s_d[t], s_d[t + 1] - s_d[t]);
+    } else {
+        const double le = pj.lam_m * xs.fac[idx];
+        if (le <= lam[0]) {
+            l0 = 0;
+            wl = 0.0f;
+        } else if (le >= lam[nl - 1]) {
+            l0 = nl - 2;
+            wl = 1.0f;
+        } else {
+            int l = pj.lam_hint < 0 ? 0 : pj.lam_hint > nl - 2 ? nl - 2 : pj.lam_hint;
+            while (lam[l + 1] <= le) ++l;
+            while (lam[l] > le) --l;
+            l0 = l;
+            wl = __fdividef((float)(le - lam[l0]), (float)(lam[l0 + 1] - lam[l0]));
+        }
+    }
+    const int2 q = xs.ab[idx];
+    const int np = xs.np, nTp = xs.nT * xs.np;
+    const int o00 = q.x * np + q.y, o10 = (q.x + 1) * np + q.y, o01 = q.x * np + q.y + 1, o11 = (q.x + 1) * np + q.y + 1;
+    const float2 ww = xs.w32[idx];
+    const float wT = ww.x, wp = ww.y;
+    float ls[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float *sg = xs.lnsig_f + (int64_t)(l0 + e) * nTp;
+        ls[e] = (1 - wT) * (1 - wp) * __ldg(sg + o00) + wT * (1 - wp) * __ldg(sg + o10) + (1 - wT) * wp * __ldg(sg + o01) +
+                wT * wp * __ldg(sg + o11);
+    }
+    reinterpret_cast<float *>(pj.rec)[idx] = G.rho[idx] * __expf((1.0f - wl) * ls[0] + wl * ls[1]);
+}
+
+cudaError_t xsec_cells(const DevGrid &hg, const XsecDev &xs, int2 *ab, double2 *w, double *fac, float2 *w32, float *dlt,
+                       float *minmax, cudaStream_t st)
+{
+    count_launch(2);
     const unsigned nb = (unsigned)((hg.ncell + PREP_BLOCK - 1) / PREP_BLOCK);
-    k_xsec_cells<<<nb, PREP_BLOCK, 0, st>>>(hg, xs, ab, w, fac);
+    k_xsec_cells<<<nb, PREP_BLOCK, 0, st>>>(hg, xs, ab, w, fac, w32, dlt);
+    k_minmax_f<<<1, 1024, 0, st>>>(dlt, hg.ncell, minmax);
     return cudaGetLastError();
 }
 
@@ -490,8 +562,8 @@ cudaError_t prep_xsec(int precision, const DevGrid &hg, const XsecDev &xs, const
 {
     count_launch(1);
     const dim3 g1((unsigned)((hg.ncell + PREP_BLOCK - 1) / PREP_BLOCK), (unsigned)njobs);
-    if (precision == GCMC_FP64) k_prep_xsec<double><<<g1, PREP_BLOCK, 0, st>>>(hg, xs, djobs);
-    else k_prep_xsec<float><<<g1, PREP_BLOCK, 0, st>>>(hg, xs, djobs);
+    if (precision == GCMC_FP64) k_prep_xsec<<<g1, PREP_BLOCK, 0, st>>>(hg, xs, djobs);
+    else k_prep_xsec_f32<<<g1, PREP_BLOCK, 0, st>>>(hg, xs, djobs);
     return cudaGetLastError();
 }
 

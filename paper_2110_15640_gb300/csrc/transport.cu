@@ -28,6 +28,7 @@ template <typename real> struct Packet {
     real om, gg, pg;       // cell record at the interaction
     real bimp;             // chord impact parameter / R_TOA
     int ci, cj, ck;
+    int cell0;             // flat index of the cell the current peel-off leaves from
     int steps;
     int hint;              // launch cell of this lane's previous packet of the same work item (-1: none)
     int ended, end_e, end_idx;   // the current ray has ended (persistent kernel: processed at the refill point)
@@ -254,6 +255,7 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
     P.ci = i;
     P.cj = j;
     P.ck = k;
+    P.cell0 = idx;
     P.W = P.W0 = reinterpret_cast<const real *>(J.wcell)[idx];
     S.ledger(0, P.W0);
     P.stage = 0;
@@ -322,6 +324,7 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
             P.ci = R.i;
             P.cj = R.j;
             P.ck = R.k;
+            P.cell0 = idx;
             if constexpr (sizeof(real) == 4) {
                 const float4 rc = __ldg(reinterpret_cast<const float4 *>(J.rec) + idx);
                 P.om = rc.y;
@@ -357,6 +360,12 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
             f = P.W * P.om * theta_mix<real>(mu, P.pg, P.gg) * ex;
         }
         S.tally(P.obs, f, P.n, J.n_obs);
+        if (J.cf && f < (real)1.0e9 && f >= (real)0) {
+            // the same fixed-point contribution, by the cell the peel-off left from
+            const int kind = (!SCAT || P.stage == 0) ? 0 : 1;
+            atomicAdd(J.cf + (int64_t)(kind * J.n_obs + P.obs) * J.cf_ncell + P.cell0,
+                      (unsigned long long)to_fix<real>(f));
+        }
         ++P.obs;
         if (P.obs < J.n_obs) {
             start_peel<real>(P, J, S);
@@ -782,7 +791,8 @@ static cudaError_t persistent_dispatch(int block, int blocks_per_sm, int nsm, co
                                        int one_grid, int tab_n, unsigned long long *work, cudaStream_t st)
 {
     // FP32 absorber-only batches (the emission and limb-chord hot path) have variants compiled for
-    // 6 and 8 resident 128-thread blocks per SM; blocks_per_sm selects them
+    // 6 and 8 resident 128-thread blocks per SM (register caps 80 and 64); blocks_per_sm selects them.
+    // (Capped scattering variants spill and ran slower on the phase curve.)
     if constexpr (sizeof(real) == 4 && !SCAT) {
         if (block <= 128 && blocks_per_sm >= 8)
             return persistent_run<real, SCAT, 8>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,

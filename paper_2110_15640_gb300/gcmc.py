@@ -108,6 +108,7 @@ def lib():
             "gcmc_run_batch": ([C.c_void_p, P(gcmc_job), C.c_int, P(gcmc_launch_cfg), C.c_void_p, C.c_int,
                                 P(gcmc_stats)], C.c_int),
             "gcmc_submit": ([C.c_void_p, P(gcmc_job), C.c_int, P(gcmc_launch_cfg), P(C.c_uint64)], C.c_int),
+            "gcmc_run_contrib": ([C.c_void_p, P(gcmc_job), C.c_void_p, C.c_void_p, P(gcmc_stats)], C.c_int),
             "gcmc_poll": ([C.c_void_p, C.c_uint64, C.c_void_p, P(gcmc_stats)], C.c_int),
             "gcmc_run_packets_debug": ([C.c_void_p, P(gcmc_job), C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -143,7 +144,7 @@ def lib():
 
 EXPORTED = ["gcmc_create", "gcmc_destroy", "gcmc_set_stream", "gcmc_set_allocator", "gcmc_last_error",
             "gcmc_upload_grid", "gcmc_upload_opacity", "gcmc_set_source", "gcmc_run_packets", "gcmc_run_batch",
-            "gcmc_submit", "gcmc_poll", "gcmc_run_packets_debug", "gcmc_prep_cells", "gcmc_postscale",
+            "gcmc_submit", "gcmc_poll", "gcmc_run_contrib", "gcmc_run_packets_debug", "gcmc_prep_cells", "gcmc_postscale",
             "gcmc_selftest_philox", "gcmc_version", "gcmc_release_grid", "gcmc_release_opacity",
             "gcmc_set_profiling", "gcmc_get_profile", "gcmc_kernel_launches", "gcmc_gather_bench",
             "gcmc_emission_pdf_noalloc", "gcmc_server_create", "gcmc_server_submit", "gcmc_server_progress",
@@ -334,6 +335,16 @@ class Context:
         out = np.zeros((len(jobs), MAX_OBS))
         self._check(lib().gcmc_run_batch(self.h, arr, len(jobs), cfgp, _ptr(out), MEM_HOST, sts), "gcmc_run_batch")
         return out, sts
+
+    def run_contrib(self, job, ncell, n_obs=1):
+        """One albedo or emission job with contribution functions: (tallies [MAX_OBS],
+        cf [2][n_obs][ncell] sums of f by the cell each peel-off leaves from (thermal, scattered),
+        gcmc_stats).  The contribution function of a cell is cf / tally."""
+        out = np.zeros(MAX_OBS)
+        cf = np.zeros((2, n_obs, ncell))
+        st = gcmc_stats()
+        self._check(lib().gcmc_run_contrib(self.h, C.byref(job), _ptr(out), _ptr(cf), C.byref(st)), "gcmc_run_contrib")
+        return out, cf, st
 
     def submit(self, jobs, cfg=None):
         arr = (gcmc_job * len(jobs))(*jobs)
