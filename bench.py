@@ -366,6 +366,24 @@ def main():
         t = float(tt.item())
     value = steps_per_step * args.steps * world / t
 
+    # ---------------- the same batch captured into a CUDA graph and replayed
+    graph_line = None
+    if world == 1:
+        gr = ctx.graph(jobs, cfg)
+        for _ in range(2):
+            gr.launch(tall)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            gr.launch(tall)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        tg = g0.elapsed_time(g1) / 1e3
+        gr.close()
+        graph_line = {"value": steps_per_step * args.steps / tg, "unit": "packet-steps/s",
+                      "ms_per_step": 1e3 * tg / args.steps}
+
     # ---------------- plain form: one launch per job (same work)
     outp = torch.zeros(gcmc.MAX_OBS, dtype=torch.float64, device="cuda")
     with torch.cuda.stream(stream):
@@ -454,6 +472,7 @@ def main():
                            "ms_per_step": 1e3 * t_plain / args.plain_steps if args.plain_steps else None,
                            "launches_per_step": len(jobs)},
             "batched_over_plain": value / plain_value if plain_value else None,
+            "graph_form": graph_line,
             "e2e": {"value": e2e_value, "unit": "packet-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * t_e2e},
             "roofline": {"bound": "fp64" if f64 else "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

@@ -192,6 +192,20 @@ typedef struct {
 gcmc_status gcmc_run_batch(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, const gcmc_launch_cfg *cfg,
                            double *tallies_out, int tallies_memory, gcmc_stats *stats_out);
 
+/* Captured batches: the batched form (cell tables of every job, one persistent transport launch,
+   tallies) planned once and captured into a CUDA graph on the context's stream (which must not be the
+   default stream), to be replayed step after step without host-side planning or launch overhead.
+   The graph owns its workspace; the grids, opacities and sources it uses must stay uploaded.
+   gcmc_graph_launch replays it asynchronously and, if tallies_out (device [n_jobs][GCMC_MAX_OBS]) is
+   not NULL, copies the tallies there; gcmc_graph_read synchronises and returns the last replay's
+   tallies (host [n_jobs][GCMC_MAX_OBS], may be NULL) and stats ([n_jobs] or NULL). */
+typedef struct gcmc_graph gcmc_graph;
+gcmc_status gcmc_graph_create(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, const gcmc_launch_cfg *cfg,
+                              gcmc_graph **out);
+gcmc_status gcmc_graph_launch(gcmc_graph *g, double *tallies_out);
+gcmc_status gcmc_graph_read(gcmc_graph *g, double *tallies_out, gcmc_stats *stats_out);
+gcmc_status gcmc_graph_destroy(gcmc_graph *g);
+
 /* Contribution functions (Sect. 6): one albedo or emission job run with per-cell counters of the
    peel-off contributions, attributed to the cell each peel-off leaves from.  cf_out (host,
    [2][n_obs][ncell], n_obs the job's observer count) receives the sums of f over packets, in the

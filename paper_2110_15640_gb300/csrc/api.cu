@@ -1769,3 +1769,133 @@ gcmc_status gcmc_server_destroy(gcmc_server *sv, double timeout_s)
 }
 
 }  // extern "C"
+
+// ==================================================================== captured batches (CUDA graphs)
+// A batch planned once and captured, with its cell-table kernels, the persistent transport launch and
+// the conversion of the tallies, into one CUDA graph that replays on the context's stream.  The graph
+// owns its workspace and its pinned job-record staging; replays recompute everything (cell tables
+// included) from the resident grids and opacities.
+struct gcmc_graph {
+    gcmc_ctx *ctx = nullptr;
+    Plan P;
+    void *ws = nullptr;
+    char *stage_h = nullptr;
+    double *d_tally = nullptr;        // [n_jobs][MAX_OBS]
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int n_jobs = 0;
+    long long kernels = 0;            // kernels in the graph (counted while capturing)
+};
+
+namespace {
+void graph_free(gcmc_graph *g)
+{
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->stage_h) cudaFreeHost(g->stage_h);
+    dfree(g->ctx, g->ws);
+    dfree(g->ctx, g->d_tally);
+    delete g;
+}
+}  // namespace
+
+extern "C" {
+
+gcmc_status gcmc_graph_create(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, const gcmc_launch_cfg *cfg,
+                              gcmc_graph **out)
+{
+    if (!ctx || !jobs || !out) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    if (!ctx->stream) return fail(ctx, GCMC_ERR_ARG, "capture needs a non-default stream (gcmc_set_stream)");
+    const int chunk = cfg && cfg->chunk > 0 ? cfg->chunk : 1024;
+    gcmc_graph *g = new gcmc_graph();
+    g->ctx = ctx;
+    g->n_jobs = n_jobs;
+    gcmc_status s = plan_run(ctx, jobs, n_jobs, chunk, g->P);
+    if (s) {
+        delete g;
+        return s;
+    }
+    Plan &P = g->P;
+    const int prec = P.jobs[0].precision;
+    for (const DevJob &d : P.jobs)
+        if (d.precision != prec) {
+            delete g;
+            return fail(ctx, GCMC_ERR_ARG, "a batch runs in one precision");
+        }
+    g->ws = dalloc(ctx, P.ws_bytes);
+    g->d_tally = (double *)dalloc(ctx, (size_t)n_jobs * MAX_OBS * sizeof(double));
+    if (!g->ws || !g->d_tally || cudaMallocHost((void **)&g->stage_h, n_jobs * (sizeof(PrepJob) + sizeof(DevJob))) != cudaSuccess) {
+        graph_free(g);
+        return fail(ctx, GCMC_ERR_OOM, "graph workspace");
+    }
+    char *base = (char *)g->ws;
+    const long long l0 = g_launches.load();
+    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        graph_free(g);
+        return cuda_fail(ctx, e, "begin capture");
+    }
+    s = stage(ctx, P, base, nullptr, g->stage_h);
+    if (!s) {
+        const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
+        e = launch_persistent(prec, P.scatter, ctx->d_grids, dj, n_jobs, P.total_items, chunk, cfg ? cfg->block : 0,
+                              cfg ? cfg->blocks_per_sm : 0, cfg && cfg->interval > 0 ? cfg->interval : 1,
+                              cfg && cfg->refill_min > 0 ? cfg->refill_min : 16, P.one_grid, P.tab_n,
+                              reinterpret_cast<unsigned long long *>(base + P.off_work), ctx->stream);
+        if (e == cudaSuccess) {
+            count_launch(1);
+            k_acc_to_tallies<<<(n_jobs * MAX_OBS + 127) / 128, 128, 0, ctx->stream>>>(
+                reinterpret_cast<unsigned long long *>(base + P.off_acc), n_jobs, g->d_tally);
+            e = cudaGetLastError();
+        }
+    }
+    const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &g->graph);
+    g->kernels = g_launches.load() - l0;
+    g_launches.fetch_sub(g->kernels);   // captured, not launched: replays count them
+    if (s || e != cudaSuccess || ec != cudaSuccess) {
+        graph_free(g);
+        if (s) return s;
+        return cuda_fail(ctx, e != cudaSuccess ? e : ec, "capture");
+    }
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) {
+        graph_free(g);
+        return cuda_fail(ctx, e, "graph instantiate");
+    }
+    *out = g;
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_graph_launch(gcmc_graph *g, double *tallies_out)
+{
+    if (!g) return GCMC_ERR_ARG;
+    gcmc_ctx *ctx = g->ctx;
+    cudaSetDevice(ctx->device);
+    count_launch((int)g->kernels);
+    CK(cudaGraphLaunch(g->exec, ctx->stream));
+    if (tallies_out)
+        CK(cudaMemcpyAsync(tallies_out, g->d_tally, (size_t)g->n_jobs * MAX_OBS * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+    return GCMC_OK;
+}
+
+gcmc_status gcmc_graph_read(gcmc_graph *g, double *tallies_out, gcmc_stats *stats_out)
+{
+    if (!g) return GCMC_ERR_ARG;
+    gcmc_ctx *ctx = g->ctx;
+    cudaSetDevice(ctx->device);
+    return finish_run(ctx, g->P, (char *)g->ws, tallies_out, GCMC_MEM_HOST, stats_out, 1);
+}
+
+gcmc_status gcmc_graph_destroy(gcmc_graph *g)
+{
+    if (!g) return GCMC_ERR_ARG;
+    cudaSetDevice(g->ctx->device);
+    cudaStreamSynchronize(g->ctx->stream);
+    graph_free(g);
+    return GCMC_OK;
+}
+
+}  // extern "C"

@@ -109,6 +109,10 @@ def lib():
                                 P(gcmc_stats)], C.c_int),
             "gcmc_submit": ([C.c_void_p, P(gcmc_job), C.c_int, P(gcmc_launch_cfg), P(C.c_uint64)], C.c_int),
             "gcmc_run_contrib": ([C.c_void_p, P(gcmc_job), C.c_void_p, C.c_void_p, P(gcmc_stats)], C.c_int),
+            "gcmc_graph_create": ([C.c_void_p, P(gcmc_job), C.c_int, P(gcmc_launch_cfg), P(C.c_void_p)], C.c_int),
+            "gcmc_graph_launch": ([C.c_void_p, C.c_void_p], C.c_int),
+            "gcmc_graph_read": ([C.c_void_p, C.c_void_p, P(gcmc_stats)], C.c_int),
+            "gcmc_graph_destroy": ([C.c_void_p], C.c_int),
             "gcmc_poll": ([C.c_void_p, C.c_uint64, C.c_void_p, P(gcmc_stats)], C.c_int),
             "gcmc_run_packets_debug": ([C.c_void_p, P(gcmc_job), C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -144,7 +148,8 @@ def lib():
 
 EXPORTED = ["gcmc_create", "gcmc_destroy", "gcmc_set_stream", "gcmc_set_allocator", "gcmc_last_error",
             "gcmc_upload_grid", "gcmc_upload_opacity", "gcmc_set_source", "gcmc_run_packets", "gcmc_run_batch",
-            "gcmc_submit", "gcmc_poll", "gcmc_run_contrib", "gcmc_run_packets_debug", "gcmc_prep_cells", "gcmc_postscale",
+            "gcmc_submit", "gcmc_poll", "gcmc_run_contrib", "gcmc_graph_create", "gcmc_graph_launch",
+            "gcmc_graph_read", "gcmc_graph_destroy", "gcmc_run_packets_debug", "gcmc_prep_cells", "gcmc_postscale",
             "gcmc_selftest_philox", "gcmc_version", "gcmc_release_grid", "gcmc_release_opacity",
             "gcmc_set_profiling", "gcmc_get_profile", "gcmc_kernel_launches", "gcmc_gather_bench",
             "gcmc_emission_pdf_noalloc", "gcmc_server_create", "gcmc_server_submit", "gcmc_server_progress",
@@ -345,6 +350,10 @@ class Context:
         st = gcmc_stats()
         self._check(lib().gcmc_run_contrib(self.h, C.byref(job), _ptr(out), _ptr(cf), C.byref(st)), "gcmc_run_contrib")
         return out, cf, st
+
+    def graph(self, jobs, cfg=None):
+        """A captured batch (gcmc_graph_*): Graph.launch(tallies=None) replays it on the context's stream."""
+        return Graph(self, jobs, cfg)
 
     def submit(self, jobs, cfg=None):
         arr = (gcmc_job * len(jobs))(*jobs)
@@ -610,3 +619,31 @@ class Server:
             if time.perf_counter() - t0 > timeout_s:
                 raise GcmcError(ERR_TIMEOUT, f"{len(want) - len(got)} served jobs still open after {timeout_s} s")
         return [got[t] for t in tickets]
+
+
+class Graph:
+    """A batch captured into a CUDA graph (gcmc_graph_*)."""
+
+    def __init__(self, ctx: Context, jobs, cfg=None):
+        self.ctx = ctx
+        self.n = len(jobs)
+        arr = (gcmc_job * len(jobs))(*jobs)
+        self.h = C.c_void_p()
+        ctx._check(lib().gcmc_graph_create(ctx.h, arr, len(jobs), C.byref(cfg) if cfg is not None else None,
+                                           C.byref(self.h)), "gcmc_graph_create")
+
+    def launch(self, tallies=None):
+        """Replay asynchronously; tallies: optional torch CUDA tensor [n_jobs][MAX_OBS] float64."""
+        self.ctx._check(lib().gcmc_graph_launch(self.h, _ptr(tallies)), "gcmc_graph_launch")
+
+    def read(self):
+        """(tallies [n_jobs][MAX_OBS], stats [n_jobs]) of the last replay (synchronises)."""
+        out = np.zeros((self.n, MAX_OBS))
+        sts = (gcmc_stats * self.n)()
+        self.ctx._check(lib().gcmc_graph_read(self.h, _ptr(out), sts), "gcmc_graph_read")
+        return out, sts
+
+    def close(self):
+        if self.h:
+            lib().gcmc_graph_destroy(self.h)
+            self.h = C.c_void_p()
