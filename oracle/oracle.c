@@ -82,6 +82,9 @@ typedef struct {
     double w_rr, p_surv, tau_peel_cut, tau_vert_max, beta_emis, hg_iso_eps;
     int32_t scatter_emission, pad;
     int64_t max_steps;
+    int32_t cloud_phase;   /* 0: Henyey-Greenstein; 1: two-term HG with the paper's defaults (Sect. 3) */
+    int32_t pad2;
+    double surface_albedo; /* Lambertian lower boundary of this albedo (0: black) */
 } orc_source;
 
 typedef struct {
@@ -172,6 +175,38 @@ double orc_phase_hg(double mu, double g)
 double orc_theta(double mu, double pgas, double g)
 {
     return (pgas * orc_phase_rayleigh(mu) + (1.0 - pgas) * orc_phase_hg(mu, g)) / (4.0 * ORC_PI);
+}
+
+/* two-term HG (Sect. 3): P = a P_HG(g1) + (1 - a) P_HG(g2), with the defaults the paper uses for a
+   single asymmetry factor g: g1 = g, g2 = -g/2, a = 1 - g2^2 */
+void orc_tthg_params(double g, double *g1, double *g2, double *a)
+{
+    *g1 = g;
+    *g2 = -0.5 * g;
+    *a = 1.0 - (*g2) * (*g2);
+}
+
+double orc_phase_tthg(double mu, double g)
+{
+    double g1, g2, a;
+    orc_tthg_params(g, &g1, &g2, &a);
+    return a * orc_phase_hg(mu, g1) + (1.0 - a) * orc_phase_hg(mu, g2);
+}
+
+/* expected phase function per steradian of the gas / cloud mixture, cloud phase function of the kind */
+double orc_theta_kind(double mu, double pgas, double g, int kind)
+{
+    const double pc = kind == 1 ? orc_phase_tthg(mu, g) : orc_phase_hg(mu, g);
+    return (pgas * orc_phase_rayleigh(mu) + (1.0 - pgas) * pc) / (4.0 * ORC_PI);
+}
+
+/* cosine of a cloud scattering: HG, or the two-term HG, whose term is chosen by zc < a (zc uniform) */
+double orc_sample_cloud(double g, double zc, double z, double eps, int kind)
+{
+    if (kind != 1) return orc_sample_hg(g, z, eps);
+    double g1, g2, a;
+    orc_tthg_params(g, &g1, &g2, &a);
+    return orc_sample_hg(zc < a ? g1 : g2, z, eps);
 }
 
 /* new direction at polar angle acos(mu) and azimuth psi about d; the azimuth origin is the
@@ -607,12 +642,12 @@ static void perp_basis(const double s[3], double e1[3], double e2[3])
 
 /* peel-off optical depth from x (cell c) towards o; returns exp(-tau) or 0 if occulted / cut */
 static double peel(march_ctx *M, const double x0[3], const int c0[3], const double o[3], double cut,
-                   double *tau_out, int *status)
+                   double *tau_out, int *status, int entry)
 {
     double x[3] = {x0[0], x0[1], x0[2]};
     int c[3] = {c0[0], c0[1], c0[2]};
     double tau = 0.0;
-    int st = march(M, x, o, c, -1, -1.0, cut, &tau);
+    int st = march(M, x, o, c, entry, -1.0, cut, &tau);
     *tau_out = tau;
     *status = st;
     if (st == END_ESCAPE) return exp(-tau);
@@ -698,7 +733,7 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
             double tau;
             int st;
             trace_put(&M, -2, 0.0);
-            double e = peel(&M, x, c, S->obs[o], S->tau_peel_cut, &tau, &st);
+            double e = peel(&M, x, c, S->obs[o], S->tau_peel_cut, &tau, &st, -1);
             if (first_tau < 0) first_tau = tau;
             if (st == END_CAP) break;
             f_obs[o] += W * e / (4.0 * ORC_PI);
@@ -727,6 +762,57 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
         trace_put(&M, -1, 0.0);
         int st = march(&M, x, d, c, entry, tau_t, INFINITY, &tau);
         if (st == END_ESCAPE) { kahan(&acc->ledger[1], &acc->ledger_c[1], W); break; }
+        if (st == END_BOTTOM && S->surface_albedo > 0.0) {
+            /* Lambertian reflection at the lower boundary (Sect. 3): peel-offs with the Lambert phase
+               function mu_o / pi per steradian, then weight A_s (survival) or reflection with
+               probability A_s (analog), cosine sqrt(zeta) about the outward normal */
+            const double As = S->surface_albedo;
+            const double rr = sqrt(dot3(x, x));
+            const double nrm[3] = {x[0] / rr, x[1] / rr, x[2] / rr};
+            const int64_t sidx = flat(G, c);
+            int capped = 0;
+            for (int o = 0; o < S->n_obs; ++o) {
+                /* the point lies on the lower boundary: its root there is dropped; directions into
+                   the planet contribute nothing and are not traced */
+                const double mo = dot3(nrm, S->obs[o]);
+                if (!(mo > 0.0)) continue;
+                double tau_o = 0.0;
+                int so = END_ESCAPE;
+                trace_put(&M, -2, 0.0);
+                const double e = peel(&M, x, c, S->obs[o], S->tau_peel_cut, &tau_o, &so, F_RIN);
+                if (so == END_CAP) { capped = 1; break; }
+                const double fo = W * As * (mo / ORC_PI) * e;
+                f_obs[o] += fo;
+                if (A->cf) cf_put(acc, sidx, 1, o, fo);
+            }
+            if (capped) { kahan(&acc->ledger[6], &acc->ledger_c[6], W); break; }
+            if (S->survival) {
+                kahan(&acc->ledger[3], &acc->ledger_c[3], W * (1.0 - As));
+                W *= As;
+                if (W < S->w_rr * W0) {
+                    double v[4];
+                    draw(A->seed, n, ev | 0x80000000u, A->job_key, v);
+                    if (v[1] < S->p_surv) {
+                        double Wn = W / S->p_surv;
+                        kahan(&acc->ledger[4], &acc->ledger_c[4], Wn - W);
+                        W = Wn;
+                    } else {
+                        kahan(&acc->ledger[5], &acc->ledger_c[5], W);
+                        break;
+                    }
+                }
+            } else {
+                double v[4];
+                draw(A->seed, n, ev | 0x80000000u, A->job_key, v);
+                if (!(v[0] < As)) { kahan(&acc->ledger[3], &acc->ledger_c[3], W); break; }
+            }
+            double nd[3];
+            orc_turn(nrm, sqrt(u[2]), 2.0 * ORC_PI * u[3], nd);
+            d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
+            entry = F_RIN;
+            ++ev;
+            continue;
+        }
         if (st == END_BOTTOM) { kahan(&acc->ledger[3], &acc->ledger_c[3], W); break; }
         if (st != END_INTERACT) { kahan(&acc->ledger[st == END_CAP ? 6 : 7], &acc->ledger_c[st == END_CAP ? 6 : 7], W); break; }
         int64_t idx = flat(G, c);
@@ -738,10 +824,11 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
             double tau_o;
             int so;
             trace_put(&M, -2, 0.0);
-            double e = peel(&M, x, c, S->obs[o], S->tau_peel_cut, &tau_o, &so);
+            double e = peel(&M, x, c, S->obs[o], S->tau_peel_cut, &tau_o, &so, -1);
             if (so == END_CAP) { capped = 1; break; }
-            f_obs[o] += W * om * orc_theta(dot3(d, S->obs[o]), pg, gg) * e;
-            if (A->cf) cf_put(acc, idx, 1, o, W * om * orc_theta(dot3(d, S->obs[o]), pg, gg) * e);
+            const double fo = W * om * orc_theta_kind(dot3(d, S->obs[o]), pg, gg, S->cloud_phase) * e;
+            f_obs[o] += fo;
+            if (A->cf) cf_put(acc, idx, 1, o, fo);
         }
         if (capped) { kahan(&acc->ledger[6], &acc->ledger_c[6], W); break; }
         if (W * om == 0.0) { kahan(&acc->ledger[2], &acc->ledger_c[2], W); break; }
@@ -765,7 +852,10 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
             draw(A->seed, n, ev | 0x80000000u, A->job_key, v);
             if (!(v[0] < om)) { kahan(&acc->ledger[2], &acc->ledger_c[2], W); break; }
         }
-        double mu = (u[1] < pg) ? orc_sample_rayleigh(u[2]) : orc_sample_hg(gg, u[2], S->hg_iso_eps);
+        /* scatterer: gas if u1 < P_gas, else cloud; the cloud's own choice (two-term HG) uses u1's
+           remaining uniform (u1 - P_gas) / (1 - P_gas) */
+        double mu = (u[1] < pg) ? orc_sample_rayleigh(u[2])
+                                : orc_sample_cloud(gg, (u[1] - pg) / (1.0 - pg), u[2], S->hg_iso_eps, S->cloud_phase);
         double nd[3];
         orc_turn(d, mu, 2.0 * ORC_PI * u[3], nd);
         d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];

@@ -53,7 +53,8 @@ class Source_c(C.Structure):
                 ("obs", (C.c_double * 3) * MAX_OBS),
                 ("w_rr", C.c_double), ("p_surv", C.c_double), ("tau_peel_cut", C.c_double),
                 ("tau_vert_max", C.c_double), ("beta_emis", C.c_double), ("hg_iso_eps", C.c_double),
-                ("scatter_emission", C.c_int32), ("pad", C.c_int32), ("max_steps", C.c_int64)]
+                ("scatter_emission", C.c_int32), ("pad", C.c_int32), ("max_steps", C.c_int64),
+                ("cloud_phase", C.c_int32), ("pad2", C.c_int32), ("surface_albedo", C.c_double)]
 
 
 class Run_c(C.Structure):
@@ -83,6 +84,12 @@ def lib():
             _lib.orc_phase_hg.restype = D
             _lib.orc_theta.argtypes = [D, D, D]
             _lib.orc_theta.restype = D
+            _lib.orc_phase_tthg.argtypes = [D, D]
+            _lib.orc_phase_tthg.restype = D
+            _lib.orc_theta_kind.argtypes = [D, D, D, C.c_int]
+            _lib.orc_theta_kind.restype = D
+            _lib.orc_sample_cloud.argtypes = [D, D, D, D, C.c_int]
+            _lib.orc_sample_cloud.restype = D
             _lib.orc_planck.argtypes = [D, D]
             _lib.orc_planck.restype = D
             _lib.orc_turn.argtypes = [P(D), D, D, P(D)]
@@ -146,6 +153,18 @@ def phase_rayleigh(mu):
 
 def theta(mu, pgas, g):
     return lib().orc_theta(float(mu), float(pgas), float(g))
+
+
+def phase_tthg(mu, g):
+    return lib().orc_phase_tthg(float(mu), float(g))
+
+
+def theta_kind(mu, pgas, g, kind):
+    return lib().orc_theta_kind(float(mu), float(pgas), float(g), int(kind))
+
+
+def sample_cloud(g, zc, z, kind, eps=1e-4):
+    return lib().orc_sample_cloud(float(g), float(zc), float(z), float(eps), int(kind))
 
 
 def planck(lam, T):
@@ -244,6 +263,8 @@ def _source_struct(src, obs):
     s.tau_vert_max, s.beta_emis, s.hg_iso_eps = float(op.tau_vert_max), float(op.beta_emis), float(op.hg_iso_eps)
     s.scatter_emission = int(op.scatter_emission)
     s.max_steps = int(op.max_steps)
+    s.cloud_phase = int(getattr(op, "cloud_phase", 0))
+    s.surface_albedo = float(getattr(op, "surface_albedo", 0.0))
     return s, len(obs)
 
 

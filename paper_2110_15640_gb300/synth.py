@@ -127,6 +127,8 @@ class Options:
     scatter_emission: int = 0    # emission: follow packets after the launch peel-off
     max_steps: int = 1 << 22     # per-packet cap on cell segments
     hg_iso_eps: float = 1.0e-4   # |g| below this samples isotropically
+    cloud_phase: int = 0         # 0 Henyey-Greenstein clouds, 1 two-term HG (g1 = g, g2 = -g/2, a = 1 - g2^2)
+    surface_albedo: float = 0.0  # Lambertian lower boundary (0: black)
 
 
 @dataclasses.dataclass
@@ -518,9 +520,10 @@ def uniform_absorber_sphere(alpha=2.0e-6, R0=R_JUP, H_atm=5.0e6, nlon=4, nlat=4,
 
 
 def slab_sphere_albedo(omega=0.5, tau=20.0, phase="iso", g=0.0, n_packets=100_000, seed=12, thin=1.0e-4,
-                       nlon=8, nlat=8, survival=1):
+                       nlon=8, nlat=8, survival=1, surface_albedo=0.0, obs=None):
     """Homogeneous one-layer atmosphere of thickness thin * R0 and vertical optical depth tau on a
-    black sphere: locally a plane-parallel slab.  phase = 'iso' (HG with g = 0), 'hg' or 'rayleigh'."""
+    black (or Lambertian, surface_albedo) sphere: locally a plane-parallel slab.  phase = 'iso'
+    (HG with g = 0), 'hg', 'tthg' (two-term HG of asymmetry g) or 'rayleigh'."""
     R0 = R_JUP
     H = thin * R0
     grid = uniform_grid(nlon, nlat, 1, R0, R0 + H, rho=1.0)
@@ -530,10 +533,12 @@ def slab_sphere_albedo(omega=0.5, tau=20.0, phase="iso", g=0.0, n_packets=100_00
                              qcld=np.zeros(1), wcld=np.zeros(1), gcld=np.zeros(1))
     else:
         opac = AlbedoOpacity(kabs=np.array([0.0]), kray=np.array([0.0]), qcld=np.ones(1),
-                             wcld=np.array([omega]), gcld=np.array([g if phase == "hg" else 0.0]),
+                             wcld=np.array([omega]), gcld=np.array([g if phase in ("hg", "tthg") else 0.0]),
                              acld=np.full(grid.ncell, kext, np.float32))
-    src = Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[1.0, 0.0, 0.0]]),
-                 opts=Options(survival=survival, w_rr=1e-4))
+    src = Source(star=np.array([1.0, 0.0, 0.0]),
+                 obs=np.array([[1.0, 0.0, 0.0]]) if obs is None else np.atleast_2d(np.asarray(obs, np.float64)),
+                 opts=Options(survival=survival, w_rr=1e-4, cloud_phase=1 if phase == "tthg" else 0,
+                              surface_albedo=surface_albedo))
     jobs = [Job(lam_idx=0, g_idx=0, n_packets=n_packets, key=0)]
     return Workload(f"slab_{phase}_w{omega}_t{tau}", MODE_ALBEDO, grid, opac, src, jobs, seed)
 
