@@ -142,9 +142,23 @@ typedef struct {
     int32_t scatter_emission; /* emission: 1 = follow packets after the launch peel-off */
     int32_t precision;        /* GCMC_FP32 (FP32 march, FP64 near-tangent roots) or GCMC_FP64 */
     int64_t max_steps;        /* per-packet cap on cell segments (stats count capped packets) */
+    int32_t cloud_phase;      /* cloud phase function (Sect. 3): GCMC_CLOUD_HG, or GCMC_CLOUD_TTHG, the two-term
+                                 HG of one asymmetry g: a P_HG(g) + (1 - a) P_HG(-g/2), a = 1 - g^2/4; a
+                                 scattering picks the term from its gas/cloud uniform u1 rescaled to
+                                 (u1 - P_gas) / (1 - P_gas) */
+    int32_t pad2;
+    double surface_albedo;    /* Lambertian lower boundary of this albedo in [0, 1] (Sect. 3); 0 = black.  A packet
+                                 that reaches it peels off towards each observer above the local horizon
+                                 with weight A_s mu_o / pi and leaves with cosine sqrt(zeta) about the normal,
+                                 weight A_s (survival biasing) or probability A_s (analog).  Albedo mode only:
+                                 emission and transmission packets do not fly */
 } gcmc_source_desc;
 
-/* Register a source description; *source_id receives its id.  Errors: GCMC_ERR_ARG. */
+#define GCMC_CLOUD_HG 0
+#define GCMC_CLOUD_TTHG 1
+
+/* Register a source description; *source_id receives its id.  Errors: GCMC_ERR_ARG (not unit vectors,
+   options out of range, unknown cloud_phase, surface_albedo outside [0, 1]). */
 gcmc_status gcmc_set_source(gcmc_ctx *ctx, int grid_id, const gcmc_source_desc *desc, int *source_id);
 
 /* ---------------------------------------------------------------- running packets */

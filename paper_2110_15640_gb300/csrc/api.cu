@@ -350,6 +350,9 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
         d.p_surv = s.p_surv;
         d.tau_cut = s.tau_peel_cut;
         d.hg_eps = s.hg_iso_eps;
+        d.cloud_phase = s.cloud_phase;
+        d.surf_as = s.surface_albedo;
+        d.surf_as_f = (float)s.surface_albedo;
         for (int a = 0; a < 3; ++a) {
             d.star_f[a] = (float)d.star[a];
             d.e1_f[a] = (float)d.e1[a];
@@ -964,6 +967,10 @@ gcmc_status gcmc_set_source(gcmc_ctx *ctx, int grid_id, const gcmc_source_desc *
     if (!(d->p_surv > 0.0 && d->p_surv <= 1.0) || !(d->w_rr >= 0.0) || !(d->tau_peel_cut > 0.0) ||
         !(d->beta_emis >= 0.0 && d->beta_emis <= 1.0) || !(d->tau_vert_max > 0.0))
         return fail(ctx, GCMC_ERR_ARG, "options out of range");
+    if (d->cloud_phase != GCMC_CLOUD_HG && d->cloud_phase != GCMC_CLOUD_TTHG)
+        return fail(ctx, GCMC_ERR_ARG, "unknown cloud_phase");
+    if (!(d->surface_albedo >= 0.0 && d->surface_albedo <= 1.0))
+        return fail(ctx, GCMC_ERR_ARG, "surface_albedo must be in [0, 1]");
     *source_id = (int)ctx->sources.size();
     ctx->sources.push_back(*d);
     return GCMC_OK;

@@ -66,7 +66,7 @@ struct __align__(16) Rec64 {
 
 struct DevJob {
     int32_t mode, n_obs, grid_slot, survival;
-    int32_t precision, pad0;
+    int32_t precision, cloud_phase;   // cloud_phase: GCMC_CLOUD_HG or GCMC_CLOUD_TTHG
     uint32_t key, pad1;
     uint64_t seed;
     int64_t n_packets;
@@ -80,10 +80,11 @@ struct DevJob {
     double star[3], e1[3], e2[3];
     double obs[MAX_OBS][3];
     double w_rr, p_surv, tau_cut, hg_eps;
+    double surf_as;             // Lambertian surface albedo (0: black lower boundary)
     // the same vectors and constants rounded once to FP32, for FP32 marches
     float star_f[3], e1_f[3], e2_f[3];
     float obs_f[MAX_OBS][3];
-    float w_rr_f, p_surv_f, hg_eps_f, pad2;
+    float w_rr_f, p_surv_f, hg_eps_f, surf_as_f;
     unsigned long long *acc;    // [ACC_SLOTS]
     // contribution functions (Sect. 6), or NULL: [2][n_obs][cf_ncell] fixed-point sums of the peel-off
     // contributions by the cell they leave from, [0] thermal (emission launch), [1] scattered
@@ -101,6 +102,7 @@ template <> struct JV<double> {
     static __device__ __forceinline__ double w_rr(const DevJob &J) { return J.w_rr; }
     static __device__ __forceinline__ double p_surv(const DevJob &J) { return J.p_surv; }
     static __device__ __forceinline__ double hg_eps(const DevJob &J) { return J.hg_eps; }
+    static __device__ __forceinline__ double surf_as(const DevJob &J) { return J.surf_as; }
 };
 template <> struct JV<float> {
     static __device__ __forceinline__ float star(const DevJob &J, int q) { return J.star_f[q]; }
@@ -110,6 +112,7 @@ template <> struct JV<float> {
     static __device__ __forceinline__ float w_rr(const DevJob &J) { return J.w_rr_f; }
     static __device__ __forceinline__ float p_surv(const DevJob &J) { return J.p_surv_f; }
     static __device__ __forceinline__ float hg_eps(const DevJob &J) { return J.hg_eps_f; }
+    static __device__ __forceinline__ float surf_as(const DevJob &J) { return J.surf_as_f; }
 };
 
 // ------------------------------------------------------------------ Philox4x32-10 (Salmon et al. 2011)

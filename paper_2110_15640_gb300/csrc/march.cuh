@@ -299,13 +299,32 @@ template <typename real> __device__ __forceinline__ real sample_hg(real g, real 
     return mu;
 }
 
-// probability per steradian of scattering by angle acos(mu): (P_gas P_Ray + (1 - P_gas) P_HG) / (4 pi)
-template <typename real> __device__ __forceinline__ real theta_mix(real mu, real pg, real g)
+// Henyey-Greenstein phase function, normalised to 2 over mu in [-1, 1]
+template <typename real> __device__ __forceinline__ real phase_hg(real mu, real g)
+{
+    const real den = (real)1 + g * g - (real)2 * g * mu;
+    return ((real)1 - g * g) * M<real>::rsqrt_(den) * M<real>::div_((real)1, den);
+}
+
+// two-term HG of one asymmetry g (Sect. 3): terms g1 = g, g2 = -g/2, weight a = 1 - g2^2 on the first
+template <typename real> __device__ __forceinline__ void tthg_terms(real g, real &g2, real &a)
+{
+    g2 = (real)-0.5 * g;
+    a = (real)1 - g2 * g2;
+}
+
+// probability per steradian of scattering by angle acos(mu): (P_gas P_Ray + (1 - P_gas) P_cloud) / (4 pi),
+// P_cloud the HG function, or the two-term HG when tthg is set
+template <typename real> __device__ __forceinline__ real theta_mix(real mu, real pg, real g, bool tthg = false)
 {
     const real pr = (real)0.75 * ((real)1 + mu * mu);
-    const real den = (real)1 + g * g - (real)2 * g * mu;
-    const real ph = ((real)1 - g * g) * M<real>::rsqrt_(den) * M<real>::div_((real)1, den);
-    return (pg * pr + ((real)1 - pg) * ph) * (real)(1.0 / (4.0 * PI));
+    real pc = phase_hg<real>(mu, g);
+    if (tthg) {
+        real g2, a;
+        tthg_terms<real>(g, g2, a);
+        pc = a * pc + ((real)1 - a) * phase_hg<real>(mu, g2);
+    }
+    return (pg * pr + ((real)1 - pg) * pc) * (real)(1.0 / (4.0 * PI));
 }
 
 // direction at polar angle acos(mu), azimuth psi about d (azimuth origin as in the standard

@@ -297,9 +297,67 @@ __device__ void after_peels_scatter(Packet<real> &P, const DevJob &J, SinkT &S)
     }
     const uint4 w = draw_words(J.seed, P.n, P.ev, J.key);
     const real u1 = u01<real>(w.y), u2 = u01<real>(w.z), u3 = u01<real>(w.w);
-    const real mu = (u1 < P.pg) ? sample_rayleigh<real>(u2) : sample_hg<real>(P.gg, u2, JV<real>::hg_eps(J));
+    real mu;
+    if (u1 < P.pg) {
+        mu = sample_rayleigh<real>(u2);
+    } else {
+        // cloud: HG, or the two-term HG whose term is chosen by u1 rescaled to (u1 - P_gas) / (1 - P_gas)
+        real gs = P.gg;
+        if (J.cloud_phase == GCMC_CLOUD_TTHG) {
+            real g2, a;
+            tthg_terms<real>(P.gg, g2, a);
+            gs = M<real>::div_(u1 - P.pg, (real)1 - P.pg) < a ? P.gg : g2;
+        }
+        mu = sample_hg<real>(gs, u2, JV<real>::hg_eps(J));
+    }
     real dx = P.fx, dy = P.fy, dz = P.fz;
     turn<real>(dx, dy, dz, mu, (real)(2.0 * PI) * u3);
+    ++P.ev;
+    start_flight<real>(P, J, S, dx, dy, dz);
+}
+
+// first observer, from o on, above the horizon of the surface point (normal in fx, fy, fz)
+template <typename real>
+__device__ __forceinline__ int surface_obs(const Packet<real> &P, const DevJob &J, int o)
+{
+    for (; o < J.n_obs; ++o)
+        if (P.fx * JV<real>::obs(J, o, 0) + P.fy * JV<real>::obs(J, o, 1) + P.fz * JV<real>::obs(J, o, 2) > (real)0) break;
+    return o;
+}
+
+// Lambertian reflection after the surface peel-offs (Sect. 3): weight A_s (survival biasing, then
+// roulette) or reflection with probability A_s (analog); the absorbed part ends at the lower boundary.
+// New direction: cosine sqrt(u2) about the normal, azimuth 2 pi u3, from the flight's own draws.
+template <typename real, class SinkT>
+__device__ void after_peels_surface(Packet<real> &P, const DevJob &J, SinkT &S)
+{
+    const real As = JV<real>::surf_as(J);
+    if (J.survival) {
+        S.ledger(3, P.W * ((real)1 - As));
+        P.W *= As;
+        if (P.W < JV<real>::w_rr(J) * P.W0) {
+            const uint4 v = draw_words(J.seed, P.n, P.ev | 0x80000000u, J.key);
+            if (u01<real>(v.y) < JV<real>::p_surv(J)) {
+                const real Wn = P.W / JV<real>::p_surv(J);
+                S.ledger(4, Wn - P.W);
+                P.W = Wn;
+            } else {
+                S.ledger(5, P.W);
+                finish<real>(P, S);
+                return;
+            }
+        }
+    } else {
+        const uint4 v = draw_words(J.seed, P.n, P.ev | 0x80000000u, J.key);
+        if (!(u01<real>(v.x) < As)) {
+            S.ledger(3, P.W);
+            finish<real>(P, S);
+            return;
+        }
+    }
+    const uint4 w = draw_words(J.seed, P.n, P.ev, J.key);
+    real dx = P.fx, dy = P.fy, dz = P.fz;
+    turn<real>(dx, dy, dz, M<real>::sqrt_(u01<real>(w.z)), (real)(2.0 * PI) * u01<real>(w.w));
     ++P.ev;
     start_flight<real>(P, J, S, dx, dy, dz);
 }
@@ -310,6 +368,26 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
     Ray<real> &R = P.ray;
     if constexpr (SCAT) {
         if (P.kind == K_FLIGHT) {
+            if (e == E_BOTTOM && JV<real>::surf_as(J) > (real)0) {
+                // a reflecting lower boundary: surface point and its outward normal (kept in fx, fy, fz),
+                // then the peel-offs towards the observers above its horizon
+                P.ix = R.cx + R.s * R.dx;
+                P.iy = R.cy + R.s * R.dy;
+                P.iz = R.cz + R.s * R.dz;
+                const real rr = M<real>::sqrt_(P.ix * P.ix + P.iy * P.iy + P.iz * P.iz);
+                P.fx = M<real>::div_(P.ix, rr);
+                P.fy = M<real>::div_(P.iy, rr);
+                P.fz = M<real>::div_(P.iz, rr);
+                P.ci = R.i;
+                P.cj = R.j;
+                P.ck = R.k;
+                P.cell0 = idx;
+                P.stage = 2;
+                P.obs = surface_obs<real>(P, J, 0);
+                if (P.obs < J.n_obs) start_peel<real>(P, J, S);
+                else after_peels_surface<real>(P, J, S);
+                return;
+            }
             if (e != E_INTERACT) {
                 S.ledger(e == E_ESCAPE ? 1 : e == E_BOTTOM ? 3 : e == E_CAP ? 6 : 7, P.W);
                 finish<real>(P, S);
@@ -357,7 +435,8 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
             f = P.W * ex * (real)(1.0 / (4.0 * PI));
         } else {
             const real mu = P.fx * JV<real>::obs(J, P.obs, 0) + P.fy * JV<real>::obs(J, P.obs, 1) + P.fz * JV<real>::obs(J, P.obs, 2);
-            f = P.W * P.om * theta_mix<real>(mu, P.pg, P.gg) * ex;
+            if (P.stage == 2) f = P.W * JV<real>::surf_as(J) * (mu * (real)(1.0 / PI)) * ex;   // Lambert: mu_o / pi
+            else f = P.W * P.om * theta_mix<real>(mu, P.pg, P.gg, J.cloud_phase == GCMC_CLOUD_TTHG) * ex;
         }
         S.tally(P.obs, f, P.n, J.n_obs);
         if (J.cf && f < (real)1.0e9 && f >= (real)0) {
@@ -367,13 +446,17 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
                       (unsigned long long)to_fix<real>(f));
         }
         ++P.obs;
+        if constexpr (SCAT) {
+            if (P.stage == 2) P.obs = surface_obs<real>(P, J, P.obs);
+        }
         if (P.obs < J.n_obs) {
             start_peel<real>(P, J, S);
             return;
         }
         if constexpr (SCAT) {
             if (J.mode == GCMC_ALBEDO) {
-                after_peels_scatter<real>(P, J, S);
+                if (P.stage == 2) after_peels_surface<real>(P, J, S);
+                else after_peels_scatter<real>(P, J, S);
                 return;
             }
         }

@@ -46,7 +46,8 @@ class gcmc_source_desc(C.Structure):
                 ("obs", (C.c_double * 3) * MAX_OBS), ("w_rr", C.c_double), ("p_surv", C.c_double),
                 ("tau_peel_cut", C.c_double), ("tau_vert_max", C.c_double), ("beta_emis", C.c_double),
                 ("hg_iso_eps", C.c_double), ("scatter_emission", C.c_int32), ("precision", C.c_int32),
-                ("max_steps", C.c_int64)]
+                ("max_steps", C.c_int64), ("cloud_phase", C.c_int32), ("pad2", C.c_int32),
+                ("surface_albedo", C.c_double)]
 
 
 class gcmc_stats(C.Structure):
@@ -308,6 +309,8 @@ class Context:
         d.scatter_emission = int(op.scatter_emission)
         d.precision = int(precision)
         d.max_steps = int(op.max_steps)
+        d.cloud_phase = int(op.cloud_phase)
+        d.surface_albedo = float(op.surface_albedo)
         sid = C.c_int()
         self._check(lib().gcmc_set_source(self.h, int(grid_id), C.byref(d), C.byref(sid)), "gcmc_set_source")
         return sid.value
