@@ -31,7 +31,12 @@
  *     optical depth above them is < tau_vert_max; W = (L_i/L_tot)/q_i; the cell is drawn by
  *     inverse CDF with the stratified uniform (n + z)/N (the per-cell allocation
  *     N_i ~ N q_i of Sect. 4.3); position uniform in r^3, sin(lat), lon.
- *   - Transmission: b ~ U[R0, R_TOA], psi ~ U[0, 2 pi), chord along -star, W = 1.
+ *   - Transmission: b ~ U[R0, R_TOA], psi ~ U[0, 2 pi), chord along -star, W = 1, or with stellar
+ *     limb darkening W = I(mu)/I(centre) at the chord's position on the stellar disk (0 off the
+ *     disk: not traced).  The chord gives column 0, W (1 - e^-tau) b / R_TOA.  With multiple
+ *     scattering the packet then flies from its launch point along -star; each scattering peels off
+ *     towards -star into column 1 with f b / R_TOA (the host subtracts Omega_star times it).
+ *     A packet's weight ends in exactly one ledger entry (a capped chord: "capped" only).
  *   - Doppler: theta, theta_v in the v_LOS formula are polar angles (colatitudes);
  *     v_LOS > 0 is motion away from the observer; opacity interpolated linearly in ln(sigma)
  *     between the bracketing table wavelengths (weight linear in lambda), bilinear in
@@ -85,6 +90,15 @@ typedef struct {
     int32_t cloud_phase;   /* 0: Henyey-Greenstein; 1: two-term HG with the paper's defaults (Sect. 3) */
     int32_t pad2;
     double surface_albedo; /* Lambertian lower boundary of this albedo (0: black) */
+    int32_t trans_scatter; /* transmission: after the chord the packet scatters, with peel-offs towards
+                              the transit observer (Sect. 5.1); needs scattering cell records */
+    int32_t ld_law;        /* stellar limb-darkening law (Sect. 5.1): 0 none, 1 linear, 2 quadratic,
+                              3 square-root, 4 logarithmic, 5 power-2, 6 four-coefficient */
+    double ld_coef[4];
+    double star_radius;    /* m */
+    double star_dist;      /* m (used by the host post-scale only) */
+    double transit_xy[2];  /* planet centre on the sky plane relative to the stellar disk centre, along the
+                              launch basis (e1, e2), m */
 } orc_source;
 
 typedef struct {
@@ -198,6 +212,27 @@ double orc_theta_kind(double mu, double pgas, double g, int kind)
 {
     const double pc = kind == 1 ? orc_phase_tthg(mu, g) : orc_phase_hg(mu, g);
     return (pgas * orc_phase_rayleigh(mu) + (1.0 - pgas) * pc) / (4.0 * ORC_PI);
+}
+
+/* limb-darkening laws (Sect. 5.1: the stellar intensity at zenith-angle cosine mu relative to the disk
+   centre, mu = 1); each of these equals 1 at mu = 1.  Negative values (bad coefficients) count as 0. */
+double orc_limb(int law, const double c[4], double mu)
+{
+    const double x = 1.0 - mu;
+    double I;
+    switch (law) {
+    case 1: I = 1.0 - c[0] * x; break;
+    case 2: I = 1.0 - c[0] * x - c[1] * x * x; break;
+    case 3: I = 1.0 - c[0] * x - c[1] * (1.0 - sqrt(mu)); break;
+    case 4: I = 1.0 - c[0] * x - c[1] * (mu > 0.0 ? mu * log(mu) : 0.0); break;
+    case 5: I = 1.0 - c[0] * (1.0 - pow(mu, c[1])); break;
+    case 6:
+        I = 1.0;
+        for (int k = 1; k <= 4; ++k) I -= c[k - 1] * (1.0 - pow(mu, 0.5 * k));
+        break;
+    default: I = 1.0;
+    }
+    return I > 0.0 ? I : 0.0;
 }
 
 /* cosine of a cloud scattering: HG, or the two-term HG, whose term is chosen by zc < a (zc uniform) */
@@ -654,6 +689,14 @@ static double peel(march_ctx *M, const double x0[3], const int c0[3], const doub
     return 0.0;
 }
 
+/* tally columns of a job: one per observer (albedo, emission); transmission: the chord (direct)
+   column, plus the scattered-light column when packets scatter after their chord */
+static int tally_cols(const orc_source *S, int mode)
+{
+    if (mode == 2) return S->trans_scatter ? 2 : 1;
+    return S->n_obs;
+}
+
 static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int64_t *pk_steps, double *pk_tau,
                        int32_t *tr_cell, double *tr_len, int32_t *tr_n, int32_t tr_max)
 {
@@ -666,12 +709,18 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
     double R0 = G->r_edges[0];
     double u[4];
     double f_obs[ORC_MAX_OBS];
-    for (int o = 0; o < S->n_obs; ++o) f_obs[o] = 0.0;
+    for (int o = 0; o < ORC_MAX_OBS; ++o) f_obs[o] = 0.0;
     double first_tau = -1.0;
     double x[3], d[3];
     int c[3], entry = -1;
     double W = 0.0, W0 = 0.0;
     int transport = 0;
+    /* peel-off targets: every observer (albedo, emission), or in transmission the transit observer
+       -star, whose scattered light goes to column 1 weighted by the launch b / R_TOA (Sect. 5.1) */
+    const int trans = A->mode == 2;
+    const double antistar[3] = {-S->star[0], -S->star[1], -S->star[2]};
+    const int n_peel = trans ? 1 : S->n_obs;
+    double peel_scale = 1.0;
 
     draw(A->seed, n, 0u, A->job_key, u);
     if (A->mode == 0 || A->mode == 2) {
@@ -688,20 +737,40 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
         locate_angles(G, x, c);
         entry = F_ROUT;
         W = W0 = 1.0;
+        if (trans && S->ld_law) {
+            /* limb darkening (Sect. 5.1): the chord's sky-plane position on the stellar disk gives the
+               stellar zenith-angle cosine mu, and the packet carries I(mu) / I(disk centre); a chord
+               that misses the stellar disk carries nothing and is not traced */
+            const double X = S->transit_xy[0] + b * cos(psi), Y = S->transit_xy[1] + b * sin(psi);
+            const double q = (X * X + Y * Y) / (S->star_radius * S->star_radius);
+            W = W0 = q < 1.0 ? orc_limb(S->ld_law, S->ld_coef, sqrt(1.0 - q)) : 0.0;
+        }
         kahan(&acc->ledger[0], &acc->ledger_c[0], W0);
         if (A->mode == 0) {
             transport = 1;
-        } else {
+        } else if (W > 0.0) {
+            const double x_l[3] = {x[0], x[1], x[2]};
+            const int c_l[3] = {c[0], c[1], c[2]};
             trace_put(&M, -3, 0.0);
             double tau = 0.0;
             int st = march(&M, x, d, c, entry, -1.0, S->tau_peel_cut, &tau);
             double contrib;
             if (st == END_ESCAPE) contrib = (1.0 - exp(-tau)) * b / Rtoa;
             else if (st == END_CUTOFF || st == END_BOTTOM) contrib = b / Rtoa;
-            else { contrib = 0.0; kahan(&acc->ledger[st == END_CAP ? 6 : 7], &acc->ledger_c[st == END_CAP ? 6 : 7], W); }
+            else contrib = 0.0;
             first_tau = tau;
-            f_obs[0] += contrib;
-            kahan(&acc->ledger[1], &acc->ledger_c[1], W);
+            f_obs[0] += W * contrib;
+            if (st == END_CAP || st == END_LOST) {
+                kahan(&acc->ledger[st == END_CAP ? 6 : 7], &acc->ledger_c[st == END_CAP ? 6 : 7], W);
+            } else if (S->trans_scatter) {
+                /* multiple scattering (Sect. 5.1): the packet itself starts at the launch point */
+                x[0] = x_l[0]; x[1] = x_l[1]; x[2] = x_l[2];
+                c[0] = c_l[0]; c[1] = c_l[1]; c[2] = c_l[2];
+                peel_scale = b / Rtoa;
+                transport = 1;
+            } else {
+                kahan(&acc->ledger[1], &acc->ledger_c[1], W);
+            }
         }
     } else {
         /* emission launch: stratified draw over the hybrid pdf */
@@ -771,18 +840,19 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
             const double nrm[3] = {x[0] / rr, x[1] / rr, x[2] / rr};
             const int64_t sidx = flat(G, c);
             int capped = 0;
-            for (int o = 0; o < S->n_obs; ++o) {
+            for (int o = 0; o < n_peel; ++o) {
                 /* the point lies on the lower boundary: its root there is dropped; directions into
                    the planet contribute nothing and are not traced */
-                const double mo = dot3(nrm, S->obs[o]);
+                const double *od = trans ? antistar : S->obs[o];
+                const double mo = dot3(nrm, od);
                 if (!(mo > 0.0)) continue;
                 double tau_o = 0.0;
                 int so = END_ESCAPE;
                 trace_put(&M, -2, 0.0);
-                const double e = peel(&M, x, c, S->obs[o], S->tau_peel_cut, &tau_o, &so, F_RIN);
+                const double e = peel(&M, x, c, od, S->tau_peel_cut, &tau_o, &so, F_RIN);
                 if (so == END_CAP) { capped = 1; break; }
                 const double fo = W * As * (mo / ORC_PI) * e;
-                f_obs[o] += fo;
+                f_obs[trans ? 1 : o] += fo * peel_scale;
                 if (A->cf) cf_put(acc, sidx, 1, o, fo);
             }
             if (capped) { kahan(&acc->ledger[6], &acc->ledger_c[6], W); break; }
@@ -820,14 +890,15 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
         double gg = C->g ? C->g[idx] : 0.0;
         double pg = C->pgas ? C->pgas[idx] : 1.0;
         int capped = 0;
-        for (int o = 0; o < S->n_obs; ++o) {
+        for (int o = 0; o < n_peel; ++o) {
+            const double *od = trans ? antistar : S->obs[o];
             double tau_o;
             int so;
             trace_put(&M, -2, 0.0);
-            double e = peel(&M, x, c, S->obs[o], S->tau_peel_cut, &tau_o, &so, -1);
+            double e = peel(&M, x, c, od, S->tau_peel_cut, &tau_o, &so, -1);
             if (so == END_CAP) { capped = 1; break; }
-            const double fo = W * om * orc_theta_kind(dot3(d, S->obs[o]), pg, gg, S->cloud_phase) * e;
-            f_obs[o] += fo;
+            const double fo = W * om * orc_theta_kind(dot3(d, od), pg, gg, S->cloud_phase) * e;
+            f_obs[trans ? 1 : o] += fo * peel_scale;
             if (A->cf) cf_put(acc, idx, 1, o, fo);
         }
         if (capped) { kahan(&acc->ledger[6], &acc->ledger_c[6], W); break; }
@@ -863,7 +934,7 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
         ++ev;
     }
 
-    for (int o = 0; o < S->n_obs; ++o) {
+    for (int o = 0; o < tally_cols(S, A->mode); ++o) {
         kahan(&acc->tally[o], &acc->tally_c[o], f_obs[o]);
         if (pk_f) pk_f[o] = f_obs[o];
     }
@@ -898,7 +969,7 @@ static void run_chunk(const job_t *J, int64_t ch, acc_t *acc)
             tl = A->tr_len + q * A->max_trace;
             tn = A->tr_n + q;
         }
-        run_packet(J, n, acc, A->pk_f ? A->pk_f + q * J->S->n_obs : NULL, A->pk_steps ? A->pk_steps + q : NULL,
+        run_packet(J, n, acc, A->pk_f ? A->pk_f + q * tally_cols(J->S, A->mode) : NULL, A->pk_steps ? A->pk_steps + q : NULL,
                    A->pk_tau ? A->pk_tau + q : NULL, tc, tl, tn, A->max_trace);
     }
 }
@@ -945,7 +1016,7 @@ int orc_run(const orc_grid *G, const orc_cells *C, const orc_source *S, orc_run_
     int64_t steps = 0;
     int cf_oom = 0;
     for (int64_t ch = 0; ch < nch; ++ch) {
-        for (int o = 0; o < S->n_obs; ++o) kahan(&ts[o], &tc[o], chunks[ch].tally[o]);
+        for (int o = 0; o < tally_cols(S, A->mode); ++o) kahan(&ts[o], &tc[o], chunks[ch].tally[o]);
         for (int q = 0; q < 8; ++q) kahan(&ls[q], &lc[q], chunks[ch].ledger[q]);
         steps += chunks[ch].steps;
         /* contributions in packet order: the sums do not depend on the thread count */
@@ -957,7 +1028,7 @@ int orc_run(const orc_grid *G, const orc_cells *C, const orc_source *S, orc_run_
         cf_oom |= chunks[ch].cf_oom;
         free(chunks[ch].cf);
     }
-    for (int o = 0; o < S->n_obs; ++o) A->tally[o] = ts[o];
+    for (int o = 0; o < tally_cols(S, A->mode); ++o) A->tally[o] = ts[o];
     if (A->ledger) for (int q = 0; q < 8; ++q) A->ledger[q] = ls[q];
     if (A->steps) A->steps[0] = steps;
     free(chunks);

@@ -54,7 +54,9 @@ class Source_c(C.Structure):
                 ("w_rr", C.c_double), ("p_surv", C.c_double), ("tau_peel_cut", C.c_double),
                 ("tau_vert_max", C.c_double), ("beta_emis", C.c_double), ("hg_iso_eps", C.c_double),
                 ("scatter_emission", C.c_int32), ("pad", C.c_int32), ("max_steps", C.c_int64),
-                ("cloud_phase", C.c_int32), ("pad2", C.c_int32), ("surface_albedo", C.c_double)]
+                ("cloud_phase", C.c_int32), ("pad2", C.c_int32), ("surface_albedo", C.c_double),
+                ("trans_scatter", C.c_int32), ("ld_law", C.c_int32), ("ld_coef", C.c_double * 4),
+                ("star_radius", C.c_double), ("star_dist", C.c_double), ("transit_xy", C.c_double * 2)]
 
 
 class Run_c(C.Structure):
@@ -90,6 +92,8 @@ def lib():
             _lib.orc_theta_kind.restype = D
             _lib.orc_sample_cloud.argtypes = [D, D, D, D, C.c_int]
             _lib.orc_sample_cloud.restype = D
+            _lib.orc_limb.argtypes = [C.c_int, P(D), D]
+            _lib.orc_limb.restype = D
             _lib.orc_planck.argtypes = [D, D]
             _lib.orc_planck.restype = D
             _lib.orc_turn.argtypes = [P(D), D, D, P(D)]
@@ -167,6 +171,11 @@ def sample_cloud(g, zc, z, kind, eps=1e-4):
     return lib().orc_sample_cloud(float(g), float(zc), float(z), float(eps), int(kind))
 
 
+def limb(law, coef, mu):
+    c = (C.c_double * 4)(*[float(v) for v in (list(coef) + [0.0] * 4)[:4]])
+    return lib().orc_limb(int(law), c, float(mu))
+
+
 def planck(lam, T):
     return lib().orc_planck(float(lam), float(T))
 
@@ -241,6 +250,9 @@ def prep_cells(wl, job):
         return prep_albedo(wl.grid, wl.opac, job.lam_idx)
     if wl.mode == 1:
         return prep_emission(wl.grid, wl.opac, job.lam_idx, job.g_idx, wl.source.opts)
+    if hasattr(wl.opac, "kray"):
+        # transmission through scattering opacities (gas + clouds at the job's wavelength)
+        return prep_albedo(wl.grid, wl.opac, job.lam_idx)
     return prep_xsec(wl.grid, wl.opac, job.lam_idx)
 
 
@@ -265,7 +277,23 @@ def _source_struct(src, obs):
     s.max_steps = int(op.max_steps)
     s.cloud_phase = int(getattr(op, "cloud_phase", 0))
     s.surface_albedo = float(getattr(op, "surface_albedo", 0.0))
+    s.trans_scatter = int(getattr(op, "trans_scatter", 0))
+    s.ld_law = int(getattr(op, "ld_law", 0))
+    for i, v in enumerate((list(getattr(op, "ld_coef", ())) + [0.0] * 4)[:4]):
+        s.ld_coef[i] = float(v)
+    s.star_radius = float(getattr(op, "star_radius", 0.0))
+    s.star_dist = float(getattr(op, "star_dist", 0.0))
+    for i, v in enumerate(getattr(op, "transit_xy", (0.0, 0.0))):
+        s.transit_xy[i] = float(v)
     return s, len(obs)
+
+
+def tally_cols(wl, job):
+    """Tally columns of a job: one per observer (albedo, emission); transmission: the chord column,
+    plus the scattered-light column when packets scatter after their chord."""
+    if wl.mode == 2:
+        return 2 if int(getattr(wl.source.opts, "trans_scatter", 0)) else 1
+    return len(job_observers(wl, job))
 
 
 def job_observers(wl, job):
@@ -288,11 +316,12 @@ def run(wl, job, cells=None, packet0=0, n_run=None, nthreads=1, per_packet=False
                  _dp(keep["wcell"]), float(cells.get("cdf_total", 0.0)), 0.0)
     obs = job_observers(wl, job)
     sc, nobs = _source_struct(wl.source, obs)
+    ncol = tally_cols(wl, job)
     n_run = job.n_packets - packet0 if n_run is None else int(n_run)
-    tally = np.zeros(nobs)
+    tally = np.zeros(ncol)
     ledger = np.zeros(8)
     steps = np.zeros(1, np.int64)
-    pk_f = np.zeros((n_run, nobs)) if per_packet else None
+    pk_f = np.zeros((n_run, ncol)) if per_packet else None
     pk_steps = np.zeros(n_run, np.int64) if per_packet else None
     pk_tau = np.zeros(n_run) if per_packet else None
     n_trace = min(int(n_trace), n_run)
@@ -333,3 +362,32 @@ def postscale(wl, job, tally_sum, n_packets, cells=None):
         return {"L_p": Lp, "I_p": Ip, "F_p": math.pi * Ip}
     Ip = (g.R_toa - g.R0) / n_packets * g.R_toa * np.asarray(tally_sum)
     return {"I_p": Ip, "area_over_pi": g.R0 ** 2 + 2.0 * Ip}
+
+def transit(wl, tally, n_packets):
+    """Transit observables (Sect. 5.1) from a transmission job's tally columns (chord, scattered).
+
+    I_p = (R_TOA - R0)/N R_TOA (T_chord - Omega_star T_scat): the scattered light is the packets' power
+    per steradian towards the observer, relative to the stellar intensity times the solid angle
+    Omega_star of the stellar disk seen from the planet.  With limb darkening the planet's opaque
+    core blocks the intensity at the planet centre, and the depth divides by the disk-averaged
+    intensity 2 int_0^1 mu I(mu)/I(1) dmu."""
+    from scipy import integrate
+    g, op = wl.grid, wl.source.opts
+    k = (g.R_toa - g.R0) / n_packets * g.R_toa
+    t = np.atleast_1d(np.asarray(tally, np.float64))
+    I_dir = k * t[0]
+    I_sca = k * t[1] if len(t) > 1 else 0.0
+    Rs, a = float(getattr(op, "star_radius", 0.0)), float(getattr(op, "star_dist", 0.0))
+    omega_star = 2.0 * math.pi * (1.0 - math.sqrt(1.0 - (Rs / a) ** 2)) if a > Rs > 0 else 0.0
+    I_p = I_dir - omega_star * I_sca
+    law, coef = int(getattr(op, "ld_law", 0)), list(getattr(op, "ld_coef", (0.0,) * 4))
+    if law:
+        q = (op.transit_xy[0] ** 2 + op.transit_xy[1] ** 2) / Rs ** 2
+        w_core = limb(law, coef, math.sqrt(1.0 - q)) if q < 1.0 else 0.0
+        n_ld = integrate.quad(lambda m: 2.0 * m * limb(law, coef, m), 0.0, 1.0, epsabs=1e-13, epsrel=1e-12)[0]
+    else:
+        w_core, n_ld = 1.0, 1.0
+    area = w_core * g.R0 ** 2 + 2.0 * I_p
+    return {"I_p_direct": I_dir, "I_p_scattered": I_sca, "omega_star": omega_star, "I_p": I_p,
+            "w_core": w_core, "n_ld": n_ld, "area_over_pi": area,
+            "depth": area / (Rs ** 2 * n_ld) if Rs > 0 else float("nan")}

@@ -129,6 +129,13 @@ class Options:
     hg_iso_eps: float = 1.0e-4   # |g| below this samples isotropically
     cloud_phase: int = 0         # 0 Henyey-Greenstein clouds, 1 two-term HG (g1 = g, g2 = -g/2, a = 1 - g2^2)
     surface_albedo: float = 0.0  # Lambertian lower boundary (0: black)
+    trans_scatter: int = 0       # transmission on scattering opacities: packets scatter after their chord
+    ld_law: int = 0              # stellar limb darkening: 0 none, 1 linear, 2 quadratic, 3 square-root,
+                                 # 4 logarithmic, 5 power-2, 6 four-coefficient
+    ld_coef: tuple = (0.0, 0.0, 0.0, 0.0)
+    star_radius: float = 0.0     # m
+    star_dist: float = 0.0       # m, planet-star distance
+    transit_xy: tuple = (0.0, 0.0)   # planet centre on the stellar disk along the launch basis (e1, e2), m
 
 
 @dataclasses.dataclass
@@ -517,6 +524,22 @@ def uniform_absorber_sphere(alpha=2.0e-6, R0=R_JUP, H_atm=5.0e6, nlon=4, nlat=4,
     src = Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[-1.0, 0.0, 0.0]]), opts=Options())
     jobs = [Job(lam_idx=0, g_idx=0, n_packets=n_packets, key=0)]
     return Workload("uniform_absorber", MODE_TRANSMISSION, grid, xs, src, jobs, seed)
+
+
+def uniform_scattering_sphere(alpha=8.0e-9, omega=1.0e-3, g=0.5, R0=R_JUP, H_atm=R_JUP, nlon=4, nlat=4, nr=4,
+                              n_packets=20000, seed=14, trans_scatter=1, survival=1, ld_law=0,
+                              ld_coef=(0.0, 0.0, 0.0, 0.0), star_radius=0.0, star_dist=0.0, transit_xy=(0.0, 0.0)):
+    """Transmission through a uniform shell R0..R0+H of extinction alpha, single-scattering albedo omega
+    and HG asymmetry g, all in one cloud component (P_gas = 0): chord tau(b) = 2 alpha sqrt(R_toa^2 - b^2).
+    The default thick shell (R_toa = 2 R0) has chord optical depths up to ~2."""
+    grid = uniform_grid(nlon, nlat, nr, R0, R0 + H_atm, rho=1.0)
+    opac = AlbedoOpacity(kabs=np.array([0.0]), kray=np.array([0.0]), qcld=np.ones(1), wcld=np.array([omega]),
+                         gcld=np.array([g]), acld=np.full(grid.ncell, alpha, np.float32))
+    opts = Options(survival=survival, trans_scatter=trans_scatter, ld_law=ld_law, ld_coef=tuple(ld_coef),
+                   star_radius=star_radius, star_dist=star_dist, transit_xy=tuple(transit_xy))
+    src = Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[-1.0, 0.0, 0.0]]), opts=opts)
+    jobs = [Job(lam_idx=0, g_idx=0, n_packets=n_packets, key=0)]
+    return Workload("uniform_scatterer", MODE_TRANSMISSION, grid, opac, src, jobs, seed)
 
 
 def slab_sphere_albedo(omega=0.5, tau=20.0, phase="iso", g=0.0, n_packets=100_000, seed=12, thin=1.0e-4,

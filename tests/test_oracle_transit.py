@@ -1,0 +1,120 @@
+"""Pins of the oracle's transmission with multiple scattering and stellar limb darkening (Sect. 5.1),
+against closed forms and quadratures written from the geometry, not from the oracle:
+
+* each limb-darkening law equals 1 at the disk centre, and its disk normalisation 2 int mu I dmu
+  equals the law's closed-form integral;
+* on a uniform shell, the chord column is (1/(R_t - R0)) int (b/R_t)(1 - e^-tau(b)) db with
+  tau(b) = 2 alpha sqrt(R_t^2 - b^2); with limb darkening the integrand carries the azimuthal mean of
+  I(mu) over the chord's ring on the stellar disk (central and grazing transits);
+* the scattered column's first order: a packet launched at b scatters first at optical depth t
+  (pdf e^-t) and peels off forwards through the rest of its chord, so
+  E[f b/R_t | b] = omega Theta(0 deg) tau(b) e^-tau(b) (b/R_t), up to terms of order omega^2;
+  HG g = 0.5 makes forward and backward Theta differ 27-fold and the thick shell (R_t = 2 R0) makes
+  b/R_t range over [0.5, 1], so a wrong peel direction or a missing b/R_t fails;
+* the ledger closes under survival biasing and analog scattering;
+* the transit post-scale: no scattering and no limb darkening give R0^2 + 2 I_p."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import oracle as O
+from paper_2110_15640_gb300 import synth as S
+
+LAWS = [
+    (1, [0.6, 0, 0, 0], lambda c: 1 - c[0] / 3),
+    (2, [0.4, 0.25, 0, 0], lambda c: 1 - c[0] / 3 - c[1] / 6),
+    (3, [0.3, 0.35, 0, 0], lambda c: 1 - c[0] / 3 - c[1] / 5),
+    (4, [0.5, 0.2, 0, 0], lambda c: 1 - c[0] / 3 + 2 * c[1] / 9),
+    (5, [0.7, 0.6, 0, 0], lambda c: 1 - c[0] * c[1] / (c[1] + 2)),
+    (6, [0.5, -0.2, 0.4, -0.1], lambda c: 1 - sum(c[k - 1] * k / (k + 4) for k in range(1, 5))),
+]
+
+
+@pytest.mark.parametrize("law,coef,norm", LAWS)
+def test_limb_darkening_laws(law, coef, norm):
+    assert abs(O.limb(law, coef, 1.0) - 1.0) < 1e-15
+    n = integrate.quad(lambda m: 2 * m * O.limb(law, coef, m), 0, 1, epsabs=1e-13, epsrel=1e-12)[0]
+    assert abs(n - norm(coef)) < 1e-9
+    assert O.limb(0, coef, 0.3) == 1.0
+
+
+def _shell(wl):
+    g = wl.grid
+    alpha = float(np.float32(wl.opac.acld[0]))
+    return g.R0, g.R_toa, alpha
+
+
+def _mc(wl, col):
+    r = O.run(wl, wl.jobs[0], per_packet=True, nthreads=8)
+    f = r["pk_f"][:, col]
+    return f.mean(), f.std() / math.sqrt(len(f)), r
+
+
+def test_chord_column_uniform_shell_no_ld():
+    wl = S.uniform_scattering_sphere(omega=0.0, n_packets=400_000)
+    R0, Rt, a = _shell(wl)
+    tau = lambda b: 2 * a * math.sqrt(max(Rt * Rt - b * b, 0.0))  # noqa: E731
+    ref = integrate.quad(lambda b: (b / Rt) * (1 - math.exp(-tau(b))), R0, Rt, epsrel=1e-12)[0] / (Rt - R0)
+    est, sig, r = _mc(wl, 0)
+    assert abs(est - ref) < 3 * sig, (est, ref, sig)
+    assert np.all(r["pk_f"][:, 1] == 0.0)          # omega = 0: no scattered light
+
+
+def _ring_mean_ld(b, law, coef, Rs, tx, ty):
+    def I(psi):
+        X, Y = tx + b * math.cos(psi), ty + b * math.sin(psi)
+        q = (X * X + Y * Y) / (Rs * Rs)
+        return O.limb(law, coef, math.sqrt(1 - q)) if q < 1 else 0.0
+    return integrate.quad(I, 0, 2 * math.pi, epsrel=1e-8, limit=200)[0] / (2 * math.pi)
+
+
+@pytest.mark.parametrize("where", ["central", "grazing"])
+def test_chord_column_with_limb_darkening(where):
+    Rs = 5.0 * S.R_JUP
+    txy = (0.0, 0.0) if where == "central" else (0.3 * Rs, 0.75 * Rs)   # grazing: part of the ring is off the star
+    law, coef = 2, [0.4, 0.25, 0.0, 0.0]
+    wl = S.uniform_scattering_sphere(omega=0.0, n_packets=400_000, ld_law=law, ld_coef=coef, star_radius=Rs,
+                                     transit_xy=txy)
+    R0, Rt, a = _shell(wl)
+    tau = lambda b: 2 * a * math.sqrt(max(Rt * Rt - b * b, 0.0))  # noqa: E731
+    ref = integrate.quad(lambda b: (b / Rt) * (1 - math.exp(-tau(b))) * _ring_mean_ld(b, law, coef, Rs, *txy),
+                         R0, Rt, epsrel=1e-7, limit=200)[0] / (Rt - R0)
+    est, sig, r = _mc(wl, 0)
+    assert abs(est - ref) < 3 * sig, (est, ref, sig)
+    if where == "grazing":
+        assert (r["pk_f"][:, 0] == 0).mean() > 0.01     # chords off the stellar disk carry nothing
+        assert r["ledger"][0] < 0.99 * wl.jobs[0].n_packets
+
+
+def test_scattered_column_first_order():
+    omega, g = 1.0e-3, 0.5
+    wl = S.uniform_scattering_sphere(omega=omega, g=g, n_packets=1_000_000)
+    R0, Rt, a = _shell(wl)
+    theta_fwd = (1 - g * g) / (1 - g) ** 3 / (4 * math.pi)
+    tau = lambda b: 2 * a * math.sqrt(max(Rt * Rt - b * b, 0.0))  # noqa: E731
+    ref = integrate.quad(lambda b: (b / Rt) * omega * theta_fwd * tau(b) * math.exp(-tau(b)), R0, Rt,
+                         epsrel=1e-12)[0] / (Rt - R0)
+    est, sig, r = _mc(wl, 1)
+    # second and higher orders carry another factor omega (survival biasing) times a probability < 1
+    assert abs(est - ref) < 3 * sig + omega * ref, (est, ref, sig)
+    assert abs(est - ref) < 0.01 * ref
+
+
+@pytest.mark.parametrize("survival", [1, 0])
+def test_ledger_closes_transmission_scattering(survival):
+    wl = S.uniform_scattering_sphere(omega=0.8, n_packets=20_000, survival=survival, ld_law=2,
+                                     ld_coef=[0.4, 0.25], star_radius=5 * S.R_JUP, transit_xy=(0.0, 2 * S.R_JUP))
+    L = O.run(wl, wl.jobs[0], nthreads=4)["ledger"]
+    assert L[1] > 0 and L[2] > 0
+    assert abs((L[0] + L[4]) - (L[1] + L[2] + L[3] + L[5] + L[6] + L[7])) <= 1e-12 * L[0]
+
+
+def test_transit_postscale_reduces_to_area():
+    wl = S.uniform_scattering_sphere(omega=0.0, trans_scatter=0, n_packets=1000)
+    r = O.run(wl, wl.jobs[0], nthreads=4)
+    t = O.transit(wl, r["tally"], 1000)
+    ref = O.postscale(wl, wl.jobs[0], r["tally"][0], 1000)
+    assert t["I_p_scattered"] == 0.0 and t["w_core"] == 1.0 and t["n_ld"] == 1.0
+    assert abs(t["area_over_pi"] / ref["area_over_pi"] - 1) < 1e-15
