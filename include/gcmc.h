@@ -9,7 +9,8 @@
  *   GCMC_ALBEDO        scattered starlight with peel-off towards the observer (Sect. 4.6, 5.2)
  *   GCMC_EMISSION      thermal emission from the atmospheric volume (Sect. 4.3, 4.6, 5.3)
  *   GCMC_TRANSMISSION  limb chords through the annulus (Sect. 5.1), with per-cell Doppler-shifted
- *                      high-resolution opacity (Sect. 7)
+ *                      high-resolution opacity (Sect. 7); or on scattering opacities, optionally with
+ *                      multiple scattering after the chord; optional stellar limb darkening
  *
  * Conventions
  *  - Status: every call returns 0 (GCMC_OK) or a negative GCMC_ERR_* code; no exceptions cross
@@ -152,13 +153,37 @@ typedef struct {
                                  with weight A_s mu_o / pi and leaves with cosine sqrt(zeta) about the normal,
                                  weight A_s (survival biasing) or probability A_s (analog).  Albedo mode only:
                                  emission and transmission packets do not fly */
+    /* transmission (Sect. 5.1) */
+    int32_t trans_scatter;    /* 1 = multiple scattering: after its chord (tally column 0) the packet flies from its
+                                 launch point along -star and every scattering peels off towards the transit
+                                 observer -star into column 1, weighted by the launch b / R_TOA.  Needs
+                                 scattering opacities (GCMC_OPAC_ALBEDO); 0 = chords only */
+    int32_t ld_law;           /* stellar limb darkening: GCMC_LD_NONE or a law below; the packet carries
+                                 I(mu)/I(disk centre), mu the stellar zenith-angle cosine behind its chord */
+    double ld_coef[4];        /* linear u; quadratic c1 c2; square-root c d; logarithmic e f (mu ln mu term);
+                                 power-2 c alpha (1 - c (1 - mu^alpha)); four-coefficient a1..a4 */
+    double star_radius;       /* m, > 0 when ld_law is set */
+    double star_dist;         /* m, planet-star distance: the solid angle of the stellar disk for the scattered
+                                 light (gcmc_transit); 0 when unused */
+    double transit_xy[2];     /* sky-plane position of the planet centre relative to the stellar disk centre, m,
+                                 along the launch basis e1 = star x z / |star x z| (star x x when |star_z| >= 0.9),
+                                 e2 = star x e1: a chord launched at (b, psi) sits at transit_xy + b (cos psi, sin psi) */
 } gcmc_source_desc;
+
+#define GCMC_LD_NONE 0
+#define GCMC_LD_LINEAR 1
+#define GCMC_LD_QUADRATIC 2
+#define GCMC_LD_SQRT 3
+#define GCMC_LD_LOG 4
+#define GCMC_LD_POWER2 5
+#define GCMC_LD_CLARET4 6
 
 #define GCMC_CLOUD_HG 0
 #define GCMC_CLOUD_TTHG 1
 
 /* Register a source description; *source_id receives its id.  Errors: GCMC_ERR_ARG (not unit vectors,
-   options out of range, unknown cloud_phase, surface_albedo outside [0, 1]). */
+   options out of range, unknown cloud_phase, surface_albedo outside [0, 1], unknown ld_law, limb
+   darkening without a stellar radius, star_dist neither 0 nor above star_radius). */
 gcmc_status gcmc_set_source(gcmc_ctx *ctx, int grid_id, const gcmc_source_desc *desc, int *source_id);
 
 /* ---------------------------------------------------------------- running packets */
@@ -184,7 +209,8 @@ typedef struct {
 } gcmc_job;
 
 /* Plain form: one job, one cell-table preparation and one transport launch (one thread per packet).
-   tallies_out: [n_obs] sums over packets of f (the host divides by N, see gcmc_postscale), in
+   tallies_out: one column per observer (albedo, emission); transmission: the chord column, plus the
+   scattered-light column when the source sets trans_scatter; sums over packets of f (the host divides by N, see gcmc_postscale), in
    host or device memory per tallies_memory.  stats_out may be NULL.  Synchronises the stream
    when tallies_memory is GCMC_MEM_HOST or stats_out is not NULL. */
 gcmc_status gcmc_run_packets(gcmc_ctx *ctx, const gcmc_job *job, double *tallies_out, int tallies_memory,
@@ -238,7 +264,8 @@ gcmc_status gcmc_submit(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, const g
 gcmc_status gcmc_poll(gcmc_ctx *ctx, uint64_t ticket, double *tallies_out, gcmc_stats *stats_out);
 
 /* Parity/debug form of gcmc_run_packets: runs packets [packet0, packet0 + n_run) of `job` and
-   writes per-packet results to HOST arrays: pk_f [n_run][n_obs] (f per observer), pk_steps
+   writes per-packet results to HOST arrays: pk_f [n_run][columns] (f per tally column, as in
+   gcmc_run_packets), pk_steps
    [n_run], pk_tau [n_run] (optical depth of the packet's first peel-off or chord march), and for
    the first n_trace packets the segment list: tr_cell [n_trace][max_trace] (flat cell index, or
    -1 before a flight, -2 before a peel-off, -3 before a chord), tr_len, tr_n [n_trace].
@@ -265,6 +292,24 @@ typedef struct {
     double F_p;               /* emission: pi I_p */
     double area;              /* transmission: R0^2 + 2 <I_p>  (= (R_p/R_star)^2 R_star^2) */
 } gcmc_observables;
+
+typedef struct {
+    double I_p_direct;        /* (R_TOA - R0)/N R_TOA tally[0]: the chords, weighted by limb darkening */
+    double I_p_scattered;     /* (R_TOA - R0)/N R_TOA tally[1]: scattered light, per steradian */
+    double omega_star;        /* solid angle of the stellar disk seen from the planet, 2 pi (1 - sqrt(1 - (R_star / d)^2)) */
+    double I_p;               /* I_p_direct - omega_star I_p_scattered */
+    double w_core;            /* limb-darkening factor at the planet centre (blocked by the opaque core), 1 without */
+    double n_ld;              /* disk-averaged I(mu)/I(centre): 2 int_0^1 mu I(mu) dmu / I(1), 1 without */
+    double area;              /* w_core R0^2 + 2 I_p */
+    double depth;             /* area / (R_star^2 n_ld), the transit depth (0 when star_radius is 0) */
+} gcmc_transit_obs;
+
+/* Transit observables (Sect. 5.1) of one transmission job from its tally columns: tally[0] the chords,
+   tally[1] the scattered light (read only when the source sets trans_scatter).  The scattered power per
+   steradian counts against the blocked area through omega_star, which needs star_radius and star_dist
+   (otherwise omega_star = 0).  Errors: GCMC_ERR_ARG (bad ids, n_packets <= 0, NULL pointers). */
+gcmc_status gcmc_transit(gcmc_ctx *ctx, int grid_id, int source_id, const double *tally, int64_t n_packets,
+                         gcmc_transit_obs *out);
 
 /* Observables of one job from its tally sum over N packets (l_tot from the job's stats for emission). */
 gcmc_status gcmc_postscale(gcmc_ctx *ctx, int grid_id, int mode, double tally, int64_t n_packets, double l_tot,

@@ -214,12 +214,17 @@ gcmc_status check_job(gcmc_ctx *ctx, const gcmc_job &j)
     if (o.grid != j.grid_id) return fail(ctx, GCMC_ERR_ARG, "opacity released or belongs to another grid");
     if (j.mode < 0 || j.mode > 2) return fail(ctx, GCMC_ERR_ARG, "bad mode");
     const int want = j.mode == GCMC_ALBEDO ? GCMC_OPAC_ALBEDO : j.mode == GCMC_EMISSION ? GCMC_OPAC_KTABLE : GCMC_OPAC_XSEC;
-    if (o.kind != want) return fail(ctx, GCMC_ERR_ARG, "opacity kind does not match the mode");
+    // transmission runs on cross-sections (chords) or on scattering opacities (chords, optionally
+    // followed by multiple scattering)
+    const bool kind_ok = o.kind == want || (j.mode == GCMC_TRANSMISSION && o.kind == GCMC_OPAC_ALBEDO);
+    if (!kind_ok) return fail(ctx, GCMC_ERR_ARG, "opacity kind does not match the mode");
     if (j.n_packets < 0) return fail(ctx, GCMC_ERR_ARG, "negative n_packets");
     const gcmc_source_desc &s = ctx->sources[j.source_id];
     if (j.obs_idx >= s.n_obs) return fail(ctx, GCMC_ERR_ARG, "obs_idx out of range");
     if (j.mode == GCMC_EMISSION && s.scatter_emission)
         return fail(ctx, GCMC_ERR_ARG, "scattering after emission needs scattering opacities (not in k-tables)");
+    if (j.mode == GCMC_TRANSMISSION && s.trans_scatter && o.kind != GCMC_OPAC_ALBEDO)
+        return fail(ctx, GCMC_ERR_ARG, "multiple scattering in transmission needs scattering opacities");
     if (o.kind == GCMC_OPAC_ALBEDO || o.kind == GCMC_OPAC_XSEC) {
         if (j.lam_idx < 0 || j.lam_idx >= o.nlam) return fail(ctx, GCMC_ERR_ARG, "lam_idx out of range");
     } else if (j.lam_idx < 0 || j.lam_idx >= o.kt.nb || j.g_idx < 0 || j.g_idx >= o.kt.ng) {
@@ -270,7 +275,7 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
         const int64_t ncell = ctx->grids[j.grid_id].dg.ncell;
         const size_t esz = prec == GCMC_FP64 ? 8 : 4;
         P.off_rec[q] = ws;
-        ws += align256((size_t)ncell * (j.mode == GCMC_ALBEDO ? 4 * esz : esz));
+        ws += align256((size_t)ncell * (ctx->opacs[j.opac_id].kind == GCMC_OPAC_ALBEDO ? 4 * esz : esz));
         if (j.mode == GCMC_EMISSION) {
             const int64_t nblk = std::max<int64_t>((ncell + EMIS_SCAN_BLOCK - 1) / EMIS_SCAN_BLOCK,
                                                    emis_col_blocks(ctx->grids[j.grid_id].dg));
@@ -328,7 +333,8 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
         DevJob &d = P.jobs[q];
         std::memset(&d, 0, sizeof(d));
         d.mode = j.mode;
-        if (j.mode == GCMC_ALBEDO) P.scatter = true;
+        d.rec4 = ctx->opacs[j.opac_id].kind == GCMC_OPAC_ALBEDO;
+        if (d.rec4) P.scatter = true;
         d.grid_slot = j.grid_id;
         d.survival = s.survival;
         d.precision = s.precision == GCMC_FP64 ? GCMC_FP64 : GCMC_FP32;
@@ -346,6 +352,22 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
             for (int o = 0; o < d.n_obs; ++o)
                 for (int a = 0; a < 3; ++a) d.obs[o][a] = s.obs[o][a];
         }
+        if (j.mode == GCMC_TRANSMISSION) {
+            // the transit observer looks along the chords, -star
+            d.n_obs = 1;
+            for (int a = 0; a < 3; ++a) d.obs[0][a] = -s.star[a];
+            d.trans_scatter = s.trans_scatter ? 1 : 0;
+            d.ld_law = s.ld_law;
+            for (int c = 0; c < 4; ++c) d.ld_c[c] = s.ld_coef[c];
+            d.star_r = s.star_radius;
+            d.tr_x = s.transit_xy[0];
+            d.tr_y = s.transit_xy[1];
+        }
+        d.n_tal = j.mode == GCMC_TRANSMISSION ? 1 + d.trans_scatter : d.n_obs;
+        for (int c = 0; c < 4; ++c) d.ld_c_f[c] = (float)d.ld_c[c];
+        d.star_r_f = (float)d.star_r;
+        d.tr_x_f = (float)d.tr_x;
+        d.tr_y_f = (float)d.tr_y;
         d.w_rr = s.w_rr;
         d.p_surv = s.p_surv;
         d.tau_cut = s.tau_peel_cut;
@@ -445,9 +467,9 @@ gcmc_status stage(gcmc_ctx *ctx, Plan &P, char *base, double *lum = nullptr, cha
         const GridH &gh = ctx->grids[G.grid];
         const OpacH &oh = ctx->opacs[G.opac];
         cudaError_t e;
-        if (G.mode == GCMC_ALBEDO) {
+        if (oh.kind == GCMC_OPAC_ALBEDO) {
             e = prep_albedo(G.precision, ctx->d_grids + G.grid, gh.dg, oh.alb, gp, m, ctx->stream);
-        } else if (G.mode == GCMC_EMISSION) {
+        } else if (oh.kind == GCMC_OPAC_KTABLE) {
             const gcmc_source_desc &s = ctx->sources[G.source];
             e = prep_emission(G.precision, gh.dg, oh.kt, gp, m, s.tau_vert_max, s.beta_emis, ctx->stream);
         } else {
@@ -570,11 +592,11 @@ gcmc_status finish_run(gcmc_ctx *ctx, Plan &P, char *base, double *tallies_out, 
     CK(cudaStreamSynchronize(ctx->stream));
     for (int q = 0; q < n; ++q) {
         double t[MAX_OBS];
-        unpack(ctx->h_acc + (size_t)q * ACC_SLOTS, ctx->h_info + 4 * q, P.jobs[q].n_obs, t,
+        unpack(ctx->h_acc + (size_t)q * ACC_SLOTS, ctx->h_info + 4 * q, P.jobs[q].n_tal, t,
                stats ? stats + (stats_stride_jobs ? q : 0) : nullptr);
         if (tallies_out && tallies_memory == GCMC_MEM_HOST) {
             if (stats_stride_jobs) std::memcpy(tallies_out + (size_t)q * MAX_OBS, t, sizeof(t));
-            else std::memcpy(tallies_out, t, sizeof(double) * P.jobs[q].n_obs);
+            else std::memcpy(tallies_out, t, sizeof(double) * P.jobs[q].n_tal);
         }
     }
     return GCMC_OK;
@@ -971,6 +993,13 @@ gcmc_status gcmc_set_source(gcmc_ctx *ctx, int grid_id, const gcmc_source_desc *
         return fail(ctx, GCMC_ERR_ARG, "unknown cloud_phase");
     if (!(d->surface_albedo >= 0.0 && d->surface_albedo <= 1.0))
         return fail(ctx, GCMC_ERR_ARG, "surface_albedo must be in [0, 1]");
+    if (d->ld_law < GCMC_LD_NONE || d->ld_law > GCMC_LD_CLARET4) return fail(ctx, GCMC_ERR_ARG, "unknown ld_law");
+    if (d->ld_law != GCMC_LD_NONE && !(d->star_radius > 0.0))
+        return fail(ctx, GCMC_ERR_ARG, "limb darkening needs star_radius > 0");
+    if (!(d->star_dist == 0.0 || d->star_dist > d->star_radius))
+        return fail(ctx, GCMC_ERR_ARG, "star_dist must be 0 or above star_radius");
+    for (int c = 0; c < 4; ++c)
+        if (!std::isfinite(d->ld_coef[c])) return fail(ctx, GCMC_ERR_ARG, "limb-darkening coefficients must be finite");
     *source_id = (int)ctx->sources.size();
     ctx->sources.push_back(*d);
     return GCMC_OK;
@@ -1137,7 +1166,7 @@ gcmc_status gcmc_run_packets_debug(gcmc_ctx *ctx, const gcmc_job *job, int64_t p
     if ((s = ensure_arena(ctx, P.ws_bytes))) return s;
     char *base = (char *)ctx->arena;
     if ((s = stage(ctx, P, base))) return s;
-    const int nobs = P.jobs[0].n_obs;
+    const int nobs = P.jobs[0].n_tal;
     HostLog hl{};
     std::vector<void *> tmp;
     cudaError_t e = cudaSuccess;
@@ -1206,7 +1235,7 @@ gcmc_status gcmc_prep_cells(gcmc_ctx *ctx, const gcmc_job *job, double *alpha, d
     }
     const bool f64 = P.jobs[0].precision == GCMC_FP64;
     const size_t esz = f64 ? 8 : 4;
-    const int nrec = job->mode == GCMC_ALBEDO ? 4 : 1;
+    const int nrec = P.jobs[0].rec4 ? 4 : 1;
     std::vector<char> raw(ncell * nrec * esz);
     CK(cudaMemcpyAsync(raw.data(), base + P.off_rec[0], raw.size(), cudaMemcpyDeviceToHost, ctx->stream));
     std::vector<long long> cq;
@@ -1268,6 +1297,91 @@ gcmc_status gcmc_postscale(gcmc_ctx *ctx, int grid_id, int mode, double tally, i
     } else {
         return fail(ctx, GCMC_ERR_ARG, "bad mode");
     }
+    return GCMC_OK;
+}
+
+// stellar limb darkening I(mu)/I(disk centre) of the laws of gcmc_source_desc, before clipping at 0
+static double limb_raw(int law, const double *c, double mu)
+{
+    const double x = 1.0 - mu;
+    double I = 1.0;
+    switch (law) {
+    case GCMC_LD_LINEAR: I = 1.0 - c[0] * x; break;
+    case GCMC_LD_QUADRATIC: I = 1.0 - c[0] * x - c[1] * x * x; break;
+    case GCMC_LD_SQRT: I = 1.0 - c[0] * x - c[1] * (1.0 - std::sqrt(mu)); break;
+    case GCMC_LD_LOG: I = 1.0 - c[0] * x - c[1] * (mu > 0.0 ? mu * std::log(mu) : 0.0); break;
+    case GCMC_LD_POWER2: I = 1.0 - c[0] * (1.0 - std::pow(mu, c[1])); break;
+    case GCMC_LD_CLARET4:
+        for (int k = 1; k <= 4; ++k) I -= c[k - 1] * (1.0 - std::pow(mu, 0.5 * k));
+        break;
+    default: break;
+    }
+    return I;
+}
+
+// the law as packets use it: negative values (bad coefficients) count as 0
+static double limb_host(int law, const double *c, double mu)
+{
+    const double I = limb_raw(law, c, mu);
+    return I > 0.0 ? I : 0.0;
+}
+
+// disk average 2 int_0^1 mu I(mu) dmu of a law, in closed form where the law stays non-negative
+// (Gauss-Legendre on [0, 1] in sqrt(mu) otherwise, where clipping at 0 makes the integrand kinked)
+static double limb_norm(int law, const double *c)
+{
+    bool nonneg = true;
+    for (int t = 0; t <= 1000 && nonneg; ++t) nonneg = limb_raw(law, c, t / 1000.0) >= 0.0;
+    if (nonneg) {
+        switch (law) {
+        case GCMC_LD_LINEAR: return 1.0 - c[0] / 3.0;
+        case GCMC_LD_QUADRATIC: return 1.0 - c[0] / 3.0 - c[1] / 6.0;
+        case GCMC_LD_SQRT: return 1.0 - c[0] / 3.0 - c[1] / 5.0;
+        case GCMC_LD_LOG: return 1.0 - c[0] / 3.0 + 2.0 * c[1] / 9.0;
+        case GCMC_LD_POWER2: return 1.0 - c[0] * c[1] / (c[1] + 2.0);
+        case GCMC_LD_CLARET4: {
+            double n = 1.0;
+            for (int k = 1; k <= 4; ++k) n -= c[k - 1] * k / (k + 4.0);
+            return n;
+        }
+        default: return 1.0;
+        }
+    }
+    // composite midpoint rule in t = sqrt(mu): 2 int mu I dmu = 4 int t^3 I(t^2) dt
+    const int n = 200000;
+    double sum = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double t = (i + 0.5) / n;
+        sum += 4.0 * t * t * t * limb_host(law, c, t * t);
+    }
+    return sum / n;
+}
+
+gcmc_status gcmc_transit(gcmc_ctx *ctx, int grid_id, int source_id, const double *tally, int64_t n_packets,
+                         gcmc_transit_obs *out)
+{
+    if (!ctx || !tally || !out) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    if (grid_id < 0 || grid_id >= (int)ctx->grids.size()) return fail(ctx, GCMC_ERR_ARG, "bad grid_id");
+    if (source_id < 0 || source_id >= (int)ctx->sources.size()) return fail(ctx, GCMC_ERR_ARG, "bad source_id");
+    if (n_packets <= 0) return fail(ctx, GCMC_ERR_ARG, "n_packets must be positive");
+    std::memset(out, 0, sizeof(*out));
+    const gcmc_source_desc &s = ctx->sources[source_id];
+    const double R0 = ctx->grids[grid_id].dg.R0, Rt = ctx->grids[grid_id].dg.Rtoa;
+    const double k = (Rt - R0) / (double)n_packets * Rt;
+    out->I_p_direct = k * tally[0];
+    out->I_p_scattered = s.trans_scatter ? k * tally[1] : 0.0;
+    const double Rs = s.star_radius, a = s.star_dist;
+    out->omega_star = (a > Rs && Rs > 0.0) ? 2.0 * PI * (1.0 - std::sqrt(1.0 - (Rs / a) * (Rs / a))) : 0.0;
+    out->I_p = out->I_p_direct - out->omega_star * out->I_p_scattered;
+    out->w_core = 1.0;
+    out->n_ld = 1.0;
+    if (s.ld_law != GCMC_LD_NONE) {
+        const double q = (s.transit_xy[0] * s.transit_xy[0] + s.transit_xy[1] * s.transit_xy[1]) / (Rs * Rs);
+        out->w_core = q < 1.0 ? limb_host(s.ld_law, s.ld_coef, std::sqrt(1.0 - q)) : 0.0;
+        out->n_ld = limb_norm(s.ld_law, s.ld_coef);
+    }
+    out->area = out->w_core * R0 * R0 + 2.0 * out->I_p;
+    out->depth = Rs > 0.0 ? out->area / (Rs * Rs * out->n_ld) : 0.0;
     return GCMC_OK;
 }
 
@@ -1506,7 +1620,7 @@ gcmc_status server_admit(gcmc_server *sv)
         j.bytes = P.ws_bytes;
         j.slot = slot;
         sv->free_slots.pop_back();
-        j.n_obs = P.jobs[0].n_obs;
+        j.n_obs = P.jobs[0].n_tal;
         j.n_items = (j.job.n_packets + sv->cfg.chunk - 1) / sv->cfg.chunk;
         j.djob = reinterpret_cast<const DevJob *>((char *)ws + P.off_jobs);
         j.gen = (++sv->next_gen) & 0xFFFFFFu;

@@ -67,7 +67,11 @@ struct __align__(16) Rec64 {
 struct DevJob {
     int32_t mode, n_obs, grid_slot, survival;
     int32_t precision, cloud_phase;   // cloud_phase: GCMC_CLOUD_HG or GCMC_CLOUD_TTHG
-    uint32_t key, pad1;
+    uint32_t key;
+    int32_t n_tal;              // tally columns: n_obs; transmission: 1, or 2 with multiple scattering
+    int32_t rec4;               // cell records are (alpha, omega, g, P_gas) (scattering opacities), else alpha
+    int32_t trans_scatter;      // transmission: packets scatter after their chord (column 1)
+    int32_t ld_law, pad3;       // stellar limb-darkening law (GCMC_LD_*)
     uint64_t seed;
     int64_t n_packets;
     int64_t chunk_begin;        // first work item of this job (batched launches)
@@ -81,10 +85,12 @@ struct DevJob {
     double obs[MAX_OBS][3];
     double w_rr, p_surv, tau_cut, hg_eps;
     double surf_as;             // Lambertian surface albedo (0: black lower boundary)
+    double ld_c[4], star_r, tr_x, tr_y;   // limb-darkening coefficients, stellar radius, planet offset on the disk
     // the same vectors and constants rounded once to FP32, for FP32 marches
     float star_f[3], e1_f[3], e2_f[3];
     float obs_f[MAX_OBS][3];
     float w_rr_f, p_surv_f, hg_eps_f, surf_as_f;
+    float ld_c_f[4], star_r_f, tr_x_f, tr_y_f, pad4;
     unsigned long long *acc;    // [ACC_SLOTS]
     // contribution functions (Sect. 6), or NULL: [2][n_obs][cf_ncell] fixed-point sums of the peel-off
     // contributions by the cell they leave from, [0] thermal (emission launch), [1] scattered
@@ -103,6 +109,10 @@ template <> struct JV<double> {
     static __device__ __forceinline__ double p_surv(const DevJob &J) { return J.p_surv; }
     static __device__ __forceinline__ double hg_eps(const DevJob &J) { return J.hg_eps; }
     static __device__ __forceinline__ double surf_as(const DevJob &J) { return J.surf_as; }
+    static __device__ __forceinline__ double ld_c(const DevJob &J, int q) { return J.ld_c[q]; }
+    static __device__ __forceinline__ double star_r(const DevJob &J) { return J.star_r; }
+    static __device__ __forceinline__ double tr_x(const DevJob &J) { return J.tr_x; }
+    static __device__ __forceinline__ double tr_y(const DevJob &J) { return J.tr_y; }
 };
 template <> struct JV<float> {
     static __device__ __forceinline__ float star(const DevJob &J, int q) { return J.star_f[q]; }
@@ -113,6 +123,10 @@ template <> struct JV<float> {
     static __device__ __forceinline__ float p_surv(const DevJob &J) { return J.p_surv_f; }
     static __device__ __forceinline__ float hg_eps(const DevJob &J) { return J.hg_eps_f; }
     static __device__ __forceinline__ float surf_as(const DevJob &J) { return J.surf_as_f; }
+    static __device__ __forceinline__ float ld_c(const DevJob &J, int q) { return J.ld_c_f[q]; }
+    static __device__ __forceinline__ float star_r(const DevJob &J) { return J.star_r_f; }
+    static __device__ __forceinline__ float tr_x(const DevJob &J) { return J.tr_x_f; }
+    static __device__ __forceinline__ float tr_y(const DevJob &J) { return J.tr_y_f; }
 };
 
 // ------------------------------------------------------------------ Philox4x32-10 (Salmon et al. 2011)

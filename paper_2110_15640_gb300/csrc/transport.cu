@@ -160,6 +160,26 @@ __device__ __forceinline__ int cdf_find(const long long *__restrict__ cb, int nc
     return lo;
 }
 
+// stellar limb darkening (Sect. 5.1): I(mu) / I(disk centre) for the laws GCMC_LD_*, negative values as 0
+template <typename real> __device__ real limb(const DevJob &J, real mu)
+{
+    const real x = (real)1 - mu;
+    const real c0 = JV<real>::ld_c(J, 0), c1 = JV<real>::ld_c(J, 1);
+    real I = (real)1;
+    switch (J.ld_law) {
+    case GCMC_LD_LINEAR: I = (real)1 - c0 * x; break;
+    case GCMC_LD_QUADRATIC: I = (real)1 - c0 * x - c1 * x * x; break;
+    case GCMC_LD_SQRT: I = (real)1 - c0 * x - c1 * ((real)1 - M<real>::sqrt_(mu)); break;
+    case GCMC_LD_LOG: I = (real)1 - c0 * x - c1 * (mu > (real)0 ? mu * log(mu) : (real)0); break;
+    case GCMC_LD_POWER2: I = (real)1 - c0 * ((real)1 - pow(mu, c1)); break;
+    case GCMC_LD_CLARET4:
+        for (int k = 1; k <= 4; ++k) I -= JV<real>::ld_c(J, k - 1) * ((real)1 - pow(mu, (real)(0.5 * k)));
+        break;
+    default: break;
+    }
+    return I > (real)0 ? I : (real)0;
+}
+
 // S2: packet launch (Sect. 5: albedo disk, emission hybrid pdf, transmission annulus)
 template <typename real, bool SCAT, class SinkT>
 __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64_t n, SinkT &S)
@@ -193,6 +213,13 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
         int i, j;
         locate_angles<real>(G, x[0], x[1], x[2], i, j);
         P.W = P.W0 = (real)1;
+        if (J.mode == GCMC_TRANSMISSION && J.ld_law != GCMC_LD_NONE) {
+            // the chord's sky-plane position on the stellar disk gives the stellar zenith-angle cosine
+            const real X = JV<real>::tr_x(J) + b * cp, Y = JV<real>::tr_y(J) + b * sp;
+            const real Rs = JV<real>::star_r(J);
+            const real q = M<real>::div_(X * X + Y * Y, Rs * Rs);
+            P.W = P.W0 = q < (real)1 ? limb<real>(J, M<real>::sqrt_((real)1 - q)) : (real)0;
+        }
         S.ledger(0, P.W0);
         P.ix = x[0];
         P.iy = x[1];
@@ -207,6 +234,10 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
             }
         }
         P.bimp = b / Rt;
+        if (P.W == (real)0) {   // a chord off the stellar disk carries nothing and is not traced
+            finish<real>(P, S);
+            return;
+        }
         S.trace(n, -3, (real)0);
         start_ray<real>(P, x[0], x[1], x[2], d[0], d[1], d[2], i, j, G.nr - 1, K_CHORD, (real)-1);
         return;
@@ -438,7 +469,15 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
             if (P.stage == 2) f = P.W * JV<real>::surf_as(J) * (mu * (real)(1.0 / PI)) * ex;   // Lambert: mu_o / pi
             else f = P.W * P.om * theta_mix<real>(mu, P.pg, P.gg, J.cloud_phase == GCMC_CLOUD_TTHG) * ex;
         }
-        S.tally(P.obs, f, P.n, J.n_obs);
+        int col = P.obs;
+        if constexpr (SCAT) {
+            // transmission: scattered light goes to column 1, weighted by the launch b / R_TOA
+            if (J.mode == GCMC_TRANSMISSION) {
+                col = 1;
+                f = f * P.bimp;
+            }
+        }
+        S.tally(col, f, P.n, J.n_tal);
         if (J.cf && f < (real)1.0e9 && f >= (real)0) {
             // the same fixed-point contribution, by the cell the peel-off left from
             const int kind = (!SCAT || P.stage == 0) ? 0 : 1;
@@ -454,7 +493,7 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
             return;
         }
         if constexpr (SCAT) {
-            if (J.mode == GCMC_ALBEDO) {
+            if (J.mode != GCMC_EMISSION) {
                 if (P.stage == 2) after_peels_surface<real>(P, J, S);
                 else after_peels_scatter<real>(P, J, S);
                 return;
@@ -463,18 +502,27 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
         finish<real>(P, S);
         return;
     }
-    // chord
-    real c;
+    // chord (column 0: W (1 - e^-tau) b / R_TOA)
+    const bool through = e == E_ESCAPE || e == E_CUTOFF || e == E_BOTTOM;
+    real c = (real)0;
     if (e == E_ESCAPE) c = ((real)1 - M<real>::exp_(-R.tau)) * P.bimp;
-    else if (e == E_CUTOFF || e == E_BOTTOM) c = P.bimp;
-    else {
-        c = (real)0;
-        S.ledger(e == E_CAP ? 6 : 7, P.W);
-    }
+    else if (through) c = P.bimp;
     if constexpr (SinkT::is_log) {
         if (S.lg.pk_tau) S.lg.pk_tau[P.n - S.lg.packet0] = (double)R.tau;
     }
-    S.tally(0, c, P.n, J.n_obs);
+    S.tally(0, P.W * c, P.n, J.n_tal);
+    if (!through) {
+        S.ledger(e == E_CAP ? 6 : 7, P.W);
+        finish<real>(P, S);
+        return;
+    }
+    if constexpr (SCAT) {
+        if (J.trans_scatter) {
+            // multiple scattering (Sect. 5.1): the packet itself flies from its launch point along -star
+            start_flight<real>(P, J, S, -JV<real>::star(J, 0), -JV<real>::star(J, 1), -JV<real>::star(J, 2));
+            return;
+        }
+    }
     S.ledger(1, P.W);
     finish<real>(P, S);
 }
@@ -559,7 +607,7 @@ template <typename real> __device__ __forceinline__ JobC<real> job_consts(const 
     c.max_steps = (int)min(J.max_steps, (int64_t)INT_MAX);
     c.tau_cut = (real)J.tau_cut;
     c.rec = reinterpret_cast<const real *>(J.rec);
-    c.rec_stride = J.mode == GCMC_ALBEDO ? 4 : 1;
+    c.rec_stride = J.rec4 ? 4 : 1;
     return c;
 }
 

@@ -47,7 +47,9 @@ class gcmc_source_desc(C.Structure):
                 ("tau_peel_cut", C.c_double), ("tau_vert_max", C.c_double), ("beta_emis", C.c_double),
                 ("hg_iso_eps", C.c_double), ("scatter_emission", C.c_int32), ("precision", C.c_int32),
                 ("max_steps", C.c_int64), ("cloud_phase", C.c_int32), ("pad2", C.c_int32),
-                ("surface_albedo", C.c_double)]
+                ("surface_albedo", C.c_double), ("trans_scatter", C.c_int32), ("ld_law", C.c_int32),
+                ("ld_coef", C.c_double * 4), ("star_radius", C.c_double), ("star_dist", C.c_double),
+                ("transit_xy", C.c_double * 2)]
 
 
 class gcmc_stats(C.Structure):
@@ -81,6 +83,12 @@ class gcmc_server_stats(C.Structure):
 class gcmc_observables(C.Structure):
     _fields_ = [("S", C.c_double), ("A_g", C.c_double), ("A_g_R0", C.c_double), ("L_p", C.c_double),
                 ("I_p", C.c_double), ("F_p", C.c_double), ("area", C.c_double)]
+
+
+class gcmc_transit_obs(C.Structure):
+    _fields_ = [("I_p_direct", C.c_double), ("I_p_scattered", C.c_double), ("omega_star", C.c_double),
+                ("I_p", C.c_double), ("w_core", C.c_double), ("n_ld", C.c_double), ("area", C.c_double),
+                ("depth", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -121,6 +129,7 @@ def lib():
             "gcmc_prep_cells": ([C.c_void_p, P(gcmc_job)] + [C.c_void_p] * 7 + [P(gcmc_stats)], C.c_int),
             "gcmc_postscale": ([C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int64, C.c_double,
                                 P(gcmc_observables)], C.c_int),
+            "gcmc_transit": ([C.c_void_p, C.c_int, C.c_int, P(C.c_double), C.c_int64, P(gcmc_transit_obs)], C.c_int),
             "gcmc_selftest_philox": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
             "gcmc_version": ([], C.c_char_p),
             "gcmc_release_grid": ([C.c_void_p, C.c_int], C.c_int),
@@ -154,7 +163,8 @@ EXPORTED = ["gcmc_create", "gcmc_destroy", "gcmc_set_stream", "gcmc_set_allocato
             "gcmc_selftest_philox", "gcmc_version", "gcmc_release_grid", "gcmc_release_opacity",
             "gcmc_set_profiling", "gcmc_get_profile", "gcmc_kernel_launches", "gcmc_gather_bench",
             "gcmc_emission_pdf_noalloc", "gcmc_server_create", "gcmc_server_submit", "gcmc_server_progress",
-            "gcmc_server_result", "gcmc_server_query", "gcmc_server_destroy", "gcmc_server_times"]
+            "gcmc_server_result", "gcmc_server_query", "gcmc_server_destroy", "gcmc_server_times",
+            "gcmc_transit"]
 NOALLOC_MAX_CELLS = 4194304
 
 
@@ -311,6 +321,12 @@ class Context:
         d.max_steps = int(op.max_steps)
         d.cloud_phase = int(op.cloud_phase)
         d.surface_albedo = float(op.surface_albedo)
+        d.trans_scatter = int(op.trans_scatter)
+        d.ld_law = int(op.ld_law)
+        for i, v in enumerate((list(op.ld_coef) + [0.0] * 4)[:4]):
+            d.ld_coef[i] = float(v)
+        d.star_radius, d.star_dist = float(op.star_radius), float(op.star_dist)
+        d.transit_xy[0], d.transit_xy[1] = (float(v) for v in op.transit_xy)
         sid = C.c_int()
         self._check(lib().gcmc_set_source(self.h, int(grid_id), C.byref(d), C.byref(sid)), "gcmc_set_source")
         return sid.value
@@ -408,6 +424,14 @@ class Context:
         self._check(lib().gcmc_postscale(self.h, int(grid_id), int(mode), float(tally), int(n_packets), float(l_tot),
                                          C.byref(o)), "gcmc_postscale")
         return {f: getattr(o, f) for f, _ in gcmc_observables._fields_}
+
+    def transit(self, grid_id, source_id, tally, n_packets):
+        """Transit observables of a transmission job from its tally columns (chord, scattered)."""
+        t = (C.c_double * 2)(*[float(v) for v in (list(np.atleast_1d(tally)) + [0.0, 0.0])[:2]])
+        o = gcmc_transit_obs()
+        self._check(lib().gcmc_transit(self.h, int(grid_id), int(source_id), t, int(n_packets), C.byref(o)),
+                    "gcmc_transit")
+        return {f: getattr(o, f) for f, _ in gcmc_transit_obs._fields_}
 
     def release_grid(self, grid_id):
         self._check(lib().gcmc_release_grid(self.h, int(grid_id)), "gcmc_release_grid")
