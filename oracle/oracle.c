@@ -78,6 +78,12 @@ typedef struct {
     const double *wcell;   /* emission: [ncell] launch weight */
     double cdf_total;
     double pad;
+    /* emission with per-packet g-ordinate sampling (Sect. 4.7): alpha, cdf and wcell hold ng tables
+       [g][ncell]; packet g is drawn with probability q(g) and carries W_g = p(g) / q(g) */
+    int32_t ng, pad2;
+    const double *g_qcdf;  /* [ng] cumulative q(g) */
+    const double *g_w;     /* [ng] W_g */
+    const double *g_cdftot;/* [ng] total of each g's cumulative hybrid pdf */
 } orc_cells;
 
 typedef struct {
@@ -776,12 +782,28 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
         /* emission launch: stratified draw over the hybrid pdf */
         /* stratified draw: packet n takes the point (n + z) / N of the cumulative pdf, i.e.
            (n + z) * (cdf_total / N) on the un-normalised cumulative sum */
-        double target = ((double)n + u[0]) * (C->cdf_total / (double)A->n_packets);
         int64_t ncell = (int64_t)G->nlon * G->nlat * G->nr;
+        const double *cdf = C->cdf, *wcell = C->wcell;
+        double Wg = 1.0;
+        double target = ((double)n + u[0]) * (C->cdf_total / (double)A->n_packets);
+        if (C->ng > 0) {
+            /* per-packet g-ordinate (Sect. 4.7): g with probability q(g) from the fourth word of
+               event 1, then the cell from that g's pdf with the launch uniform (no stratification:
+               the packets of one g are a random subset) */
+            double v[4];
+            draw(A->seed, n, 1u, A->job_key, v);
+            int g = 0;
+            while (g < C->ng - 1 && !(C->g_qcdf[g] > v[3])) ++g;
+            cdf = C->cdf + (int64_t)g * ncell;
+            wcell = C->wcell + (int64_t)g * ncell;
+            M.alpha = C->alpha + (int64_t)g * ncell;
+            Wg = C->g_w[g];
+            target = u[0] * C->g_cdftot[g];
+        }
         int64_t lo = 0, hi = ncell - 1;
         while (lo < hi) {
             int64_t mid = (lo + hi) / 2;
-            if (C->cdf[mid] > target) hi = mid; else lo = mid + 1;
+            if (cdf[mid] > target) hi = mid; else lo = mid + 1;
         }
         int64_t idx = lo;
         c[0] = (int)(idx % G->nlon);
@@ -796,7 +818,7 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
         x[0] = r * cl * cos(ph);
         x[1] = r * cl * sin(ph);
         x[2] = r * sl;
-        W = W0 = C->wcell[idx];
+        W = W0 = Wg * wcell[idx];
         kahan(&acc->ledger[0], &acc->ledger_c[0], W0);
         for (int o = 0; o < S->n_obs; ++o) {
             double tau;

@@ -45,7 +45,9 @@ class Cells_c(C.Structure):
     _fields_ = [("alpha", C.POINTER(C.c_double)), ("omega", C.POINTER(C.c_double)),
                 ("g", C.POINTER(C.c_double)), ("pgas", C.POINTER(C.c_double)),
                 ("cdf", C.POINTER(C.c_double)), ("wcell", C.POINTER(C.c_double)),
-                ("cdf_total", C.c_double), ("pad", C.c_double)]
+                ("cdf_total", C.c_double), ("pad", C.c_double),
+                ("ng", C.c_int32), ("pad2", C.c_int32), ("g_qcdf", C.POINTER(C.c_double)),
+                ("g_w", C.POINTER(C.c_double)), ("g_cdftot", C.POINTER(C.c_double))]
 
 
 class Source_c(C.Structure):
@@ -249,11 +251,46 @@ def prep_cells(wl, job):
     if wl.mode == 0:
         return prep_albedo(wl.grid, wl.opac, job.lam_idx)
     if wl.mode == 1:
+        if job.g_idx < 0:
+            return prep_band(wl, job)
         return prep_emission(wl.grid, wl.opac, job.lam_idx, job.g_idx, wl.source.opts)
     if hasattr(wl.opac, "kray"):
         # transmission through scattering opacities (gas + clouds at the job's wavelength)
         return prep_albedo(wl.grid, wl.opac, job.lam_idx)
     return prep_xsec(wl.grid, wl.opac, job.lam_idx)
+
+
+def g_table(wg, L_g, bias=0, beta=0.5):
+    """Per-packet g-ordinate sampling (Sect. 4.7) of an emission band: unbiased p(g) = w_g L_g / sum w L;
+    the sampling pdf q(g) = p(g) (bias 0), 1/N_g (bias 1, uniform) or (1 - beta) p(g) + beta / N_g
+    (bias 2, composite); each packet of ordinate g carries W_g = p(g) / q(g)."""
+    wg = np.asarray(wg, np.float64)
+    L_g = np.asarray(L_g, np.float64)
+    ng = len(wg)
+    wl_ = wg * L_g
+    p = wl_ / wl_.sum()
+    if bias == 0:
+        q = p.copy()
+    elif bias == 1:
+        q = np.full(ng, 1.0 / ng)
+    else:
+        q = (1.0 - beta) * p + beta / ng
+    W = np.where(q > 0, p / np.where(q > 0, q, 1.0), 0.0)
+    return {"p": p, "q": q, "W": W, "qcdf": np.cumsum(q), "L_band": float(wl_.sum())}
+
+
+def prep_band(wl, job):
+    """S1 of an emission band job with per-packet g sampling: every g-ordinate's cell tables and the
+    g table; tables are concatenated [g][ncell]."""
+    op = wl.source.opts
+    ng = len(wl.opac.wg)
+    per = [prep_emission(wl.grid, wl.opac, job.lam_idx, g, op) for g in range(ng)]
+    gt = g_table(wl.opac.wg, [c["L_tot"] for c in per], int(getattr(op, "g_bias", 0)),
+                 float(getattr(op, "g_beta", 0.5)))
+    out = {k: np.concatenate([c[k] for c in per]) for k in ("alpha", "L", "cdf", "wcell")}
+    out.update(per_g=per, gtab=gt, L_tot=gt["L_band"], cdf_total=1.0,
+               cdf_tot_g=np.array([c["cdf_total"] for c in per]))
+    return out
 
 
 # ------------------------------------------------------------------ packets
@@ -312,8 +349,13 @@ def run(wl, job, cells=None, packet0=0, n_run=None, nthreads=1, per_packet=False
         cells = prep_cells(wl, job)
     G = _GridHandle(wl.grid)
     keep = {k: _f64(cells.get(k)) for k in ("alpha", "omega", "g", "pgas", "cdf", "wcell")}
+    gt = cells.get("gtab")
+    if gt is not None:
+        keep.update(qcdf=_f64(gt["qcdf"]), gw=_f64(gt["W"]), gct=_f64(cells["cdf_tot_g"]))
     cc = Cells_c(_dp(keep["alpha"]), _dp(keep["omega"]), _dp(keep["g"]), _dp(keep["pgas"]), _dp(keep["cdf"]),
-                 _dp(keep["wcell"]), float(cells.get("cdf_total", 0.0)), 0.0)
+                 _dp(keep["wcell"]), float(cells.get("cdf_total", 0.0)), 0.0,
+                 len(gt["qcdf"]) if gt is not None else 0, 0, _dp(keep.get("qcdf")), _dp(keep.get("gw")),
+                 _dp(keep.get("gct")))
     obs = job_observers(wl, job)
     sc, nobs = _source_struct(wl.source, obs)
     ncol = tally_cols(wl, job)

@@ -136,6 +136,8 @@ class Options:
     star_radius: float = 0.0     # m
     star_dist: float = 0.0       # m, planet-star distance
     transit_xy: tuple = (0.0, 0.0)   # planet centre on the stellar disk along the launch basis (e1, e2), m
+    g_bias: int = 0              # emission band jobs (per-packet g): 0 q = p, 1 uniform, 2 composite
+    g_beta: float = 0.5          # composite: q = (1 - g_beta) p + g_beta / N_g
 
 
 @dataclasses.dataclass
@@ -281,12 +283,23 @@ def hotjupiter_grid(nlon=128, nlat=64, nr=50, p_top=1e-6, p_bot=100.0, wind=Fals
     return build_grid(nlon, nlat, nr, p_top, p_bot, T3, grav=grav, lat_edges=lat_e, lon_edges=lon_e, wind=W), m
 
 
-def make_ktable(rng, nb=30, ng=8, nT=20, npr=15, lam_lo=1e-6, lam_hi=5e-6, sigma_ln=2.0, aT=1.0, ap=0.3):
+def make_ktable(rng, nb=30, ng=8, nT=20, npr=15, lam_lo=1e-6, lam_hi=5e-6, sigma_ln=2.0, aT=1.0, ap=0.3,
+                split=None):
+    """Synthetic correlated-k table: Gauss-Legendre g-ordinates on [0, 1], or with split = (n1, n2, gs)
+    a split quadrature of n1 points on [0, gs] and n2 on [gs, 1] (e.g. 8 + 8 with gs = 0.9)."""
     from scipy.special import ndtri
     lam = np.geomspace(lam_lo, lam_hi, nb)
-    x, w = np.polynomial.legendre.leggauss(ng)
-    gpts = 0.5 * (x + 1.0)
-    wg = 0.5 * w
+    if split is None:
+        x, w = np.polynomial.legendre.leggauss(ng)
+        gpts = 0.5 * (x + 1.0)
+        wg = 0.5 * w
+    else:
+        n1, n2, gs = split
+        x1, w1 = np.polynomial.legendre.leggauss(n1)
+        x2, w2 = np.polynomial.legendre.leggauss(n2)
+        gpts = np.concatenate([0.5 * gs * (x1 + 1.0), gs + 0.5 * (1.0 - gs) * (x2 + 1.0)])
+        wg = np.concatenate([0.5 * gs * w1, 0.5 * (1.0 - gs) * w2])
+        ng = n1 + n2
     Tg = np.geomspace(500.0, 3000.0, nT)
     pg = np.geomspace(1e-6 * BAR, 100.0 * BAR, npr)
     kmed = 10.0 ** rng.uniform(-5.0, -1.0, nb)
@@ -298,19 +311,25 @@ def make_ktable(rng, nb=30, ng=8, nT=20, npr=15, lam_lo=1e-6, lam_hi=5e-6, sigma
 
 
 def config2_emission(n_packets=1_000_000, seed=2, nlon=128, nlat=64, nr=50, nb=30, ng=8,
-                     bands=None, gpoints=None, obs=None):
+                     bands=None, gpoints=None, obs=None, split=None, per_packet_g=False, g_bias=0, g_beta=0.5):
     """Emission: 128 x 64 x 50 hot-Jupiter grid (1e-6..100 bar), correlated-k 30 bands x 8
-    g-ordinates, scattering off, observer at the substellar direction, 1e6 packets per (band, g)."""
+    g-ordinates, scattering off, observer at the substellar direction, 1e6 packets per (band, g).
+    per_packet_g: one job per band whose packets draw their g-ordinate (g_bias, g_beta; split gives
+    a split quadrature, e.g. (8, 8, 0.9))."""
     rng = np.random.default_rng(seed)
     grid, _ = hotjupiter_grid(nlon, nlat, nr)
-    kt = make_ktable(rng, nb=nb, ng=ng)
+    kt = make_ktable(rng, nb=nb, ng=ng, split=split)
+    ng = len(kt.wg)
     if obs is None:
         obs = np.array([[1.0, 0.0, 0.0]])
     src = Source(star=np.array([1.0, 0.0, 0.0]), obs=np.asarray(obs, np.float64),
-                 opts=Options(scatter_emission=0))
+                 opts=Options(scatter_emission=0, g_bias=g_bias, g_beta=g_beta))
     bands = range(nb) if bands is None else bands
     gpoints = range(ng) if gpoints is None else gpoints
-    jobs = [Job(lam_idx=b, g_idx=g, n_packets=int(n_packets), key=(b << 8) | g) for b in bands for g in gpoints]
+    if per_packet_g:
+        jobs = [Job(lam_idx=b, g_idx=-1, n_packets=int(n_packets), key=(b << 8) | 0xFF) for b in bands]
+    else:
+        jobs = [Job(lam_idx=b, g_idx=g, n_packets=int(n_packets), key=(b << 8) | g) for b in bands for g in gpoints]
     return Workload(f"emission_{nlon}x{nlat}x{nr}_{nb}bx{ng}g", MODE_EMISSION, grid, kt, src, jobs, seed)
 
 
@@ -567,16 +586,20 @@ def slab_sphere_albedo(omega=0.5, tau=20.0, phase="iso", g=0.0, n_packets=100_00
 
 
 def isothermal_emitter(tau=2.0, T=1500.0, thin=1.0e-4, nlon=8, nlat=8, nr=4, n_packets=100_000, seed=13,
-                       lam=2.0e-6):
-    """Isothermal, uniform-kappa shell with scattering off: escaping intensity B (1 - exp(-tau/mu))."""
+                       lam=2.0e-6, taus=None, wg=None, g_bias=0, g_beta=0.5):
+    """Isothermal, uniform-kappa shell with scattering off: escaping intensity B (1 - exp(-tau/mu)).
+    taus, wg: a band of g-ordinates with vertical optical depths taus and weights wg, run as one
+    job with per-packet g sampling."""
     R0 = R_JUP
     H = thin * R0
     grid = uniform_grid(nlon, nlat, nr, R0, R0 + H, rho=1.0, T=T, p=1.0e4)
-    kap = tau / H
-    kt = KTable(lam=np.array([lam]), wg=np.array([1.0]), gpts=np.array([0.5]),
+    taus = np.array([tau]) if taus is None else np.asarray(taus, np.float64)
+    wg = np.array([1.0]) if wg is None else np.asarray(wg, np.float64)
+    kap = taus / H
+    kt = KTable(lam=np.array([lam]), wg=wg, gpts=(np.arange(len(taus)) + 0.5) / len(taus),
                 Tg=np.array([500.0, 3000.0]), pg=np.array([1.0, 1.0e7]),
-                k=np.full((1, 1, 2, 2), kap, np.float32))
+                k=np.broadcast_to(kap[None, :, None, None], (1, len(taus), 2, 2)).astype(np.float32))
     src = Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[1.0, 0.0, 0.0]]),
-                 opts=Options(scatter_emission=0))
-    jobs = [Job(lam_idx=0, g_idx=0, n_packets=n_packets, key=0)]
+                 opts=Options(scatter_emission=0, g_bias=g_bias, g_beta=g_beta))
+    jobs = [Job(lam_idx=0, g_idx=0 if len(taus) == 1 else -1, n_packets=n_packets, key=0)]
     return Workload("isothermal_emitter", MODE_EMISSION, grid, kt, src, jobs, seed)
