@@ -121,6 +121,8 @@ typedef struct {
     double view_theta;        /* observer polar angle (colatitude), rad, for v_LOS (Sect. 7) */
     double view_phi;          /* observer longitude, rad */
     double omega_rot;         /* planetary rotation rate, rad/s */
+    const double *gw;         /* GCMC_OPAC_KTABLE: [ng] g-ordinate weights (sum 1), needed by band jobs
+                                 (g_idx = -1); may be NULL */
 } gcmc_opacity_desc;
 
 /* Copy an opacity description for grid `grid_id` to the device.  *opac_id receives its id.
@@ -168,7 +170,19 @@ typedef struct {
     double transit_xy[2];     /* sky-plane position of the planet centre relative to the stellar disk centre, m,
                                  along the launch basis e1 = star x z / |star x z| (star x x when |star_z| >= 0.9),
                                  e2 = star x e1: a chord launched at (b, psi) sits at transit_xy + b (cos psi, sin psi) */
+    /* emission band jobs (g_idx = -1, Sect. 4.7): each packet draws its g-ordinate with probability q(g)
+       (fourth word of its event-1 draw) and carries W_g = p(g)/q(g), p(g) = w_g L_g / sum_g w_g L_g; its cell
+       then comes from that g's hybrid pdf (launch uniform, no stratification).  stats.l_tot of a band job
+       is L_band = sum_g w_g L_g and stats.n_emit_cells the sum over g. */
+    int32_t g_bias;           /* GCMC_GBIAS_NONE q = p, GCMC_GBIAS_UNIFORM q = 1/N_g,
+                                 GCMC_GBIAS_COMPOSITE q = (1 - g_beta) p + g_beta / N_g */
+    int32_t pad3;
+    double g_beta;            /* composite fraction in [0, 1] */
 } gcmc_source_desc;
+
+#define GCMC_GBIAS_NONE 0
+#define GCMC_GBIAS_UNIFORM 1
+#define GCMC_GBIAS_COMPOSITE 2
 
 #define GCMC_LD_NONE 0
 #define GCMC_LD_LINEAR 1
@@ -201,7 +215,8 @@ typedef struct {
 typedef struct {
     int32_t grid_id, opac_id, source_id, mode;
     int32_t lam_idx;          /* wavelength (albedo, xsec) or band (k-table) index */
-    int32_t g_idx;            /* g-ordinate (k-table); ignored otherwise */
+    int32_t g_idx;            /* g-ordinate (k-table), or -1: a band job whose packets draw their g-ordinate
+                                 (Sect. 4.7, gcmc_source_desc.g_bias); ignored otherwise */
     int32_t obs_idx;          /* -1: tally every observer of the source; else only observer obs_idx */
     uint32_t job_key;         /* 32-bit key of the job in the Philox counter */
     int64_t n_packets;

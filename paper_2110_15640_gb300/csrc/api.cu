@@ -168,6 +168,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Group {
     int grid, opac, mode, precision, source;
     std::vector<int> members;
+    int nprep = 0;                      // cell-table preparations (a band job has one per g-ordinate)
 };
 
 struct Plan {
@@ -177,6 +178,8 @@ struct Plan {
     std::vector<int> job_group;         // group of job q
     std::vector<Group> groups;
     std::vector<size_t> off_rec, off_cdf, off_w, off_info, off_bsum, off_bcnt;
+    std::vector<int> ng_s;              // g-ordinates a band job samples (0: one g-ordinate)
+    std::vector<int64_t> nblk;          // emission scan blocks per preparation
     std::vector<size_t> g_first;
     size_t off_jobs = 0, off_prep = 0, off_acc = 0, off_work = 0, off_gather = 0, ws_bytes = 0;
     int64_t total_items = 0;
@@ -227,8 +230,10 @@ gcmc_status check_job(gcmc_ctx *ctx, const gcmc_job &j)
         return fail(ctx, GCMC_ERR_ARG, "multiple scattering in transmission needs scattering opacities");
     if (o.kind == GCMC_OPAC_ALBEDO || o.kind == GCMC_OPAC_XSEC) {
         if (j.lam_idx < 0 || j.lam_idx >= o.nlam) return fail(ctx, GCMC_ERR_ARG, "lam_idx out of range");
-    } else if (j.lam_idx < 0 || j.lam_idx >= o.kt.nb || j.g_idx < 0 || j.g_idx >= o.kt.ng) {
+    } else if (j.lam_idx < 0 || j.lam_idx >= o.kt.nb || j.g_idx < -1 || j.g_idx >= o.kt.ng) {
         return fail(ctx, GCMC_ERR_ARG, "band / g index out of range");
+    } else if (j.g_idx == -1 && !o.kt.gw) {
+        return fail(ctx, GCMC_ERR_ARG, "a band job (g_idx = -1) needs the k-table's g weights");
     }
     return GCMC_OK;
 }
@@ -250,9 +255,12 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
     P.off_info.assign(n, 0);
     P.off_bsum.assign(n, 0);
     P.off_bcnt.assign(n, 0);
+    P.ng_s.assign(n, 0);
+    P.nblk.assign(n, 0);
     for (int q = 0; q < n; ++q) {
         const gcmc_job &j = jobs[q];
         const gcmc_source_desc &s = ctx->sources[j.source_id];
+        if (j.mode == GCMC_EMISSION && j.g_idx < 0) P.ng_s[q] = ctx->opacs[j.opac_id].kt.ng;
         const int prec = s.precision == GCMC_FP64 ? GCMC_FP64 : GCMC_FP32;
         int gi = -1;
         for (size_t g = 0; g < P.groups.size(); ++g) {
@@ -266,29 +274,34 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
             gi = (int)P.groups.size() - 1;
         }
         P.groups[gi].members.push_back(q);
+        P.groups[gi].nprep += std::max(1, P.ng_s[q]);
         P.job_group[q] = gi;
     }
-    size_t ws = 0;
+    size_t ws = 0, n_prep = 0;
     for (int q = 0; q < n; ++q) {
         const gcmc_job &j = jobs[q];
         const int prec = ctx->sources[j.source_id].precision == GCMC_FP64 ? GCMC_FP64 : GCMC_FP32;
         const int64_t ncell = ctx->grids[j.grid_id].dg.ncell;
         const size_t esz = prec == GCMC_FP64 ? 8 : 4;
+        const int m = std::max(1, P.ng_s[q]);     // tables per job: one per g-ordinate of a band job
+        n_prep += m;
         P.off_rec[q] = ws;
-        ws += align256((size_t)ncell * (ctx->opacs[j.opac_id].kind == GCMC_OPAC_ALBEDO ? 4 * esz : esz));
+        ws += align256((size_t)m * ncell * (ctx->opacs[j.opac_id].kind == GCMC_OPAC_ALBEDO ? 4 * esz : esz));
         if (j.mode == GCMC_EMISSION) {
             const int64_t nblk = std::max<int64_t>((ncell + EMIS_SCAN_BLOCK - 1) / EMIS_SCAN_BLOCK,
                                                    emis_col_blocks(ctx->grids[j.grid_id].dg));
+            P.nblk[q] = nblk;
             P.off_cdf[q] = ws;
-            ws += align256(ncell * 8);
+            ws += align256((size_t)m * ncell * 8);
             P.off_w[q] = ws;
-            ws += align256(ncell * esz);
+            ws += align256((size_t)m * ncell * esz);
             P.off_info[q] = ws;
-            ws += 256;
+            // band job: summary info block, the g table, then one info block per g-ordinate
+            ws += P.ng_s[q] ? 256 + align256((size_t)m * GTAB_ROW * 8) + (size_t)m * GINFO_STRIDE * 8 : 256;
             P.off_bsum[q] = ws;
-            ws += align256(nblk * 8);
+            ws += align256((size_t)m * nblk * 8);
             P.off_bcnt[q] = ws;
-            ws += align256(nblk * 8);
+            ws += align256((size_t)m * nblk * 8);
         }
     }
     const size_t ng = P.groups.size();
@@ -296,7 +309,7 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
     P.off_jobs = ws;
     ws += align256(n * sizeof(DevJob));
     P.off_prep = ws;
-    ws += align256(n * sizeof(PrepJob));
+    ws += align256(n_prep * sizeof(PrepJob));
     P.off_acc = ws;
     ws += align256((size_t)n * ACC_SLOTS * 8);
     P.off_work = ws;
@@ -324,7 +337,15 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
                 pj.lam_m = o.lam[j.lam_idx];
                 xsec_window(o, pj);
             }
-            P.prep.push_back(pj);
+            if (P.ng_s[q]) {
+                // a band job: the tables of every g-ordinate, prepared like ng single jobs
+                for (int gi = 0; gi < P.ng_s[q]; ++gi) {
+                    pj.g = gi;
+                    P.prep.push_back(pj);
+                }
+            } else {
+                P.prep.push_back(pj);
+            }
         }
     }
     for (int q = 0; q < n; ++q) {
@@ -364,6 +385,12 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
             d.tr_y = s.transit_xy[1];
         }
         d.n_tal = j.mode == GCMC_TRANSMISSION ? 1 + d.trans_scatter : d.n_obs;
+        d.ng_s = P.ng_s[q];
+        if (d.ng_s) {
+            d.g_bias = s.g_bias;
+            d.g_beta = s.g_beta;
+            d.gw = ctx->opacs[j.opac_id].kt.gw;
+        }
         for (int c = 0; c < 4; ++c) d.ld_c_f[c] = (float)d.ld_c[c];
         d.star_r_f = (float)d.star_r;
         d.tr_x_f = (float)d.tr_x;
@@ -397,11 +424,44 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
     return GCMC_OK;
 }
 
+// a band job's g-sampling table (Sect. 4.7) from its g-ordinates' luminosities:
+// p(g) = w_g L_g / sum w L, q(g) by the source's bias, W_g = p / q; summary info L_band = sum w L
+__device__ void band_table(DevJob &J)
+{
+    const int ng = J.ng_s;
+    double sum = 0.0, ninc = 0.0;
+    for (int g = 0; g < ng; ++g) {
+        const double *inf = J.ginfo + (size_t)g * GINFO_STRIDE;
+        const double wl = J.gw[g] * inf[INFO_LTOT];
+        J.gtab[g * GTAB_ROW + 2] = wl;
+        sum += wl;
+        ninc += inf[INFO_NINCL];
+    }
+    double cum = 0.0;
+    for (int g = 0; g < ng; ++g) {
+        const double p = sum > 0.0 ? J.gtab[g * GTAB_ROW + 2] / sum : 0.0;
+        const double qg = J.g_bias == GCMC_GBIAS_UNIFORM     ? 1.0 / ng
+                          : J.g_bias == GCMC_GBIAS_COMPOSITE ? (1.0 - J.g_beta) * p + J.g_beta / ng
+                                                              : p;
+        cum += qg;
+        J.gtab[g * GTAB_ROW] = cum;
+        J.gtab[g * GTAB_ROW + 1] = qg > 0.0 ? p / qg : 0.0;
+        reinterpret_cast<long long *>(J.gtab)[g * GTAB_ROW + 3] =
+            reinterpret_cast<const long long *>(J.ginfo + (size_t)g * GINFO_STRIDE)[INFO_QTOT];
+    }
+    double *summary = const_cast<double *>(J.info);   // the band job's own summary block in its workspace
+    summary[INFO_LTOT] = sum;
+    summary[INFO_NINCL] = ninc;
+    summary[INFO_CDFTOT] = cum;
+}
+
 __global__ void k_finalize_jobs(DevJob *jobs, int n)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
-    if (jobs[q].mode == GCMC_EMISSION) {
+    if (jobs[q].mode == GCMC_EMISSION && jobs[q].ng_s > 0) {
+        band_table(jobs[q]);
+    } else if (jobs[q].mode == GCMC_EMISSION) {
         const long long qtot = reinterpret_cast<const long long *>(jobs[q].info)[INFO_QTOT];
         jobs[q].cdf_step_fix = jobs[q].n_packets > 0 ? qtot / jobs[q].n_packets : 0;
     }
@@ -433,25 +493,38 @@ gcmc_status stage(gcmc_ctx *ctx, Plan &P, char *base, double *lum = nullptr, cha
     const int n = (int)P.jobs.size();
     for (int q = 0; q < n; ++q) {
         DevJob &d = P.jobs[q];
-        PrepJob &pj = P.prep[P.prep_pos[q]];
-        pj.rec = base + P.off_rec[q];
-        d.rec = pj.rec;
+        const int m = std::max(1, P.ng_s[q]);
+        const size_t ncell = (size_t)ctx->grids[P.groups[P.job_group[q]].grid].dg.ncell;
+        const size_t esz = d.precision == GCMC_FP64 ? 8 : 4;
         d.acc = reinterpret_cast<unsigned long long *>(base + P.off_acc) + (size_t)q * ACC_SLOTS;
+        for (int gi = 0; gi < m; ++gi) {
+            PrepJob &pj = P.prep[P.prep_pos[q] + gi];
+            pj.rec = base + P.off_rec[q] + gi * ncell * esz;
+            if (d.mode == GCMC_EMISSION) {
+                pj.cdf = reinterpret_cast<long long *>(base + P.off_cdf[q]) + gi * ncell;
+                pj.wcell = base + P.off_w[q] + gi * ncell * esz;
+                pj.info = reinterpret_cast<double *>(base + P.off_info[q]) +
+                          (P.ng_s[q] ? (256 + align256((size_t)m * GTAB_ROW * 8)) / 8 + (size_t)gi * GINFO_STRIDE : 0);
+                pj.bsum = reinterpret_cast<double *>(base + P.off_bsum[q]) + gi * P.nblk[q];
+                pj.bcnt = reinterpret_cast<double *>(base + P.off_bcnt[q]) + gi * P.nblk[q];
+                pj.lum = P.ng_s[q] ? nullptr : lum;
+            }
+        }
+        const PrepJob &p0 = P.prep[P.prep_pos[q]];
+        d.rec = p0.rec;
         if (d.mode == GCMC_EMISSION) {
-            pj.cdf = reinterpret_cast<long long *>(base + P.off_cdf[q]);
-            pj.wcell = base + P.off_w[q];
-            pj.info = reinterpret_cast<double *>(base + P.off_info[q]);
-            pj.bsum = reinterpret_cast<double *>(base + P.off_bsum[q]);
-            pj.bcnt = reinterpret_cast<double *>(base + P.off_bcnt[q]);
-            pj.lum = lum;
-            d.cdf = pj.cdf;
-            d.wcell = pj.wcell;
-            d.info = pj.info;
+            d.cdf = p0.cdf;
+            d.wcell = p0.wcell;
+            d.info = reinterpret_cast<double *>(base + P.off_info[q]);   // a band job's summary block
+            if (P.ng_s[q]) {
+                d.gtab = reinterpret_cast<double *>(base + P.off_info[q] + 256);
+                d.ginfo = p0.info;
+            }
         }
     }
     PrepJob *dprep = reinterpret_cast<PrepJob *>(base + P.off_prep);
     DevJob *djobs = reinterpret_cast<DevJob *>(base + P.off_jobs);
-    const size_t bp = n * sizeof(PrepJob), bj = n * sizeof(DevJob);
+    const size_t bp = P.prep.size() * sizeof(PrepJob), bj = n * sizeof(DevJob);
     cudaEvent_t stg_ev = nullptr;
     char *hs = host_stage ? host_stage : stage_buffer(ctx, bp + bj, &stg_ev);
     if (!hs) return fail(ctx, GCMC_ERR_OOM, "pinned staging");
@@ -463,7 +536,7 @@ gcmc_status stage(gcmc_ctx *ctx, Plan &P, char *base, double *lum = nullptr, cha
     for (size_t g = 0; g < P.groups.size(); ++g) {
         const Group &G = P.groups[g];
         const PrepJob *gp = dprep + P.g_first[g];
-        const int m = (int)G.members.size();
+        const int m = G.nprep;
         const GridH &gh = ctx->grids[G.grid];
         const OpacH &oh = ctx->opacs[G.opac];
         cudaError_t e;
@@ -897,6 +970,18 @@ gcmc_status gcmc_upload_opacity(gcmc_ctx *ctx, int grid_id, const gcmc_opacity_d
                         const double l11 = lnk[sl * nT * np + (size_t)a1 * np + b1];
                         node[i] = make_float4(k[i], (float)(l10 - l00), (float)(l01 - l00), (float)(l11 - l10 - l01 + l00));
                     }
+            O.kt.gw = nullptr;
+            if (d->gw) {
+                std::vector<double> gw;
+                if (!fetch(ctx, d->gw, d->ng, d->memory, gw)) return fail(ctx, GCMC_ERR_ARG, "g weights missing");
+                double sw = 0.0;
+                for (double w : gw) {
+                    if (!(w >= 0.0) || !std::isfinite(w)) return fail(ctx, GCMC_ERR_ARG, "g weights must be >= 0");
+                    sw += w;
+                }
+                if (!(sw > 0.0)) return fail(ctx, GCMC_ERR_ARG, "g weights sum to 0");
+                O.kt.gw = dput(ctx, O.owned, gw.data(), d->ng, e);
+            }
             O.kt.lnk = dput(ctx, O.owned, lnk.data(), nk, e);
             O.kt.node_f = dput(ctx, O.owned, node.data(), nk, e);
             O.kt.Tg = dput(ctx, O.owned, Tg.data(), d->nT, e);
@@ -1000,6 +1085,8 @@ gcmc_status gcmc_set_source(gcmc_ctx *ctx, int grid_id, const gcmc_source_desc *
         return fail(ctx, GCMC_ERR_ARG, "star_dist must be 0 or above star_radius");
     for (int c = 0; c < 4; ++c)
         if (!std::isfinite(d->ld_coef[c])) return fail(ctx, GCMC_ERR_ARG, "limb-darkening coefficients must be finite");
+    if (d->g_bias < GCMC_GBIAS_NONE || d->g_bias > GCMC_GBIAS_COMPOSITE) return fail(ctx, GCMC_ERR_ARG, "unknown g_bias");
+    if (!(d->g_beta >= 0.0 && d->g_beta <= 1.0)) return fail(ctx, GCMC_ERR_ARG, "g_beta must be in [0, 1]");
     *source_id = (int)ctx->sources.size();
     ctx->sources.push_back(*d);
     return GCMC_OK;
@@ -1217,6 +1304,8 @@ gcmc_status gcmc_prep_cells(gcmc_ctx *ctx, const gcmc_job *job, double *alpha, d
                             double *lum, double *cdf, double *wcell, gcmc_stats *stats_out)
 {
     if (!ctx || !job) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    if (job->mode == GCMC_EMISSION && job->g_idx < 0)
+        return fail(ctx, GCMC_ERR_ARG, "cell tables are per g-ordinate: give g_idx >= 0");
     cudaSetDevice(ctx->device);
     Plan P;
     gcmc_status s = plan_run(ctx, job, 1, 128, P);
@@ -1803,6 +1892,8 @@ gcmc_status gcmc_server_submit(gcmc_server *sv, const gcmc_job *job, uint64_t *t
     if (s) return s;
     if (job->n_packets < 1) return fail(ctx, GCMC_ERR_ARG, "a served job needs n_packets >= 1");
     if (ctx->sources[job->source_id].precision == GCMC_FP64) return fail(ctx, GCMC_ERR_ARG, "the server runs FP32 jobs");
+    if (job->mode == GCMC_EMISSION && job->g_idx < 0)
+        return fail(ctx, GCMC_ERR_ARG, "band jobs are not served: submit one job per g-ordinate");
     const DevGrid &g = ctx->grids[job->grid_id].dg;
     if (tab_entries(g.nlon, g.nlat, g.nr) > sv->tab_n)
         return fail(ctx, GCMC_ERR_ARG, "grid larger than every grid present when the server was created");
@@ -1947,7 +2038,8 @@ gcmc_status gcmc_graph_create(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, c
         }
     g->ws = dalloc(ctx, P.ws_bytes);
     g->d_tally = (double *)dalloc(ctx, (size_t)n_jobs * MAX_OBS * sizeof(double));
-    if (!g->ws || !g->d_tally || cudaMallocHost((void **)&g->stage_h, n_jobs * (sizeof(PrepJob) + sizeof(DevJob))) != cudaSuccess) {
+    if (!g->ws || !g->d_tally ||
+        cudaMallocHost((void **)&g->stage_h, P.prep.size() * sizeof(PrepJob) + n_jobs * sizeof(DevJob)) != cudaSuccess) {
         graph_free(g);
         return fail(ctx, GCMC_ERR_OOM, "graph workspace");
     }

@@ -40,6 +40,8 @@ enum {
     F_NONE = face_code(0, 0, 0)
 };
 enum { FLAG_OVERFLOW = 1, FLAG_LOST = 2, FLAG_BAD = 4 };
+constexpr int GINFO_STRIDE = 32;    // doubles between the info blocks of a band job's g-ordinates
+constexpr int GTAB_ROW = 4;         // doubles per g row of a band job's sampling table
 
 struct DevGrid {
     int32_t nlon, nlat, nr, pad;
@@ -72,6 +74,11 @@ struct DevJob {
     int32_t rec4;               // cell records are (alpha, omega, g, P_gas) (scattering opacities), else alpha
     int32_t trans_scatter;      // transmission: packets scatter after their chord (column 1)
     int32_t ld_law, pad3;       // stellar limb-darkening law (GCMC_LD_*)
+    int32_t ng_s, g_bias;       // band job: g-ordinates drawn per packet (0: one g-ordinate); q(g) option
+    double g_beta;              // composite fraction of q(g)
+    const double *gw;           // [ng] g-ordinate weights (band jobs)
+    double *gtab;               // band job: [ng] rows {cumulative q, W_g, w_g L_g, Q_tot(g) as int64 bits}
+    const double *ginfo;        // band job: each g-ordinate's info block, GINFO_STRIDE doubles apart
     uint64_t seed;
     int64_t n_packets;
     int64_t chunk_begin;        // first work item of this job (batched launches)

@@ -59,6 +59,7 @@ struct KtabDev {               // device k-table (natural logs in FP64)
     const double2 *w64;        // [ncell] (wT, wp) in FP64
     const float2 *w32;         // [ncell] the same rounded to FP32
     const double *vb;          // [nb][ncell] 4 pi V_i B_lambda(T_i) at each band centre
+    const double *gw;          // [ng] g-ordinate weights, or NULL (band jobs need them)
 };
 
 struct XsecDev {

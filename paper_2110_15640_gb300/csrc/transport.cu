@@ -31,6 +31,7 @@ template <typename real> struct Packet {
     int cell0;             // flat index of the cell the current peel-off leaves from
     int steps;
     int hint;              // launch cell of this lane's previous packet of the same work item (-1: none)
+    int goff;              // band job: offset of the packet's g-ordinate table (g * ncell), else 0
     int ended, end_e, end_idx;   // the current ray has ended (persistent kernel: processed at the refill point)
     uint32_t ev;
     int64_t n;
@@ -189,6 +190,7 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
     P.alive = 1;
     P.ended = 0;
     P.ev = 2;
+    P.goff = 0;
     if constexpr (SinkT::is_log) {
         if (S.lg.pk_tau) S.lg.pk_tau[n - S.lg.packet0] = -1.0;
         if (S.lg.pk_steps) S.lg.pk_steps[n - S.lg.packet0] = 0;
@@ -245,11 +247,31 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
     // emission: stratified inverse-CDF draw of the cell over the hybrid pdf
     // stratified target (n + u) Q_tot / N in 2^62 fixed point with u = (m + 1/2) 2^-24, m the top 24
     // bits of the word: n step + floor((2m + 1) step / 2^25), exact integer arithmetic (< Q_tot)
-    const unsigned long long step = (unsigned long long)J.cdf_step_fix;
-    const long long target = (long long)((unsigned long long)n * step +
-                                         __umul64hi((unsigned long long)(2u * (w.x >> 8) + 1u) << 39, step));
-    const int idx = cdf_find(J.cdf, (int)G.ncell, target, P.hint);
-    P.hint = idx;
+    const long long *cdf = J.cdf;
+    const real *wcell = reinterpret_cast<const real *>(J.wcell);
+    real Wg = (real)1;
+    int idx;
+    if (J.ng_s > 0) {
+        // band job (Sect. 4.7): g-ordinate with probability q(g) from the fourth word of event 1 (decided in
+        // FP64), then the cell from that g's pdf with the launch uniform, u Q_tot(g) in exact integers
+        const uint4 w1 = draw_words(J.seed, n, 1u, J.key);
+        const double ug = u01<double>(w1.w);
+        int g = 0;
+        while (g < J.ng_s - 1 && !(J.gtab[g * GTAB_ROW] > ug)) ++g;
+        P.goff = g * (int)G.ncell;
+        cdf += P.goff;
+        wcell += P.goff;
+        Wg = (real)J.gtab[g * GTAB_ROW + 1];
+        const unsigned long long qg = (unsigned long long)reinterpret_cast<const long long *>(J.gtab)[g * GTAB_ROW + 3];
+        const long long target = (long long)__umul64hi((unsigned long long)(2u * (w.x >> 8) + 1u) << 39, qg);
+        idx = cdf_find(cdf, (int)G.ncell, target, -1);
+    } else {
+        const unsigned long long step = (unsigned long long)J.cdf_step_fix;
+        const long long target = (long long)((unsigned long long)n * step +
+                                             __umul64hi((unsigned long long)(2u * (w.x >> 8) + 1u) << 39, step));
+        idx = cdf_find(cdf, (int)G.ncell, target, P.hint);
+        P.hint = idx;
+    }
     const int nll = G.nlon * G.nlat;
     const int k = (int)(((uint64_t)idx * G.mag_ll) >> 40);
     const int rem = idx - k * nll;
@@ -287,7 +309,7 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
     P.cj = j;
     P.ck = k;
     P.cell0 = idx;
-    P.W = P.W0 = reinterpret_cast<const real *>(J.wcell)[idx];
+    P.W = P.W0 = Wg * wcell[idx];
     S.ledger(0, P.W0);
     P.stage = 0;
     P.obs = 0;
@@ -542,8 +564,8 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
     ++P.steps;
     const int idx = (R.k * T.nlat + R.j) * T.nlon + R.i;
     real a;
-    if constexpr (SCAT) a = __ldg(jc.rec + jc.rec_stride * idx);
-    else a = __ldg(jc.rec + idx);
+    if constexpr (SCAT) a = __ldg(jc.rec + jc.rec_stride * idx + P.goff);
+    else a = __ldg(jc.rec + idx + P.goff);
     int face = F_NONE;
     const real sx = cell_exit<real>(G, T, R, face);
     const real seg = sx - R.s;

@@ -38,7 +38,8 @@ class gcmc_opacity_desc(C.Structure):
                 ("nb", C.c_int32), ("ng", C.c_int32), ("nT", C.c_int32), ("np", C.c_int32),
                 ("lam", C.c_void_p), ("Tg", C.c_void_p), ("pg", C.c_void_p), ("k", C.c_void_p),
                 ("nl", C.c_int32), ("pad", C.c_int32), ("xlam", C.c_void_p), ("sigma", C.c_void_p),
-                ("view_theta", C.c_double), ("view_phi", C.c_double), ("omega_rot", C.c_double)]
+                ("view_theta", C.c_double), ("view_phi", C.c_double), ("omega_rot", C.c_double),
+                ("gw", C.c_void_p)]
 
 
 class gcmc_source_desc(C.Structure):
@@ -49,7 +50,8 @@ class gcmc_source_desc(C.Structure):
                 ("max_steps", C.c_int64), ("cloud_phase", C.c_int32), ("pad2", C.c_int32),
                 ("surface_albedo", C.c_double), ("trans_scatter", C.c_int32), ("ld_law", C.c_int32),
                 ("ld_coef", C.c_double * 4), ("star_radius", C.c_double), ("star_dist", C.c_double),
-                ("transit_xy", C.c_double * 2)]
+                ("transit_xy", C.c_double * 2), ("g_bias", C.c_int32), ("pad3", C.c_int32),
+                ("g_beta", C.c_double)]
 
 
 class gcmc_stats(C.Structure):
@@ -269,7 +271,8 @@ class Context:
                             gcld=_host(opac.gcld, np.float64), acld=_host(opac.acld, np.float32))
             elif kind == OPAC_KTABLE:
                 keep = dict(lam=_host(opac.lam, np.float64), Tg=_host(opac.Tg, np.float64),
-                            pg=_host(opac.pg, np.float64), k=_host(opac.k, np.float32))
+                            pg=_host(opac.pg, np.float64), k=_host(opac.k, np.float32),
+                            gw=_host(opac.wg, np.float64))
             else:
                 keep = dict(xlam=_host(opac.lam, np.float64), Tg=_host(opac.Tg, np.float64),
                             pg=_host(opac.pg, np.float64), sigma=_host(opac.sigma, np.float32))
@@ -279,7 +282,7 @@ class Context:
                 setattr(d, f, _ptr(keep.get(f)))
         elif kind == OPAC_KTABLE:
             d.nb, d.ng, d.nT, d.np = opac.k.shape
-            for f in ("lam", "Tg", "pg", "k"):
+            for f in ("lam", "Tg", "pg", "k", "gw"):
                 setattr(d, f, _ptr(keep.get(f)))
         else:
             d.nl, d.nT, d.np = opac.sigma.shape
@@ -327,6 +330,7 @@ class Context:
             d.ld_coef[i] = float(v)
         d.star_radius, d.star_dist = float(op.star_radius), float(op.star_dist)
         d.transit_xy[0], d.transit_xy[1] = (float(v) for v in op.transit_xy)
+        d.g_bias, d.g_beta = int(op.g_bias), float(op.g_beta)
         sid = C.c_int()
         self._check(lib().gcmc_set_source(self.h, int(grid_id), C.byref(d), C.byref(sid)), "gcmc_set_source")
         return sid.value
@@ -534,7 +538,7 @@ def load_workload(ctx, wl, precision=FP32, device_inputs=False):
                       wcld=dev(o.wcld, np.float64), gcld=dev(o.gcld, np.float64), acld=dev(o.acld, np.float32))
         elif o.kind == OPAC_KTABLE:
             oa = dict(lam=dev(o.lam, np.float64), Tg=dev(o.Tg, np.float64), pg=dev(o.pg, np.float64),
-                      k=dev(o.k, np.float32))
+                      k=dev(o.k, np.float32), gw=dev(o.wg, np.float64))
         else:
             oa = dict(xlam=dev(o.lam, np.float64), Tg=dev(o.Tg, np.float64), pg=dev(o.pg, np.float64),
                       sigma=dev(o.sigma, np.float32))
