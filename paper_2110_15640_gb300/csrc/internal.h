@@ -146,9 +146,9 @@ cudaError_t launch_serve(const DevGrid *grids, const ServeQueue &q, int block, i
 
 // transport
 size_t transport_smem(int block);
-cudaError_t launch_plain(int precision, bool scatter, const DevGrid *grids, const DevJob *job, int64_t packet0,
+cudaError_t launch_plain(int precision, bool scatter, bool band, const DevGrid *grids, const DevJob *job, int64_t packet0,
                          int64_t n_run, const HostLog *hl, int tab_entries_n, cudaStream_t st);
-cudaError_t launch_persistent(int precision, bool scatter, const DevGrid *grids, const DevJob *jobs, int n_jobs,
+cudaError_t launch_persistent(int precision, bool scatter, bool band, const DevGrid *grids, const DevJob *jobs, int n_jobs,
                               int64_t total_items, int chunk, int block, int blocks_per_sm, int interval, int refill_min,
                               int one_grid, int tab_n, unsigned long long *work, cudaStream_t st);
 

@@ -162,7 +162,7 @@ __device__ __forceinline__ int cdf_find(const long long *__restrict__ cb, int nc
 }
 
 // stellar limb darkening (Sect. 5.1): I(mu) / I(disk centre) for the laws GCMC_LD_*, negative values as 0
-template <typename real> __device__ real limb(const DevJob &J, real mu)
+template <typename real> __device__ __noinline__ real limb(const DevJob &J, real mu)
 {
     const real x = (real)1 - mu;
     const real c0 = JV<real>::ld_c(J, 0), c1 = JV<real>::ld_c(J, 1);
@@ -179,6 +179,23 @@ template <typename real> __device__ real limb(const DevJob &J, real mu)
     default: break;
     }
     return I > (real)0 ? I : (real)0;
+}
+
+// band job (Sect. 4.7): g-ordinate with probability q(g) from the fourth word of event 1 (decided in
+// FP64), then the cell from that g's pdf with the launch uniform, u Q_tot(g) in exact integers; returns
+// the cell, the packet's table offset g ncell and its weight W_g
+template <typename real>
+__device__ __noinline__ int band_draw(const DevJob &J, const DevGrid &G, int64_t n, uint32_t wx, int &goff, real &Wg)
+{
+    const uint4 w1 = draw_words(J.seed, n, 1u, J.key);
+    const double ug = u01<double>(w1.w);
+    int g = 0;
+    while (g < J.ng_s - 1 && !(J.gtab[g * GTAB_ROW] > ug)) ++g;
+    goff = g * (int)G.ncell;
+    Wg = (real)J.gtab[g * GTAB_ROW + 1];
+    const unsigned long long qg = (unsigned long long)reinterpret_cast<const long long *>(J.gtab)[g * GTAB_ROW + 3];
+    const long long target = (long long)__umul64hi((unsigned long long)(2u * (wx >> 8) + 1u) << 39, qg);
+    return cdf_find(J.cdf + goff, (int)G.ncell, target, -1);
 }
 
 // S2: packet launch (Sect. 5: albedo disk, emission hybrid pdf, transmission annulus)
@@ -247,29 +264,17 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
     // emission: stratified inverse-CDF draw of the cell over the hybrid pdf
     // stratified target (n + u) Q_tot / N in 2^62 fixed point with u = (m + 1/2) 2^-24, m the top 24
     // bits of the word: n step + floor((2m + 1) step / 2^25), exact integer arithmetic (< Q_tot)
-    const long long *cdf = J.cdf;
     const real *wcell = reinterpret_cast<const real *>(J.wcell);
     real Wg = (real)1;
     int idx;
     if (J.ng_s > 0) {
-        // band job (Sect. 4.7): g-ordinate with probability q(g) from the fourth word of event 1 (decided in
-        // FP64), then the cell from that g's pdf with the launch uniform, u Q_tot(g) in exact integers
-        const uint4 w1 = draw_words(J.seed, n, 1u, J.key);
-        const double ug = u01<double>(w1.w);
-        int g = 0;
-        while (g < J.ng_s - 1 && !(J.gtab[g * GTAB_ROW] > ug)) ++g;
-        P.goff = g * (int)G.ncell;
-        cdf += P.goff;
+        idx = band_draw<real>(J, G, n, w.x, P.goff, Wg);
         wcell += P.goff;
-        Wg = (real)J.gtab[g * GTAB_ROW + 1];
-        const unsigned long long qg = (unsigned long long)reinterpret_cast<const long long *>(J.gtab)[g * GTAB_ROW + 3];
-        const long long target = (long long)__umul64hi((unsigned long long)(2u * (w.x >> 8) + 1u) << 39, qg);
-        idx = cdf_find(cdf, (int)G.ncell, target, -1);
     } else {
         const unsigned long long step = (unsigned long long)J.cdf_step_fix;
         const long long target = (long long)((unsigned long long)n * step +
                                              __umul64hi((unsigned long long)(2u * (w.x >> 8) + 1u) << 39, step));
-        idx = cdf_find(cdf, (int)G.ncell, target, P.hint);
+        idx = cdf_find(J.cdf, (int)G.ncell, target, P.hint);
         P.hint = idx;
     }
     const int nll = G.nlon * G.nlat;
@@ -549,8 +554,9 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
     finish<real>(P, S);
 }
 
-// one cell step (S3-S7) of the packet's current ray
-template <typename real, bool SCAT, class SinkT>
+// one cell step (S3-S7) of the packet's current ray; BAND kernels read the packet's g-ordinate table
+// (band jobs), the others skip that offset
+template <typename real, bool SCAT, bool BAND, class SinkT>
 __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const DevGrid &G, const Tabs<real> &T,
                                      const JobC<real> &jc, SinkT &S)
 {
@@ -564,8 +570,9 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
     ++P.steps;
     const int idx = (R.k * T.nlat + R.j) * T.nlon + R.i;
     real a;
-    if constexpr (SCAT) a = __ldg(jc.rec + jc.rec_stride * idx + P.goff);
-    else a = __ldg(jc.rec + idx + P.goff);
+    const int go = BAND ? P.goff : 0;
+    if constexpr (SCAT) a = __ldg(jc.rec + jc.rec_stride * idx + go);
+    else a = __ldg(jc.rec + idx + go);
     int face = F_NONE;
     const real sx = cell_exit<real>(G, T, R, face);
     const real seg = sx - R.s;
@@ -633,7 +640,7 @@ template <typename real> __device__ __forceinline__ JobC<real> job_consts(const 
     return c;
 }
 
-template <typename real, bool SCAT, bool LOG>
+template <typename real, bool SCAT, bool LOG, bool BAND>
 __global__ void __launch_bounds__(256) k_transport_plain(const DevGrid *__restrict__ grids,
                                                          const DevJob *__restrict__ jobp, int64_t packet0, int64_t n_run,
                                                          LogOut lg)
@@ -657,7 +664,7 @@ __global__ void __launch_bounds__(256) k_transport_plain(const DevGrid *__restri
         launch<real, SCAT>(P, J, G, packet0 + q, S);
         while (P.alive) {
             if (P.ended) settle<real, SCAT>(P, J, S);
-            else step<real, SCAT>(P, J, G, T, jc, S);
+            else step<real, SCAT, BAND>(P, J, G, T, jc, S);
         }
     }
     __syncwarp();
@@ -667,7 +674,7 @@ __global__ void __launch_bounds__(256) k_transport_plain(const DevGrid *__restri
 // One work item (packets p0 .. p1-1 of job J) on one warp: lanes whose packets have finished are
 // refilled together once at least refill_min of them are idle; rays that ended are settled at
 // those points; between them every live lane takes `interval` cell steps.
-template <typename real, bool SCAT, class SinkT>
+template <typename real, bool SCAT, bool BAND, class SinkT>
 __device__ __forceinline__ void run_item(const DevJob &J, const DevGrid &G, const Tabs<real> &T, int64_t p0, int64_t p1,
                                          int interval, int refill_min, SinkT &S)
 {
@@ -693,14 +700,14 @@ __device__ __forceinline__ void run_item(const DevJob &J, const DevGrid &G, cons
         }
         if (!__any_sync(0xffffffffu, P.alive)) break;
         for (int t = 0; t < interval; ++t)
-            if (P.alive && !P.ended) step<real, SCAT>(P, J, G, T, jc, S);
+            if (P.alive && !P.ended) step<real, SCAT, BAND>(P, J, G, T, jc, S);
     }
     __syncwarp();
 }
 
 // MINB > 0: compiled for MINB resident 128-thread blocks per SM (register cap 65536 / (128 MINB));
 // MINB = 0: any block size up to 256, at most 128 registers (two 256-thread blocks per SM)
-template <typename real, bool SCAT, int MINB>
+template <typename real, bool SCAT, int MINB, bool BAND>
 __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 2) k_transport_persistent(const DevGrid *__restrict__ grids,
                                                               const DevJob *__restrict__ jobs, int n_jobs,
                                                               int64_t total_items, int chunk, int interval,
@@ -743,7 +750,7 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 2) k_transport
             __syncwarp();
         }
         const int64_t p0 = ((int64_t)item - J.chunk_begin) * chunk;
-        run_item<real, SCAT>(J, G, T, p0, min(p0 + (int64_t)chunk, J.n_packets), interval, refill_min, S);
+        run_item<real, SCAT, BAND>(J, G, T, p0, min(p0 + (int64_t)chunk, J.n_packets), interval, refill_min, S);
         flush(S.sm, S.stride, J.acc);
     }
 }
@@ -859,7 +866,7 @@ __global__ void __launch_bounds__(128, 4) k_transport_serve(const DevGrid *__res
             __syncwarp();
         }
         const int64_t p0 = (int64_t)item * chunk;
-        run_item<real, SCAT>(J, G, T, p0, min(p0 + (int64_t)chunk, J.n_packets), interval, refill_min, S);
+        run_item<real, SCAT, false>(J, G, T, p0, min(p0 + (int64_t)chunk, J.n_packets), interval, refill_min, S);
         flush(S.sm, S.stride, J.acc);
         __threadfence();
         unsigned long long fin = 0;
@@ -882,15 +889,17 @@ size_t transport_smem(int block) { return (size_t)NSLOT * block * sizeof(unsigne
 
 static size_t tab_bytes(int precision, int entries) { return (size_t)entries * (precision == GCMC_FP64 ? 16 : 8); }
 
+// the logging (parity) kernels always read band tables; the others only when the job is a band job
 template <typename real, bool SCAT>
 static void plain_dispatch(unsigned nb, int block, size_t sm, cudaStream_t st, const DevGrid *grids, const DevJob *job,
-                           int64_t packet0, int64_t n_run, const LogOut &lg, bool log)
+                           int64_t packet0, int64_t n_run, const LogOut &lg, bool log, bool band)
 {
-    if (log) k_transport_plain<real, SCAT, true><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
-    else k_transport_plain<real, SCAT, false><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
+    if (log) k_transport_plain<real, SCAT, true, true><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
+    else if (band) k_transport_plain<real, SCAT, false, true><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
+    else k_transport_plain<real, SCAT, false, false><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
 }
 
-cudaError_t launch_plain(int precision, bool scatter, const DevGrid *grids, const DevJob *job, int64_t packet0,
+cudaError_t launch_plain(int precision, bool scatter, bool band, const DevGrid *grids, const DevJob *job, int64_t packet0,
                          int64_t n_run, const HostLog *hl, int tab_entries_n, cudaStream_t st)
 {
     const int block = 128;
@@ -912,21 +921,21 @@ cudaError_t launch_plain(int precision, bool scatter, const DevGrid *grids, cons
     count_launch(1);
     const unsigned g = (unsigned)nb;
     if (precision == GCMC_FP64) {
-        if (scatter) plain_dispatch<double, true>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr);
-        else plain_dispatch<double, false>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr);
+        if (scatter) plain_dispatch<double, true>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr, band);
+        else plain_dispatch<double, false>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr, band);
     } else {
-        if (scatter) plain_dispatch<float, true>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr);
-        else plain_dispatch<float, false>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr);
+        if (scatter) plain_dispatch<float, true>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr, band);
+        else plain_dispatch<float, false>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr, band);
     }
     return cudaGetLastError();
 }
 
-template <typename real, bool SCAT, int MINB>
+template <typename real, bool SCAT, int MINB, bool BAND>
 static cudaError_t persistent_run(int block, int blocks_per_sm, int nsm, const DevGrid *grids, const DevJob *jobs,
                                   int n_jobs, int64_t total_items, int chunk, int interval, int refill_min, int one_grid,
                                   int tab_n, unsigned long long *work, cudaStream_t st)
 {
-    auto kern = k_transport_persistent<real, SCAT, MINB>;
+    auto kern = k_transport_persistent<real, SCAT, MINB, BAND>;
     const size_t sm = transport_smem(block) + (size_t)tab_n * sizeof(typename Pair<real>::type) * (one_grid ? 1 : block / 32);
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int occ = 0;
@@ -941,21 +950,25 @@ static cudaError_t persistent_run(int block, int blocks_per_sm, int nsm, const D
 template <typename real, bool SCAT>
 static cudaError_t persistent_dispatch(int block, int blocks_per_sm, int nsm, const DevGrid *grids, const DevJob *jobs,
                                        int n_jobs, int64_t total_items, int chunk, int interval, int refill_min,
-                                       int one_grid, int tab_n, unsigned long long *work, cudaStream_t st)
+                                       int one_grid, int tab_n, unsigned long long *work, bool band, cudaStream_t st)
 {
+    // batches with band jobs run the uncapped variant that reads each packet's g-ordinate table
+    if (band)
+        return persistent_run<real, SCAT, 0, true>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+                                                   interval, refill_min, one_grid, tab_n, work, st);
     // FP32 absorber-only batches (the emission and limb-chord hot path) have variants compiled for
     // 6 and 8 resident 128-thread blocks per SM (register caps 80 and 64); blocks_per_sm selects them.
     // (Capped scattering variants spill and ran slower on the phase curve.)
     if constexpr (sizeof(real) == 4 && !SCAT) {
         if (block <= 128 && blocks_per_sm >= 8)
-            return persistent_run<real, SCAT, 8>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+            return persistent_run<real, SCAT, 8, false>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
                                                  interval, refill_min, one_grid, tab_n, work, st);
         if (block <= 128 && blocks_per_sm >= 6)
-            return persistent_run<real, SCAT, 6>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+            return persistent_run<real, SCAT, 6, false>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
                                                  interval, refill_min, one_grid, tab_n, work, st);
     }
-    return persistent_run<real, SCAT, 0>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk, interval,
-                                         refill_min, one_grid, tab_n, work, st);
+    return persistent_run<real, SCAT, 0, false>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+                                                interval, refill_min, one_grid, tab_n, work, st);
 }
 
 cudaError_t launch_serve(const DevGrid *grids, const ServeQueue &q, int block, int blocks_per_sm, int chunk, int interval,
@@ -983,7 +996,7 @@ cudaError_t launch_serve(const DevGrid *grids, const ServeQueue &q, int block, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_persistent(int precision, bool scatter, const DevGrid *grids, const DevJob *jobs, int n_jobs,
+cudaError_t launch_persistent(int precision, bool scatter, bool band, const DevGrid *grids, const DevJob *jobs, int n_jobs,
                               int64_t total_items, int chunk, int block, int blocks_per_sm, int interval, int refill_min,
                               int one_grid, int tab_n, unsigned long long *work, cudaStream_t st)
 {
@@ -998,15 +1011,15 @@ cudaError_t launch_persistent(int precision, bool scatter, const DevGrid *grids,
     if (precision == GCMC_FP64) {
         if (scatter)
             return persistent_dispatch<double, true>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
-                                                     interval, refill_min, one_grid, tab_n, work, st);
+                                                     interval, refill_min, one_grid, tab_n, work, band, st);
         return persistent_dispatch<double, false>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
-                                                  interval, refill_min, one_grid, tab_n, work, st);
+                                                  interval, refill_min, one_grid, tab_n, work, band, st);
     }
     if (scatter)
         return persistent_dispatch<float, true>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
-                                                interval, refill_min, one_grid, tab_n, work, st);
+                                                interval, refill_min, one_grid, tab_n, work, band, st);
     return persistent_dispatch<float, false>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
-                                             interval, refill_min, one_grid, tab_n, work, st);
+                                             interval, refill_min, one_grid, tab_n, work, band, st);
 }
 
 }  // namespace gcmc

@@ -505,7 +505,7 @@ def workload_arrays(wl, where):
                   wcld=put(o.wcld, np.float64), gcld=put(o.gcld, np.float64), acld=put(o.acld, np.float32))
     elif o.kind == OPAC_KTABLE:
         oa = dict(lam=put(o.lam, np.float64), Tg=put(o.Tg, np.float64), pg=put(o.pg, np.float64),
-                  k=put(o.k, np.float32))
+                  k=put(o.k, np.float32), gw=put(o.wg, np.float64))
     else:
         oa = dict(xlam=put(o.lam, np.float64), Tg=put(o.Tg, np.float64), pg=put(o.pg, np.float64),
                   sigma=put(o.sigma, np.float32))

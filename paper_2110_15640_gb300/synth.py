@@ -366,6 +366,28 @@ def config3_phase_curve(seed=3, nlon=128, nlat=64, nr=50, nlam=40, nphase=24, n_
                     seed, notes=dict(phases_deg=phases.tolist()))
 
 
+R_SUN = 6.957e8
+AU = 1.495978707e11
+
+
+def config6_transit_scatter(seed=6, nlon=128, nlat=64, nr=50, nlam=40, n_packets=200_000, lam_lo=0.3e-6,
+                            lam_hi=1.0e-6):
+    """Optical transmission spectrum with multiple scattering (Sect. 5.1): the phase-curve atmosphere
+    (Rayleigh gas + cloud deck, omega 0.9, two-term HG g = 0.6) seen in transit, quadratic stellar limb
+    darkening (Sun-like star at 0.05 AU, transit impact parameter 0.3), n_packets chords per wavelength."""
+    grid, m = hotjupiter_grid(nlon, nlat, nr)
+    lam = np.geomspace(lam_lo, lam_hi, nlam)
+    kray = 3.1e-5 * (lam / 0.5e-6) ** -4
+    kabs = 5.0e-5 * 10.0 ** (0.5 * np.sin(12.0 * np.log(lam / lam_lo)))
+    opac = AlbedoOpacity(kabs=kabs, kray=kray, qcld=np.ones(nlam), wcld=np.full(nlam, 0.9),
+                         gcld=np.full(nlam, 0.6), acld=cloud_profile(grid, m))
+    opts = Options(trans_scatter=1, cloud_phase=1, ld_law=2, ld_coef=(0.45, 0.2, 0.0, 0.0), star_radius=R_SUN,
+                   star_dist=0.05 * AU, transit_xy=(0.0, 0.3 * R_SUN))
+    src = Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[-1.0, 0.0, 0.0]]), opts=opts)
+    jobs = [Job(lam_idx=l, g_idx=0, n_packets=int(n_packets), key=l) for l in range(nlam)]
+    return Workload(f"transit_scatter_{nlon}x{nlat}x{nr}_{nlam}l", MODE_TRANSMISSION, grid, opac, src, jobs, seed)
+
+
 def wind_field(nlon, nlat, nr, lat_edges, lon_edges, u_jet=5000.0, v_dn=3000.0):
     """(u east, v north, w up) in m/s: cos^2(lat) eastward jet + day->night great-circle flow
     |v| = v_dn sin(angular distance from the substellar point at lon 0, lat 0)."""
