@@ -13,7 +13,9 @@ request-latency summary (p50/p99) of a 1000-request sample of the serving stream
 `--impl reference` times the FP64 CPU oracle on the same workload instead.
 
 Other workloads (--workload): albedo (32x16x20, FP64), phasecurve (40 wavelengths x 24 phases),
-transmission (9532 wavelengths, Doppler cross sections), serving (the full request stream).
+transmission (9532 wavelengths, Doppler cross sections), transit-scatter (40 optical wavelengths in
+transit with multiple scattering and limb darkening), band (the emission workload as 30 band jobs
+whose packets draw their g-ordinate), serving (the full request stream).
 """
 import argparse
 import json
@@ -32,7 +34,7 @@ OPS_PER_STEP = 64          # FP32-pipe operations of one cell step (counted from
 # DRAM bytes (read + write) of the persistent transport kernel per emission job of the 128x64x50 grid,
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 8-job band-0 launch: the traffic
 # grows with the number of job tables the launch touches
-TRAFFIC_PER_EMISSION_JOB = 48.4e6 / 8
+TRAFFIC_PER_EMISSION_JOB = (47.92e6 + 0.32e6) / 8
 PEAK_FP32_OPS = 152 * 128 * 2.07e9   # GB300: SMs x FP32 lanes x max SM clock (an FMA counts as one op)
 PEAK_FP64_OPS = 152 * 2 * 2.07e9     # GB300: FP64 issue is 1/64 of FP32 (2 lanes per SM per clock)
 
@@ -55,7 +57,8 @@ def parse():
     ap.add_argument("--refill", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
-    ap.add_argument("--workload", default="emission", choices=["emission", "albedo", "phasecurve", "transmission", "serving"])
+    ap.add_argument("--workload", default="emission", choices=["emission", "albedo", "phasecurve", "transmission", "transit-scatter", "band",
+                             "serving"])
     ap.add_argument("--requests", type=int, default=10_000, help="serving: requests in the stream")
     ap.add_argument("--hbm-budget-gb", type=float, default=16.0, help="serving: admitted workspace")
     ap.add_argument("--serving-requests", type=int, default=1000,
@@ -79,6 +82,11 @@ def workload(args, rank):
         wl = synth.config3_phase_curve()
     elif args.workload == "transmission":
         wl = synth.config4_transmission()
+    elif args.workload == "transit-scatter":
+        wl = synth.config6_transit_scatter()
+    elif args.workload == "band":
+        wl = synth.config2_emission(n_packets=args.packets * args.gpoints, nb=30, ng=8, bands=range(args.bands),
+                                    per_packet_g=True, g_bias=2)
     else:
         wl = synth.config2_emission(n_packets=args.packets, nb=30, ng=8, bands=range(args.bands),
                                     gpoints=range(args.gpoints))
@@ -87,8 +95,10 @@ def workload(args, rank):
 
 
 # oracle sample per workload for the CPU baseline: (jobs, packets per job or None for all)
-CPU_SAMPLE = {"emission": (48, 1_000_000), "albedo": (1, None), "phasecurve": (24, None), "transmission": (480, None)}
-REF_SAMPLE = {"emission": (2, 200_000), "albedo": (1, None), "phasecurve": (2, None), "transmission": (96, None)}
+CPU_SAMPLE = {"emission": (48, 1_000_000), "albedo": (1, None), "phasecurve": (24, None), "transmission": (480, None),
+              "transit-scatter": (8, 400_000), "band": (12, 1_000_000)}
+REF_SAMPLE = {"emission": (2, 200_000), "albedo": (1, None), "phasecurve": (2, None), "transmission": (96, None),
+              "transit-scatter": (2, 20_000), "band": (2, 200_000)}
 
 
 class ClockSampler:
@@ -413,7 +423,9 @@ def main():
         jb = gcmc.workload_jobs(wl, g2, o2, ctx.set_sources(g2, wl.source, prec))
         tl, st2 = ctx.run_batch(jb, cfg=cfg)
         obs = [ctx.postscale(g2, wl.mode, tl[q][0], j.n_packets, st2[q].l_tot) for q, j in enumerate(wl.jobs)]
-        if wl.mode == gcmc.EMISSION:
+        if wl.mode == gcmc.EMISSION and wl.jobs[0].g_idx < 0:     # band jobs: L_p already sums over g
+            F_band = {"spectrum_F_p_band_mean": float(np.mean([o["F_p"] for o in obs]))}
+        elif wl.mode == gcmc.EMISSION:
             F = np.zeros((args.bands, args.gpoints))
             for q, j in enumerate(wl.jobs):
                 F[j.lam_idx, j.g_idx] = obs[q]["F_p"]
@@ -431,7 +443,7 @@ def main():
     f64 = prec == gcmc.FP64
     tr_avg = tr_ms / max(ntr, 1) / 1e3
     achieved = OPS_PER_STEP * steps_per_step / tr_avg / 1e12
-    rec_bytes = 16 if wl.mode == gcmc.ALBEDO else 4
+    rec_bytes = 16 if wl.opac.kind == gcmc.OPAC_ALBEDO else 4
     gather = ctx.gather_bench(wl.grid.ncell, rec_bytes, 1 << 30)
     clocks = clk.summary()
 
@@ -451,7 +463,8 @@ def main():
                          f"{dt:.1f} s"}
     if rank == 0:
         g = wl.grid
-        per_step_bytes = len(jobs) * g.ncell * (rec_bytes + (12 if wl.mode == gcmc.EMISSION else 0))
+        tables = len(jobs) * (len(wl.opac.wg) if wl.mode == gcmc.EMISSION and wl.jobs[0].g_idx < 0 else 1)
+        per_step_bytes = tables * g.ncell * (rec_bytes + (12 if wl.mode == gcmc.EMISSION else 0))
         peak = (PEAK_FP64_OPS if f64 else PEAK_FP32_OPS) / 1e12
         line = {
             "metric": "packet-steps/s", "value": value, "unit": "packet-steps/s", "n_gpus": world,

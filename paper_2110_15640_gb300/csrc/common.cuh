@@ -69,16 +69,7 @@ struct __align__(16) Rec64 {
 struct DevJob {
     int32_t mode, n_obs, grid_slot, survival;
     int32_t precision, cloud_phase;   // cloud_phase: GCMC_CLOUD_HG or GCMC_CLOUD_TTHG
-    uint32_t key;
-    int32_t n_tal;              // tally columns: n_obs; transmission: 1, or 2 with multiple scattering
-    int32_t rec4;               // cell records are (alpha, omega, g, P_gas) (scattering opacities), else alpha
-    int32_t trans_scatter;      // transmission: packets scatter after their chord (column 1)
-    int32_t ld_law, pad3;       // stellar limb-darkening law (GCMC_LD_*)
-    int32_t ng_s, g_bias;       // band job: g-ordinates drawn per packet (0: one g-ordinate); q(g) option
-    double g_beta;              // composite fraction of q(g)
-    const double *gw;           // [ng] g-ordinate weights (band jobs)
-    double *gtab;               // band job: [ng] rows {cumulative q, W_g, w_g L_g, Q_tot(g) as int64 bits}
-    const double *ginfo;        // band job: each g-ordinate's info block, GINFO_STRIDE doubles apart
+    uint32_t key, pad1;
     uint64_t seed;
     int64_t n_packets;
     int64_t chunk_begin;        // first work item of this job (batched launches)
@@ -91,18 +82,27 @@ struct DevJob {
     double star[3], e1[3], e2[3];
     double obs[MAX_OBS][3];
     double w_rr, p_surv, tau_cut, hg_eps;
-    double surf_as;             // Lambertian surface albedo (0: black lower boundary)
-    double ld_c[4], star_r, tr_x, tr_y;   // limb-darkening coefficients, stellar radius, planet offset on the disk
     // the same vectors and constants rounded once to FP32, for FP32 marches
     float star_f[3], e1_f[3], e2_f[3];
     float obs_f[MAX_OBS][3];
-    float w_rr_f, p_surv_f, hg_eps_f, surf_as_f;
-    float ld_c_f[4], star_r_f, tr_x_f, tr_y_f, pad4;
+    float w_rr_f, p_surv_f, hg_eps_f, pad2;
     unsigned long long *acc;    // [ACC_SLOTS]
     // contribution functions (Sect. 6), or NULL: [2][n_obs][cf_ncell] fixed-point sums of the peel-off
     // contributions by the cell they leave from, [0] thermal (emission launch), [1] scattered
     unsigned long long *cf;
     int64_t cf_ncell;
+    // options read outside the march (kept after the fields every packet launch reads)
+    int32_t n_tal;              // tally columns: n_obs; transmission: 1, or 2 with multiple scattering
+    int32_t rec4;               // cell records are (alpha, omega, g, P_gas) (scattering opacities), else alpha
+    int32_t trans_scatter;      // transmission: packets scatter after their chord (column 1)
+    int32_t ld_law;             // stellar limb-darkening law (GCMC_LD_*)
+    int32_t ng_s, g_bias;       // band job: g-ordinates drawn per packet (0: one g-ordinate); q(g) option
+    double g_beta;              // composite fraction of q(g)
+    const double *gw;           // [ng] g-ordinate weights (band jobs)
+    double *gtab;               // band job: [ng] rows {cumulative q, W_g, w_g L_g, Q_tot(g) as int64 bits}
+    const double *ginfo;        // band job: each g-ordinate's info block, GINFO_STRIDE doubles apart
+    double surf_as, ld_c[4], star_r, tr_x, tr_y;   // surface albedo; limb darkening, stellar radius, planet offset
+    float surf_as_f, ld_c_f[4], star_r_f, tr_x_f, tr_y_f;
 };
 
 // job constants in the march precision (FP32 marches read the copies rounded on the host)

@@ -199,7 +199,8 @@ __device__ __noinline__ int band_draw(const DevJob &J, const DevGrid &G, int64_t
 }
 
 // S2: packet launch (Sect. 5: albedo disk, emission hybrid pdf, transmission annulus)
-template <typename real, bool SCAT, class SinkT>
+// (BAND: the kernel may run band jobs; the g draw is compiled only there)
+template <typename real, bool SCAT, bool BAND, class SinkT>
 __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64_t n, SinkT &S)
 {
     P.n = n;
@@ -267,7 +268,7 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
     const real *wcell = reinterpret_cast<const real *>(J.wcell);
     real Wg = (real)1;
     int idx;
-    if (J.ng_s > 0) {
+    if (BAND && J.ng_s > 0) {
         idx = band_draw<real>(J, G, n, w.x, P.goff, Wg);
         wcell += P.goff;
     } else {
@@ -661,7 +662,7 @@ __global__ void __launch_bounds__(256) k_transport_plain(const DevGrid *__restri
     if (q < n_run) {
         Packet<real> P;
         P.hint = -1;
-        launch<real, SCAT>(P, J, G, packet0 + q, S);
+        launch<real, SCAT, BAND>(P, J, G, packet0 + q, S);
         while (P.alive) {
             if (P.ended) settle<real, SCAT>(P, J, S);
             else step<real, SCAT, BAND>(P, J, G, T, jc, S);
@@ -694,7 +695,7 @@ __device__ __forceinline__ void run_item(const DevJob &J, const DevGrid &G, cons
             const int n_idle = __popc(idle);
             if (n_idle >= min(refill_min, left)) {
                 const int mine = next + __popc(idle & lt);
-                if (!P.alive && mine < count) launch<real, SCAT>(P, J, G, p0 + mine, S);
+                if (!P.alive && mine < count) launch<real, SCAT, BAND>(P, J, G, p0 + mine, S);
                 next += n_idle;
             }
         }
