@@ -503,6 +503,10 @@ double orc_planck(double lam, double T) { return planck_lambda(lam, T); }
 
 /* Emission cell tables for one (band, g): alpha = rho k(T, p); L_i = 4 pi V_i alpha_i B(T_i);
    hybrid pdf over the cells with vertical tau above them < tau_vert_max; cdf and launch weight. */
+void orc_emission_tables(const orc_grid *G, const double *T, const double *alpha, double lam, double tau_vert_max,
+                         double beta, double *L, double *cdf, double *wcell, double *out_Ltot,
+                         double *out_cdf_total, int64_t *out_nincl);
+
 void orc_prep_emission(const orc_grid *G, const double *T, const double *p, const double *rho,
                        const float *ktab /* [nT][np] slice for this (band, g) */, int nT, int np,
                        const double *Tg, const double *pg, double lam, double tau_vert_max, double beta,
@@ -521,6 +525,19 @@ void orc_prep_emission(const orc_grid *G, const double *T, const double *p, cons
         double lk = (1 - wT) * (1 - wp) * l00 + wT * (1 - wp) * l10 + (1 - wT) * wp * l01 + wT * wp * l11;
         alpha[idx] = rho[idx] * exp(lk);
     }
+    orc_emission_tables(G, T, alpha, lam, tau_vert_max, beta, L, cdf, wcell, out_Ltot, out_cdf_total, out_nincl);
+}
+
+/* Emission cell tables from the cells' extinction alpha (Sect. 4.3, 4.6): the tau_vert cut (a cell emits
+   while the vertical optical depth above it is below tau_vert_max), L_i = 4 pi V_i alpha_i B_lambda(T_i),
+   the hybrid pdf q_i = (1 - beta) L_i / L_tot + beta / n_incl, its cumulative sum and the launch weights
+   (L_i / L_tot) / q_i.  Used with k-table opacities and with Doppler-shifted cross-sections (Sect. 7). */
+void orc_emission_tables(const orc_grid *G, const double *T, const double *alpha, double lam, double tau_vert_max,
+                         double beta, double *L, double *cdf, double *wcell, double *out_Ltot,
+                         double *out_cdf_total, int64_t *out_nincl)
+{
+    int64_t nl = G->nlon, nt = G->nlat, nr = G->nr;
+    int64_t ncell = nl * nt * nr;
     /* volumes and luminosities */
     char *incl = (char *)calloc((size_t)ncell, 1);
     for (int64_t j = 0; j < nt; ++j)

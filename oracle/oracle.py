@@ -106,6 +106,8 @@ def lib():
             _lib.orc_prep_emission.argtypes = [P(Grid_c), P(D), P(D), P(D), P(C.c_float), C.c_int, C.c_int,
                                                P(D), P(D), D, D, D, P(D), P(D), P(D), P(D), P(D), P(D),
                                                P(C.c_int64)]
+            _lib.orc_emission_tables.argtypes = [P(Grid_c), P(D), P(D), D, D, D, P(D), P(D), P(D), P(D), P(D),
+                                                 P(C.c_int64)]
             _lib.orc_prep_xsec.argtypes = [P(Grid_c), P(D), P(D), P(D), P(D), P(C.c_float), C.c_int, C.c_int,
                                            C.c_int, P(D), P(D), P(D), D, D, D, D, P(D), P(D)]
             _lib.orc_run.argtypes = [P(Grid_c), P(Cells_c), P(Source_c), P(Run_c)]
@@ -231,6 +233,23 @@ def prep_emission(grid, kt, band, gidx, opts):
     return out
 
 
+def prep_emission_xsec(grid, xs, lam_idx, opts):
+    """Emission cell tables on cross-section opacities (high resolution, Sect. 7): alpha from the
+    Doppler-shifted cross-sections of each cell, then the same tau_vert cut, luminosities and hybrid pdf
+    as with k-tables, with B at the job's rest wavelength."""
+    n = grid.ncell
+    G = _GridHandle(grid)
+    alpha = _f64(prep_xsec(grid, xs, lam_idx)["alpha"])
+    T = _f64(grid.T)
+    out = {k: np.zeros(n) for k in ("L", "cdf", "wcell")}
+    Ltot, ctot, ninc = C.c_double(), C.c_double(), C.c_int64()
+    lib().orc_emission_tables(C.byref(G.c), _dp(T), _dp(alpha), float(xs.lam[lam_idx]), float(opts.tau_vert_max),
+                              float(opts.beta_emis), _dp(out["L"]), _dp(out["cdf"]), _dp(out["wcell"]),
+                              C.byref(Ltot), C.byref(ctot), C.byref(ninc))
+    out.update(alpha=alpha, L_tot=Ltot.value, cdf_total=ctot.value, n_incl=ninc.value)
+    return out
+
+
 def prep_xsec(grid, xs, lam_idx):
     n = grid.ncell
     G = _GridHandle(grid)
@@ -251,6 +270,8 @@ def prep_cells(wl, job):
     if wl.mode == 0:
         return prep_albedo(wl.grid, wl.opac, job.lam_idx)
     if wl.mode == 1:
+        if not hasattr(wl.opac, "wg"):
+            return prep_emission_xsec(wl.grid, wl.opac, job.lam_idx, wl.source.opts)
         if job.g_idx < 0:
             return prep_band(wl, job)
         return prep_emission(wl.grid, wl.opac, job.lam_idx, job.g_idx, wl.source.opts)

@@ -366,6 +366,24 @@ def config3_phase_curve(seed=3, nlon=128, nlat=64, nr=50, nlam=40, nphase=24, n_
                     seed, notes=dict(phases_deg=phases.tolist()))
 
 
+def config7_emission_hires(n_packets=100_000, seed=7, nlon=96, nlat=48, nr=60, n_lam=9532, lam_subset=None,
+                           n_lines=5000, p_top=1e-6, p_bot=100.0, rot_period_days=3.5):
+    """High-resolution emission (Sect. 7): C2's day-night temperature structure and C4's winds on the
+    96 x 48 x 60 grid, sigma(lambda, T, p) at R = 1e5 over 1.0-1.1 um with per-cell Doppler shifts
+    towards an observer over the dayside (+x), n_packets per wavelength."""
+    rng = np.random.default_rng(seed)
+    grid, _ = hotjupiter_grid(nlon, nlat, nr, p_top=p_top, p_bot=p_bot, wind=True)
+    xs, margin = make_xsec_table(rng, n_lines=n_lines, n_lam=n_lam)
+    xs.omega_rot = 2.0 * math.pi / (rot_period_days * 86400.0)
+    xs.view_theta = 0.5 * math.pi      # observer on the +x axis: colatitude 90 deg, longitude 0
+    xs.view_phi = 0.0
+    src = Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[1.0, 0.0, 0.0]]), opts=Options(scatter_emission=0))
+    lams = range(n_lam) if lam_subset is None else lam_subset
+    jobs = [Job(lam_idx=margin + l, g_idx=0, n_packets=int(n_packets), key=l) for l in lams]
+    return Workload(f"emission_hires_{nlon}x{nlat}x{nr}_{n_lam}l", MODE_EMISSION, grid, xs, src, jobs, seed,
+                    notes=dict(margin=margin))
+
+
 R_SUN = 6.957e8
 AU = 1.495978707e11
 
