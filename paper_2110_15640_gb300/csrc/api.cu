@@ -220,7 +220,9 @@ gcmc_status check_job(gcmc_ctx *ctx, const gcmc_job &j)
     const int want = j.mode == GCMC_ALBEDO ? GCMC_OPAC_ALBEDO : j.mode == GCMC_EMISSION ? GCMC_OPAC_KTABLE : GCMC_OPAC_XSEC;
     // transmission runs on cross-sections (chords) or on scattering opacities (chords, optionally
     // followed by multiple scattering)
-    const bool kind_ok = o.kind == want || (j.mode == GCMC_TRANSMISSION && o.kind == GCMC_OPAC_ALBEDO);
+    // emission runs on k-tables or on cross-sections (high resolution, Doppler-shifted)
+    const bool kind_ok = o.kind == want || (j.mode == GCMC_TRANSMISSION && o.kind == GCMC_OPAC_ALBEDO) ||
+                         (j.mode == GCMC_EMISSION && o.kind == GCMC_OPAC_XSEC);
     if (!kind_ok) return fail(ctx, GCMC_ERR_ARG, "opacity kind does not match the mode");
     if (j.n_packets < 0) return fail(ctx, GCMC_ERR_ARG, "negative n_packets");
     const gcmc_source_desc &s = ctx->sources[j.source_id];
@@ -547,6 +549,9 @@ gcmc_status stage(gcmc_ctx *ctx, Plan &P, char *base, double *lum = nullptr, cha
         } else if (oh.kind == GCMC_OPAC_KTABLE) {
             const gcmc_source_desc &s = ctx->sources[G.source];
             e = prep_emission(G.precision, gh.dg, oh.kt, gp, m, s.tau_vert_max, s.beta_emis, ctx->stream);
+        } else if (G.mode == GCMC_EMISSION) {
+            const gcmc_source_desc &s = ctx->sources[G.source];
+            e = prep_emission_xsec(G.precision, gh.dg, oh.xs, gp, m, s.tau_vert_max, s.beta_emis, ctx->stream);
         } else {
             e = prep_xsec(G.precision, gh.dg, oh.xs, gp, m, ctx->stream);
         }

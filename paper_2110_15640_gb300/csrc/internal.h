@@ -95,6 +95,8 @@ cudaError_t prep_albedo(int precision, const DevGrid *dgrid, const DevGrid &hgri
 cudaError_t prep_emission(int precision, const DevGrid &hgrid, const KtabDev &kt, const PrepJob *djobs, int njobs,
                           double tau_vert_max, double beta, cudaStream_t st);
 int emis_col_blocks(const DevGrid &g);     // partial-sum blocks of the column kernel
+cudaError_t prep_emission_xsec(int precision, const DevGrid &hgrid, const XsecDev &xs, const PrepJob *djobs, int njobs,
+                               double tau_vert_max, double beta, cudaStream_t st);
 cudaError_t prep_xsec(int precision, const DevGrid &hgrid, const XsecDev &xs, const PrepJob *djobs, int njobs,
                       cudaStream_t st);
 // per-cell tables of an opacity on its grid (at upload): interpolation cells and weights, and

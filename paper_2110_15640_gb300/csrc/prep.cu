@@ -206,6 +206,70 @@ __global__ void __launch_bounds__(COL_BLOCK) k_emis_column(DevGrid G, KtabDev kt
     }
 }
 
+// The same column walk for cells whose extinction is already in the job's table (Doppler-shifted
+// cross-sections, Sect. 7): L_i = 4 pi V_i B_lambda(T_i) alpha_i with B at the job's wavelength.
+template <typename real>
+__global__ void __launch_bounds__(COL_BLOCK) k_emis_column_alpha(DevGrid G, const PrepJob *__restrict__ jobs,
+                                                                 double tau_vert_max)
+{
+    extern __shared__ __align__(16) unsigned char col_smem[];
+    real *s_dr = reinterpret_cast<real *>(col_smem);     // layer thicknesses [nr]
+    __shared__ double red_s[COL_BLOCK / 32];
+    __shared__ int red_c[COL_BLOCK / 32];
+    for (int k = threadIdx.x; k < G.nr; k += blockDim.x) s_dr[k] = (real)(G.r[k + 1] - G.r[k]);
+    __syncthreads();
+    const PrepJob &pj = jobs[blockIdx.y];
+    const int64_t ncol = (int64_t)G.nlon * G.nlat;
+    const int64_t col = (int64_t)blockIdx.x * COL_BLOCK + threadIdx.x;
+    double lsum = 0.0;
+    int cnt = 0;
+    if (col < ncol) {
+        const real *__restrict__ rec = reinterpret_cast<const real *>(pj.rec);
+        double *__restrict__ lb = reinterpret_cast<double *>(pj.cdf);
+        double *__restrict__ lum = pj.lum;
+        const double l = pj.lam_m;
+        const double c1 = 2.0 * H_PLANCK * C_LIGHT * C_LIGHT / (l * l * l * l * l);
+        const double hck = H_PLANCK * C_LIGHT / (l * K_BOLTZ);
+        const real tmax = (real)tau_vert_max;
+        real above = (real)0;
+        for (int k = G.nr - 1; k >= 0; --k) {
+            const int64_t idx = k * ncol + col;
+            const real alpha = rec[idx];
+            const bool incl = above < tmax;
+            above += alpha * s_dr[k];
+            const double L = 4.0 * PI * G.vol[idx] * (c1 / expm1(hck / (double)G.T[idx])) * (double)alpha;
+            if (lum) lum[idx] = L;
+            if (incl) {
+                lb[idx] = L;
+                lsum += L;
+                ++cnt;
+            } else {
+                lb[idx] = -1.0;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+        cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red_s[threadIdx.x >> 5] = lsum;
+        red_c[threadIdx.x >> 5] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        int c = 0;
+        for (int q = 0; q < COL_BLOCK / 32; ++q) {
+            s += red_s[q];
+            c += red_c[q];
+        }
+        pj.bsum[blockIdx.x] = s;
+        pj.bcnt[blockIdx.x] = (double)c;
+    }
+}
+
 // per-block sums of L over the emitting cells (L >= 0) and their count, for an L array given directly
 // (the allocation-free entry point)
 __global__ void k_emis_reduce(int64_t ncell, const PrepJob *__restrict__ jobs)
@@ -376,6 +440,20 @@ __global__ void k_emis_cdf_add(int64_t ncell, const PrepJob *__restrict__ jobs)
     else pj.cdf[idx] = v;
 }
 
+// the hybrid pdf, fixed-point CDF and launch weights from the column kernels' luminosities and sums
+static cudaError_t emission_pdf(bool f64, const DevGrid &hg, const PrepJob *djobs, int njobs, int ncolb, double beta,
+                                cudaStream_t st)
+{
+    k_emis_total<<<(njobs + 127) / 128, 128, 0, st>>>(ncolb, djobs, njobs, beta);
+    const int nblk = (int)((hg.ncell + EMIS_SCAN_BLOCK - 1) / EMIS_SCAN_BLOCK);
+    const dim3 g3((unsigned)nblk, (unsigned)njobs);
+    if (f64) k_emis_pdf<double><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
+    else k_emis_pdf<float><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
+    k_emis_scan_blocks<<<(njobs + 3) / 4, 128, 0, st>>>(nblk, djobs, njobs);
+    k_emis_cdf_add<long long><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs);
+    return cudaGetLastError();
+}
+
 cudaError_t prep_emission(int precision, const DevGrid &hg, const KtabDev &kt, const PrepJob *djobs, int njobs,
                           double tau_vert_max, double beta, cudaStream_t st)
 {
@@ -385,14 +463,23 @@ cudaError_t prep_emission(int precision, const DevGrid &hg, const KtabDev &kt, c
     const dim3 gc((unsigned)ncolb, (unsigned)njobs);
     if (f64) k_emis_column<double><<<gc, COL_BLOCK, hg.nr * sizeof(double), st>>>(hg, kt, djobs, tau_vert_max);
     else k_emis_column<float><<<gc, COL_BLOCK, hg.nr * sizeof(float), st>>>(hg, kt, djobs, tau_vert_max);
-    k_emis_total<<<(njobs + 127) / 128, 128, 0, st>>>(ncolb, djobs, njobs, beta);
-    const int nblk = (int)((hg.ncell + EMIS_SCAN_BLOCK - 1) / EMIS_SCAN_BLOCK);
-    const dim3 g3((unsigned)nblk, (unsigned)njobs);
-    if (f64) k_emis_pdf<double><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
-    else k_emis_pdf<float><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
-    k_emis_scan_blocks<<<(njobs + 3) / 4, 128, 0, st>>>(nblk, djobs, njobs);
-    k_emis_cdf_add<long long><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs);
-    return cudaGetLastError();
+    return emission_pdf(f64, hg, djobs, njobs, ncolb, beta, st);
+}
+
+// emission on cross-section opacities (Sect. 7): each job's Doppler-shifted extinction, then the column
+// walk and the hybrid pdf
+cudaError_t prep_emission_xsec(int precision, const DevGrid &hg, const XsecDev &xs, const PrepJob *djobs, int njobs,
+                               double tau_vert_max, double beta, cudaStream_t st)
+{
+    cudaError_t e = prep_xsec(precision, hg, xs, djobs, njobs, st);
+    if (e != cudaSuccess) return e;
+    count_launch(5);
+    const bool f64 = precision == GCMC_FP64;
+    const int ncolb = emis_col_blocks(hg);
+    const dim3 gc((unsigned)ncolb, (unsigned)njobs);
+    if (f64) k_emis_column_alpha<double><<<gc, COL_BLOCK, hg.nr * sizeof(double), st>>>(hg, djobs, tau_vert_max);
+    else k_emis_column_alpha<float><<<gc, COL_BLOCK, hg.nr * sizeof(float), st>>>(hg, djobs, tau_vert_max);
+    return emission_pdf(f64, hg, djobs, njobs, ncolb, beta, st);
 }
 
 // ------------------------------------------------------------------ transmission (Doppler cross-sections)
