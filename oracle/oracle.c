@@ -105,6 +105,11 @@ typedef struct {
     double star_dist;      /* m (used by the host post-scale only) */
     double transit_xy[2];  /* planet centre on the sky plane relative to the stellar disk centre, along the
                               launch basis (e1, e2), m */
+    int32_t g_bias;        /* (the library's band-job options; the oracle reads its g table from orc_cells) */
+    int32_t pad3;
+    double g_beta;
+    int32_t forced_first;  /* forced first scattering (Sect. 4.2) */
+    int32_t cont_abs;      /* continuous absorption (Sect. 4.1) */
 } orc_source;
 
 typedef struct {
@@ -351,6 +356,9 @@ typedef struct {
     int32_t *tr_cell;
     double *tr_len;
     int32_t tr_n, tr_max;
+    /* a second optical depth accumulated along the same path (continuous absorption), or NULL */
+    const double *alpha2;
+    double tau2;
 } march_ctx;
 
 static inline int64_t flat(const orc_grid *G, const int c[3]) { return ((int64_t)c[2] * G->nlat + c[1]) * G->nlon + c[0]; }
@@ -423,10 +431,12 @@ static int march(march_ctx *M, double x[3], const double d[3], int c[3], int ent
             double l = (tau_target - *tau_acc) / a;
             for (int i = 0; i < 3; ++i) x[i] += l * d[i];
             *tau_acc = tau_target;
+            if (M->alpha2) M->tau2 += M->alpha2[idx] * l;
             trace_put(M, (int32_t)idx, l);
             return END_INTERACT;
         }
         *tau_acc += a * best;
+        if (M->alpha2) M->tau2 += M->alpha2[idx] * best;
         trace_put(M, (int32_t)idx, best);
         for (int i = 0; i < 3; ++i) x[i] += best * d[i];
         switch (bestf) {
@@ -450,7 +460,7 @@ int orc_trace_ray(const orc_grid *G, const double *alpha, const double o[3], con
                   int32_t start_cell_flat, int32_t entry_face, int32_t max_seg,
                   int32_t *cells, double *lens, int32_t *end_status)
 {
-    march_ctx M = {G, alpha, 0, (int64_t)1 << 40, cells, lens, 0, max_seg};
+    march_ctx M = {G, alpha, 0, (int64_t)1 << 40, cells, lens, 0, max_seg, NULL, 0.0};
     double x[3] = {o[0], o[1], o[2]};
     int c[3];
     c[0] = start_cell_flat % G->nlon;
@@ -681,6 +691,7 @@ typedef struct {
     const orc_cells *C;
     const orc_source *S;
     const orc_run_args *A;
+    const double *a_sca, *a_abs;   /* continuous absorption: omega alpha and (1 - omega) alpha per cell */
 } job_t;
 
 static void perp_basis(const double s[3], double e1[3], double e2[3])
@@ -727,7 +738,7 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
     const orc_cells *C = J->C;
     const orc_source *S = J->S;
     const orc_run_args *A = J->A;
-    march_ctx M = {G, C->alpha, 0, S->max_steps, tr_cell, tr_len, 0, tr_max};
+    march_ctx M = {G, C->alpha, 0, S->max_steps, tr_cell, tr_len, 0, tr_max, NULL, 0.0};
     double Rtoa = G->r_edges[G->nr];
     double R0 = G->r_edges[0];
     double u[4];
@@ -863,12 +874,54 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
     }
 
     uint32_t ev = 2;
+    int first = 1;
+    /* continuous absorption (Sect. 4.1): flights sample their optical depth in the scattering opacity
+       omega alpha, the weight decays by e^-tau_abs along the path, and every interaction scatters */
+    const int ca = S->cont_abs && J->a_sca != NULL;
     while (transport) {
         draw(A->seed, n, ev, A->job_key, u);
         double tau_t = -log(u[0]);
+        if (first && S->forced_first) {
+            /* forced first scattering (Sect. 4.2): the optical depth tau_m of the first flight's path to
+               the grid boundary (in the flight's own opacity); the packet interacts before it, carrying
+               W (1 - e^-tau_m) with the truncated-exponential tau = -ln(1 - zeta (1 - e^-tau_m)), and
+               W e^-tau_m leaves unscattered.  Not forced when the path runs past the cut-off depth or
+               ends on a reflecting surface. */
+            double tau_m = 0.0;
+            int sm = END_ESCAPE;
+            trace_put(&M, -4, 0.0);
+            if (ca) { M.alpha = J->a_sca; M.alpha2 = J->a_abs; M.tau2 = 0.0; }
+            (void)peel(&M, x, c, d, S->tau_peel_cut, &tau_m, &sm, entry);
+            const double tau2_m = M.tau2;
+            if (ca) { M.alpha = C->alpha; M.alpha2 = NULL; }
+            if (sm == END_CAP) { kahan(&acc->ledger[6], &acc->ledger_c[6], W); break; }
+            if (sm == END_ESCAPE || (sm == END_BOTTOM && !(S->surface_albedo > 0.0))) {
+                const double p = -expm1(-tau_m);
+                const double rem = W * exp(-tau_m);
+                const int q = sm == END_ESCAPE ? 1 : 3;
+                if (ca) {
+                    const double kept = rem * exp(-tau2_m);
+                    kahan(&acc->ledger[q], &acc->ledger_c[q], kept);
+                    kahan(&acc->ledger[2], &acc->ledger_c[2], rem - kept);
+                } else {
+                    kahan(&acc->ledger[q], &acc->ledger_c[q], rem);
+                }
+                W *= p;
+                tau_t = -log1p(-u[0] * p);
+            }
+        }
+        first = 0;
         double tau = 0.0;
         trace_put(&M, -1, 0.0);
+        if (ca) { M.alpha = J->a_sca; M.alpha2 = J->a_abs; M.tau2 = 0.0; }
         int st = march(&M, x, d, c, entry, tau_t, INFINITY, &tau);
+        if (ca) {
+            M.alpha = C->alpha;
+            M.alpha2 = NULL;
+            const double Wn = W * exp(-M.tau2);
+            kahan(&acc->ledger[2], &acc->ledger_c[2], W - Wn);
+            W = Wn;
+        }
         if (st == END_ESCAPE) { kahan(&acc->ledger[1], &acc->ledger_c[1], W); break; }
         if (st == END_BOTTOM && S->surface_albedo > 0.0) {
             /* Lambertian reflection at the lower boundary (Sect. 3): peel-offs with the Lambert phase
@@ -925,7 +978,7 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
         if (st == END_BOTTOM) { kahan(&acc->ledger[3], &acc->ledger_c[3], W); break; }
         if (st != END_INTERACT) { kahan(&acc->ledger[st == END_CAP ? 6 : 7], &acc->ledger_c[st == END_CAP ? 6 : 7], W); break; }
         int64_t idx = flat(G, c);
-        double om = C->omega ? C->omega[idx] : 0.0;
+        double om = ca ? 1.0 : (C->omega ? C->omega[idx] : 0.0);
         double gg = C->g ? C->g[idx] : 0.0;
         double pg = C->pgas ? C->pgas[idx] : 1.0;
         int capped = 0;
@@ -1031,7 +1084,20 @@ static void *worker(void *arg)
 int orc_run(const orc_grid *G, const orc_cells *C, const orc_source *S, orc_run_args *A)
 {
     if (S->n_obs < 1 || S->n_obs > ORC_MAX_OBS) return -1;
-    job_t J = {G, C, S, A};
+    job_t J = {G, C, S, A, NULL, NULL};
+    double *a_sca = NULL, *a_abs = NULL;
+    if (S->cont_abs && C->omega) {
+        const int64_t ncell = (int64_t)G->nlon * G->nlat * G->nr;
+        a_sca = (double *)malloc(sizeof(double) * (size_t)ncell);
+        a_abs = (double *)malloc(sizeof(double) * (size_t)ncell);
+        if (!a_sca || !a_abs) { free(a_sca); free(a_abs); return -2; }
+        for (int64_t i = 0; i < ncell; ++i) {
+            a_sca[i] = C->alpha[i] * C->omega[i];
+            a_abs[i] = C->alpha[i] - a_sca[i];
+        }
+        J.a_sca = a_sca;
+        J.a_abs = a_abs;
+    }
     int64_t nch = (A->n_run + CHUNK - 1) / CHUNK;
     acc_t *chunks = (acc_t *)calloc((size_t)(nch > 0 ? nch : 1), sizeof(acc_t));
     if (!chunks) return -2;
@@ -1071,6 +1137,8 @@ int orc_run(const orc_grid *G, const orc_cells *C, const orc_source *S, orc_run_
     if (A->ledger) for (int q = 0; q < 8; ++q) A->ledger[q] = ls[q];
     if (A->steps) A->steps[0] = steps;
     free(chunks);
+    free(a_sca);
+    free(a_abs);
     return cf_oom ? -3 : 0;
 }
 

@@ -58,7 +58,9 @@ class Source_c(C.Structure):
                 ("scatter_emission", C.c_int32), ("pad", C.c_int32), ("max_steps", C.c_int64),
                 ("cloud_phase", C.c_int32), ("pad2", C.c_int32), ("surface_albedo", C.c_double),
                 ("trans_scatter", C.c_int32), ("ld_law", C.c_int32), ("ld_coef", C.c_double * 4),
-                ("star_radius", C.c_double), ("star_dist", C.c_double), ("transit_xy", C.c_double * 2)]
+                ("star_radius", C.c_double), ("star_dist", C.c_double), ("transit_xy", C.c_double * 2),
+                ("g_bias", C.c_int32), ("pad3", C.c_int32), ("g_beta", C.c_double),
+                ("forced_first", C.c_int32), ("cont_abs", C.c_int32)]
 
 
 class Run_c(C.Structure):
@@ -343,6 +345,8 @@ def _source_struct(src, obs):
     s.star_dist = float(getattr(op, "star_dist", 0.0))
     for i, v in enumerate(getattr(op, "transit_xy", (0.0, 0.0))):
         s.transit_xy[i] = float(v)
+    s.forced_first = int(getattr(op, "forced_first", 0))
+    s.cont_abs = int(getattr(op, "cont_abs", 0))
     return s, len(obs)
 
 

@@ -138,6 +138,8 @@ class Options:
     transit_xy: tuple = (0.0, 0.0)   # planet centre on the stellar disk along the launch basis (e1, e2), m
     g_bias: int = 0              # emission band jobs (per-packet g): 0 q = p, 1 uniform, 2 composite
     g_beta: float = 0.5          # composite: q = (1 - g_beta) p + g_beta / N_g
+    forced_first: int = 0        # forced first scattering
+    cont_abs: int = 0            # continuous absorption
 
 
 @dataclasses.dataclass
@@ -602,7 +604,7 @@ def uniform_scattering_sphere(alpha=8.0e-9, omega=1.0e-3, g=0.5, R0=R_JUP, H_atm
 
 
 def slab_sphere_albedo(omega=0.5, tau=20.0, phase="iso", g=0.0, n_packets=100_000, seed=12, thin=1.0e-4,
-                       nlon=8, nlat=8, survival=1, surface_albedo=0.0, obs=None):
+                       nlon=8, nlat=8, survival=1, surface_albedo=0.0, obs=None, forced_first=0, cont_abs=0):
     """Homogeneous one-layer atmosphere of thickness thin * R0 and vertical optical depth tau on a
     black (or Lambertian, surface_albedo) sphere: locally a plane-parallel slab.  phase = 'iso'
     (HG with g = 0), 'hg', 'tthg' (two-term HG of asymmetry g) or 'rayleigh'."""
@@ -620,7 +622,7 @@ def slab_sphere_albedo(omega=0.5, tau=20.0, phase="iso", g=0.0, n_packets=100_00
     src = Source(star=np.array([1.0, 0.0, 0.0]),
                  obs=np.array([[1.0, 0.0, 0.0]]) if obs is None else np.atleast_2d(np.asarray(obs, np.float64)),
                  opts=Options(survival=survival, w_rr=1e-4, cloud_phase=1 if phase == "tthg" else 0,
-                              surface_albedo=surface_albedo))
+                              surface_albedo=surface_albedo, forced_first=forced_first, cont_abs=cont_abs))
     jobs = [Job(lam_idx=0, g_idx=0, n_packets=n_packets, key=0)]
     return Workload(f"slab_{phase}_w{omega}_t{tau}", MODE_ALBEDO, grid, opac, src, jobs, seed)
 
