@@ -30,7 +30,9 @@ constexpr int ACC_FLAGS = MAX_OBS + 10;
 constexpr int ACC_SLOTS = 32;            // padded (256 bytes per job)
 constexpr double FIX_SCALE = 4294967296.0;   // 2^32: fixed-point resolution of tallies and ledger
 
-enum { K_FLIGHT = 0, K_PEEL = 1, K_CHORD = 2 };
+// ray kinds: a flight to an interaction, a peel-off, a limb chord, and the march that measures a forced
+// first flight's optical depth to the grid boundary
+enum { K_FLIGHT = 0, K_PEEL = 1, K_CHORD = 2, K_FORCE = 3 };
 enum { E_CONT = -1, E_INTERACT = 0, E_ESCAPE = 1, E_BOTTOM = 2, E_CUTOFF = 3, E_CAP = 4, E_LOST = 5 };
 // exit faces, encoded as the cell-index change they cause: bits 0-1 dk + 1, bits 2-3 dj + 1, bits 4-5 di + 1
 constexpr int face_code(int dk, int dj, int di) { return (dk + 1) | ((dj + 1) << 2) | ((di + 1) << 4); }
@@ -103,6 +105,8 @@ struct DevJob {
     const double *ginfo;        // band job: each g-ordinate's info block, GINFO_STRIDE doubles apart
     double surf_as, ld_c[4], star_r, tr_x, tr_y;   // surface albedo; limb darkening, stellar radius, planet offset
     float surf_as_f, ld_c_f[4], star_r_f, tr_x_f, tr_y_f;
+    int32_t forced_first;       // forced first scattering (albedo; transmission with multiple scattering)
+    int32_t cont_abs;           // continuous absorption (scattering records only)
 };
 
 // job constants in the march precision (FP32 marches read the copies rounded on the host)

@@ -27,6 +27,7 @@ template <typename real> struct Ray {
     real crz;               // (o x d)_z: sign gives the direction of azimuthal motion
     real B, dz2;            // zc dz and dz^2 (cone coefficients that depend on the ray only)
     real tau, tau_target;   // accumulated optical depth; interaction target (< 0: none)
+    real tau2;              // continuous absorption: absorption optical depth along a flight
     int i, j, k;            // current cell
 };
 

@@ -237,7 +237,12 @@ __global__ void __launch_bounds__(COL_BLOCK) k_emis_column_alpha(DevGrid G, cons
             const real alpha = rec[idx];
             const bool incl = above < tmax;
             above += alpha * s_dr[k];
-            const double L = 4.0 * PI * G.vol[idx] * (c1 / expm1(hck / (double)G.T[idx])) * (double)alpha;
+            // B_lambda(T_i) per cell and job: FP64 for FP64 runs; FP32 runs evaluate the exponential in FP32
+            // (~1e-7 relative, below the FP32 extinction's own rounding), the sums stay FP64
+            double B;
+            if constexpr (sizeof(real) == 8) B = c1 / expm1(hck / (double)G.T[idx]);
+            else B = (double)((float)c1 / expm1f((float)hck / G.T[idx]));
+            const double L = 4.0 * PI * G.vol[idx] * B * (double)alpha;
             if (lum) lum[idx] = L;
             if (incl) {
                 lb[idx] = L;

@@ -40,6 +40,7 @@ template <typename real> struct Packet {
 // per-job constants kept in registers for a work item
 template <typename real> struct JobC {
     int max_steps;
+    int contabs;           // continuous absorption: flights march in omega alpha and accumulate (1 - omega) alpha
     real tau_cut;
     const real *rec;       // march table: alpha, or the first component of the albedo records
     int rec_stride;        // 4 for albedo records, else 1
@@ -103,6 +104,7 @@ __device__ __forceinline__ void start_ray(Packet<real> &P, real ox, real oy, rea
     P.ray.j = j;
     P.ray.k = k;
     P.ray.tau = (real)0;
+    P.ray.tau2 = (real)0;
     P.ray.tau_target = tau_target;
     P.kind = kind;
 }
@@ -115,13 +117,36 @@ __device__ __forceinline__ void start_peel(Packet<real> &P, const DevJob &J, Sin
                     P.cj, P.ck, K_PEEL, (real)-1);
 }
 
+// a flight from the packet's point; forced: its optical depth follows the exponential truncated at the
+// boundary, -ln(1 - zeta p) with p = 1 - e^-tau_m (Sect. 4.2; p may round to 1 for deep paths, where the
+// truncated form still applies)
 template <typename real, class SinkT>
-__device__ __forceinline__ void start_flight(Packet<real> &P, const DevJob &J, SinkT &S, real dx, real dy, real dz)
+__device__ __forceinline__ void start_flight(Packet<real> &P, const DevJob &J, SinkT &S, real dx, real dy, real dz,
+                                             bool forced = false, real p = (real)1)
 {
     const uint4 w = draw_words(J.seed, P.n, P.ev, J.key);
-    const real tau = -M<real>::log_(u01<real>(w.x));
+    real tau;
+    if (forced) {
+        if constexpr (sizeof(real) == 8) tau = -log1p(-u01<real>(w.x) * p);
+        else tau = -log1pf(-u01<real>(w.x) * p);
+    } else {
+        tau = -M<real>::log_(u01<real>(w.x));
+    }
     S.trace(P.n, -1, (real)0);
     start_ray<real>(P, P.ix, P.iy, P.iz, dx, dy, dz, P.ci, P.cj, P.ck, K_FLIGHT, tau);
+}
+
+// the first flight from the launch point along -star: forced (a boundary march first) or plain
+template <typename real, class SinkT>
+__device__ __forceinline__ void start_first_flight(Packet<real> &P, const DevJob &J, SinkT &S)
+{
+    if (J.forced_first) {
+        S.trace(P.n, -4, (real)0);
+        start_ray<real>(P, P.ix, P.iy, P.iz, -JV<real>::star(J, 0), -JV<real>::star(J, 1), -JV<real>::star(J, 2), P.ci,
+                        P.cj, P.ck, K_FORCE, (real)-1);
+    } else {
+        start_flight<real>(P, J, S, -JV<real>::star(J, 0), -JV<real>::star(J, 1), -JV<real>::star(J, 2));
+    }
 }
 
 template <typename real, class SinkT>
@@ -249,7 +274,7 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
         P.ck = G.nr - 1;
         if constexpr (SCAT) {
             if (J.mode == GCMC_ALBEDO) {
-                start_flight<real>(P, J, S, d[0], d[1], d[2]);
+                start_first_flight<real>(P, J, S);
                 return;
             }
         }
@@ -426,6 +451,42 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
 {
     Ray<real> &R = P.ray;
     if constexpr (SCAT) {
+        if (P.kind == K_FORCE) {
+            // forced first scattering (Sect. 4.2): R.tau is the optical depth of the first flight's path to
+            // the grid boundary; W e^-tau leaves unscattered, W (1 - e^-tau) interacts before it.  Not
+            // forced past the cut-off depth or when the path ends on a reflecting surface.
+            if (e == E_CAP) {
+                S.ledger(6, P.W);
+                finish<real>(P, S);
+                return;
+            }
+            real p = (real)1;
+            const bool forced = e == E_ESCAPE || (e == E_BOTTOM && !(JV<real>::surf_as(J) > (real)0));
+            if (forced) {
+                real em;
+                if constexpr (sizeof(real) == 8) em = expm1(-R.tau);
+                else em = expm1f(-R.tau);
+                p = -em;
+                const real rem = P.W * M<real>::exp_(-R.tau);
+                const int q = e == E_ESCAPE ? 1 : 3;
+                if (J.cont_abs) {
+                    const real kept = rem * M<real>::exp_(-R.tau2);
+                    S.ledger(q, kept);
+                    S.ledger(2, rem - kept);
+                } else {
+                    S.ledger(q, rem);
+                }
+                P.W *= p;
+            }
+            start_flight<real>(P, J, S, -JV<real>::star(J, 0), -JV<real>::star(J, 1), -JV<real>::star(J, 2), forced, p);
+            return;
+        }
+        if (P.kind == K_FLIGHT && J.cont_abs) {
+            // continuous absorption (Sect. 4.1): the weight decays by e^-tau_abs along the flight
+            const real Wn = P.W * M<real>::exp_(-R.tau2);
+            S.ledger(2, P.W - Wn);
+            P.W = Wn;
+        }
         if (P.kind == K_FLIGHT) {
             if (e == E_BOTTOM && JV<real>::surf_as(J) > (real)0) {
                 // a reflecting lower boundary: surface point and its outward normal (kept in fx, fy, fz),
@@ -473,6 +534,7 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
                 P.gg = rc.g;
                 P.pg = rc.pg;
             }
+            if (J.cont_abs) P.om = (real)1;   // continuous absorption: the interaction is a scattering
             P.stage = 1;
             P.obs = 0;
             start_peel<real>(P, J, S);
@@ -547,7 +609,7 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
     if constexpr (SCAT) {
         if (J.trans_scatter) {
             // multiple scattering (Sect. 5.1): the packet itself flies from its launch point along -star
-            start_flight<real>(P, J, S, -JV<real>::star(J, 0), -JV<real>::star(J, 1), -JV<real>::star(J, 2));
+            start_first_flight<real>(P, J, S);
             return;
         }
     }
@@ -572,14 +634,29 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
     const int idx = (R.k * T.nlat + R.j) * T.nlon + R.i;
     real a;
     const int go = BAND ? P.goff : 0;
-    if constexpr (SCAT) a = __ldg(jc.rec + jc.rec_stride * idx + go);
-    else a = __ldg(jc.rec + idx + go);
+    real a2 = (real)0;
+    if constexpr (SCAT) {
+        if (jc.contabs) {
+            // continuous absorption: flights (and the forcing march) run in the scattering opacity omega alpha
+            // and accumulate the absorption (1 - omega) alpha
+            const auto aw = __ldg(reinterpret_cast<const typename Pair<real>::type *>(jc.rec + 4 * idx));
+            const bool fl = P.kind == K_FLIGHT || P.kind == K_FORCE;
+            const real as = aw.x * aw.y;
+            a = fl ? as : aw.x;
+            a2 = fl ? aw.x - as : (real)0;
+        } else {
+            a = __ldg(jc.rec + jc.rec_stride * idx + go);
+        }
+    } else {
+        a = __ldg(jc.rec + idx + go);
+    }
     int face = F_NONE;
     const real sx = cell_exit<real>(G, T, R, face);
     const real seg = sx - R.s;
     if constexpr (SCAT) {
         if (R.tau_target >= (real)0 && a > (real)0 && R.tau + a * seg >= R.tau_target) {
             const real l = M<real>::div_(R.tau_target - R.tau, a);
+            if (jc.contabs) R.tau2 += a2 * l;
             S.trace(P.n, idx, l);
             R.s += l;
             R.tau = R.tau_target;
@@ -590,6 +667,9 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
         }
     }
     R.tau += a * seg;
+    if constexpr (SCAT) {
+        if (jc.contabs) R.tau2 += a2 * seg;
+    }
     S.trace(P.n, idx, seg);
     R.s = sx;
     int e = cross_face(T, face, R.i, R.j, R.k);
@@ -638,6 +718,7 @@ template <typename real> __device__ __forceinline__ JobC<real> job_consts(const 
     c.tau_cut = (real)J.tau_cut;
     c.rec = reinterpret_cast<const real *>(J.rec);
     c.rec_stride = J.rec4 ? 4 : 1;
+    c.contabs = J.cont_abs;
     return c;
 }
 
