@@ -15,7 +15,8 @@ request-latency summary (p50/p99) of a 1000-request sample of the serving stream
 Other workloads (--workload): albedo (32x16x20, FP64), phasecurve (40 wavelengths x 24 phases),
 transmission (9532 wavelengths, Doppler cross sections), transit-scatter (40 optical wavelengths in
 transit with multiple scattering and limb darkening), band (the emission workload as 30 band jobs
-whose packets draw their g-ordinate), serving (the full request stream).
+whose packets draw their g-ordinate), emission-hires (952 of the 9532 high-resolution wavelengths in
+emission with Doppler-shifted cross-sections), serving (the full request stream).
 """
 import argparse
 import json
@@ -58,7 +59,9 @@ def parse():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
     ap.add_argument("--workload", default="emission", choices=["emission", "albedo", "phasecurve", "transmission", "transit-scatter", "band",
-                             "serving"])
+                             "emission-hires", "serving"])
+    ap.add_argument("--forced-first", action="store_true", help="scattering workloads: forced first scattering")
+    ap.add_argument("--cont-abs", action="store_true", help="scattering workloads: continuous absorption")
     ap.add_argument("--requests", type=int, default=10_000, help="serving: requests in the stream")
     ap.add_argument("--hbm-budget-gb", type=float, default=16.0, help="serving: admitted workspace")
     ap.add_argument("--serving-requests", type=int, default=1000,
@@ -84,21 +87,27 @@ def workload(args, rank):
         wl = synth.config4_transmission()
     elif args.workload == "transit-scatter":
         wl = synth.config6_transit_scatter()
+    elif args.workload == "emission-hires":
+        wl = synth.config7_emission_hires(lam_subset=range(0, 9532, 10))
     elif args.workload == "band":
         wl = synth.config2_emission(n_packets=args.packets * args.gpoints, nb=30, ng=8, bands=range(args.bands),
                                     per_packet_g=True, g_bias=2)
     else:
         wl = synth.config2_emission(n_packets=args.packets, nb=30, ng=8, bands=range(args.bands),
                                     gpoints=range(args.gpoints))
+    if args.forced_first or args.cont_abs:
+        wl.source.opts.forced_first = int(args.forced_first)
+        wl.source.opts.cont_abs = int(args.cont_abs)
+        wl.name += ("_forced" if args.forced_first else "") + ("_contabs" if args.cont_abs else "")
     wl.seed = shard.rank_seed(wl.seed, rank)
     return wl
 
 
 # oracle sample per workload for the CPU baseline: (jobs, packets per job or None for all)
 CPU_SAMPLE = {"emission": (48, 1_000_000), "albedo": (1, None), "phasecurve": (24, None), "transmission": (480, None),
-              "transit-scatter": (8, 400_000), "band": (12, 1_000_000)}
+              "transit-scatter": (8, 400_000), "band": (12, 1_000_000), "emission-hires": (40, None)}
 REF_SAMPLE = {"emission": (2, 200_000), "albedo": (1, None), "phasecurve": (2, None), "transmission": (96, None),
-              "transit-scatter": (2, 20_000), "band": (2, 200_000)}
+              "transit-scatter": (2, 20_000), "band": (2, 200_000), "emission-hires": (4, None)}
 
 
 class ClockSampler:
@@ -423,7 +432,8 @@ def main():
         jb = gcmc.workload_jobs(wl, g2, o2, ctx.set_sources(g2, wl.source, prec))
         tl, st2 = ctx.run_batch(jb, cfg=cfg)
         obs = [ctx.postscale(g2, wl.mode, tl[q][0], j.n_packets, st2[q].l_tot) for q, j in enumerate(wl.jobs)]
-        if wl.mode == gcmc.EMISSION and wl.jobs[0].g_idx < 0:     # band jobs: L_p already sums over g
+        if wl.mode == gcmc.EMISSION and (wl.jobs[0].g_idx < 0 or wl.opac.kind == gcmc.OPAC_XSEC):
+            # band jobs (L_p sums over g) and high-resolution wavelengths: the mean over jobs
             F_band = {"spectrum_F_p_band_mean": float(np.mean([o["F_p"] for o in obs]))}
         elif wl.mode == gcmc.EMISSION:
             F = np.zeros((args.bands, args.gpoints))

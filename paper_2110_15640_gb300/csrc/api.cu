@@ -184,7 +184,7 @@ struct Plan {
     size_t off_jobs = 0, off_prep = 0, off_acc = 0, off_work = 0, off_gather = 0, ws_bytes = 0;
     int64_t total_items = 0;
     bool scatter = false;               // some job follows scattered packets (albedo)
-    bool band = false;                  // some job is a band job (per-packet g-ordinate tables)
+    int feat = 0;                       // optional kernel code the jobs need (FEAT_BAND, FEAT_EXT)
     int one_grid = 1;                   // every job uses the same grid
     int tab_n = 0;                      // largest march-table size (pair entries) of the jobs' grids
 };
@@ -390,9 +390,12 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
         d.n_tal = j.mode == GCMC_TRANSMISSION ? 1 + d.trans_scatter : d.n_obs;
         d.forced_first = s.forced_first ? 1 : 0;
         d.cont_abs = s.cont_abs && d.rec4 ? 1 : 0;   // needs the scattering records' omega
+        if (s.surface_albedo > 0.0 || s.cloud_phase == GCMC_CLOUD_TTHG || (j.mode == GCMC_TRANSMISSION &&
+            (s.trans_scatter || s.ld_law != GCMC_LD_NONE)) || d.forced_first || d.cont_abs)
+            P.feat |= FEAT_EXT;
         d.ng_s = P.ng_s[q];
         if (d.ng_s) {
-            P.band = true;
+            P.feat |= FEAT_BAND;
             d.g_bias = s.g_bias;
             d.g_beta = s.g_beta;
             d.gw = ctx->opacs[j.opac_id].kt.gw;
@@ -1117,7 +1120,7 @@ gcmc_status gcmc_run_packets(gcmc_ctx *ctx, const gcmc_job *job, double *tallies
     if ((s = stage(ctx, P, base))) return s;
     prof_mark(ctx);
     const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
-    cudaError_t e = launch_plain(P.jobs[0].precision, P.scatter, P.band, ctx->d_grids, dj, 0, job->n_packets, nullptr, P.tab_n,
+    cudaError_t e = launch_plain(P.jobs[0].precision, P.scatter, P.feat, ctx->d_grids, dj, 0, job->n_packets, nullptr, P.tab_n,
                                  ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "transport launch");
     prof_mark(ctx);
@@ -1142,7 +1145,7 @@ gcmc_status gcmc_run_batch(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, cons
     if ((s = stage(ctx, P, base))) return s;
     prof_mark(ctx);
     const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
-    cudaError_t e = launch_persistent(prec, P.scatter, P.band, ctx->d_grids, dj, n_jobs, P.total_items, chunk, cfg ? cfg->block : 0,
+    cudaError_t e = launch_persistent(prec, P.scatter, P.feat, ctx->d_grids, dj, n_jobs, P.total_items, chunk, cfg ? cfg->block : 0,
                                       cfg ? cfg->blocks_per_sm : 0, cfg && cfg->interval > 0 ? cfg->interval : 1,
                                       cfg && cfg->refill_min > 0 ? cfg->refill_min : 16, P.one_grid, P.tab_n,
                                       reinterpret_cast<unsigned long long *>(base + P.off_work), ctx->stream);
@@ -1173,7 +1176,7 @@ gcmc_status gcmc_run_contrib(gcmc_ctx *ctx, const gcmc_job *job, double *tallies
     P.jobs[0].cf_ncell = ncell;
     if (e == cudaSuccess && (s = stage(ctx, P, base)) == GCMC_OK) {
         const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
-        e = launch_persistent(P.jobs[0].precision, P.scatter, P.band, ctx->d_grids, dj, 1, P.total_items, chunk, 128, 0, 4, 8,
+        e = launch_persistent(P.jobs[0].precision, P.scatter, P.feat, ctx->d_grids, dj, 1, P.total_items, chunk, 128, 0, 4, 8,
                               P.one_grid, P.tab_n, reinterpret_cast<unsigned long long *>(base + P.off_work), ctx->stream);
     }
     std::vector<unsigned long long> h(ncf);
@@ -1208,7 +1211,7 @@ gcmc_status gcmc_submit(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, const g
         return s;
     }
     const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
-    cudaError_t e = launch_persistent(prec, P.scatter, P.band, ctx->d_grids, dj, n_jobs, P.total_items, chunk, cfg ? cfg->block : 0,
+    cudaError_t e = launch_persistent(prec, P.scatter, P.feat, ctx->d_grids, dj, n_jobs, P.total_items, chunk, cfg ? cfg->block : 0,
                                       cfg ? cfg->blocks_per_sm : 0, cfg && cfg->interval > 0 ? cfg->interval : 1,
                                       cfg && cfg->refill_min > 0 ? cfg->refill_min : 16, P.one_grid, P.tab_n,
                                       reinterpret_cast<unsigned long long *>(base + P.off_work), ctx->stream);
@@ -1290,7 +1293,7 @@ gcmc_status gcmc_run_packets_debug(gcmc_ctx *ctx, const gcmc_job *job, int64_t p
     }
     if (e == cudaSuccess) {
         const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
-        e = launch_plain(P.jobs[0].precision, P.scatter, P.band, ctx->d_grids, dj, packet0, n_run, &hl, P.tab_n, ctx->stream);
+        e = launch_plain(P.jobs[0].precision, P.scatter, P.feat, ctx->d_grids, dj, packet0, n_run, &hl, P.tab_n, ctx->stream);
     }
     if (e == cudaSuccess) {
         if (pk_f) e = cudaMemcpyAsync(pk_f, hl.pk_f, (size_t)n_run * nobs * 8, cudaMemcpyDeviceToHost, ctx->stream);
@@ -2064,7 +2067,7 @@ gcmc_status gcmc_graph_create(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, c
     s = stage(ctx, P, base, nullptr, g->stage_h);
     if (!s) {
         const DevJob *dj = reinterpret_cast<const DevJob *>(base + P.off_jobs);
-        e = launch_persistent(prec, P.scatter, P.band, ctx->d_grids, dj, n_jobs, P.total_items, chunk, cfg ? cfg->block : 0,
+        e = launch_persistent(prec, P.scatter, P.feat, ctx->d_grids, dj, n_jobs, P.total_items, chunk, cfg ? cfg->block : 0,
                               cfg ? cfg->blocks_per_sm : 0, cfg && cfg->interval > 0 ? cfg->interval : 1,
                               cfg && cfg->refill_min > 0 ? cfg->refill_min : 16, P.one_grid, P.tab_n,
                               reinterpret_cast<unsigned long long *>(base + P.off_work), ctx->stream);

@@ -148,9 +148,15 @@ cudaError_t launch_serve(const DevGrid *grids, const ServeQueue &q, int block, i
 
 // transport
 size_t transport_smem(int block);
-cudaError_t launch_plain(int precision, bool scatter, bool band, const DevGrid *grids, const DevJob *job, int64_t packet0,
+// Optional code compiled into a transport-kernel variant (template FEAT): band jobs' per-packet
+// g-ordinate tables, and the optional physics of scattered packets (surfaces, two-term HG clouds,
+// multiple scattering in transmission, stellar limb darkening, forced first scattering, continuous
+// absorption).  Batches that use none of them run variants without that code.
+constexpr int FEAT_BAND = 1, FEAT_EXT = 2;
+
+cudaError_t launch_plain(int precision, bool scatter, int feat, const DevGrid *grids, const DevJob *job, int64_t packet0,
                          int64_t n_run, const HostLog *hl, int tab_entries_n, cudaStream_t st);
-cudaError_t launch_persistent(int precision, bool scatter, bool band, const DevGrid *grids, const DevJob *jobs, int n_jobs,
+cudaError_t launch_persistent(int precision, bool scatter, int feat, const DevGrid *grids, const DevJob *jobs, int n_jobs,
                               int64_t total_items, int chunk, int block, int blocks_per_sm, int interval, int refill_min,
                               int one_grid, int tab_n, unsigned long long *work, cudaStream_t st);
 

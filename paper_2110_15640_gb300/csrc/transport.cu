@@ -224,8 +224,7 @@ __device__ __noinline__ int band_draw(const DevJob &J, const DevGrid &G, int64_t
 }
 
 // S2: packet launch (Sect. 5: albedo disk, emission hybrid pdf, transmission annulus)
-// (BAND: the kernel may run band jobs; the g draw is compiled only there)
-template <typename real, bool SCAT, bool BAND, class SinkT>
+template <typename real, bool SCAT, int FEAT, class SinkT>
 __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64_t n, SinkT &S)
 {
     P.n = n;
@@ -258,12 +257,14 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
         int i, j;
         locate_angles<real>(G, x[0], x[1], x[2], i, j);
         P.W = P.W0 = (real)1;
-        if (J.mode == GCMC_TRANSMISSION && J.ld_law != GCMC_LD_NONE) {
-            // the chord's sky-plane position on the stellar disk gives the stellar zenith-angle cosine
-            const real X = JV<real>::tr_x(J) + b * cp, Y = JV<real>::tr_y(J) + b * sp;
-            const real Rs = JV<real>::star_r(J);
-            const real q = M<real>::div_(X * X + Y * Y, Rs * Rs);
-            P.W = P.W0 = q < (real)1 ? limb<real>(J, M<real>::sqrt_((real)1 - q)) : (real)0;
+        if constexpr ((FEAT & FEAT_EXT) != 0) {
+            if (J.mode == GCMC_TRANSMISSION && J.ld_law != GCMC_LD_NONE) {
+                // the chord's sky-plane position on the stellar disk gives the stellar zenith-angle cosine
+                const real X = JV<real>::tr_x(J) + b * cp, Y = JV<real>::tr_y(J) + b * sp;
+                const real Rs = JV<real>::star_r(J);
+                const real q = M<real>::div_(X * X + Y * Y, Rs * Rs);
+                P.W = P.W0 = q < (real)1 ? limb<real>(J, M<real>::sqrt_((real)1 - q)) : (real)0;
+            }
         }
         S.ledger(0, P.W0);
         P.ix = x[0];
@@ -274,7 +275,8 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
         P.ck = G.nr - 1;
         if constexpr (SCAT) {
             if (J.mode == GCMC_ALBEDO) {
-                start_first_flight<real>(P, J, S);
+                if constexpr ((FEAT & FEAT_EXT) != 0) start_first_flight<real>(P, J, S);
+                else start_flight<real>(P, J, S, d[0], d[1], d[2]);
                 return;
             }
         }
@@ -293,7 +295,7 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
     const real *wcell = reinterpret_cast<const real *>(J.wcell);
     real Wg = (real)1;
     int idx;
-    if (BAND && J.ng_s > 0) {
+    if ((FEAT & FEAT_BAND) && J.ng_s > 0) {
         idx = band_draw<real>(J, G, n, w.x, P.goff, Wg);
         wcell += P.goff;
     } else {
@@ -347,7 +349,7 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
     start_peel<real>(P, J, S);
 }
 
-template <typename real, class SinkT>
+template <typename real, int FEAT, class SinkT>
 __device__ void after_peels_scatter(Packet<real> &P, const DevJob &J, SinkT &S)
 {
     const real om = P.om;
@@ -387,10 +389,12 @@ __device__ void after_peels_scatter(Packet<real> &P, const DevJob &J, SinkT &S)
     } else {
         // cloud: HG, or the two-term HG whose term is chosen by u1 rescaled to (u1 - P_gas) / (1 - P_gas)
         real gs = P.gg;
-        if (J.cloud_phase == GCMC_CLOUD_TTHG) {
-            real g2, a;
-            tthg_terms<real>(P.gg, g2, a);
-            gs = M<real>::div_(u1 - P.pg, (real)1 - P.pg) < a ? P.gg : g2;
+        if constexpr ((FEAT & FEAT_EXT) != 0) {
+            if (J.cloud_phase == GCMC_CLOUD_TTHG) {
+                real g2, a;
+                tthg_terms<real>(P.gg, g2, a);
+                gs = M<real>::div_(u1 - P.pg, (real)1 - P.pg) < a ? P.gg : g2;
+            }
         }
         mu = sample_hg<real>(gs, u2, JV<real>::hg_eps(J));
     }
@@ -446,11 +450,12 @@ __device__ void after_peels_surface(Packet<real> &P, const DevJob &J, SinkT &S)
     start_flight<real>(P, J, S, dx, dy, dz);
 }
 
-template <typename real, bool SCAT, class SinkT>
+template <typename real, bool SCAT, int FEAT, class SinkT>
 __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int idx)
 {
+    constexpr bool EXT = (FEAT & FEAT_EXT) != 0;
     Ray<real> &R = P.ray;
-    if constexpr (SCAT) {
+    if constexpr (SCAT && EXT) {
         if (P.kind == K_FORCE) {
             // forced first scattering (Sect. 4.2): R.tau is the optical depth of the first flight's path to
             // the grid boundary; W e^-tau leaves unscattered, W (1 - e^-tau) interacts before it.  Not
@@ -487,8 +492,7 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
             S.ledger(2, P.W - Wn);
             P.W = Wn;
         }
-        if (P.kind == K_FLIGHT) {
-            if (e == E_BOTTOM && JV<real>::surf_as(J) > (real)0) {
+        if (P.kind == K_FLIGHT && e == E_BOTTOM && JV<real>::surf_as(J) > (real)0) {
                 // a reflecting lower boundary: surface point and its outward normal (kept in fx, fy, fz),
                 // then the peel-offs towards the observers above its horizon
                 P.ix = R.cx + R.s * R.dx;
@@ -507,7 +511,10 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
                 if (P.obs < J.n_obs) start_peel<real>(P, J, S);
                 else after_peels_surface<real>(P, J, S);
                 return;
-            }
+        }
+    }
+    if constexpr (SCAT) {
+        if (P.kind == K_FLIGHT) {
             if (e != E_INTERACT) {
                 S.ledger(e == E_ESCAPE ? 1 : e == E_BOTTOM ? 3 : e == E_CAP ? 6 : 7, P.W);
                 finish<real>(P, S);
@@ -534,7 +541,9 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
                 P.gg = rc.g;
                 P.pg = rc.pg;
             }
-            if (J.cont_abs) P.om = (real)1;   // continuous absorption: the interaction is a scattering
+            if constexpr (EXT) {
+                if (J.cont_abs) P.om = (real)1;   // continuous absorption: the interaction is a scattering
+            }
             P.stage = 1;
             P.obs = 0;
             start_peel<real>(P, J, S);
@@ -556,11 +565,15 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
             f = P.W * ex * (real)(1.0 / (4.0 * PI));
         } else {
             const real mu = P.fx * JV<real>::obs(J, P.obs, 0) + P.fy * JV<real>::obs(J, P.obs, 1) + P.fz * JV<real>::obs(J, P.obs, 2);
-            if (P.stage == 2) f = P.W * JV<real>::surf_as(J) * (mu * (real)(1.0 / PI)) * ex;   // Lambert: mu_o / pi
-            else f = P.W * P.om * theta_mix<real>(mu, P.pg, P.gg, J.cloud_phase == GCMC_CLOUD_TTHG) * ex;
+            if constexpr (EXT) {
+                if (P.stage == 2) f = P.W * JV<real>::surf_as(J) * (mu * (real)(1.0 / PI)) * ex;   // Lambert: mu_o / pi
+                else f = P.W * P.om * theta_mix<real>(mu, P.pg, P.gg, J.cloud_phase == GCMC_CLOUD_TTHG) * ex;
+            } else {
+                f = P.W * P.om * theta_mix<real>(mu, P.pg, P.gg) * ex;
+            }
         }
         int col = P.obs;
-        if constexpr (SCAT) {
+        if constexpr (SCAT && EXT) {
             // transmission: scattered light goes to column 1, weighted by the launch b / R_TOA
             if (J.mode == GCMC_TRANSMISSION) {
                 col = 1;
@@ -575,7 +588,7 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
                       (unsigned long long)to_fix<real>(f));
         }
         ++P.obs;
-        if constexpr (SCAT) {
+        if constexpr (SCAT && EXT) {
             if (P.stage == 2) P.obs = surface_obs<real>(P, J, P.obs);
         }
         if (P.obs < J.n_obs) {
@@ -584,8 +597,13 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
         }
         if constexpr (SCAT) {
             if (J.mode != GCMC_EMISSION) {
-                if (P.stage == 2) after_peels_surface<real>(P, J, S);
-                else after_peels_scatter<real>(P, J, S);
+                if constexpr (EXT) {
+                    if (P.stage == 2) {
+                        after_peels_surface<real>(P, J, S);
+                        return;
+                    }
+                }
+                after_peels_scatter<real, FEAT>(P, J, S);
                 return;
             }
         }
@@ -606,7 +624,7 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
         finish<real>(P, S);
         return;
     }
-    if constexpr (SCAT) {
+    if constexpr (SCAT && EXT) {
         if (J.trans_scatter) {
             // multiple scattering (Sect. 5.1): the packet itself flies from its launch point along -star
             start_first_flight<real>(P, J, S);
@@ -617,9 +635,9 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
     finish<real>(P, S);
 }
 
-// one cell step (S3-S7) of the packet's current ray; BAND kernels read the packet's g-ordinate table
-// (band jobs), the others skip that offset
-template <typename real, bool SCAT, bool BAND, class SinkT>
+// one cell step (S3-S7) of the packet's current ray; FEAT_BAND kernels read the packet's g-ordinate
+// table (band jobs), FEAT_EXT kernels carry continuous absorption
+template <typename real, bool SCAT, int FEAT, class SinkT>
 __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const DevGrid &G, const Tabs<real> &T,
                                      const JobC<real> &jc, SinkT &S)
 {
@@ -633,9 +651,9 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
     ++P.steps;
     const int idx = (R.k * T.nlat + R.j) * T.nlon + R.i;
     real a;
-    const int go = BAND ? P.goff : 0;
+    const int go = (FEAT & FEAT_BAND) ? P.goff : 0;
     real a2 = (real)0;
-    if constexpr (SCAT) {
+    if constexpr (SCAT && (FEAT & FEAT_EXT) != 0) {
         if (jc.contabs) {
             // continuous absorption: flights (and the forcing march) run in the scattering opacity omega alpha
             // and accumulate the absorption (1 - omega) alpha
@@ -647,6 +665,8 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
         } else {
             a = __ldg(jc.rec + jc.rec_stride * idx + go);
         }
+    } else if constexpr (SCAT) {
+        a = __ldg(jc.rec + jc.rec_stride * idx + go);
     } else {
         a = __ldg(jc.rec + idx + go);
     }
@@ -656,7 +676,9 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
     if constexpr (SCAT) {
         if (R.tau_target >= (real)0 && a > (real)0 && R.tau + a * seg >= R.tau_target) {
             const real l = M<real>::div_(R.tau_target - R.tau, a);
-            if (jc.contabs) R.tau2 += a2 * l;
+            if constexpr ((FEAT & FEAT_EXT) != 0) {
+                if (jc.contabs) R.tau2 += a2 * l;
+            }
             S.trace(P.n, idx, l);
             R.s += l;
             R.tau = R.tau_target;
@@ -667,7 +689,7 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
         }
     }
     R.tau += a * seg;
-    if constexpr (SCAT) {
+    if constexpr (SCAT && (FEAT & FEAT_EXT) != 0) {
         if (jc.contabs) R.tau2 += a2 * seg;
     }
     S.trace(P.n, idx, seg);
@@ -684,11 +706,11 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
 }
 
 // the end of the packet's current ray: tally, next ray, interaction or finish
-template <typename real, bool SCAT, class SinkT>
+template <typename real, bool SCAT, int FEAT, class SinkT>
 __device__ __forceinline__ void settle(Packet<real> &P, const DevJob &J, SinkT &S)
 {
     P.ended = 0;
-    on_end<real, SCAT>(P, J, S, P.end_e, P.end_idx);
+    on_end<real, SCAT, FEAT>(P, J, S, P.end_e, P.end_idx);
 }
 
 // warp-reduce the per-thread accumulators and add them to the job's totals
@@ -722,7 +744,7 @@ template <typename real> __device__ __forceinline__ JobC<real> job_consts(const 
     return c;
 }
 
-template <typename real, bool SCAT, bool LOG, bool BAND>
+template <typename real, bool SCAT, bool LOG, int FEAT>
 __global__ void __launch_bounds__(256) k_transport_plain(const DevGrid *__restrict__ grids,
                                                          const DevJob *__restrict__ jobp, int64_t packet0, int64_t n_run,
                                                          LogOut lg)
@@ -743,10 +765,10 @@ __global__ void __launch_bounds__(256) k_transport_plain(const DevGrid *__restri
     if (q < n_run) {
         Packet<real> P;
         P.hint = -1;
-        launch<real, SCAT, BAND>(P, J, G, packet0 + q, S);
+        launch<real, SCAT, FEAT>(P, J, G, packet0 + q, S);
         while (P.alive) {
-            if (P.ended) settle<real, SCAT>(P, J, S);
-            else step<real, SCAT, BAND>(P, J, G, T, jc, S);
+            if (P.ended) settle<real, SCAT, FEAT>(P, J, S);
+            else step<real, SCAT, FEAT>(P, J, G, T, jc, S);
         }
     }
     __syncwarp();
@@ -756,7 +778,7 @@ __global__ void __launch_bounds__(256) k_transport_plain(const DevGrid *__restri
 // One work item (packets p0 .. p1-1 of job J) on one warp: lanes whose packets have finished are
 // refilled together once at least refill_min of them are idle; rays that ended are settled at
 // those points; between them every live lane takes `interval` cell steps.
-template <typename real, bool SCAT, bool BAND, class SinkT>
+template <typename real, bool SCAT, int FEAT, class SinkT>
 __device__ __forceinline__ void run_item(const DevJob &J, const DevGrid &G, const Tabs<real> &T, int64_t p0, int64_t p1,
                                          int interval, int refill_min, SinkT &S)
 {
@@ -769,27 +791,27 @@ __device__ __forceinline__ void run_item(const DevJob &J, const DevGrid &G, cons
     P.hint = -1;
     P.ended = 0;
     for (;;) {
-        if (P.alive && P.ended) settle<real, SCAT>(P, J, S);
+        if (P.alive && P.ended) settle<real, SCAT, FEAT>(P, J, S);
         const unsigned idle = __ballot_sync(0xffffffffu, !P.alive);
         const int left = count - next;
         if (idle && left > 0) {
             const int n_idle = __popc(idle);
             if (n_idle >= min(refill_min, left)) {
                 const int mine = next + __popc(idle & lt);
-                if (!P.alive && mine < count) launch<real, SCAT, BAND>(P, J, G, p0 + mine, S);
+                if (!P.alive && mine < count) launch<real, SCAT, FEAT>(P, J, G, p0 + mine, S);
                 next += n_idle;
             }
         }
         if (!__any_sync(0xffffffffu, P.alive)) break;
         for (int t = 0; t < interval; ++t)
-            if (P.alive && !P.ended) step<real, SCAT, BAND>(P, J, G, T, jc, S);
+            if (P.alive && !P.ended) step<real, SCAT, FEAT>(P, J, G, T, jc, S);
     }
     __syncwarp();
 }
 
 // MINB > 0: compiled for MINB resident 128-thread blocks per SM (register cap 65536 / (128 MINB));
 // MINB = 0: any block size up to 256, at most 128 registers (two 256-thread blocks per SM)
-template <typename real, bool SCAT, int MINB, bool BAND>
+template <typename real, bool SCAT, int MINB, int FEAT>
 __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 2) k_transport_persistent(const DevGrid *__restrict__ grids,
                                                               const DevJob *__restrict__ jobs, int n_jobs,
                                                               int64_t total_items, int chunk, int interval,
@@ -832,7 +854,7 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 2) k_transport
             __syncwarp();
         }
         const int64_t p0 = ((int64_t)item - J.chunk_begin) * chunk;
-        run_item<real, SCAT, BAND>(J, G, T, p0, min(p0 + (int64_t)chunk, J.n_packets), interval, refill_min, S);
+        run_item<real, SCAT, FEAT>(J, G, T, p0, min(p0 + (int64_t)chunk, J.n_packets), interval, refill_min, S);
         flush(S.sm, S.stride, J.acc);
     }
 }
@@ -948,7 +970,7 @@ __global__ void __launch_bounds__(128, 4) k_transport_serve(const DevGrid *__res
             __syncwarp();
         }
         const int64_t p0 = (int64_t)item * chunk;
-        run_item<real, SCAT, false>(J, G, T, p0, min(p0 + (int64_t)chunk, J.n_packets), interval, refill_min, S);
+        run_item<real, SCAT, FEAT_EXT>(J, G, T, p0, min(p0 + (int64_t)chunk, J.n_packets), interval, refill_min, S);
         flush(S.sm, S.stride, J.acc);
         __threadfence();
         unsigned long long fin = 0;
@@ -971,17 +993,18 @@ size_t transport_smem(int block) { return (size_t)NSLOT * block * sizeof(unsigne
 
 static size_t tab_bytes(int precision, int entries) { return (size_t)entries * (precision == GCMC_FP64 ? 16 : 8); }
 
-// the logging (parity) kernels always read band tables; the others only when the job is a band job
+// the logging (parity) kernels carry every optional feature; the others only when the job needs one
 template <typename real, bool SCAT>
 static void plain_dispatch(unsigned nb, int block, size_t sm, cudaStream_t st, const DevGrid *grids, const DevJob *job,
-                           int64_t packet0, int64_t n_run, const LogOut &lg, bool log, bool band)
+                           int64_t packet0, int64_t n_run, const LogOut &lg, bool log, int feat)
 {
-    if (log) k_transport_plain<real, SCAT, true, true><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
-    else if (band) k_transport_plain<real, SCAT, false, true><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
-    else k_transport_plain<real, SCAT, false, false><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
+    constexpr int ALL = FEAT_BAND | FEAT_EXT;
+    if (log) k_transport_plain<real, SCAT, true, ALL><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
+    else if (feat) k_transport_plain<real, SCAT, false, ALL><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
+    else k_transport_plain<real, SCAT, false, 0><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
 }
 
-cudaError_t launch_plain(int precision, bool scatter, bool band, const DevGrid *grids, const DevJob *job, int64_t packet0,
+cudaError_t launch_plain(int precision, bool scatter, int feat, const DevGrid *grids, const DevJob *job, int64_t packet0,
                          int64_t n_run, const HostLog *hl, int tab_entries_n, cudaStream_t st)
 {
     const int block = 128;
@@ -1003,21 +1026,21 @@ cudaError_t launch_plain(int precision, bool scatter, bool band, const DevGrid *
     count_launch(1);
     const unsigned g = (unsigned)nb;
     if (precision == GCMC_FP64) {
-        if (scatter) plain_dispatch<double, true>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr, band);
-        else plain_dispatch<double, false>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr, band);
+        if (scatter) plain_dispatch<double, true>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr, feat);
+        else plain_dispatch<double, false>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr, feat);
     } else {
-        if (scatter) plain_dispatch<float, true>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr, band);
-        else plain_dispatch<float, false>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr, band);
+        if (scatter) plain_dispatch<float, true>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr, feat);
+        else plain_dispatch<float, false>(g, block, sm, st, grids, job, packet0, n_run, lg, hl != nullptr, feat);
     }
     return cudaGetLastError();
 }
 
-template <typename real, bool SCAT, int MINB, bool BAND>
+template <typename real, bool SCAT, int MINB, int FEAT>
 static cudaError_t persistent_run(int block, int blocks_per_sm, int nsm, const DevGrid *grids, const DevJob *jobs,
                                   int n_jobs, int64_t total_items, int chunk, int interval, int refill_min, int one_grid,
                                   int tab_n, unsigned long long *work, cudaStream_t st)
 {
-    auto kern = k_transport_persistent<real, SCAT, MINB, BAND>;
+    auto kern = k_transport_persistent<real, SCAT, MINB, FEAT>;
     const size_t sm = transport_smem(block) + (size_t)tab_n * sizeof(typename Pair<real>::type) * (one_grid ? 1 : block / 32);
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int occ = 0;
@@ -1032,24 +1055,35 @@ static cudaError_t persistent_run(int block, int blocks_per_sm, int nsm, const D
 template <typename real, bool SCAT>
 static cudaError_t persistent_dispatch(int block, int blocks_per_sm, int nsm, const DevGrid *grids, const DevJob *jobs,
                                        int n_jobs, int64_t total_items, int chunk, int interval, int refill_min,
-                                       int one_grid, int tab_n, unsigned long long *work, bool band, cudaStream_t st)
+                                       int one_grid, int tab_n, unsigned long long *work, int feat, cudaStream_t st)
 {
-    // batches with band jobs run the uncapped variant that reads each packet's g-ordinate table
-    if (band)
-        return persistent_run<real, SCAT, 0, true>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
-                                                   interval, refill_min, one_grid, tab_n, work, st);
+    // batches that need optional features run uncapped variants compiled with them: every combination
+    // for the FP32 absorber-only kernel (emission band jobs, limb-darkened chords), all of them otherwise
+    if (feat) {
+        if constexpr (sizeof(real) == 4 && !SCAT) {
+            if (feat == FEAT_BAND)
+                return persistent_run<real, SCAT, 0, FEAT_BAND>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items,
+                                                                chunk, interval, refill_min, one_grid, tab_n, work, st);
+            if (feat == FEAT_EXT)
+                return persistent_run<real, SCAT, 0, FEAT_EXT>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items,
+                                                               chunk, interval, refill_min, one_grid, tab_n, work, st);
+        }
+        return persistent_run<real, SCAT, 0, FEAT_BAND | FEAT_EXT>(block, blocks_per_sm, nsm, grids, jobs, n_jobs,
+                                                                   total_items, chunk, interval, refill_min, one_grid,
+                                                                   tab_n, work, st);
+    }
     // FP32 absorber-only batches (the emission and limb-chord hot path) have variants compiled for
     // 6 and 8 resident 128-thread blocks per SM (register caps 80 and 64); blocks_per_sm selects them.
     // (Capped scattering variants spill and ran slower on the phase curve.)
     if constexpr (sizeof(real) == 4 && !SCAT) {
         if (block <= 128 && blocks_per_sm >= 8)
-            return persistent_run<real, SCAT, 8, false>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+            return persistent_run<real, SCAT, 8, 0>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
                                                  interval, refill_min, one_grid, tab_n, work, st);
         if (block <= 128 && blocks_per_sm >= 6)
-            return persistent_run<real, SCAT, 6, false>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+            return persistent_run<real, SCAT, 6, 0>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
                                                  interval, refill_min, one_grid, tab_n, work, st);
     }
-    return persistent_run<real, SCAT, 0, false>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+    return persistent_run<real, SCAT, 0, 0>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
                                                 interval, refill_min, one_grid, tab_n, work, st);
 }
 
@@ -1078,7 +1112,7 @@ cudaError_t launch_serve(const DevGrid *grids, const ServeQueue &q, int block, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_persistent(int precision, bool scatter, bool band, const DevGrid *grids, const DevJob *jobs, int n_jobs,
+cudaError_t launch_persistent(int precision, bool scatter, int feat, const DevGrid *grids, const DevJob *jobs, int n_jobs,
                               int64_t total_items, int chunk, int block, int blocks_per_sm, int interval, int refill_min,
                               int one_grid, int tab_n, unsigned long long *work, cudaStream_t st)
 {
@@ -1093,15 +1127,15 @@ cudaError_t launch_persistent(int precision, bool scatter, bool band, const DevG
     if (precision == GCMC_FP64) {
         if (scatter)
             return persistent_dispatch<double, true>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
-                                                     interval, refill_min, one_grid, tab_n, work, band, st);
+                                                     interval, refill_min, one_grid, tab_n, work, feat, st);
         return persistent_dispatch<double, false>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
-                                                  interval, refill_min, one_grid, tab_n, work, band, st);
+                                                  interval, refill_min, one_grid, tab_n, work, feat, st);
     }
     if (scatter)
         return persistent_dispatch<float, true>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
-                                                interval, refill_min, one_grid, tab_n, work, band, st);
+                                                interval, refill_min, one_grid, tab_n, work, feat, st);
     return persistent_dispatch<float, false>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
-                                             interval, refill_min, one_grid, tab_n, work, band, st);
+                                             interval, refill_min, one_grid, tab_n, work, feat, st);
 }
 
 }  // namespace gcmc
