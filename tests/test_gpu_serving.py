@@ -96,3 +96,40 @@ def test_server_rejects_bad_jobs(setup):
             sv.submit(bad)
     finally:
         sv.close()
+
+
+def test_served_optional_physics(setup):
+    """Jobs with the optional physics (two-term HG clouds over a Lambertian surface, forced first scattering
+    with continuous absorption, transmission with multiple scattering and limb darkening) through the
+    server: bit-identical alone and in a mix, and equal to the batched form up to FP32 rounding."""
+    import dataclasses
+    from paper_2110_15640_gb300 import synth
+    gcmc, sw, ctx, _ = setup
+    wl = synth.config3_phase_curve(nlon=12, nlat=6, nr=10, nlam=2, nphase=4, n_lo=20000, n_hi=20000)
+    opac = dataclasses.replace(wl.opac, kabs=wl.opac.kabs * 1e-3, kray=wl.opac.kray * 0.1)
+    base = dataclasses.replace(wl.source.opts, cloud_phase=1)
+    variants = [dataclasses.replace(base, surface_albedo=0.5),
+                dataclasses.replace(base, forced_first=1, cont_abs=1)]
+    gid = ctx.upload_grid(wl.grid)
+    oid = ctx.upload_opacity(gid, opac)
+    jobs = []
+    for k, op in enumerate(variants):
+        sid = ctx.set_source(gid, dataclasses.replace(wl.source, opts=op))
+        jobs.append(gcmc.Context.job(gid, oid, sid, gcmc.ALBEDO, 1, 0, 20000, 3, 40 + k))
+    tr_opts = dataclasses.replace(base, trans_scatter=1, ld_law=2, ld_coef=(0.4, 0.25, 0.0, 0.0), star_radius=7.0e8,
+                                  star_dist=7.0e9, transit_xy=(0.0, 3.0e8))
+    sid_t = ctx.set_source(gid, synth.Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[-1.0, 0.0, 0.0]]),
+                                             opts=tr_opts))
+    jobs.append(gcmc.Context.job(gid, oid, sid_t, gcmc.TRANSMISSION, 1, 0, 20000, 3, 50))
+    sv = gcmc.Server(ctx, max_jobs=4)
+    try:
+        mixed = sv.run_all(jobs)
+        for q, j in enumerate(jobs):
+            alone = sv.run_all([j])[0]
+            assert np.array_equal(alone[0], mixed[q][0]) and alone[1].steps == mixed[q][1].steps
+    finally:
+        sv.close()
+    tb, sb = ctx.run_batch(jobs)
+    for q, j in enumerate(jobs):
+        np.testing.assert_allclose(mixed[q][0][:2], tb[q][:2], rtol=1e-3, atol=j.n_packets * 2.0 ** -32)
+        assert abs(mixed[q][1].steps - sb[q].steps) <= max(2, 1e-3 * sb[q].steps)
