@@ -179,10 +179,11 @@ typedef struct {
     int32_t pad3;
     double g_beta;            /* composite fraction in [0, 1] */
     /* variance reduction for scattered packets (albedo; transmission with multiple scattering) */
-    int32_t forced_first;     /* 1 = forced first scattering (Sect. 4.2): a march along the first flight gives the
-                                 optical depth tau_m to the grid boundary; W e^-tau_m leaves unscattered and the
-                                 packet, weight W (1 - e^-tau_m), interacts at tau = -ln(1 - zeta (1 - e^-tau_m)).
-                                 Not forced past tau_peel_cut or when the path ends on a reflecting surface */
+    int32_t forced_first;     /* forced scattering (Sect. 4.2): 1 = the first flight only (forced first scattering),
+                                 2 = every flight.  A march along the flight gives the optical depth tau_m to the
+                                 grid boundary; W e^-tau_m leaves unscattered and the packet, weight
+                                 W (1 - e^-tau_m), interacts at tau = -ln(1 - zeta (1 - e^-tau_m)).  Not forced
+                                 past tau_peel_cut or when the path ends on a reflecting surface */
     int32_t cont_abs;         /* 1 = continuous absorption (Sect. 4.1): flights sample their optical depth in the
                                  scattering opacity omega alpha, the weight decays by e^-tau_abs along the path
                                  (booked as absorbed) and every interaction scatters (peel-offs without omega) */

@@ -108,7 +108,7 @@ typedef struct {
     int32_t g_bias;        /* (the library's band-job options; the oracle reads its g table from orc_cells) */
     int32_t pad3;
     double g_beta;
-    int32_t forced_first;  /* forced first scattering (Sect. 4.2) */
+    int32_t forced_first;  /* forced scattering (Sect. 4.2): 1 the first flight only, 2 every flight */
     int32_t cont_abs;      /* continuous absorption (Sect. 4.1) */
 } orc_source;
 
@@ -881,9 +881,10 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
     while (transport) {
         draw(A->seed, n, ev, A->job_key, u);
         double tau_t = -log(u[0]);
-        if (first && S->forced_first) {
-            /* forced first scattering (Sect. 4.2): the optical depth tau_m of the first flight's path to
-               the grid boundary (in the flight's own opacity); the packet interacts before it, carrying
+        if ((first && S->forced_first == 1) || S->forced_first == 2) {
+            /* forced scattering (Sect. 4.2), on the first flight or on every flight: the optical depth tau_m
+               of the flight's path to the grid boundary (in the flight's own opacity); the packet interacts
+               before it, carrying
                W (1 - e^-tau_m) with the truncated-exponential tau = -ln(1 - zeta (1 - e^-tau_m)), and
                W e^-tau_m leaves unscattered.  Not forced when the path runs past the cut-off depth or
                ends on a reflecting surface. */
@@ -967,6 +968,17 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
                 double v[4];
                 draw(A->seed, n, ev | 0x80000000u, A->job_key, v);
                 if (!(v[0] < As)) { kahan(&acc->ledger[3], &acc->ledger_c[3], W); break; }
+                if (W < S->w_rr * W0) {
+                    /* forcing and continuous absorption change weights in analog mode too */
+                    if (v[1] < S->p_surv) {
+                        double Wn = W / S->p_surv;
+                        kahan(&acc->ledger[4], &acc->ledger_c[4], Wn - W);
+                        W = Wn;
+                    } else {
+                        kahan(&acc->ledger[5], &acc->ledger_c[5], W);
+                        break;
+                    }
+                }
             }
             double nd[3];
             orc_turn(nrm, sqrt(u[2]), 2.0 * ORC_PI * u[3], nd);
@@ -1014,6 +1026,17 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
             double v[4];
             draw(A->seed, n, ev | 0x80000000u, A->job_key, v);
             if (!(v[0] < om)) { kahan(&acc->ledger[2], &acc->ledger_c[2], W); break; }
+            if (W < S->w_rr * W0) {
+                /* forcing and continuous absorption change weights in analog mode too */
+                if (v[1] < S->p_surv) {
+                    double Wn = W / S->p_surv;
+                    kahan(&acc->ledger[4], &acc->ledger_c[4], Wn - W);
+                    W = Wn;
+                } else {
+                    kahan(&acc->ledger[5], &acc->ledger_c[5], W);
+                    break;
+                }
+            }
         }
         /* scatterer: gas if u1 < P_gas, else cloud; the cloud's own choice (two-term HG) uses u1's
            remaining uniform (u1 - P_gas) / (1 - P_gas) */

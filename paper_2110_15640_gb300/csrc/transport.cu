@@ -136,17 +136,36 @@ __device__ __forceinline__ void start_flight(Packet<real> &P, const DevJob &J, S
     start_ray<real>(P, P.ix, P.iy, P.iz, dx, dy, dz, P.ci, P.cj, P.ck, K_FLIGHT, tau);
 }
 
-// the first flight from the launch point along -star: forced (a boundary march first) or plain
+// a forced flight: the march to the grid boundary along (dx, dy, dz), kept in fx, fy, fz for the flight
+template <typename real, class SinkT>
+__device__ __forceinline__ void start_force(Packet<real> &P, SinkT &S, real dx, real dy, real dz)
+{
+    P.fx = dx;
+    P.fy = dy;
+    P.fz = dz;
+    S.trace(P.n, -4, (real)0);
+    start_ray<real>(P, P.ix, P.iy, P.iz, dx, dy, dz, P.ci, P.cj, P.ck, K_FORCE, (real)-1);
+}
+
+// the first flight from the launch point along -star: forced (forced_first 1 or 2) or plain
 template <typename real, class SinkT>
 __device__ __forceinline__ void start_first_flight(Packet<real> &P, const DevJob &J, SinkT &S)
 {
-    if (J.forced_first) {
-        S.trace(P.n, -4, (real)0);
-        start_ray<real>(P, P.ix, P.iy, P.iz, -JV<real>::star(J, 0), -JV<real>::star(J, 1), -JV<real>::star(J, 2), P.ci,
-                        P.cj, P.ck, K_FORCE, (real)-1);
-    } else {
-        start_flight<real>(P, J, S, -JV<real>::star(J, 0), -JV<real>::star(J, 1), -JV<real>::star(J, 2));
+    if (J.forced_first) start_force<real>(P, S, -JV<real>::star(J, 0), -JV<real>::star(J, 1), -JV<real>::star(J, 2));
+    else start_flight<real>(P, J, S, -JV<real>::star(J, 0), -JV<real>::star(J, 1), -JV<real>::star(J, 2));
+}
+
+// a flight after a scattering or a surface reflection: forced when every flight is (forced_first 2)
+template <typename real, bool EXT, class SinkT>
+__device__ __forceinline__ void start_next_flight(Packet<real> &P, const DevJob &J, SinkT &S, real dx, real dy, real dz)
+{
+    if constexpr (EXT) {
+        if (J.forced_first == 2) {
+            start_force<real>(P, S, dx, dy, dz);
+            return;
+        }
     }
+    start_flight<real>(P, J, S, dx, dy, dz);
 }
 
 template <typename real, class SinkT>
@@ -380,6 +399,18 @@ __device__ void after_peels_scatter(Packet<real> &P, const DevJob &J, SinkT &S)
             finish<real>(P, S);
             return;
         }
+        if (P.W < JV<real>::w_rr(J) * P.W0) {
+            // forcing and continuous absorption change weights in analog mode too: the same roulette
+            if (u01<real>(v.y) < JV<real>::p_surv(J)) {
+                const real Wn = P.W / JV<real>::p_surv(J);
+                S.ledger(4, Wn - P.W);
+                P.W = Wn;
+            } else {
+                S.ledger(5, P.W);
+                finish<real>(P, S);
+                return;
+            }
+        }
     }
     const uint4 w = draw_words(J.seed, P.n, P.ev, J.key);
     const real u1 = u01<real>(w.y), u2 = u01<real>(w.z), u3 = u01<real>(w.w);
@@ -401,7 +432,7 @@ __device__ void after_peels_scatter(Packet<real> &P, const DevJob &J, SinkT &S)
     real dx = P.fx, dy = P.fy, dz = P.fz;
     turn<real>(dx, dy, dz, mu, (real)(2.0 * PI) * u3);
     ++P.ev;
-    start_flight<real>(P, J, S, dx, dy, dz);
+    start_next_flight<real, (FEAT & FEAT_EXT) != 0>(P, J, S, dx, dy, dz);
 }
 
 // first observer, from o on, above the horizon of the surface point (normal in fx, fy, fz)
@@ -442,12 +473,24 @@ __device__ void after_peels_surface(Packet<real> &P, const DevJob &J, SinkT &S)
             finish<real>(P, S);
             return;
         }
+        if (P.W < JV<real>::w_rr(J) * P.W0) {
+            // forcing and continuous absorption change weights in analog mode too: the same roulette
+            if (u01<real>(v.y) < JV<real>::p_surv(J)) {
+                const real Wn = P.W / JV<real>::p_surv(J);
+                S.ledger(4, Wn - P.W);
+                P.W = Wn;
+            } else {
+                S.ledger(5, P.W);
+                finish<real>(P, S);
+                return;
+            }
+        }
     }
     const uint4 w = draw_words(J.seed, P.n, P.ev, J.key);
     real dx = P.fx, dy = P.fy, dz = P.fz;
     turn<real>(dx, dy, dz, M<real>::sqrt_(u01<real>(w.z)), (real)(2.0 * PI) * u01<real>(w.w));
     ++P.ev;
-    start_flight<real>(P, J, S, dx, dy, dz);
+    start_next_flight<real, true>(P, J, S, dx, dy, dz);
 }
 
 template <typename real, bool SCAT, int FEAT, class SinkT>
@@ -457,9 +500,10 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
     Ray<real> &R = P.ray;
     if constexpr (SCAT && EXT) {
         if (P.kind == K_FORCE) {
-            // forced first scattering (Sect. 4.2): R.tau is the optical depth of the first flight's path to
-            // the grid boundary; W e^-tau leaves unscattered, W (1 - e^-tau) interacts before it.  Not
-            // forced past the cut-off depth or when the path ends on a reflecting surface.
+            // forced scattering (Sect. 4.2): R.tau is the optical depth of the flight's path to the grid
+            // boundary; W e^-tau leaves unscattered, W (1 - e^-tau) interacts before it.  Not forced past
+            // the cut-off depth or when the path ends on a reflecting surface.  The flight's direction is
+            // in fx, fy, fz.
             if (e == E_CAP) {
                 S.ledger(6, P.W);
                 finish<real>(P, S);
@@ -483,7 +527,7 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
                 }
                 P.W *= p;
             }
-            start_flight<real>(P, J, S, -JV<real>::star(J, 0), -JV<real>::star(J, 1), -JV<real>::star(J, 2), forced, p);
+            start_flight<real>(P, J, S, P.fx, P.fy, P.fz, forced, p);
             return;
         }
         if (P.kind == K_FLIGHT && J.cont_abs) {

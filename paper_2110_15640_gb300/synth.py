@@ -138,7 +138,7 @@ class Options:
     transit_xy: tuple = (0.0, 0.0)   # planet centre on the stellar disk along the launch basis (e1, e2), m
     g_bias: int = 0              # emission band jobs (per-packet g): 0 q = p, 1 uniform, 2 composite
     g_beta: float = 0.5          # composite: q = (1 - g_beta) p + g_beta / N_g
-    forced_first: int = 0        # forced first scattering
+    forced_first: int = 0        # forced scattering: 1 the first flight, 2 every flight
     cont_abs: int = 0            # continuous absorption
 
 

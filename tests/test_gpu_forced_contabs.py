@@ -1,4 +1,5 @@
-"""Forced first scattering and continuous absorption (Sect. 4.1, 4.2) on the GPU, against the FP64 oracle:
+"""Forced scattering (first flight or every flight) and continuous absorption (Sect. 4.1, 4.2) on the GPU,
+against the FP64 oracle:
 
 * FP64 path: per-packet parity (cell sequences, steps, f, ledger) on the cloudy 3D atmosphere over a
   reflecting surface (first flights that end on it are not forced) and on the cloudy atmosphere in
@@ -27,13 +28,13 @@ def G():
     ctx.close()
 
 
-def cloudy(n, survival=1, transit=False):
+def cloudy(n, survival=1, transit=False, ff=1):
     """The phase-curve atmosphere on a 12x6x10 grid, gas absorption cut 1000x and Rayleigh 10x, two-term HG
     clouds, forced first scattering and continuous absorption; either over a Lambertian surface (A_s =
     0.5, four phase observers) or seen in transit with multiple scattering."""
     wl = S.config3_phase_curve(nlon=12, nlat=6, nr=10, nlam=2, nphase=4, n_lo=n, n_hi=n)
     opac = dataclasses.replace(wl.opac, kabs=wl.opac.kabs * 1e-3, kray=wl.opac.kray * 0.1)
-    opts = dataclasses.replace(wl.source.opts, cloud_phase=1, survival=survival, forced_first=1, cont_abs=1)
+    opts = dataclasses.replace(wl.source.opts, cloud_phase=1, survival=survival, forced_first=ff, cont_abs=1)
     if transit:
         opts = dataclasses.replace(opts, trans_scatter=1)
         src = S.Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[-1.0, 0.0, 0.0]]), opts=opts)
@@ -49,11 +50,11 @@ def _load(ctx, wl, prec):
     return gcmc.load_workload(ctx, wl, prec)
 
 
-@pytest.mark.parametrize("transit", [False, True])
-@pytest.mark.parametrize("survival", [1, 0])
-def test_fp64_per_packet_parity(G, survival, transit):
+@pytest.mark.parametrize("transit,survival,ff", [(False, 1, 1), (False, 0, 1), (True, 1, 1), (True, 0, 1),
+                                                 (False, 1, 2), (True, 0, 2)])
+def test_fp64_per_packet_parity(G, survival, transit, ff):
     from paper_2110_15640_gb300 import gcmc
-    wl = cloudy(3000, survival, transit)
+    wl = cloudy(3000, survival, transit, ff)
     job = wl.jobs[0]
     gid, oid, sid, jobs = _load(G, wl, gcmc.FP64)
     ncol = O.tally_cols(wl, job)
@@ -65,7 +66,9 @@ def test_fp64_per_packet_parity(G, survival, transit):
         no, ng = ref["tr_n"][q], got["tr_n"][q]
         if no == ng and np.array_equal(ref["tr_cell"][q, :no], got["tr_cell"][q, :ng]):
             lo, lg = ref["tr_len"][q, :no], got["tr_len"][q, :ng]
-            same += int(np.all(np.abs(lo - lg) <= 1e-9 * np.abs(lo) + 1e-9))
+            # every-flight forcing keeps packets scattering for hundreds of events: the two sides' FP64
+            # positions drift apart by ~1e-13 relative (~1e-5 m), negligible against 1e5 m cells
+            same += int(np.all(np.abs(lo - lg) <= 1e-9 * np.abs(lo) + 1e-5))
     assert same >= ntr - 1, f"{same}/{ntr} identical traces"
     np.testing.assert_array_equal(got["pk_steps"], ref["pk_steps"])
     # f carries e^-tau of its peel-off and, with continuous absorption, e^-tau_abs of every flight before
@@ -80,10 +83,10 @@ def test_fp64_per_packet_parity(G, survival, transit):
     assert L[2] > 0 and abs((L[0] + L[4]) - (L[1] + L[2] + L[3] + L[5] + L[6] + L[7])) <= 1e-12 * L[0]
 
 
-@pytest.mark.parametrize("transit", [False, True])
-def test_fp32_matches_oracle(G, transit):
+@pytest.mark.parametrize("transit,ff", [(False, 1), (True, 1), (False, 2)])
+def test_fp32_matches_oracle(G, transit, ff):
     from paper_2110_15640_gb300 import gcmc
-    wl = cloudy(20000, 1, transit)
+    wl = cloudy(20000, 1, transit, ff)
     job = wl.jobs[0]
     gid, oid, sid, jobs = _load(G, wl, gcmc.FP32)
     ncol = O.tally_cols(wl, job)

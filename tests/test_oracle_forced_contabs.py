@@ -1,4 +1,5 @@
-"""Pins of the oracle's forced first scattering (Sect. 4.2) and continuous absorption (Sect. 4.1):
+"""Pins of the oracle's forced scattering (Sect. 4.2: on the first flight, or on every flight) and
+continuous absorption (Sect. 4.1):
 
 * both leave the expectation unchanged: a homogeneous slab's geometric albedo with either or both
   options meets the adding-doubling value within 3 sigma (Rayleigh and isotropic, thin and thick);
@@ -23,7 +24,7 @@ def _ag(wl):
     return f.mean(), f.std() / math.sqrt(len(f)), r
 
 
-@pytest.mark.parametrize("ff,ca", [(1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("ff,ca", [(1, 0), (0, 1), (1, 1), (2, 0), (2, 1)])
 @pytest.mark.parametrize("phase,beta,omega,tau", [("rayleigh", [1.0, 0.0, 0.5], 0.6, 0.3),
                                                   ("iso", [1.0], 0.9, 2.0)])
 def test_slab_albedo_unchanged(ff, ca, phase, beta, omega, tau):
@@ -38,6 +39,15 @@ def test_forcing_lowers_variance_of_thin_slab():
     _, s0, _ = _ag(S.slab_sphere_albedo(**kw))
     _, s1, _ = _ag(S.slab_sphere_albedo(forced_first=1, **kw))
     assert s1 < 0.4 * s0, (s1, s0)
+
+
+def test_forcing_every_flight_lowers_variance_further():
+    kw = dict(omega=0.95, tau=0.2, phase="iso", n_packets=100_000)
+    _, s1, _ = _ag(S.slab_sphere_albedo(forced_first=1, **kw))
+    _, s2, r = _ag(S.slab_sphere_albedo(forced_first=2, **kw))
+    assert s2 < s1, (s2, s1)
+    L = r["ledger"]
+    assert L[1] > 0 and abs((L[0] + L[4]) - (L[1] + L[2] + L[3] + L[5] + L[6] + L[7])) <= 1e-12 * L[0]
 
 
 def test_continuous_absorption_at_omega_one_is_survival_biasing():
