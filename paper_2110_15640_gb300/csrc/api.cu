@@ -393,6 +393,7 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
         if (s.surface_albedo > 0.0 || s.cloud_phase == GCMC_CLOUD_TTHG || (j.mode == GCMC_TRANSMISSION &&
             (s.trans_scatter || s.ld_law != GCMC_LD_NONE)) || d.forced_first || d.cont_abs)
             P.feat |= FEAT_EXT;
+        if (d.cont_abs) P.feat |= FEAT_EXT | FEAT_CABS;
         d.ng_s = P.ng_s[q];
         if (d.ng_s) {
             P.feat |= FEAT_BAND;

@@ -149,10 +149,11 @@ cudaError_t launch_serve(const DevGrid *grids, const ServeQueue &q, int block, i
 // transport
 size_t transport_smem(int block);
 // Optional code compiled into a transport-kernel variant (template FEAT): band jobs' per-packet
-// g-ordinate tables, and the optional physics of scattered packets (surfaces, two-term HG clouds,
-// multiple scattering in transmission, stellar limb darkening, forced first scattering, continuous
-// absorption).  Batches that use none of them run variants without that code.
-constexpr int FEAT_BAND = 1, FEAT_EXT = 2;
+// g-ordinate tables (FEAT_BAND); the optional physics of scattered packets (FEAT_EXT: surfaces,
+// two-term HG clouds, multiple scattering in transmission, stellar limb darkening, forced scattering,
+// continuous absorption's weight bookkeeping); and continuous absorption's second optical depth in the
+// cell step (FEAT_CABS, with FEAT_EXT).  Batches that use none of them run variants without that code.
+constexpr int FEAT_BAND = 1, FEAT_EXT = 2, FEAT_CABS = 4, FEAT_ALL = 7;
 
 cudaError_t launch_plain(int precision, bool scatter, int feat, const DevGrid *grids, const DevJob *job, int64_t packet0,
                          int64_t n_run, const HostLog *hl, int tab_entries_n, cudaStream_t st);

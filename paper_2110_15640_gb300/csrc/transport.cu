@@ -680,7 +680,7 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
 }
 
 // one cell step (S3-S7) of the packet's current ray; FEAT_BAND kernels read the packet's g-ordinate
-// table (band jobs), FEAT_EXT kernels carry continuous absorption
+// table (band jobs), FEAT_CABS kernels carry continuous absorption
 template <typename real, bool SCAT, int FEAT, class SinkT>
 __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const DevGrid &G, const Tabs<real> &T,
                                      const JobC<real> &jc, SinkT &S)
@@ -697,7 +697,7 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
     real a;
     const int go = (FEAT & FEAT_BAND) ? P.goff : 0;
     real a2 = (real)0;
-    if constexpr (SCAT && (FEAT & FEAT_EXT) != 0) {
+    if constexpr (SCAT && (FEAT & FEAT_CABS) != 0) {
         if (jc.contabs) {
             // continuous absorption: flights (and the forcing march) run in the scattering opacity omega alpha
             // and accumulate the absorption (1 - omega) alpha
@@ -720,7 +720,7 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
     if constexpr (SCAT) {
         if (R.tau_target >= (real)0 && a > (real)0 && R.tau + a * seg >= R.tau_target) {
             const real l = M<real>::div_(R.tau_target - R.tau, a);
-            if constexpr ((FEAT & FEAT_EXT) != 0) {
+            if constexpr ((FEAT & FEAT_CABS) != 0) {
                 if (jc.contabs) R.tau2 += a2 * l;
             }
             S.trace(P.n, idx, l);
@@ -733,7 +733,7 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
         }
     }
     R.tau += a * seg;
-    if constexpr (SCAT && (FEAT & FEAT_EXT) != 0) {
+    if constexpr (SCAT && (FEAT & FEAT_CABS) != 0) {
         if (jc.contabs) R.tau2 += a2 * seg;
     }
     S.trace(P.n, idx, seg);
@@ -1014,7 +1014,8 @@ __global__ void __launch_bounds__(128, 4) k_transport_serve(const DevGrid *__res
             __syncwarp();
         }
         const int64_t p0 = (int64_t)item * chunk;
-        run_item<real, SCAT, FEAT_EXT>(J, G, T, p0, min(p0 + (int64_t)chunk, J.n_packets), interval, refill_min, S);
+        run_item<real, SCAT, FEAT_EXT | FEAT_CABS>(J, G, T, p0, min(p0 + (int64_t)chunk, J.n_packets), interval,
+                                                   refill_min, S);
         flush(S.sm, S.stride, J.acc);
         __threadfence();
         unsigned long long fin = 0;
@@ -1042,9 +1043,8 @@ template <typename real, bool SCAT>
 static void plain_dispatch(unsigned nb, int block, size_t sm, cudaStream_t st, const DevGrid *grids, const DevJob *job,
                            int64_t packet0, int64_t n_run, const LogOut &lg, bool log, int feat)
 {
-    constexpr int ALL = FEAT_BAND | FEAT_EXT;
-    if (log) k_transport_plain<real, SCAT, true, ALL><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
-    else if (feat) k_transport_plain<real, SCAT, false, ALL><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
+    if (log) k_transport_plain<real, SCAT, true, FEAT_ALL><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
+    else if (feat) k_transport_plain<real, SCAT, false, FEAT_ALL><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
     else k_transport_plain<real, SCAT, false, 0><<<nb, block, sm, st>>>(grids, job, packet0, n_run, lg);
 }
 
@@ -1101,20 +1101,39 @@ static cudaError_t persistent_dispatch(int block, int blocks_per_sm, int nsm, co
                                        int n_jobs, int64_t total_items, int chunk, int interval, int refill_min,
                                        int one_grid, int tab_n, unsigned long long *work, int feat, cudaStream_t st)
 {
-    // batches that need optional features run uncapped variants compiled with them: every combination
-    // for the FP32 absorber-only kernel (emission band jobs, limb-darkened chords), all of them otherwise
+    // batches that need optional features run variants compiled with them.  FP32 absorber-only kernel:
+    // band jobs (also in the capped variants) and limb-darkened chords separately; FP32 scattering
+    // kernel: the optional physics with and without continuous absorption; all of them otherwise.
     if (feat) {
         if constexpr (sizeof(real) == 4 && !SCAT) {
-            if (feat == FEAT_BAND)
-                return persistent_run<real, SCAT, 0, FEAT_BAND>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items,
-                                                                chunk, interval, refill_min, one_grid, tab_n, work, st);
+            if (feat == FEAT_BAND) {
+                if (block <= 128 && blocks_per_sm >= 8)
+                    return persistent_run<real, SCAT, 8, FEAT_BAND>(block, blocks_per_sm, nsm, grids, jobs, n_jobs,
+                                                                    total_items, chunk, interval, refill_min, one_grid,
+                                                                    tab_n, work, st);
+                if (block <= 128 && blocks_per_sm >= 6)
+                    return persistent_run<real, SCAT, 6, FEAT_BAND>(block, blocks_per_sm, nsm, grids, jobs, n_jobs,
+                                                                    total_items, chunk, interval, refill_min, one_grid,
+                                                                    tab_n, work, st);
+                return persistent_run<real, SCAT, 0, FEAT_BAND>(block, blocks_per_sm, nsm, grids, jobs, n_jobs,
+                                                                total_items, chunk, interval, refill_min, one_grid,
+                                                                tab_n, work, st);
+            }
             if (feat == FEAT_EXT)
                 return persistent_run<real, SCAT, 0, FEAT_EXT>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items,
                                                                chunk, interval, refill_min, one_grid, tab_n, work, st);
         }
-        return persistent_run<real, SCAT, 0, FEAT_BAND | FEAT_EXT>(block, blocks_per_sm, nsm, grids, jobs, n_jobs,
-                                                                   total_items, chunk, interval, refill_min, one_grid,
-                                                                   tab_n, work, st);
+        if constexpr (sizeof(real) == 4 && SCAT) {
+            if (feat == FEAT_EXT)
+                return persistent_run<real, SCAT, 0, FEAT_EXT>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items,
+                                                               chunk, interval, refill_min, one_grid, tab_n, work, st);
+            if (feat == (FEAT_EXT | FEAT_CABS))
+                return persistent_run<real, SCAT, 0, FEAT_EXT | FEAT_CABS>(block, blocks_per_sm, nsm, grids, jobs, n_jobs,
+                                                                           total_items, chunk, interval, refill_min,
+                                                                           one_grid, tab_n, work, st);
+        }
+        return persistent_run<real, SCAT, 0, FEAT_ALL>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+                                                       interval, refill_min, one_grid, tab_n, work, st);
     }
     // FP32 absorber-only batches (the emission and limb-chord hot path) have variants compiled for
     // 6 and 8 resident 128-thread blocks per SM (register caps 80 and 64); blocks_per_sm selects them.
