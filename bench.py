@@ -352,8 +352,8 @@ def main():
             cfg = gcmc.gcmc_launch_cfg(args.block, args.blocks_per_sm, args.chunk, args.interval, args.refill, 0)
             tuned = {"block": args.block or 128, "blocks_per_sm": args.blocks_per_sm, "chunk": args.chunk or 1024,
                      "interval": args.interval or 1, "refill_min": args.refill or 16}
-        else:   # untimed search on 16 jobs spread over the bands (tallies do not depend on the launch parameters)
-            cfg, tuned, _ = autotune.tune(ctx, jobs[::max(1, len(jobs) // 16)][:16], stream, reps=2)
+        else:   # untimed search on a sample spread over the job list (tallies do not depend on the launch parameters)
+            cfg, tuned, _ = autotune.tune(ctx, autotune.sample_jobs(jobs), stream, reps=2)
         _, sts = ctx.run_batch(jobs, cfg=cfg)                       # untimed: exact packet-step count
     steps_per_step = int(sum(s.steps for s in sts))
     packets_per_step = int(sum(s.packets for s in sts))

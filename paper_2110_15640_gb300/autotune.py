@@ -22,6 +22,17 @@ DEFAULT_SPACE = {
 }
 
 
+def sample_jobs(jobs, min_jobs=16, min_packets=16_000_000):
+    """Jobs spread evenly over the list, at least min_jobs of them and at least min_packets packets in
+    all (or every job): enough work items to fill the GPU at every chunk size the search tries, so
+    workloads of many small jobs are tuned on the load they present."""
+    n = len(jobs)
+    mean = max(1.0, sum(j.n_packets for j in jobs) / max(n, 1))
+    want = min(n, max(min_jobs, int(-(-min_packets // mean))))
+    stride = max(1, n // want)
+    return jobs[::stride][:want]
+
+
 def _time_cfg(ctx, jobs, cfg, reps, stream):
     import torch
 
