@@ -177,7 +177,7 @@ struct Plan {
     std::vector<int> prep_pos;          // position of job q in `prep`
     std::vector<int> job_group;         // group of job q
     std::vector<Group> groups;
-    std::vector<size_t> off_rec, off_cdf, off_w, off_info, off_bsum, off_bcnt;
+    std::vector<size_t> off_rec, off_alpha, off_cdf, off_w, off_info, off_bsum, off_bcnt;
     std::vector<int> ng_s;              // g-ordinates a band job samples (0: one g-ordinate)
     std::vector<int64_t> nblk;          // emission scan blocks per preparation
     std::vector<size_t> g_first;
@@ -253,6 +253,7 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
     P.prep_pos.resize(n);
     P.job_group.assign(n, 0);
     P.off_rec.assign(n, 0);
+    P.off_alpha.assign(n, 0);
     P.off_cdf.assign(n, 0);
     P.off_w.assign(n, 0);
     P.off_info.assign(n, 0);
@@ -290,6 +291,10 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
         n_prep += m;
         P.off_rec[q] = ws;
         ws += align256((size_t)m * ncell * (ctx->opacs[j.opac_id].kind == GCMC_OPAC_ALBEDO ? 4 * esz : esz));
+        if (ctx->opacs[j.opac_id].kind == GCMC_OPAC_ALBEDO) {   // compact alpha beside the records
+            P.off_alpha[q] = ws;
+            ws += align256((size_t)ncell * esz);
+        }
         if (j.mode == GCMC_EMISSION) {
             const int64_t nblk = std::max<int64_t>((ncell + EMIS_SCAN_BLOCK - 1) / EMIS_SCAN_BLOCK,
                                                    emis_col_blocks(ctx->grids[j.grid_id].dg));
@@ -510,6 +515,7 @@ gcmc_status stage(gcmc_ctx *ctx, Plan &P, char *base, double *lum = nullptr, cha
         for (int gi = 0; gi < m; ++gi) {
             PrepJob &pj = P.prep[P.prep_pos[q] + gi];
             pj.rec = base + P.off_rec[q] + gi * ncell * esz;
+            pj.alpha = d.rec4 ? base + P.off_alpha[q] : nullptr;
             if (d.mode == GCMC_EMISSION) {
                 pj.cdf = reinterpret_cast<long long *>(base + P.off_cdf[q]) + gi * ncell;
                 pj.wcell = base + P.off_w[q] + gi * ncell * esz;
@@ -522,6 +528,7 @@ gcmc_status stage(gcmc_ctx *ctx, Plan &P, char *base, double *lum = nullptr, cha
         }
         const PrepJob &p0 = P.prep[P.prep_pos[q]];
         d.rec = p0.rec;
+        d.arec = p0.alpha;
         if (d.mode == GCMC_EMISSION) {
             d.cdf = p0.cdf;
             d.wcell = p0.wcell;

@@ -105,7 +105,8 @@ struct DevJob {
     const double *ginfo;        // band job: each g-ordinate's info block, GINFO_STRIDE doubles apart
     double surf_as, ld_c[4], star_r, tr_x, tr_y;   // surface albedo; limb darkening, stellar radius, planet offset
     float surf_as_f, ld_c_f[4], star_r_f, tr_x_f, tr_y_f;
-    int32_t forced_first;       // forced first scattering (albedo; transmission with multiple scattering)
+    const void *arec;           // scattering records: their alpha as a compact table for the cell march
+    int32_t forced_first;       // forced scattering (albedo; transmission with multiple scattering)
     int32_t cont_abs;           // continuous absorption (scattering records only)
 };
 

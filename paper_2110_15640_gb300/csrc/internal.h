@@ -26,6 +26,7 @@ struct PrepJob {
     int32_t lam_hint, pad;
     double lam_m;              // band centre (k-table) or rest wavelength (xsec), m
     void *rec;                 // output: albedo records or alpha (march precision)
+    void *alpha;               // output with albedo records: alpha alone, the table the cell march reads
     long long *cdf;            // emission: cumulative pdf in 2^62 fixed point (first scratch for L_i as FP64)
     void *wcell;               // emission: launch weight (march precision)
     double *info;              // emission: [L_tot, n_incl, cdf_total, Q_tot bits, constants of the pdf] (device)

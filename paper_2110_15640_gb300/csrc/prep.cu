@@ -60,6 +60,7 @@ __global__ void k_prep_albedo(DevGrid G, AlbDev op, const PrepJob *__restrict__ 
     const double sca = ray + op.wcld[l] * ac;
     const double om = ext > 0.0 ? sca / ext : 0.0;
     const double pg = sca > 0.0 ? ray / sca : 1.0;
+    if (pj.alpha) reinterpret_cast<real *>(pj.alpha)[idx] = (real)ext;
     if constexpr (sizeof(real) == 4) {
         reinterpret_cast<float4 *>(pj.rec)[idx] = make_float4((float)ext, (float)om, (float)op.gcld[l], (float)pg);
     } else {

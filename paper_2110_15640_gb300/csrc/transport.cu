@@ -42,8 +42,8 @@ template <typename real> struct JobC {
     int max_steps;
     int contabs;           // continuous absorption: flights march in omega alpha and accumulate (1 - omega) alpha
     real tau_cut;
-    const real *rec;       // march table: alpha, or the first component of the albedo records
-    int rec_stride;        // 4 for albedo records, else 1
+    const real *rec;       // march table: alpha per cell
+    const real *recf;      // scattering records (alpha, omega, g, P_gas) per cell, or NULL
 };
 
 struct LogOut {
@@ -701,16 +701,14 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
         if (jc.contabs) {
             // continuous absorption: flights (and the forcing march) run in the scattering opacity omega alpha
             // and accumulate the absorption (1 - omega) alpha
-            const auto aw = __ldg(reinterpret_cast<const typename Pair<real>::type *>(jc.rec + 4 * idx));
+            const auto aw = __ldg(reinterpret_cast<const typename Pair<real>::type *>(jc.recf + 4 * idx));
             const bool fl = P.kind == K_FLIGHT || P.kind == K_FORCE;
             const real as = aw.x * aw.y;
             a = fl ? as : aw.x;
             a2 = fl ? aw.x - as : (real)0;
         } else {
-            a = __ldg(jc.rec + jc.rec_stride * idx + go);
+            a = __ldg(jc.rec + idx + go);
         }
-    } else if constexpr (SCAT) {
-        a = __ldg(jc.rec + jc.rec_stride * idx + go);
     } else {
         a = __ldg(jc.rec + idx + go);
     }
@@ -782,8 +780,8 @@ template <typename real> __device__ __forceinline__ JobC<real> job_consts(const 
     JobC<real> c;
     c.max_steps = (int)min(J.max_steps, (int64_t)INT_MAX);
     c.tau_cut = (real)J.tau_cut;
-    c.rec = reinterpret_cast<const real *>(J.rec);
-    c.rec_stride = J.rec4 ? 4 : 1;
+    c.rec = reinterpret_cast<const real *>(J.arec ? J.arec : J.rec);
+    c.recf = J.rec4 ? reinterpret_cast<const real *>(J.rec) : nullptr;
     c.contabs = J.cont_abs;
     return c;
 }
