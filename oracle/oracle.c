@@ -108,8 +108,11 @@ typedef struct {
     int32_t g_bias;        /* (the library's band-job options; the oracle reads its g table from orc_cells) */
     int32_t pad3;
     double g_beta;
-    int32_t forced_first;  /* forced scattering (Sect. 4.2): 1 the first flight only, 2 every flight */
+    int32_t forced_first;  /* biased flights (Sect. 4.2): 1 the first flight only, 2 every flight */
     int32_t cont_abs;      /* continuous absorption (Sect. 4.1) */
+    int32_t path_bias;     /* how biased flights sample tau: 0 forced scattering, 1 path length stretching,
+                              2 hybrid forced scattering with path length stretching */
+    int32_t pad4;
 } orc_source;
 
 typedef struct {
@@ -723,6 +726,16 @@ static double peel(march_ctx *M, const double x0[3], const int c0[3], const doub
     return 0.0;
 }
 
+/* a weight change of a biased flight (p/q), booked with the roulette's gain and loss so that the ledger
+   closes packet by packet */
+static void reweight(acc_t *acc, double *W, double factor)
+{
+    const double Wn = *W * factor;
+    if (Wn > *W) kahan(&acc->ledger[4], &acc->ledger_c[4], Wn - *W);
+    else kahan(&acc->ledger[5], &acc->ledger_c[5], *W - Wn);
+    *W = Wn;
+}
+
 /* tally columns of a job: one per observer (albedo, emission); transmission: the chord (direct)
    column, plus the scattered-light column when packets scatter after their chord */
 static int tally_cols(const orc_source *S, int mode)
@@ -896,7 +909,20 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
             const double tau2_m = M.tau2;
             if (ca) { M.alpha = C->alpha; M.alpha2 = NULL; }
             if (sm == END_CAP) { kahan(&acc->ledger[6], &acc->ledger_c[6], W); break; }
-            if (sm == END_ESCAPE || (sm == END_BOTTOM && !(S->surface_albedo > 0.0))) {
+            if (S->path_bias == 1) {
+                /* path length stretching (Sect. 4.2): tau from the composite of the natural exponential and
+                   one stretched to the path, q = (e^-tau + a e^-a tau) / 2 with a = 1 / (1 + tau_m); the
+                   component is chosen by the third word of the event | 2^31 draw; weight e^-tau / q.  Not
+                   applied past the cut-off depth. */
+                if (sm != END_CUTOFF) {
+                    double v[4];
+                    draw(A->seed, n, ev | 0x80000000u, A->job_key, v);
+                    const double a = 1.0 / (1.0 + tau_m);
+                    tau_t = v[2] < 0.5 ? -log(u[0]) : -log(u[0]) / a;
+                    const double q = 0.5 * (exp(-tau_t) + a * exp(-a * tau_t));
+                    reweight(acc, &W, exp(-tau_t) / q);
+                }
+            } else if (sm == END_ESCAPE || (sm == END_BOTTOM && !(S->surface_albedo > 0.0))) {
                 const double p = -expm1(-tau_m);
                 const double rem = W * exp(-tau_m);
                 const int q = sm == END_ESCAPE ? 1 : 3;
@@ -909,6 +935,15 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
                 }
                 W *= p;
                 tau_t = -log1p(-u[0] * p);
+                if (S->path_bias == 2) {
+                    /* hybrid (Sect. 4.2): within the path, the composite of the truncated exponential
+                       e^-tau / p and the uniform 1 / tau_m; weight (e^-tau / p) / q */
+                    double v[4];
+                    draw(A->seed, n, ev | 0x80000000u, A->job_key, v);
+                    if (!(v[2] < 0.5)) tau_t = u[0] * tau_m;
+                    const double ft = exp(-tau_t) / p;
+                    reweight(acc, &W, ft / (0.5 * ft + 0.5 / tau_m));
+                }
             }
         }
         first = 0;

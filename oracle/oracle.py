@@ -60,7 +60,7 @@ class Source_c(C.Structure):
                 ("trans_scatter", C.c_int32), ("ld_law", C.c_int32), ("ld_coef", C.c_double * 4),
                 ("star_radius", C.c_double), ("star_dist", C.c_double), ("transit_xy", C.c_double * 2),
                 ("g_bias", C.c_int32), ("pad3", C.c_int32), ("g_beta", C.c_double),
-                ("forced_first", C.c_int32), ("cont_abs", C.c_int32)]
+                ("forced_first", C.c_int32), ("cont_abs", C.c_int32), ("path_bias", C.c_int32), ("pad4", C.c_int32)]
 
 
 class Run_c(C.Structure):
@@ -347,6 +347,7 @@ def _source_struct(src, obs):
         s.transit_xy[i] = float(v)
     s.forced_first = int(getattr(op, "forced_first", 0))
     s.cont_abs = int(getattr(op, "cont_abs", 0))
+    s.path_bias = int(getattr(op, "path_bias", 0))
     return s, len(obs)
 
 

@@ -140,6 +140,7 @@ class Options:
     g_beta: float = 0.5          # composite: q = (1 - g_beta) p + g_beta / N_g
     forced_first: int = 0        # forced scattering: 1 the first flight, 2 every flight
     cont_abs: int = 0            # continuous absorption
+    path_bias: int = 0           # biased flights: 0 forced, 1 path length stretching, 2 hybrid
 
 
 @dataclasses.dataclass
@@ -604,7 +605,8 @@ def uniform_scattering_sphere(alpha=8.0e-9, omega=1.0e-3, g=0.5, R0=R_JUP, H_atm
 
 
 def slab_sphere_albedo(omega=0.5, tau=20.0, phase="iso", g=0.0, n_packets=100_000, seed=12, thin=1.0e-4,
-                       nlon=8, nlat=8, survival=1, surface_albedo=0.0, obs=None, forced_first=0, cont_abs=0):
+                       nlon=8, nlat=8, survival=1, surface_albedo=0.0, obs=None, forced_first=0, cont_abs=0,
+                       path_bias=0):
     """Homogeneous one-layer atmosphere of thickness thin * R0 and vertical optical depth tau on a
     black (or Lambertian, surface_albedo) sphere: locally a plane-parallel slab.  phase = 'iso'
     (HG with g = 0), 'hg', 'tthg' (two-term HG of asymmetry g) or 'rayleigh'."""
@@ -622,7 +624,8 @@ def slab_sphere_albedo(omega=0.5, tau=20.0, phase="iso", g=0.0, n_packets=100_00
     src = Source(star=np.array([1.0, 0.0, 0.0]),
                  obs=np.array([[1.0, 0.0, 0.0]]) if obs is None else np.atleast_2d(np.asarray(obs, np.float64)),
                  opts=Options(survival=survival, w_rr=1e-4, cloud_phase=1 if phase == "tthg" else 0,
-                              surface_albedo=surface_albedo, forced_first=forced_first, cont_abs=cont_abs))
+                              surface_albedo=surface_albedo, forced_first=forced_first, cont_abs=cont_abs,
+                              path_bias=path_bias))
     jobs = [Job(lam_idx=0, g_idx=0, n_packets=n_packets, key=0)]
     return Workload(f"slab_{phase}_w{omega}_t{tau}", MODE_ALBEDO, grid, opac, src, jobs, seed)
 

@@ -90,3 +90,33 @@ def test_ledger_closes(survival):
         wl.source.opts.cont_abs = 1
         L = O.run(wl, wl.jobs[0], nthreads=4)["ledger"]
         assert abs((L[0] + L[4]) - (L[1] + L[2] + L[3] + L[5] + L[6] + L[7])) <= 1e-12 * L[0]
+
+
+@pytest.mark.parametrize("ff,pb", [(1, 1), (1, 2), (2, 1), (2, 2)])
+@pytest.mark.parametrize("phase,beta,omega,tau", [("rayleigh", [1.0, 0.0, 0.5], 0.6, 0.3),
+                                                  ("iso", [1.0], 0.9, 3.0)])
+def test_slab_albedo_unchanged_by_path_biasing(ff, pb, phase, beta, omega, tau):
+    """Path length stretching (composite of the natural and the stretched exponential) and the hybrid
+    (forced, composite of the truncated exponential and the uniform in tau) leave the albedo unchanged."""
+    wl = S.slab_sphere_albedo(omega=omega, tau=tau, phase=phase, n_packets=200_000, forced_first=ff, path_bias=pb)
+    est, sig, _ = _ag(wl)
+    ref = R.AddingDoubling(beta, omega, tau, n=40).geometric_albedo()
+    assert abs(est - ref) < 3 * sig + 1e-4 * ref, (est, ref, sig)
+
+
+def test_hybrid_lowers_variance_of_thin_slab():
+    kw = dict(omega=0.6, tau=0.1, phase="rayleigh", n_packets=100_000)
+    _, s0, _ = _ag(S.slab_sphere_albedo(**kw))
+    _, s2, _ = _ag(S.slab_sphere_albedo(forced_first=1, path_bias=2, **kw))
+    assert s2 < 0.5 * s0, (s2, s0)
+
+
+@pytest.mark.parametrize("pb", [1, 2])
+@pytest.mark.parametrize("survival", [1, 0])
+def test_ledger_closes_with_path_biasing(pb, survival):
+    """The p/q reweights of biased flights are booked with the roulette's gain and loss."""
+    wl = S.slab_sphere_albedo(omega=0.9, tau=3.0, phase="rayleigh", n_packets=20_000, forced_first=2, path_bias=pb,
+                              survival=survival, cont_abs=1)
+    L = O.run(wl, wl.jobs[0], nthreads=4)["ledger"]
+    assert L[4] > 0 and L[5] > 0
+    assert abs((L[0] + L[4]) - (L[1] + L[2] + L[3] + L[5] + L[6] + L[7])) <= 1e-12 * (L[0] + L[4])
