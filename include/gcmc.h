@@ -187,6 +187,12 @@ typedef struct {
     int32_t cont_abs;         /* 1 = continuous absorption (Sect. 4.1): flights sample their optical depth in the
                                  scattering opacity omega alpha, the weight decays by e^-tau_abs along the path
                                  (booked as absorbed) and every interaction scatters (peel-offs without omega) */
+    int32_t path_bias;        /* how the flights forced_first selects sample tau (Sect. 4.2): 0 forced scattering
+                                 (above); 1 path length stretching, not forced: tau from (e^-tau + a e^-a tau) / 2,
+                                 a = 1 / (1 + tau_m); 2 hybrid: forced, tau from the mean of the truncated
+                                 exponential and the uniform on [0, tau_m].  Both reweight the packet by p/q,
+                                 booked with the roulette's gain (ledger[4]) and loss (ledger[5]) */
+    int32_t pad4;
 } gcmc_source_desc;
 
 #define GCMC_GBIAS_NONE 0
@@ -215,7 +221,8 @@ typedef struct {
     int64_t packets;          /* packets run */
     int64_t steps;            /* packet-steps: cell segments processed in flights, peel-offs and chords */
     double ledger[8];         /* sum of weights: emitted, escaped, absorbed, bottom, roulette gain,
-                                 roulette loss, step-capped, lost (emitted + gain = the rest) */
+                                 roulette loss, step-capped, lost (emitted + gain = the rest); the gain and
+                                 loss entries also book the p/q reweights of stretched or hybrid flights */
     double l_tot;             /* emission: total luminosity of the emitting cells, W/m (Sect. 5.3) */
     double cdf_total;         /* emission: total of the hybrid pdf (1 up to rounding) */
     int64_t n_emit_cells;     /* emission: cells above the tau_vert cut */

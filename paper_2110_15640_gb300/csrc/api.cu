@@ -394,6 +394,7 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
         }
         d.n_tal = j.mode == GCMC_TRANSMISSION ? 1 + d.trans_scatter : d.n_obs;
         d.forced_first = s.forced_first;
+        d.path_bias = s.path_bias;
         d.cont_abs = s.cont_abs && d.rec4 ? 1 : 0;   // needs the scattering records' omega
         if (s.surface_albedo > 0.0 || s.cloud_phase == GCMC_CLOUD_TTHG || (j.mode == GCMC_TRANSMISSION &&
             (s.trans_scatter || s.ld_law != GCMC_LD_NONE)) || d.forced_first || d.cont_abs)
@@ -1106,8 +1107,9 @@ gcmc_status gcmc_set_source(gcmc_ctx *ctx, int grid_id, const gcmc_source_desc *
     for (int c = 0; c < 4; ++c)
         if (!std::isfinite(d->ld_coef[c])) return fail(ctx, GCMC_ERR_ARG, "limb-darkening coefficients must be finite");
     if (d->g_bias < GCMC_GBIAS_NONE || d->g_bias > GCMC_GBIAS_COMPOSITE) return fail(ctx, GCMC_ERR_ARG, "unknown g_bias");
-    if (d->forced_first < 0 || d->forced_first > 2 || (d->cont_abs != 0 && d->cont_abs != 1))
-        return fail(ctx, GCMC_ERR_ARG, "forced_first is 0, 1 or 2; cont_abs 0 or 1");
+    if (d->forced_first < 0 || d->forced_first > 2 || (d->cont_abs != 0 && d->cont_abs != 1) || d->path_bias < 0 ||
+        d->path_bias > 2)
+        return fail(ctx, GCMC_ERR_ARG, "forced_first and path_bias are 0, 1 or 2; cont_abs 0 or 1");
     if (!(d->g_beta >= 0.0 && d->g_beta <= 1.0)) return fail(ctx, GCMC_ERR_ARG, "g_beta must be in [0, 1]");
     *source_id = (int)ctx->sources.size();
     ctx->sources.push_back(*d);

@@ -106,8 +106,9 @@ struct DevJob {
     double surf_as, ld_c[4], star_r, tr_x, tr_y;   // surface albedo; limb darkening, stellar radius, planet offset
     float surf_as_f, ld_c_f[4], star_r_f, tr_x_f, tr_y_f;
     const void *arec;           // scattering records: their alpha as a compact table for the cell march
-    int32_t forced_first;       // forced scattering (albedo; transmission with multiple scattering)
+    int32_t forced_first;       // biased flights: 1 the first, 2 every flight (albedo; transmission scattering)
     int32_t cont_abs;           // continuous absorption (scattering records only)
+    int32_t path_bias, pad5;    // biased flights sample tau forced (0), stretched (1) or hybrid (2)
 };
 
 // job constants in the march precision (FP32 marches read the copies rounded on the host)

@@ -117,20 +117,50 @@ __device__ __forceinline__ void start_peel(Packet<real> &P, const DevJob &J, Sin
                     P.cj, P.ck, K_PEEL, (real)-1);
 }
 
-// a flight from the packet's point; forced: its optical depth follows the exponential truncated at the
-// boundary, -ln(1 - zeta p) with p = 1 - e^-tau_m (Sect. 4.2; p may round to 1 for deep paths, where the
-// truncated form still applies)
+// how a flight samples its optical depth (Sect. 4.2): the natural exponential; forced, the exponential
+// truncated at the boundary, -ln(1 - zeta p) with p = 1 - e^-tau_m (p may round to 1 on deep paths, where
+// the truncated form still applies); path length stretching, the composite (e^-tau + a e^-a tau) / 2 with
+// a = 1 / (1 + tau_m); hybrid, forced with the composite of the truncated exponential and the uniform on
+// [0, tau_m].  The composites choose their component by the third word of the event | 2^31 draw and
+// reweight the packet by p(tau) / q(tau), booked with the roulette's gain and loss.
+enum { FL_NATURAL = 0, FL_FORCED = 1, FL_STRETCH = 2, FL_HYBRID = 3 };
+
+template <typename real, class SinkT>
+__device__ __noinline__ void reweight(Packet<real> &P, SinkT &S, real factor)
+{
+    const real Wn = P.W * factor;
+    if (Wn > P.W) S.ledger(4, Wn - P.W);
+    else S.ledger(5, P.W - Wn);
+    P.W = Wn;
+}
+
 template <typename real, class SinkT>
 __device__ __forceinline__ void start_flight(Packet<real> &P, const DevJob &J, SinkT &S, real dx, real dy, real dz,
-                                             bool forced = false, real p = (real)1)
+                                             int mode = FL_NATURAL, real p = (real)1, real taum = (real)0)
 {
     const uint4 w = draw_words(J.seed, P.n, P.ev, J.key);
     real tau;
-    if (forced) {
-        if constexpr (sizeof(real) == 8) tau = -log1p(-u01<real>(w.x) * p);
-        else tau = -log1pf(-u01<real>(w.x) * p);
-    } else {
+    if (mode == FL_NATURAL) {
         tau = -M<real>::log_(u01<real>(w.x));
+    } else {
+        const real u = u01<real>(w.x);
+        if (mode == FL_STRETCH) {
+            const uint4 v = draw_words(J.seed, P.n, P.ev | 0x80000000u, J.key);
+            const real a = (real)1 / ((real)1 + taum);
+            tau = -M<real>::log_(u);
+            if (!(u01<real>(v.z) < (real)0.5)) tau = tau / a;
+            const real q = (real)0.5 * (M<real>::exp_(-tau) + a * M<real>::exp_(-a * tau));
+            reweight<real>(P, S, M<real>::exp_(-tau) / q);
+        } else {
+            if constexpr (sizeof(real) == 8) tau = -log1p(-u * p);
+            else tau = -log1pf(-u * p);
+            if (mode == FL_HYBRID) {
+                const uint4 v = draw_words(J.seed, P.n, P.ev | 0x80000000u, J.key);
+                if (!(u01<real>(v.z) < (real)0.5)) tau = u * taum;
+                const real ft = M<real>::exp_(-tau) / p;
+                reweight<real>(P, S, ft / ((real)0.5 * ft + (real)0.5 / taum));
+            }
+        }
     }
     S.trace(P.n, -1, (real)0);
     start_ray<real>(P, P.ix, P.iy, P.iz, dx, dy, dz, P.ci, P.cj, P.ck, K_FLIGHT, tau);
@@ -510,7 +540,10 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
                 return;
             }
             real p = (real)1;
-            const bool forced = e == E_ESCAPE || (e == E_BOTTOM && !(JV<real>::surf_as(J) > (real)0));
+            const bool forced = J.path_bias != 1 &&
+                                (e == E_ESCAPE || (e == E_BOTTOM && !(JV<real>::surf_as(J) > (real)0)));
+            int mode = forced ? (J.path_bias == 2 ? FL_HYBRID : FL_FORCED) : FL_NATURAL;
+            if (J.path_bias == 1 && e != E_CUTOFF) mode = FL_STRETCH;   // stretching does not force
             if (forced) {
                 real em;
                 if constexpr (sizeof(real) == 8) em = expm1(-R.tau);
@@ -527,7 +560,7 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
                 }
                 P.W *= p;
             }
-            start_flight<real>(P, J, S, P.fx, P.fy, P.fz, forced, p);
+            start_flight<real>(P, J, S, P.fx, P.fy, P.fz, mode, p, R.tau);
             return;
         }
         if (P.kind == K_FLIGHT && J.cont_abs) {

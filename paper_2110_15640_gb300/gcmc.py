@@ -51,7 +51,8 @@ class gcmc_source_desc(C.Structure):
                 ("surface_albedo", C.c_double), ("trans_scatter", C.c_int32), ("ld_law", C.c_int32),
                 ("ld_coef", C.c_double * 4), ("star_radius", C.c_double), ("star_dist", C.c_double),
                 ("transit_xy", C.c_double * 2), ("g_bias", C.c_int32), ("pad3", C.c_int32),
-                ("g_beta", C.c_double), ("forced_first", C.c_int32), ("cont_abs", C.c_int32)]
+                ("g_beta", C.c_double), ("forced_first", C.c_int32), ("cont_abs", C.c_int32),
+                ("path_bias", C.c_int32), ("pad4", C.c_int32)]
 
 
 class gcmc_stats(C.Structure):
@@ -331,7 +332,7 @@ class Context:
         d.star_radius, d.star_dist = float(op.star_radius), float(op.star_dist)
         d.transit_xy[0], d.transit_xy[1] = (float(v) for v in op.transit_xy)
         d.g_bias, d.g_beta = int(op.g_bias), float(op.g_beta)
-        d.forced_first, d.cont_abs = int(op.forced_first), int(op.cont_abs)
+        d.forced_first, d.cont_abs, d.path_bias = int(op.forced_first), int(op.cont_abs), int(op.path_bias)
         sid = C.c_int()
         self._check(lib().gcmc_set_source(self.h, int(grid_id), C.byref(d), C.byref(sid)), "gcmc_set_source")
         return sid.value

@@ -28,13 +28,14 @@ def G():
     ctx.close()
 
 
-def cloudy(n, survival=1, transit=False, ff=1):
+def cloudy(n, survival=1, transit=False, ff=1, pb=0):
     """The phase-curve atmosphere on a 12x6x10 grid, gas absorption cut 1000x and Rayleigh 10x, two-term HG
     clouds, forced first scattering and continuous absorption; either over a Lambertian surface (A_s =
     0.5, four phase observers) or seen in transit with multiple scattering."""
     wl = S.config3_phase_curve(nlon=12, nlat=6, nr=10, nlam=2, nphase=4, n_lo=n, n_hi=n)
     opac = dataclasses.replace(wl.opac, kabs=wl.opac.kabs * 1e-3, kray=wl.opac.kray * 0.1)
-    opts = dataclasses.replace(wl.source.opts, cloud_phase=1, survival=survival, forced_first=ff, cont_abs=1)
+    opts = dataclasses.replace(wl.source.opts, cloud_phase=1, survival=survival, forced_first=ff, cont_abs=1,
+                               path_bias=pb)
     if transit:
         opts = dataclasses.replace(opts, trans_scatter=1)
         src = S.Source(star=np.array([1.0, 0.0, 0.0]), obs=np.array([[-1.0, 0.0, 0.0]]), opts=opts)
@@ -50,11 +51,12 @@ def _load(ctx, wl, prec):
     return gcmc.load_workload(ctx, wl, prec)
 
 
-@pytest.mark.parametrize("transit,survival,ff", [(False, 1, 1), (False, 0, 1), (True, 1, 1), (True, 0, 1),
-                                                 (False, 1, 2), (True, 0, 2)])
-def test_fp64_per_packet_parity(G, survival, transit, ff):
+@pytest.mark.parametrize("transit,survival,ff,pb", [(False, 1, 1, 0), (False, 0, 1, 0), (True, 1, 1, 0), (True, 0, 1, 0),
+                                                    (False, 1, 2, 0), (True, 0, 2, 0), (False, 1, 1, 1), (True, 0, 2, 1),
+                                                    (False, 0, 2, 2), (True, 1, 1, 2)])
+def test_fp64_per_packet_parity(G, survival, transit, ff, pb):
     from paper_2110_15640_gb300 import gcmc
-    wl = cloudy(3000, survival, transit, ff)
+    wl = cloudy(3000, survival, transit, ff, pb)
     job = wl.jobs[0]
     gid, oid, sid, jobs = _load(G, wl, gcmc.FP64)
     ncol = O.tally_cols(wl, job)
@@ -83,10 +85,10 @@ def test_fp64_per_packet_parity(G, survival, transit, ff):
     assert L[2] > 0 and abs((L[0] + L[4]) - (L[1] + L[2] + L[3] + L[5] + L[6] + L[7])) <= 1e-12 * L[0]
 
 
-@pytest.mark.parametrize("transit,ff", [(False, 1), (True, 1), (False, 2)])
-def test_fp32_matches_oracle(G, transit, ff):
+@pytest.mark.parametrize("transit,ff,pb", [(False, 1, 0), (True, 1, 0), (False, 2, 0), (False, 2, 1), (True, 1, 2)])
+def test_fp32_matches_oracle(G, transit, ff, pb):
     from paper_2110_15640_gb300 import gcmc
-    wl = cloudy(20000, 1, transit, ff)
+    wl = cloudy(20000, 1, transit, ff, pb)
     job = wl.jobs[0]
     gid, oid, sid, jobs = _load(G, wl, gcmc.FP32)
     ncol = O.tally_cols(wl, job)
