@@ -27,7 +27,13 @@
  *  - Determinism: tallies depend only on (grid, opacity, source, mode, lambda, g, N, seed, job
  *    key).  Packets draw counter-based Philox4x32-10 numbers keyed by (seed; packet, event, job
  *    key); tallies are accumulated as 64-bit fixed point (2^-32 resolution), so the result of a
- *    job is bit-identical whether it runs alone or batched with other jobs.
+ *    job is bit-identical whether it runs alone or batched with other jobs that use the same optional
+ *    features.  The transport kernels are compiled in variants with and without the optional physics
+ *    (surfaces, two-term HG, transmission scattering, limb darkening, biased flights, continuous
+ *    absorption) and band jobs' tables; a batch runs in the variant its jobs need, and a job batched
+ *    with jobs that need another variant can differ from its run alone at FP32 rounding.  The server
+ *    (gcmc_server_*) runs every request in its own variant, so a served request is bit-identical
+ *    alone and in any mix.
  *  - Units: SI (m, m^-1, m^2/kg, kg/m^3, K, Pa, W).  Per-cell arrays are flattened [k][j][i]
  *    with longitude fastest; k = 0 is the bottom shell.
  */

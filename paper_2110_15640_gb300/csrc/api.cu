@@ -1641,6 +1641,7 @@ struct gcmc_server {
         int64_t n_items = 0;
         const DevJob *djob = nullptr;
         bool published = false;
+        bool ext = false;             // needs the kernel variant with the optional physics
         double t[4] = {0, 0, 0, 0};   // submitted, admitted, published, completed (s since creation)
     };
     struct Result {
@@ -1669,6 +1670,7 @@ struct gcmc_server {
     uint32_t next_gen = 0;
     cudaEvent_t kdone = nullptr;
     bool kernel_started = false;
+    bool kernel_ext = false;          // the running (or last) serving kernel carries the optional physics
     int tab_n = 0;
     int64_t kernel_launches = 0, completed = 0;
     int grid_blocks = 0;
@@ -1734,6 +1736,7 @@ gcmc_status server_admit(gcmc_server *sv)
         j.slot = slot;
         sv->free_slots.pop_back();
         j.n_obs = P.jobs[0].n_tal;
+        j.ext = (P.feat & FEAT_EXT) != 0;
         j.n_items = (j.job.n_packets + sv->cfg.chunk - 1) / sv->cfg.chunk;
         j.djob = reinterpret_cast<const DevJob *>((char *)ws + P.off_jobs);
         j.gen = (++sv->next_gen) & 0xFFFFFFu;
@@ -1760,8 +1763,21 @@ gcmc_status server_publish(gcmc_server *sv)
     gcmc_ctx *ctx = sv->ctx;
     bool any = false;
     const uint64_t oldest = oldest_open(sv);
+    // Every request runs in its own kernel variant (with or without the optional physics), so that its
+    // result does not depend on what it is served with: the two variants round some FP32 operations
+    // differently.  While a ready request needs the other variant than the running kernel, nothing more
+    // is published; the kernel drains and leaves, and the next launch takes the variant of the oldest
+    // ready request (server_kick), publishing only requests of that variant.
+    const bool running = kernel_running(sv);
+    int variant = running ? (sv->kernel_ext ? 1 : 0) : -1;
+    for (const auto &j : sv->admitted) {
+        if (j.published || cudaEventQuery(j.prepped) != cudaSuccess) continue;
+        if (variant < 0) variant = j.ext ? 1 : 0;            // oldest ready request chooses the next launch
+        else if ((j.ext ? 1 : 0) != variant && running) return GCMC_OK;
+    }
     for (auto &j : sv->admitted) {
         if (j.published) continue;
+        if ((j.ext ? 1 : 0) != variant) continue;
         if (sv->next_seg - oldest >= SERVE_RING / 2) break;
         const cudaError_t e = cudaEventQuery(j.prepped);
         if (e == cudaErrorNotReady) continue;
@@ -1822,14 +1838,18 @@ gcmc_status server_kick(gcmc_server *sv)
             break;
         }
     if (!open || kernel_running(sv)) return GCMC_OK;
+    bool ext = false;   // the variant: with the optional physics when an open job needs it
+    for (const auto &j : sv->admitted)
+        if (j.published && j.ext) ext = true;
     const int idle_polls = sv->cfg.idle_us > 0 ? sv->cfg.idle_us : 2000;
     // a fresh launch: no warp idle, not leaving (stream-ordered after the previous launch)
     CK(cudaMemsetAsync(sv->q.n_idle, 0, 16, sv->s_serve));
-    cudaError_t e = launch_serve(ctx->d_grids, sv->q, sv->cfg.block, sv->cfg.blocks_per_sm, sv->cfg.chunk, sv->cfg.interval,
+    cudaError_t e = launch_serve(ext, ctx->d_grids, sv->q, sv->cfg.block, sv->cfg.blocks_per_sm, sv->cfg.chunk, sv->cfg.interval,
                                  sv->cfg.refill_min, sv->tab_n, idle_polls, &sv->grid_blocks, sv->s_serve);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "serving kernel launch");
     CK(cudaEventRecord(sv->kdone, sv->s_serve));
     sv->kernel_started = true;
+    sv->kernel_ext = ext;
     ++sv->kernel_launches;
     return GCMC_OK;
 }

@@ -144,7 +144,8 @@ struct ServeQueue {
     unsigned long long *slot_next;          // device [slots]: next item of the slot's job to claim
     unsigned long long *slot_done;          // device [slots]: items of the slot's job finished
 };
-cudaError_t launch_serve(const DevGrid *grids, const ServeQueue &q, int block, int blocks_per_sm, int chunk, int interval,
+cudaError_t launch_serve(bool ext, const DevGrid *grids, const ServeQueue &q, int block, int blocks_per_sm, int chunk,
+                         int interval,
                          int refill_min, int tab_n, int idle_polls, int *grid_blocks, cudaStream_t st);
 
 // transport

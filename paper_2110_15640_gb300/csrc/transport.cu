@@ -966,7 +966,7 @@ __device__ __forceinline__ void st_release_sys(unsigned long long *p, unsigned l
     asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-template <typename real, bool SCAT>
+template <typename real, bool SCAT, int FEAT>
 __global__ void __launch_bounds__(128, 4) k_transport_serve(const DevGrid *__restrict__ grids, ServeQueue q, int chunk,
                                                          int interval, int refill_min, int tab_n, int idle_polls)
 {
@@ -1045,8 +1045,7 @@ __global__ void __launch_bounds__(128, 4) k_transport_serve(const DevGrid *__res
             __syncwarp();
         }
         const int64_t p0 = (int64_t)item * chunk;
-        run_item<real, SCAT, FEAT_EXT | FEAT_CABS>(J, G, T, p0, min(p0 + (int64_t)chunk, J.n_packets), interval,
-                                                   refill_min, S);
+        run_item<real, SCAT, FEAT>(J, G, T, p0, min(p0 + (int64_t)chunk, J.n_packets), interval, refill_min, S);
         flush(S.sm, S.stride, J.acc);
         __threadfence();
         unsigned long long fin = 0;
@@ -1181,7 +1180,8 @@ static cudaError_t persistent_dispatch(int block, int blocks_per_sm, int nsm, co
                                                 interval, refill_min, one_grid, tab_n, work, st);
 }
 
-cudaError_t launch_serve(const DevGrid *grids, const ServeQueue &q, int block, int blocks_per_sm, int chunk, int interval,
+cudaError_t launch_serve(bool ext, const DevGrid *grids, const ServeQueue &q, int block, int blocks_per_sm, int chunk,
+                         int interval,
                          int refill_min, int tab_n, int idle_polls, int *grid_blocks, cudaStream_t st)
 {
     int dev = 0, nsm = 0;
@@ -1190,7 +1190,8 @@ cudaError_t launch_serve(const DevGrid *grids, const ServeQueue &q, int block, i
     if (block != 128) return cudaErrorInvalidValue;
     if (interval < 1) interval = 1;
     refill_min = refill_min < 1 ? 1 : refill_min > 32 ? 32 : refill_min;
-    auto kern = k_transport_serve<float, true>;
+    // the plain variant, or every optional physics (band jobs are not served)
+    auto kern = ext ? k_transport_serve<float, true, FEAT_EXT | FEAT_CABS> : k_transport_serve<float, true, 0>;
     const size_t sm = transport_smem(block) + (size_t)tab_n * sizeof(float2) * (block / 32);
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int occ = 0;

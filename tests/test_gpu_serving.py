@@ -127,6 +127,28 @@ def test_served_optional_physics(setup):
         for q, j in enumerate(jobs):
             alone = sv.run_all([j])[0]
             assert np.array_equal(alone[0], mixed[q][0]) and alone[1].steps == mixed[q][1].steps
+        # plain requests, then these while the plain kernel runs: the server switches kernel variants (the
+        # plain kernel drains before one with the optional physics starts), and every request still
+        # equals itself served alone, bit for bit
+        import time
+        plain = list(setup[3][:4])
+        t0 = time.perf_counter()
+        while sv.query().kernel_running and time.perf_counter() - t0 < 10.0:   # the last kernel leaves when idle
+            sv.progress()
+            time.sleep(0.01)
+        n0 = sv.query().kernel_launches
+        tickets = [sv.submit(j) for j in plain]
+        got = {}
+        t0 = time.perf_counter()
+        while not sv.query().kernel_running and len(got) < len(tickets) and time.perf_counter() - t0 < 10.0:
+            for t in sv.progress():
+                got[t] = sv.result(t)
+        tickets += [sv.submit(j) for j in jobs]      # held until the plain kernel has drained
+        _drain(sv, len(tickets), got)
+        assert sv.query().kernel_launches >= n0 + 2
+        for t, j in zip(tickets, plain + jobs):
+            alone = sv.run_all([j])[0]
+            assert np.array_equal(alone[0], got[t][0]) and alone[1].steps == got[t][1].steps
     finally:
         sv.close()
     tb, sb = ctx.run_batch(jobs)
