@@ -351,3 +351,32 @@ def test_doppler_zero_wind_is_unshifted_and_rotation_matches_vector_form():
     vec = u[..., None] * east + v[..., None] * north + w[..., None] * pos[None]
     refw = -(vec @ n_obs).reshape(-1) + ref
     assert np.max(np.abs(c["vlos"] - refw)) < 1e-9 * np.max(np.abs(refw))
+
+
+def test_uniform_translation_shifts_the_spectrum_by_whole_bins():
+    """A planet moving bodily away from the observer at v sees every line at lambda / (1 - v/c) (Sect. 7).
+    On a table uniform in ln(lambda) with step 1/R, v = c (1 - e^(-k/R)) moves the opacity spectrum of
+    every cell by exactly k table bins, whatever the interpolation between bins."""
+    Rres, k, n = 1.0e5, 3, 160
+    lam = 1.0e-6 * np.exp(np.arange(n) / Rres)
+    line = 1.0e-3 * (1.0 + 200.0 * np.exp(-0.5 * ((np.arange(n) - 80.0) / 6.0) ** 2))
+    sigma = np.broadcast_to(line[:, None, None], (n, 2, 2)).astype(np.float32)
+    xs = S.XsecTable(lam=lam, Tg=np.array([500.0, 3000.0]), pg=np.array([1.0, 1.0e7]), sigma=sigma)
+    g = S.uniform_grid(6, 4, 2, S.R_JUP, 1.1 * S.R_JUP)
+    v = 2.99792458e8 * -math.expm1(-k / Rres)
+    n_obs = np.array([math.sin(xs.view_theta) * math.cos(xs.view_phi),
+                      math.sin(xs.view_theta) * math.sin(xs.view_phi), math.cos(xs.view_theta)])
+    V = -v * n_obs                       # recession from the observer at speed v
+    LAT, LON = S.cell_centres(g.nlon, g.nlat, g.lat_edges, g.lon_edges)
+    east = np.stack([-np.sin(LON), np.cos(LON), 0 * LON], -1)
+    north = np.stack([-np.sin(LAT) * np.cos(LON), -np.sin(LAT) * np.sin(LON), np.cos(LAT)], -1)
+    up = np.stack([np.cos(LAT) * np.cos(LON), np.cos(LAT) * np.sin(LON), np.sin(LAT)], -1)
+    comp = [np.broadcast_to(e @ V, (g.nr, g.nlat, g.nlon)).reshape(-1) for e in (east, north, up)]
+    moving = S.Grid(**{**g.__dict__, "wind": np.stack(comp).astype(np.float32)})
+    still = [O.prep_xsec(g, xs, i)["alpha"] for i in range(n)]
+    for i in range(k, n):
+        c = O.prep_xsec(moving, xs, i)
+        assert np.allclose(c["vlos"], v, rtol=1e-6, atol=0)
+        np.testing.assert_allclose(c["alpha"], still[i - k], rtol=1e-6)
+    # the line centre moves by lambda_c v / c to first order
+    assert abs(lam[80 + k] - lam[80] - lam[80] * v / 2.99792458e8) < 1e-4 * lam[80] * v / 2.99792458e8
