@@ -29,8 +29,7 @@ def sample_jobs(jobs, min_jobs=16, min_packets=16_000_000):
     n = len(jobs)
     mean = max(1.0, sum(j.n_packets for j in jobs) / max(n, 1))
     want = min(n, max(min_jobs, int(-(-min_packets // mean))))
-    stride = max(1, n // want)
-    return jobs[::stride][:want]
+    return [jobs[(q * n) // want] for q in range(want)]
 
 
 def _time_cfg(ctx, jobs, cfg, reps, stream):
@@ -49,7 +48,7 @@ def _time_cfg(ctx, jobs, cfg, reps, stream):
 
 def tune(ctx, jobs, stream, space=None, reps=2, coordinate=True, log=None):
     """Return (best gcmc_launch_cfg, table of (cfg dict, ms)).  coordinate=True searches one axis at a
-    time from the defaults (about a dozen runs) instead of the full product."""
+    time from the defaults, twice over (about thirty runs), instead of the full product."""
     space = space or DEFAULT_SPACE
     best = {"block": 128, "blocks_per_sm": 6, "chunk": 512, "refill_min": 8, "interval": 4}
     table = []
