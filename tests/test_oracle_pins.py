@@ -296,6 +296,23 @@ def test_isothermal_shell_emission_matches_closed_form():
     assert abs(est - ref) < 3 * sig + 2e-4 * ref, (est, ref, sig)
 
 
+def test_thick_transparent_shell_emission_is_occulted_by_the_core():
+    """An optically thin isothermal shell R0..2R0 held in one cell emits uniformly per volume; towards a
+    distant observer the black core hides the points in its cylindrical shadow, of volume
+    2 pi/3 [R_TOA^3 - (R_TOA^2 - R0^2)^(3/2) - R0^3].  The visible fraction pins the launch position
+    (uniform in r^3, sin(lat) and lon) and the occultation of peel-offs by the lower boundary."""
+    wl = S.isothermal_emitter(tau=1e-6, thin=1.0, nlon=1, nlat=1, nr=1, n_packets=200_000)
+    g = wl.grid
+    r = O.run(wl, wl.jobs[0], per_packet=True, nthreads=8)
+    f = 4 * math.pi * r["pk_f"][:, 0]          # W e^-tau with W = 1 for a single emitting cell
+    est, sig = f.mean(), f.std() / math.sqrt(len(f))
+    R0, Rt = g.R0, g.R_toa
+    v_shadow = 2 * math.pi / 3 * (Rt ** 3 - (Rt ** 2 - R0 ** 2) ** 1.5 - R0 ** 3)
+    ref = 1.0 - v_shadow / (4 * math.pi / 3 * (Rt ** 3 - R0 ** 3))
+    # e^-tau of the longest path is 1 - 4e-6
+    assert abs(est - ref) < 3 * sig + 4e-6, (est, ref, sig)
+
+
 def test_emission_tables():
     wl = S.config2_emission(n_packets=1000, nlon=16, nlat=8, nr=12, nb=3, ng=2)
     g = wl.grid

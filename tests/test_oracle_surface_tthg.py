@@ -7,6 +7,8 @@ against closed forms and an independent plane-parallel solver:
   has mean cosine a g1 + (1 - a) g2, and its sampler follows its CDF (KS test);
 * a homogeneous TTHG slab on a black sphere has the geometric albedo of the adding-doubling solver fed
   the TTHG Legendre moments beta_l = (2l + 1)(a g1^l + (1 - a) g2^l);
+* through a purely absorbing layer over a white Lambert sphere the escaping fraction is (2 E3(tau))^2,
+  which pins the cosine-weighted direction of the reflected light;
 * the energy ledger closes with a reflecting surface (survival biasing and analog)."""
 import math
 
@@ -77,6 +79,21 @@ def test_tthg_slab_matches_adding_doubling(omega, tau):
     est, sig = f.mean(), f.std() / math.sqrt(len(f))
     ref = R.AddingDoubling(beta, omega, tau, n=48).geometric_albedo()
     assert abs(est - ref) < 3 * sig + 1e-4 * ref, (est, ref, sig)
+
+
+@pytest.mark.parametrize("tau", [0.2, 0.5])
+def test_lambert_reflection_through_absorbing_layer(tau):
+    """A purely absorbing thin layer of vertical depth tau over a white Lambert sphere: starlight over the
+    disk reaches the surface with mean transmission 2 E3(tau) (incidence cosines have density 2 mu), and
+    the cosine-weighted reflected light leaves with the same 2 E3(tau), so the escaping fraction of the
+    incident power is (2 E3(tau))^2 (an isotropic reflection would give 2 E3(tau) E2(tau))."""
+    from scipy.special import expn
+    wl = S.slab_sphere_albedo(omega=0.0, tau=tau, phase="iso", n_packets=200_000, surface_albedo=1.0)
+    L = O.run(wl, wl.jobs[0], nthreads=8)["ledger"]
+    est = L[1] / L[0]
+    sig = math.sqrt(est * (1 - est) / wl.jobs[0].n_packets)
+    ref = (2 * expn(3, tau)) ** 2
+    assert abs(est - ref) < 3 * sig + 1e-3 * ref, (est, ref, sig)
 
 
 @pytest.mark.parametrize("survival", [1, 0])

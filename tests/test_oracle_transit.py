@@ -12,6 +12,7 @@ against closed forms and quadratures written from the geometry, not from the ora
   HG g = 0.5 makes forward and backward Theta differ 27-fold and the thick shell (R_t = 2 R0) makes
   b/R_t range over [0.5, 1], so a wrong peel direction or a missing b/R_t fails;
 * the ledger closes under survival biasing and analog scattering;
+* the stellar solid angle Omega_star against its small-disk series pi x^2 (1 + x^2/4 + x^4/8);
 * the transit post-scale: no scattering and no limb darkening give R0^2 + 2 I_p."""
 import math
 
@@ -109,6 +110,17 @@ def test_ledger_closes_transmission_scattering(survival):
     L = O.run(wl, wl.jobs[0], nthreads=4)["ledger"]
     assert L[1] > 0 and L[2] > 0
     assert abs((L[0] + L[4]) - (L[1] + L[2] + L[3] + L[5] + L[6] + L[7])) <= 1e-12 * L[0]
+
+
+@pytest.mark.parametrize("x", [0.1, 0.01])
+def test_stellar_solid_angle_small_disk_series(x):
+    """Omega_star of a stellar disk of angular radius asin(x), x = R_star / d, against its series
+    pi x^2 (1 + x^2/4 + x^4/8): the first term is the disk area over d^2."""
+    wl = S.uniform_scattering_sphere(n_packets=10, star_radius=x * 1.0e9, star_dist=1.0e9)
+    r = O.run(wl, wl.jobs[0])
+    om = O.transit(wl, r["tally"], 10)["omega_star"]
+    ref = math.pi * x * x * (1 + x * x / 4 + x ** 4 / 8)
+    assert abs(om / ref - 1) < 1e-7, (om, ref)
 
 
 def test_transit_postscale_reduces_to_area():
