@@ -114,7 +114,12 @@ def _grids():
     lat3 = np.array([-math.pi / 2, -0.9, -0.2, 0.0, 0.35, 1.1, math.pi / 2])
     lon3 = np.linspace(0.3, 0.3 + 2 * math.pi, 6)
     g3 = S.uniform_grid(5, 6, 4, 1.0, 1.5, lat_edges=lat3, lon_edges=lon3)
-    return [g1, g2, g3]
+    # degenerate grids: two longitude cells (both edges lie in the plane y = 0, so only the half-plane
+    # test tells them apart), one longitude cell, one latitude band
+    g4 = S.uniform_grid(2, 3, 3, 1.0, 2.0)
+    g5 = S.uniform_grid(1, 1, 2, 1.0, 2.0)
+    g6 = S.uniform_grid(3, 1, 2, 1.0, 2.0)
+    return [g1, g2, g3, g4, g5, g6]
 
 
 def _random_interior_point(rng, g):
@@ -142,7 +147,7 @@ def _compare(g, o, d):
         assert abs(rl - l) <= 1e-12 * scale + 1e-10 * rl
 
 
-@pytest.mark.parametrize("gi", [0, 1, 2])
+@pytest.mark.parametrize("gi", [0, 1, 2, 3, 4, 5])
 def test_march_matches_brute_force_random_rays(gi):
     g = _grids()[gi]
     rng = np.random.default_rng(100 + gi)
@@ -250,6 +255,33 @@ def test_geometric_albedo_matches_adding_doubling(phase, beta, omega, tau):
     f = math.pi * r["pk_f"][:, 0]
     est, sig = f.mean(), f.std() / math.sqrt(len(f))
     ref = R.AddingDoubling(beta, omega, tau, n=40).geometric_albedo()
+    assert abs(est - ref) < 3 * sig + 1e-5 * ref, (est, ref, sig)
+
+
+@pytest.mark.parametrize("phase,beta,omega,tau", [AD_CASES[2], AD_CASES[4]])
+def test_analog_scattering_matches_adding_doubling(phase, beta, omega, tau):
+    """Analog mode (scatter with probability omega, else absorb) has the same expectation."""
+    wl = S.slab_sphere_albedo(omega=omega, tau=tau, phase=phase, n_packets=200_000, survival=0)
+    r = O.run(wl, wl.jobs[0], per_packet=True, nthreads=8)
+    f = math.pi * r["pk_f"][:, 0]
+    est, sig = f.mean(), f.std() / math.sqrt(len(f))
+    ref = R.AddingDoubling(beta, omega, tau, n=40).geometric_albedo()
+    assert abs(est - ref) < 3 * sig + 1e-5 * ref, (est, ref, sig)
+    assert r["ledger"][4] == 0 and r["ledger"][2] > 0
+
+
+def test_frequent_roulette_matches_adding_doubling():
+    """Russian roulette at W < 0.5 W_launch with survival probability 0.5 (so after nearly every second
+    scattering) leaves the expectation unchanged: survivors carry W / p_surv."""
+    phase, beta, omega, tau = AD_CASES[0]
+    wl = S.slab_sphere_albedo(omega=omega, tau=tau, phase=phase, n_packets=200_000)
+    wl.source.opts.w_rr, wl.source.opts.p_surv = 0.5, 0.5
+    r = O.run(wl, wl.jobs[0], per_packet=True, nthreads=8)
+    f = math.pi * r["pk_f"][:, 0]
+    est, sig = f.mean(), f.std() / math.sqrt(len(f))
+    ref = R.AddingDoubling(beta, omega, tau, n=40).geometric_albedo()
+    L = r["ledger"]
+    assert L[4] > 0.05 * L[0] and L[5] > 0.05 * L[0]
     assert abs(est - ref) < 3 * sig + 1e-5 * ref, (est, ref, sig)
 
 
@@ -368,6 +400,24 @@ def test_doppler_zero_wind_is_unshifted_and_rotation_matches_vector_form():
     vec = u[..., None] * east + v[..., None] * north + w[..., None] * pos[None]
     refw = -(vec @ n_obs).reshape(-1) + ref
     assert np.max(np.abs(c["vlos"] - refw)) < 1e-9 * np.max(np.abs(refw))
+
+
+def test_power_law_opacity_is_interpolated_exactly():
+    """k(T, p) = k0 (T/T0)^a (p/p0)^b is linear in (ln T, ln p), so the bilinear interpolation of ln k in
+    (ln T, ln p) (Sect. 7) returns it exactly between the table nodes, to the FP32 rounding of the table
+    (an interpolation linear in T or p would be off by up to percents).  Both the k-table and the
+    cross-section path."""
+    g, _ = S.hotjupiter_grid(16, 8, 12)
+    Tg, pg = np.geomspace(500.0, 3000.0, 4), np.geomspace(1e-1, 1e7, 5)
+    law = lambda T, p: 1e-3 * (T / 1500.0) ** 1.3 * (p / 1e5) ** 0.45  # noqa: E731
+    k = law(Tg[:, None], pg[None, :])
+    ref = g.rho.astype(np.float64) * law(g.T.astype(np.float64), g.p.astype(np.float64))
+    kt = S.KTable(lam=np.array([2e-6]), wg=np.array([1.0]), gpts=np.array([0.5]), Tg=Tg, pg=pg,
+                  k=k[None, None].astype(np.float32))
+    np.testing.assert_allclose(O.prep_emission(g, kt, 0, 0, S.Options())["alpha"], ref, rtol=1e-6)
+    xs = S.XsecTable(lam=np.array([1.0e-6, 1.1e-6]), Tg=Tg, pg=pg,
+                     sigma=np.broadcast_to(k, (2,) + k.shape).astype(np.float32))
+    np.testing.assert_allclose(O.prep_xsec(g, xs, 0)["alpha"], ref, rtol=1e-6)
 
 
 def test_uniform_translation_shifts_the_spectrum_by_whole_bins():

@@ -13,6 +13,8 @@ against closed forms and quadratures written from the geometry, not from the ora
   b/R_t range over [0.5, 1], so a wrong peel direction or a missing b/R_t fails;
 * the ledger closes under survival biasing and analog scattering;
 * the stellar solid angle Omega_star against its small-disk series pi x^2 (1 + x^2/4 + x^4/8);
+* an opaque planet small against the star: depth (R_TOA/R_star)^2 I(mu_c)/n_LD; scattered light
+  lowers the effective blocked area;
 * the transit post-scale: no scattering and no limb darkening give R0^2 + 2 I_p."""
 import math
 
@@ -121,6 +123,39 @@ def test_stellar_solid_angle_small_disk_series(x):
     om = O.transit(wl, r["tally"], 10)["omega_star"]
     ref = math.pi * x * x * (1 + x * x / 4 + x ** 4 / 8)
     assert abs(om / ref - 1) < 1e-7, (om, ref)
+
+
+def test_opaque_small_planet_depth_with_limb_darkening():
+    """An opaque atmosphere blocks the disk of radius R_TOA.  Small against the star (R_TOA = R_star/100),
+    it hides the intensity at its centre, so the depth is (R_TOA/R_star)^2 I(mu_c)/n_LD, with
+    mu_c = sqrt(1 - rho_c^2/R_star^2) at the planet's sky position rho_c and n_LD = 1 - c1/3 - c2/6 for
+    the quadratic law (the variation of I across the planet enters at order (R_TOA/R_star)^2)."""
+    c1, c2 = 0.4, 0.25
+    wl = S.uniform_scattering_sphere(alpha=1e-3, omega=0.0, trans_scatter=0, n_packets=100_000, ld_law=2,
+                                     ld_coef=(c1, c2, 0.0, 0.0))
+    g = wl.grid
+    Rs = 100.0 * g.R_toa
+    wl.source.opts.star_radius = Rs
+    wl.source.opts.transit_xy = (0.6 * Rs, 0.0)
+    n = wl.jobs[0].n_packets
+    r = O.run(wl, wl.jobs[0], per_packet=True, nthreads=8)
+    t = O.transit(wl, r["tally"], n)
+    mu_c = math.sqrt(1 - 0.6 ** 2)
+    ref = (g.R_toa / Rs) ** 2 * (1 - c1 * (1 - mu_c) - c2 * (1 - mu_c) ** 2) / (1 - c1 / 3 - c2 / 6)
+    f = r["pk_f"][:, 0]
+    sig = 2 * (g.R_toa - g.R0) * g.R_toa * f.std() / math.sqrt(n) / (Rs ** 2 * t["n_ld"])
+    assert abs(t["depth"] - ref) < 3 * sig + 2e-4 * ref, (t["depth"], ref, sig)
+
+
+def test_scattered_light_lowers_the_transit_area():
+    """Light the atmosphere scatters towards the observer adds to the starlight seen through the limb,
+    so with a stellar disk of non-zero solid angle the effective blocked area falls below the chords'."""
+    wl = S.uniform_scattering_sphere(omega=0.9, g=0.8, n_packets=50_000, star_radius=S.R_SUN, star_dist=0.05 * S.AU)
+    n = wl.jobs[0].n_packets
+    r = O.run(wl, wl.jobs[0], nthreads=8)
+    t = O.transit(wl, r["tally"], n)
+    assert t["I_p_scattered"] > 0 and t["omega_star"] > 0
+    assert t["area_over_pi"] < wl.grid.R0 ** 2 + 2 * t["I_p_direct"]
 
 
 def test_transit_postscale_reduces_to_area():
