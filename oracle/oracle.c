@@ -138,6 +138,11 @@ typedef struct {
 } orc_run_args;
 
 /* ------------------------------------------------------------------ Philox4x32-10 */
+/* Counter-based generator of Salmon et al. (2011, SC'11), written from its published definition: ten
+   rounds, each two 32 x 32 -> 64-bit products of counter words with the round multipliers, the high
+   halves XORed with the other counter words and the key, the key bumped by the Weyl constants between
+   rounds.  The paper does not name its generator; a counter keyed by (packet, event, job) makes every
+   packet's stream independent of how packets are scheduled. */
 static inline uint32_t mulhilo(uint32_t a, uint32_t b, uint32_t *hi)
 {
     uint64_t p = (uint64_t)a * (uint64_t)b;
@@ -284,7 +289,9 @@ enum { END_INTERACT = 0, END_ESCAPE = 1, END_BOTTOM = 2, END_CUTOFF = 3, END_CAP
 
 static inline double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
-/* the two roots of t^2 + 2 b t + c = 0 (shells); returns count */
+/* Face intersections of the spherical grid (Sect. 2: cells bounded by two radial shells, two latitude
+   cones and two longitude half-planes).  The two roots of t^2 + 2 b t + c = 0 (shells), in the stable
+   form; returns the count. */
 static int shell_roots(const double x[3], const double d[3], double r, double t[2])
 {
     double b = dot3(x, d);
@@ -744,6 +751,11 @@ static int tally_cols(const orc_source *S, int mode)
     return S->n_obs;
 }
 
+/* One packet's life: launch (albedo disk, Sect. 5.2; emission cell draw, Sect. 4.3; transmission chord,
+   Sect. 5.1), then flights of optical depth -ln(zeta) (with forcing or path biasing, Sect. 4.2), each
+   ending in an interaction with its peel-offs f = W omega Theta e^-tau (Sect. 4.6), survival biasing or
+   analog scattering and the roulette (Sect. 4.4, 4.5), a new direction (Sect. 3), or at the surface
+   (Sect. 3), the top (escape) or the black bottom.  f of each tally column is added to the tallies. */
 static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int64_t *pk_steps, double *pk_tau,
                        int32_t *tr_cell, double *tr_len, int32_t *tr_n, int32_t tr_max)
 {
