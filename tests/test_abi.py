@@ -49,3 +49,26 @@ def test_struct_layouts_match_header():
     assert C.sizeof(gcmc.gcmc_transit_obs) == 8 * 8
     assert C.sizeof(gcmc.gcmc_server_cfg) == 6 * 4 + 8 + 2 * 4
     assert C.sizeof(gcmc.gcmc_server_stats) == 5 * 8 + 2 * 4
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without the built library the product raises; there is no CPU fallback."""
+    from paper_2110_15640_gb300 import gcmc
+    monkeypatch.setattr(gcmc, "_lib", None)
+    monkeypatch.setattr(gcmc, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "libgcmc.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        gcmc.lib()
+
+
+def test_product_never_uses_the_oracle():
+    """The package (CUDA sources, binding, inputs, autotuner) neither imports nor loads the oracle."""
+    pkg = os.path.join(ROOT, "paper_2110_15640_gb300")
+    hits = []
+    for dirpath, dirnames, files in os.walk(pkg):
+        dirnames[:] = [d for d in dirnames if d not in ("_build", "__pycache__")]
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp", ".c")):
+                src = open(os.path.join(dirpath, f)).read()
+                if re.search(r"(import\s+oracle|from\s+oracle|liboracle|oracle\.c|orc_[a-z_]+\s*\()", src):
+                    hits.append(f)
+    assert not hits, hits
