@@ -243,9 +243,10 @@ def test_edge_cases(G):
 
 
 def test_degenerate_grids(G):
-    """one longitude cell, one latitude band, one radial layer"""
+    """one longitude cell, one latitude band, one radial layer; two longitude cells, whose edges both lie
+    in the plane y = 0"""
     from paper_2110_15640_gb300 import gcmc
-    for nlon, nlat, nr in ((1, 4, 3), (6, 1, 3), (1, 1, 1)):
+    for nlon, nlat, nr in ((1, 4, 3), (6, 1, 3), (1, 1, 1), (2, 3, 3), (2, 1, 2)):
         wl = S.slab_sphere_albedo(omega=0.7, tau=3.0, n_packets=2000, nlon=nlon, nlat=nlat)
         if nr != 1:
             wl.grid = S.uniform_grid(nlon, nlat, nr, wl.grid.R0, wl.grid.R_toa, rho=1.0)
