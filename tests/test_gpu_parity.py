@@ -314,6 +314,26 @@ def test_gpu_ledger_closes(G):
         assert abs(lhs - rhs) < 64 * 50000 * 2.0 ** -33 + 1e-6 * lhs
 
 
+def test_heavy_roulette_per_packet_parity(G):
+    """Roulette at W < 0.5 W_launch with survival probability 0.5 (after nearly every second scattering
+    under survival biasing): FP64 per-packet f, steps and the ledger against the oracle."""
+    from paper_2110_15640_gb300 import gcmc
+    for surv in (1,):
+        wl = S.slab_sphere_albedo(omega=0.5, tau=20.0, phase="iso", n_packets=3000, survival=surv)
+        wl.source.opts.w_rr, wl.source.opts.p_surv = 0.5, 0.5
+        gid, oid, sid, jobs = _load(G, wl, gcmc.FP64)
+        ref = O.run(wl, wl.jobs[0], per_packet=True, nthreads=8)
+        got = G.run_debug(jobs[0])
+        np.testing.assert_array_equal(got["pk_steps"], ref["pk_steps"])
+        # deep in a tau = 20 layer 7 km thick at 7e7 m, f carries e^-tau_obs of slant paths whose FP64
+        # lengths agree to the module's 1e-9; with tau_obs <= 50 (the cut) f agrees to 5e-8 (measured on
+        # a GB300: 8.6e-10 at most, identical steps)
+        np.testing.assert_allclose(got["pk_f"][:, 0], ref["pk_f"][:, 0], rtol=5e-8, atol=1e-300)
+        L = ref["ledger"]
+        np.testing.assert_allclose(list(got["stats"].ledger), L, rtol=1e-12, atol=64 * 3000 * 2.0 ** -33)
+        assert L[5] > 0.01 * L[0]
+
+
 # ------------------------------------------------------------------ full-size grid, sampled packets
 
 def test_full_size_emission_sampled_packets(G):
