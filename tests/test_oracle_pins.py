@@ -300,15 +300,31 @@ def test_adding_doubling_pins():
         assert np.max(np.abs(ad.plane_albedo() + ad.flux_transmission() - 1)) < 2e-6
 
 
-def test_hg_single_scattering_albedo():
-    g, om = 0.6, 1e-3
-    wl = S.slab_sphere_albedo(omega=om, tau=30.0, phase="hg", g=g, n_packets=100_000)
+@pytest.mark.parametrize("phase,g,p_back", [("hg", 0.6, (1 - 0.6) / (1 + 0.6) ** 2), ("iso", 0.0, 1.0),
+                                             ("rayleigh", 0.0, 1.5)])
+def test_single_scattering_albedo(phase, g, p_back):
+    """Semi-infinite, weakly scattering: A_g = omega P(mu = -1) / 8 to first order in omega (omega/8
+    isotropic, 3 omega/16 Rayleigh, omega (1 - g)/(8 (1 + g)^2) HG)."""
+    om = 1e-3
+    wl = S.slab_sphere_albedo(omega=om, tau=30.0, phase=phase, g=g, n_packets=100_000)
     r = O.run(wl, wl.jobs[0], per_packet=True, nthreads=8)
     f = math.pi * r["pk_f"][:, 0]
     est, sig = f.mean(), f.std() / math.sqrt(len(f))
-    ref = om * (1 - g) / (8 * (1 + g) ** 2)
+    ref = om * p_back / 8
     # higher orders contribute O(omega) relative
-    assert abs(est - ref) < 3 * sig + 2 * om * ref
+    assert abs(est - ref) < 3 * sig + 2 * om * ref, (est, ref, sig)
+
+
+def test_semi_infinite_isotropic_albedo_matches_h_function():
+    """A thick isotropic layer (tau = 60) against Chandrasekhar's H-function:
+    A_g = (omega/4) int_0^1 H(mu)^2 mu dmu."""
+    om = 0.9
+    wl = S.slab_sphere_albedo(omega=om, tau=60.0, phase="iso", n_packets=200_000)
+    r = O.run(wl, wl.jobs[0], per_packet=True, nthreads=8)
+    f = math.pi * r["pk_f"][:, 0]
+    est, sig = f.mean(), f.std() / math.sqrt(len(f))
+    ref = R.ag_isotropic_semi_infinite(om)
+    assert abs(est - ref) < 3 * sig + 1e-4 * ref, (est, ref, sig)
 
 
 # ------------------------------------------------------------------ emission (Sect. 5.3)
