@@ -72,3 +72,28 @@ def test_product_never_uses_the_oracle():
                 if re.search(r"(import\s+oracle|from\s+oracle|liboracle|oracle\.c|orc_[a-z_]+\s*\()", src):
                     hits.append(f)
     assert not hits, hits
+
+
+def test_header_is_plain_c_and_links_from_c(built, tmp_path):
+    """include/gcmc.h compiles as C11 and as C++ without warnings, and a C program links against the
+    library and calls it (gcmc_version needs no GPU)."""
+    prog = tmp_path / "use_gcmc.c"
+    prog.write_text('#include "gcmc.h"\n#include <stdio.h>\n'
+                    'int main(void) {\n'
+                    '    gcmc_ctx *ctx = NULL;\n'
+                    '    gcmc_status (*create)(int, gcmc_ctx **) = gcmc_create;\n'
+                    '    (void)ctx; (void)create;\n'
+                    '    printf("%s\\n", gcmc_version());\n'
+                    '    return 0;\n'
+                    '}\n')
+    inc = os.path.join(ROOT, "include")
+    libdir = os.path.dirname(built)
+    exe = tmp_path / "use_gcmc"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, str(prog), "-o", str(exe),
+                    "-L", libdir, "-lgcmc", f"-Wl,-rpath,{libdir}"], check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    assert out.startswith("gcmc")
+    cpp = tmp_path / "use_gcmc.cpp"
+    cpp.write_text('#include "gcmc.h"\nint main() { return gcmc_version() ? 0 : 1; }\n')
+    subprocess.run(["g++", "-std=c++17", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, "-fsyntax-only", str(cpp)],
+                   check=True, capture_output=True, text=True)
