@@ -70,7 +70,18 @@ def _ring_mean_ld(b, law, coef, Rs, tx, ty):
         X, Y = tx + b * math.cos(psi), ty + b * math.sin(psi)
         q = (X * X + Y * Y) / (Rs * Rs)
         return O.limb(law, coef, math.sqrt(1 - q)) if q < 1 else 0.0
-    return integrate.quad(I, 0, 2 * math.pi, epsrel=1e-8, limit=200)[0] / (2 * math.pi)
+    # the ring crosses the stellar limb where t . (cos psi, sin psi) = (Rs^2 - b^2 - |t|^2) / (2 b):
+    # integrate between those angles, where I has its kink and its square-root edge
+    r, p0 = math.hypot(tx, ty), math.atan2(ty, tx)
+    cuts = []
+    if r > 0:
+        k = (Rs * Rs - b * b - r * r) / (2 * b * r)
+        if -1 < k < 1:
+            a = math.acos(k)
+            cuts = sorted((p0 + s * a) % (2 * math.pi) for s in (-1, 1))
+    edges = [0.0] + cuts + [2 * math.pi]
+    tot = sum(integrate.quad(I, lo, hi, epsrel=1e-10, limit=200)[0] for lo, hi in zip(edges, edges[1:]) if hi > lo)
+    return tot / (2 * math.pi)
 
 
 @pytest.mark.parametrize("where", ["central", "grazing"])
