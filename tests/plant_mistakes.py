@@ -157,7 +157,7 @@ def run(scratch, name, path, old, new):
     t0 = time.time()
     cmd = [sys.executable, "-m", "pytest", "tests", "-m", "not gpu", "-x", "-q", "-p", "no:cacheprovider",
            "--ignore=tests/test_abi.py", "--ignore=tests/test_multirank.py", "--ignore=tests/test_host_logic.py",
-           "--ignore=tests/test_inputs.py"]
+           "--ignore=tests/test_inputs.py", "--ignore=tests/test_bench_host.py", "--ignore=tests/test_plant_mistakes.py"]
     try:
         r = subprocess.run(cmd, cwd=scratch, capture_output=True, text=True, timeout=180)
     except subprocess.TimeoutExpired:
