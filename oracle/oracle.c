@@ -46,6 +46,11 @@
  *     (words: tau, scatterer, mu, azimuth); event | 2^31: words (analog absorb, roulette).
  *     Uniform = ((w >> 8) + 0.5) 2^-24.
  *
+ * Pins: tests/test_oracle_*.py check every function here against something other than itself (known-
+ * answer vectors, closed forms, brute-force ray enumeration, an independent adding-doubling solver,
+ * limits with analytic answers, exact ledger closure); tests/plant_mistakes.py plants slips in a copy
+ * of this file and checks that the pins catch them.
+ *
  * Geometry (written plainly): from the current point, every face of the current cell is
  * intersected (two shells, two latitude cones or the equator plane, two longitude
  * half-planes); the nearest root with t > 0 wins, ties in face order (r-, r+, lat-, lat+,
