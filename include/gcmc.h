@@ -452,9 +452,15 @@ typedef struct {
     int32_t grid_blocks;      /* blocks of the last serving-kernel launch */
 } gcmc_server_stats;
 
+/* Create the server of a context (cfg may be NULL: all defaults).  Errors: GCMC_ERR_ARG (NULL ctx or
+   out, block other than 0 or 128, chunk not a multiple of 32, max_jobs above 32768, no grid uploaded
+   yet), GCMC_ERR_OOM, GCMC_ERR_CUDA. */
 gcmc_status gcmc_server_create(gcmc_ctx *ctx, const gcmc_server_cfg *cfg, gcmc_server **out);
 
-/* Queue one job (copied); returns its ticket.  Nothing is launched until gcmc_server_progress. */
+/* Queue one job (copied); returns its ticket.  Nothing is launched until gcmc_server_progress.
+   Errors: GCMC_ERR_ARG for a job that gcmc_run_packets would refuse, or with n_packets < 1, an FP64
+   source, a band job (g_idx = -1: submit one job per g-ordinate), or a grid larger than every grid
+   present when the server was created. */
 gcmc_status gcmc_server_submit(gcmc_server *sv, const gcmc_job *job, uint64_t *ticket);
 
 /* One pass of the request loop, never blocking: collect completed jobs (their tickets are written to
