@@ -74,14 +74,17 @@ typedef void (*gcmc_free_fn)(void *ptr, void *user);
 
 /* ---------------------------------------------------------------- context */
 
-/* Create a context on CUDA device `device`.  *out receives the handle. */
+/* Create a context on CUDA device `device`.  *out receives the handle.  Errors: GCMC_ERR_ARG (out is
+   NULL), GCMC_ERR_CUDA (no such device, or it cannot be selected), GCMC_ERR_OOM. */
 gcmc_status gcmc_create(int device, gcmc_ctx **out);
-/* Release every device buffer of the context and the context itself. */
+/* Release every device buffer of the context and the context itself.  GCMC_ERR_ARG for NULL. */
 gcmc_status gcmc_destroy(gcmc_ctx *ctx);
-/* Order all later work of the context on `cuda_stream` (a cudaStream_t; NULL = default stream). */
+/* Order all later work of the context on `cuda_stream` (a cudaStream_t; NULL = default stream).
+   GCMC_ERR_ARG for a NULL context. */
 gcmc_status gcmc_set_stream(gcmc_ctx *ctx, void *cuda_stream);
 /* Route the context's device allocations through alloc/free (e.g. a framework's caching
-   allocator).  Must be called before the first upload.  NULL restores cudaMalloc/cudaFree. */
+   allocator).  Must be called before the first upload.  NULL restores cudaMalloc/cudaFree.
+   Errors: GCMC_ERR_ARG (after an upload, or only one of alloc and free_fn given). */
 gcmc_status gcmc_set_allocator(gcmc_ctx *ctx, gcmc_alloc_fn alloc, gcmc_free_fn free_fn, void *user);
 /* Message of the last failing call on this context ("" if none).  Owned by the context. */
 const char *gcmc_last_error(gcmc_ctx *ctx);
