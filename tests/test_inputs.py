@@ -127,3 +127,28 @@ def test_generators_are_seeded(builder):
     a, b = builder(), builder()
     assert np.array_equal(a.grid.T, b.grid.T) and np.array_equal(a.grid.rho, b.grid.rho)
     assert [j.n_packets for j in a.jobs] == [j.n_packets for j in b.jobs]
+
+
+def test_transit_scatter_recipe():
+    wl = S.config6_transit_scatter()
+    g, op = wl.grid, wl.source.opts
+    assert (g.nlon, g.nlat, g.nr) == (128, 64, 50) and wl.mode == S.MODE_TRANSMISSION
+    assert len(wl.jobs) == 40 and all(j.n_packets == 200_000 for j in wl.jobs)
+    # quadratic limb darkening of a Sun-like star at 0.05 AU, transit impact parameter 0.3
+    assert op.trans_scatter == 1 and op.cloud_phase == 1 and op.ld_law == 2 and tuple(op.ld_coef[:2]) == (0.45, 0.2)
+    assert op.star_radius == S.R_SUN and abs(op.star_dist / S.AU - 0.05) < 1e-15
+    assert abs(math.hypot(*op.transit_xy) / S.R_SUN - 0.3) < 1e-12
+    assert np.array_equal(wl.source.obs[0], -wl.source.star)
+
+
+def test_emission_hires_recipe():
+    wl = S.config7_emission_hires(lam_subset=range(0, 9532, 10))
+    g, xs, m = wl.grid, wl.opac, wl.notes["margin"]
+    assert (g.nlon, g.nlat, g.nr) == (96, 48, 60) and wl.mode == S.MODE_EMISSION and g.wind is not None
+    assert len(wl.jobs) == 954 and all(j.n_packets == 100_000 for j in wl.jobs)
+    lam = np.array([xs.lam[j.lam_idx] for j in wl.jobs])
+    np.testing.assert_allclose(lam, 1.0e-6 * np.exp(np.arange(0, 9532, 10) / 1.0e5), rtol=1e-14)
+    # the observer looks at the dayside (+x): colatitude 90 deg, longitude 0
+    assert xs.view_theta == 0.5 * math.pi and xs.view_phi == 0.0
+    assert np.array_equal(wl.source.obs[0], [1.0, 0.0, 0.0]) and wl.source.opts.scatter_emission == 0
+    assert m == 8
