@@ -717,26 +717,29 @@ cudaError_t gather_bench(const void *table, int64_t n_records, int record_bytes,
 
 // ------------------------------------------------------------------ allocation-free emission pdf
 // Scratch of gcmc_emission_pdf_noalloc: per-block partial sums and counts (EMIS_SCAN_BLOCK cells per
-// block) and the job record the pdf kernels read.  File-scope device memory: one copy per GPU that
-// loads the library, kept until exit.  Every slot read by a kernel is written earlier in the same
-// call (partial sums by k_emis_reduce, offsets by k_emis_scan_blocks, the record by k_noalloc_job),
-// so nothing needs clearing between calls; overlapping calls race on it.
+// block), the job's info block (the pdf kernels write all eight of its slots; only the first three
+// are copied out to the caller's totals) and the job record the pdf kernels read.  File-scope device
+// memory: one copy per GPU that loads the library, kept until exit.  Every slot read by a kernel is
+// written earlier in the same call (partial sums by k_emis_reduce, offsets by k_emis_scan_blocks, the
+// info block by k_emis_total and k_emis_scan_blocks, the record by k_noalloc_job), so nothing needs
+// clearing between calls; overlapping calls race on it.
 namespace {
 constexpr int NOALLOC_BLOCKS = GCMC_NOALLOC_MAX_CELLS / gcmc::EMIS_SCAN_BLOCK;
 struct __align__(256) NoallocScratch {
     double bsum[NOALLOC_BLOCKS];
     double bcnt[NOALLOC_BLOCKS];
+    double info[8];
     gcmc::PrepJob job;
 };
 static __device__ __align__(256) NoallocScratch g_noalloc;
 
-__global__ void k_noalloc_job(NoallocScratch *sc, double *cdf, double *wcell, double *totals)
+__global__ void k_noalloc_job(NoallocScratch *sc, double *cdf, double *wcell)
 {
     gcmc::PrepJob j;
     memset(&j, 0, sizeof(j));
     j.cdf = reinterpret_cast<long long *>(cdf);
     j.wcell = wcell;
-    j.info = totals;
+    j.info = sc->info;
     j.bsum = sc->bsum;
     j.bcnt = sc->bcnt;
     sc->job = j;
@@ -748,7 +751,28 @@ __global__ void k_noalloc_copy(const double *__restrict__ src, double *__restric
         dst[i] = src[i];
 }
 
+// L_tot, the emitting-cell count and the cdf total out of the scratch info block
+__global__ void k_noalloc_totals(const NoallocScratch *sc, double *totals)
+{
+    if (threadIdx.x < 3) totals[threadIdx.x] = sc->info[threadIdx.x];
+}
+
 std::atomic<NoallocScratch *> g_noalloc_addr[64];   // per device: address of g_noalloc (host-side lookup)
+
+// byte ranges [a, a + na) and [b, b + nb) share a byte
+bool overlaps(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
+// status of the launch just queued (no error was pending when the call began, so one now is its own)
+gcmc_status queued_ok()
+{
+    if (cudaPeekAtLastError() == cudaSuccess) return GCMC_OK;
+    cudaGetLastError();
+    return GCMC_ERR_CUDA;
+}
 }  // namespace
 
 extern "C" gcmc_status gcmc_emission_pdf_noalloc(const double *lum, int64_t ncell, double beta, double *cdf,
@@ -757,27 +781,56 @@ extern "C" gcmc_status gcmc_emission_pdf_noalloc(const double *lum, int64_t ncel
     using namespace gcmc;
     if (!lum || !cdf || !wcell || !totals || ncell < 1 || !(beta >= 0.0 && beta <= 1.0)) return GCMC_ERR_ARG;
     if (ncell > GCMC_NOALLOC_MAX_CELLS) return GCMC_ERR_RANGE;
+    const size_t nb = (size_t)ncell * sizeof(double), tb = 3 * sizeof(double);
+    // lum may be cdf itself (in place); otherwise no two of the four arrays may share memory
+    if ((lum != cdf && overlaps(lum, nb, cdf, nb)) || overlaps(lum, nb, wcell, nb) || overlaps(lum, nb, totals, tb) ||
+        overlaps(cdf, nb, wcell, nb) || overlaps(cdf, nb, totals, tb) || overlaps(wcell, nb, totals, tb))
+        return GCMC_ERR_ARG;
+    // an error left pending by earlier work of the process is not this call's: refuse, and leave it for
+    // its owner to read
+    if (cudaPeekAtLastError() != cudaSuccess) return GCMC_ERR_CUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GCMC_ERR_CUDA;
     // set-up once per device, with that device current: the device address of the scratch array
     NoallocScratch *sc = g_noalloc_addr[dev].load();
     if (!sc) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc) != cudaSuccess || !p) return GCMC_ERR_CUDA;
+        if (cudaGetSymbolAddress(&p, g_noalloc) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return GCMC_ERR_CUDA;
+        }
         sc = static_cast<NoallocScratch *>(p);
         g_noalloc_addr[dev].store(sc);
     }
     cudaStream_t st = (cudaStream_t)stream;
     const int nblk = (int)((ncell + EMIS_SCAN_BLOCK - 1) / EMIS_SCAN_BLOCK);
-    count_launch(7);
-    k_noalloc_job<<<1, 1, 0, st>>>(sc, cdf, wcell, totals);
-    k_noalloc_copy<<<(unsigned)std::min<int64_t>((ncell + 255) / 256, 4096), 256, 0, st>>>(lum, cdf, ncell);
     const PrepJob *pj = &sc->job;
-    dim3 g3((unsigned)nblk, 1u);
+    const dim3 g3((unsigned)nblk, 1u);
+    gcmc_status s;
+    count_launch(1);
+    k_noalloc_job<<<1, 1, 0, st>>>(sc, cdf, wcell);
+    if ((s = queued_ok()) != GCMC_OK) return s;
+    if (lum != cdf) {
+        count_launch(1);
+        k_noalloc_copy<<<(unsigned)std::min<int64_t>((ncell + 255) / 256, 4096), 256, 0, st>>>(lum, cdf, ncell);
+        if ((s = queued_ok()) != GCMC_OK) return s;
+    }
+    count_launch(1);
     k_emis_reduce<<<g3, EMIS_SCAN_BLOCK, 0, st>>>(ncell, pj);
+    if ((s = queued_ok()) != GCMC_OK) return s;
+    count_launch(1);
     k_emis_total<<<1, 128, 0, st>>>(nblk, pj, 1, beta);
+    if ((s = queued_ok()) != GCMC_OK) return s;
+    count_launch(1);
     k_emis_pdf<double><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(ncell, pj, beta);
+    if ((s = queued_ok()) != GCMC_OK) return s;
+    count_launch(1);
     k_emis_scan_blocks<<<1, 32, 0, st>>>(nblk, pj, 1);
+    if ((s = queued_ok()) != GCMC_OK) return s;
+    count_launch(1);
     k_emis_cdf_add<double><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(ncell, pj);
-    return cudaGetLastError() == cudaSuccess ? GCMC_OK : GCMC_ERR_CUDA;
+    if ((s = queued_ok()) != GCMC_OK) return s;
+    count_launch(1);
+    k_noalloc_totals<<<1, 32, 0, st>>>(sc, totals);
+    return queued_ok();
 }
