@@ -248,7 +248,10 @@ typedef struct {
     uint64_t seed;
 } gcmc_job;
 
-/* Plain form: one job, one cell-table preparation and one transport launch (one thread per packet).
+/* Plain form (the paper's GPU loop, Sect. 2: one (lambda, g) job at a time): one job, one cell-table
+   preparation (S1: extinction and emission tables, Sect. 3.6, 4.3, 7) and one transport launch (one
+   thread per packet: launch, tau sampling, cell march, interaction and peel-off, Sect. 3, 4.1-4.6;
+   chords, Sect. 5.1).
    tallies_out: one column per observer (albedo, emission); transmission: the chord column, plus the
    scattered-light column when the source sets trans_scatter; sums over packets of f (the host divides by N, see gcmc_postscale), in
    host or device memory per tallies_memory.  stats_out may be NULL.  Synchronises the stream
@@ -266,14 +269,15 @@ typedef struct {
     int32_t pad;
 } gcmc_launch_cfg;
 
-/* Batched form: cell tables of every job, then ONE persistent transport launch that drains a
-   device work queue of (job, packet range) items.  tallies_out: [n_jobs][GCMC_MAX_OBS].
+/* Batched form: the jobs the paper's host loop would run one after another (Sect. 2; each job computes
+   what gcmc_run_packets computes, Sect. 3-5) as cell tables of every job, then ONE persistent transport
+   launch that drains a device work queue of (job, packet range) items.  tallies_out: [n_jobs][GCMC_MAX_OBS].
    stats_out: [n_jobs] or NULL.  cfg may be NULL (defaults). */
 gcmc_status gcmc_run_batch(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, const gcmc_launch_cfg *cfg,
                            double *tallies_out, int tallies_memory, gcmc_stats *stats_out);
 
-/* Captured batches: the batched form (cell tables of every job, one persistent transport launch,
-   tallies) planned once and captured into a CUDA graph on the context's stream (which must not be the
+/* Captured batches (the host loop of Sect. 2 replayed; each job as in Sect. 3-5): the batched form
+   (cell tables of every job, one persistent transport launch, tallies) planned once and captured into a CUDA graph on the context's stream (which must not be the
    default stream), to be replayed step after step without host-side planning or launch overhead.
    The graph owns its workspace; the grids, opacities and sources it uses must stay uploaded.
    gcmc_graph_launch replays it asynchronously and, if tallies_out (device [n_jobs][GCMC_MAX_OBS]) is
@@ -296,9 +300,10 @@ gcmc_status gcmc_graph_destroy(gcmc_graph *g);
 gcmc_status gcmc_run_contrib(gcmc_ctx *ctx, const gcmc_job *job, double *tallies_out, double *cf_out,
                              gcmc_stats *stats_out);
 
-/* Asynchronous batched form for request loops: enqueue the work on the context's stream and
-   return a ticket at once; gcmc_poll returns GCMC_ERR_NOT_READY until the ticket's work has
-   finished, then fills tallies_out [n_jobs][GCMC_MAX_OBS] (host) and stats_out (may be NULL). */
+/* Asynchronous batched form for request loops (the host loop of Sect. 2 without waiting; each job as
+   in Sect. 3-5): enqueue the work on the context's stream and return a ticket at once; gcmc_poll
+   returns GCMC_ERR_NOT_READY until the ticket's work has finished, then fills tallies_out
+   [n_jobs][GCMC_MAX_OBS] (host) and stats_out (may be NULL). */
 gcmc_status gcmc_submit(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, const gcmc_launch_cfg *cfg,
                         uint64_t *ticket);
 gcmc_status gcmc_poll(gcmc_ctx *ctx, uint64_t ticket, double *tallies_out, gcmc_stats *stats_out);
@@ -351,7 +356,11 @@ typedef struct {
 gcmc_status gcmc_transit(gcmc_ctx *ctx, int grid_id, int source_id, const double *tally, int64_t n_packets,
                          gcmc_transit_obs *out);
 
-/* Observables of one job from its tally sum over N packets (l_tot from the job's stats for emission). */
+/* Host post-scale (S9) of one job from its tally sum over N packets (l_tot from the job's stats for
+   emission): albedo S = tally/N, A_g = pi S (Sect. 5.2); emission L_p = (L_tot/N) tally, I_p =
+   L_p/(pi R_TOA^2), F_p = pi I_p (Sect. 5.3); transmission <I_p> = (R_TOA - R0) R_TOA tally/N and the
+   area R0^2 + 2 <I_p> (Sect. 5.1, Eq. trans).  Errors: GCMC_ERR_ARG (bad grid id or mode, n_packets <= 0,
+   out NULL). */
 gcmc_status gcmc_postscale(gcmc_ctx *ctx, int grid_id, int mode, double tally, int64_t n_packets, double l_tot,
                            gcmc_observables *out);
 
@@ -389,16 +398,22 @@ gcmc_status gcmc_gather_bench(gcmc_ctx *ctx, int64_t n_records, int record_bytes
    All pointers are DEVICE memory owned by the caller:
      lum     [ncell]  luminosity L_i of each cell, W/m; a negative value marks a cell excluded by the
                       tau_vert cut (as the library's own cell-table kernels mark them)
-     cdf     [ncell]  out: cumulative hybrid pdf (the pdf of cell i is cdf[i] - cdf[i-1])
+     cdf     [ncell]  out: cumulative hybrid pdf (the pdf of cell i is cdf[i] - cdf[i-1]); may be lum
+                      itself (the pdf then replaces the luminosities in place)
      wcell   [ncell]  out: launch weight (L_i / L_tot) / q_i, 0 for excluded cells
-     totals  [3]      out: L_tot, number of emitting cells, cdf total
-   beta is the hybrid biasing fraction (0..1).  Work is queued on `stream` (a cudaStream_t, NULL =
-   default stream); the call returns without waiting.  Scratch lives in a fixed array in the
-   library's device memory, one per GPU, held until the process exits; the first call on a device
-   looks up its address (do that first call before any stream capture).  Every call shares that
-   array, so calls that overlap on the GPU (e.g. on two streams) race: order them on one stream.
-   Errors: GCMC_ERR_ARG (NULL pointer, ncell < 1, beta outside [0, 1]), GCMC_ERR_RANGE (ncell >
-   GCMC_NOALLOC_MAX_CELLS), GCMC_ERR_CUDA. */
+     totals  [3]      out: L_tot, number of emitting cells, cdf total (exactly 3 doubles are written)
+   Apart from cdf == lum, the four arrays must not overlap.  beta is the hybrid biasing fraction
+   (0..1).  Work is queued on `stream` (a cudaStream_t, NULL = default stream); the call returns
+   without waiting.  Scratch lives in a fixed array in the library's device memory, one per GPU, held
+   until the process exits; the first call on a device looks up its address (do that first call before
+   any stream capture).  That look-up is kept for the process: after cudaDeviceReset on a device the
+   library's device memory is gone and this entry point must not be called on that device again.
+   Every call shares the array, so calls that overlap on the GPU (e.g. on two streams) race: order
+   them on one stream.
+   Errors: GCMC_ERR_ARG (NULL pointer, ncell < 1, beta outside [0, 1], overlapping arrays),
+   GCMC_ERR_RANGE (ncell > GCMC_NOALLOC_MAX_CELLS), GCMC_ERR_CUDA (a CUDA error was already pending
+   when the call began -- it is left pending for its owner and nothing is queued -- or one of the
+   call's own launches failed, in which case that error is cleared and reported here). */
 gcmc_status gcmc_emission_pdf_noalloc(const double *lum, int64_t ncell, double beta, double *cdf, double *wcell,
                                       double *totals, void *stream);
 
