@@ -140,6 +140,9 @@ typedef struct {
     double *cf;            /* contribution functions (Sect. 6), or NULL: [2][n_obs][ncell] sums of the
                               peel-off contributions f by the cell they leave from; [0] thermal (the
                               emission launch peel-off), [1] scattered (peel-offs at scattering events) */
+    double *tr_pos;        /* [n_trace][max_trace][3] or NULL: the end point of each traced segment (the
+                              interaction point, or the crossing point of the face it leaves by); at a
+                              march start (cell < 0) the point the march starts from.  Logging only. */
 } orc_run_args;
 
 /* ------------------------------------------------------------------ Philox4x32-10 */
@@ -374,15 +377,18 @@ typedef struct {
     /* a second optical depth accumulated along the same path (continuous absorption), or NULL */
     const double *alpha2;
     double tau2;
+    double *tr_pos;    /* [tr_max][3] or NULL */
 } march_ctx;
 
 static inline int64_t flat(const orc_grid *G, const int c[3]) { return ((int64_t)c[2] * G->nlat + c[1]) * G->nlon + c[0]; }
 
-static void trace_put(march_ctx *M, int32_t cell, double len)
+static void trace_put(march_ctx *M, int32_t cell, double len, const double x[3])
 {
     if (M->tr_cell && M->tr_n < M->tr_max) {
         M->tr_cell[M->tr_n] = cell;
         M->tr_len[M->tr_n] = len;
+        if (M->tr_pos)
+            for (int i = 0; i < 3; ++i) M->tr_pos[3 * M->tr_n + i] = x[i];
         M->tr_n++;
     }
 }
@@ -447,13 +453,13 @@ static int march(march_ctx *M, double x[3], const double d[3], int c[3], int ent
             for (int i = 0; i < 3; ++i) x[i] += l * d[i];
             *tau_acc = tau_target;
             if (M->alpha2) M->tau2 += M->alpha2[idx] * l;
-            trace_put(M, (int32_t)idx, l);
+            trace_put(M, (int32_t)idx, l, x);
             return END_INTERACT;
         }
         *tau_acc += a * best;
         if (M->alpha2) M->tau2 += M->alpha2[idx] * best;
-        trace_put(M, (int32_t)idx, best);
         for (int i = 0; i < 3; ++i) x[i] += best * d[i];
+        trace_put(M, (int32_t)idx, best, x);
         switch (bestf) {
         case F_RIN:
             if (c[2] == 0) return END_BOTTOM;
@@ -762,13 +768,13 @@ static int tally_cols(const orc_source *S, int mode)
    analog scattering and the roulette (Sect. 4.4, 4.5), a new direction (Sect. 3), or at the surface
    (Sect. 3), the top (escape) or the black bottom.  f of each tally column is added to the tallies. */
 static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int64_t *pk_steps, double *pk_tau,
-                       int32_t *tr_cell, double *tr_len, int32_t *tr_n, int32_t tr_max)
+                       int32_t *tr_cell, double *tr_len, int32_t *tr_n, int32_t tr_max, double *tr_pos)
 {
     const orc_grid *G = J->G;
     const orc_cells *C = J->C;
     const orc_source *S = J->S;
     const orc_run_args *A = J->A;
-    march_ctx M = {G, C->alpha, 0, S->max_steps, tr_cell, tr_len, 0, tr_max, NULL, 0.0};
+    march_ctx M = {G, C->alpha, 0, S->max_steps, tr_cell, tr_len, 0, tr_max, NULL, 0.0, tr_pos};
     double Rtoa = G->r_edges[G->nr];
     double R0 = G->r_edges[0];
     double u[4];
@@ -815,7 +821,7 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
         } else if (W > 0.0) {
             const double x_l[3] = {x[0], x[1], x[2]};
             const int c_l[3] = {c[0], c[1], c[2]};
-            trace_put(&M, -3, 0.0);
+            trace_put(&M, -3, 0.0, x);
             double tau = 0.0;
             int st = march(&M, x, d, c, entry, -1.0, S->tau_peel_cut, &tau);
             double contrib;
@@ -881,7 +887,7 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
         for (int o = 0; o < S->n_obs; ++o) {
             double tau;
             int st;
-            trace_put(&M, -2, 0.0);
+            trace_put(&M, -2, 0.0, x);
             double e = peel(&M, x, c, S->obs[o], S->tau_peel_cut, &tau, &st, -1);
             if (first_tau < 0) first_tau = tau;
             if (st == END_CAP) break;
@@ -920,7 +926,7 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
                ends on a reflecting surface. */
             double tau_m = 0.0;
             int sm = END_ESCAPE;
-            trace_put(&M, -4, 0.0);
+            trace_put(&M, -4, 0.0, x);
             if (ca) { M.alpha = J->a_sca; M.alpha2 = J->a_abs; M.tau2 = 0.0; }
             (void)peel(&M, x, c, d, S->tau_peel_cut, &tau_m, &sm, entry);
             const double tau2_m = M.tau2;
@@ -965,7 +971,7 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
         }
         first = 0;
         double tau = 0.0;
-        trace_put(&M, -1, 0.0);
+        trace_put(&M, -1, 0.0, x);
         if (ca) { M.alpha = J->a_sca; M.alpha2 = J->a_abs; M.tau2 = 0.0; }
         int st = march(&M, x, d, c, entry, tau_t, INFINITY, &tau);
         if (ca) {
@@ -993,7 +999,7 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
                 if (!(mo > 0.0)) continue;
                 double tau_o = 0.0;
                 int so = END_ESCAPE;
-                trace_put(&M, -2, 0.0);
+                trace_put(&M, -2, 0.0, x);
                 const double e = peel(&M, x, c, od, S->tau_peel_cut, &tau_o, &so, F_RIN);
                 if (so == END_CAP) { capped = 1; break; }
                 const double fo = W * As * (mo / ORC_PI) * e;
@@ -1050,7 +1056,7 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
             const double *od = trans ? antistar : S->obs[o];
             double tau_o;
             int so;
-            trace_put(&M, -2, 0.0);
+            trace_put(&M, -2, 0.0, x);
             double e = peel(&M, x, c, od, S->tau_peel_cut, &tau_o, &so, -1);
             if (so == END_CAP) { capped = 1; break; }
             const double fo = W * om * orc_theta_kind(dot3(d, od), pg, gg, S->cloud_phase) * e;
@@ -1131,13 +1137,15 @@ static void run_chunk(const job_t *J, int64_t ch, acc_t *acc)
         int32_t *tc = NULL;
         double *tl = NULL;
         int32_t *tn = NULL;
+        double *tp = NULL;
         if (A->tr_cell && q < A->n_trace) {
             tc = A->tr_cell + q * A->max_trace;
             tl = A->tr_len + q * A->max_trace;
             tn = A->tr_n + q;
+            if (A->tr_pos) tp = A->tr_pos + 3 * q * A->max_trace;
         }
         run_packet(J, n, acc, A->pk_f ? A->pk_f + q * tally_cols(J->S, A->mode) : NULL, A->pk_steps ? A->pk_steps + q : NULL,
-                   A->pk_tau ? A->pk_tau + q : NULL, tc, tl, tn, A->max_trace);
+                   A->pk_tau ? A->pk_tau + q : NULL, tc, tl, tn, A->max_trace, tp);
     }
 }
 

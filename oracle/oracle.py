@@ -71,7 +71,7 @@ class Run_c(C.Structure):
                 ("steps", C.POINTER(C.c_int64)), ("pk_f", C.POINTER(C.c_double)),
                 ("pk_steps", C.POINTER(C.c_int64)), ("pk_tau", C.POINTER(C.c_double)),
                 ("tr_cell", C.POINTER(C.c_int32)), ("tr_len", C.POINTER(C.c_double)),
-                ("tr_n", C.POINTER(C.c_int32)), ("cf", C.POINTER(C.c_double))]
+                ("tr_n", C.POINTER(C.c_int32)), ("cf", C.POINTER(C.c_double)), ("tr_pos", C.POINTER(C.c_double))]
 
 
 def lib():
@@ -366,11 +366,13 @@ def job_observers(wl, job):
     return obs
 
 
-def run(wl, job, cells=None, packet0=0, n_run=None, nthreads=1, per_packet=False, n_trace=0, max_trace=0, cf=False):
+def run(wl, job, cells=None, packet0=0, n_run=None, nthreads=1, per_packet=False, n_trace=0, max_trace=0, cf=False,
+        trace_pos=False):
     """Run packets of one job through the oracle; returns tallies, ledger, step count and
     (optionally) per-packet f, steps, tau and segment traces, and the contribution-function sums
     (Sect. 6): cf[kind][obs][cell] = sum of the peel-off contributions f leaving from the cell,
-    kind 0 thermal (emission launch), 1 scattered."""
+    kind 0 thermal (emission launch), 1 scattered.  trace_pos adds tr_pos [n_trace][max_trace][3]: the
+    end point of each traced segment, and at a march start (cell < 0) the point it starts from."""
     if cells is None:
         cells = prep_cells(wl, job)
     G = _GridHandle(wl.grid)
@@ -396,12 +398,13 @@ def run(wl, job, cells=None, packet0=0, n_run=None, nthreads=1, per_packet=False
     tr_cell = np.zeros((n_trace, max_trace), np.int32) if n_trace else None
     tr_len = np.zeros((n_trace, max_trace)) if n_trace else None
     tr_n = np.zeros(n_trace, np.int32) if n_trace else None
+    tr_pos = np.zeros((n_trace, max_trace, 3)) if n_trace and trace_pos else None
     cfa = np.zeros((2, nobs, wl.grid.ncell)) if cf else None
     ip = lambda a, t: a.ctypes.data_as(C.POINTER(t)) if a is not None else None  # noqa: E731
     ra = Run_c(int(wl.mode), int(job.key) & 0xFFFFFFFF, int(wl.seed), int(job.n_packets), int(packet0), n_run,
                int(nthreads), n_trace, int(max_trace), 0, _dp(tally), _dp(ledger), ip(steps, C.c_int64),
                _dp(pk_f), ip(pk_steps, C.c_int64), _dp(pk_tau), ip(tr_cell, C.c_int32), _dp(tr_len),
-               ip(tr_n, C.c_int32), _dp(cfa))
+               ip(tr_n, C.c_int32), _dp(cfa), _dp(tr_pos))
     rc = lib().orc_run(C.byref(G.c), C.byref(cc), C.byref(sc), C.byref(ra))
     if rc != 0:
         raise RuntimeError(f"oracle run failed: {rc}")
@@ -410,6 +413,8 @@ def run(wl, job, cells=None, packet0=0, n_run=None, nthreads=1, per_packet=False
         out.update(pk_f=pk_f, pk_steps=pk_steps, pk_tau=pk_tau)
     if n_trace:
         out.update(tr_cell=tr_cell, tr_len=tr_len, tr_n=tr_n)
+        if tr_pos is not None:
+            out["tr_pos"] = tr_pos
     if cf:
         out["cf"] = cfa
     return out
