@@ -9,10 +9,14 @@
 //   equator plane:           s = -zc / dz
 //   longitude half-plane:    s = -(n . c0) / (n . d), n = (-sin phi, cos phi, 0), on the phi side
 // Along a straight line the radius is convex in s, the azimuth is monotone (sign of (o x d)_z) and
-// the latitude has at most one extremum (sign of dz p^2 - zc s), so each step evaluates one shell,
-// usually one cone and one half-plane.  In FP32 the impact parameter p^2 is carried as an
-// unevaluated FP32 pair built with error-free products, so r^2 - p^2 keeps ~48 bits near grazing
-// incidence; cone roots within TAN_EPS of tangency are recomputed in FP64.
+// the latitude has at most one extremum (sign of dz p^2 - zc s), so a cell has one candidate exit
+// per face family: one shell, usually one cone, and one half-plane.  Each family's next crossing
+// depends only on the ray and the cell index of that family (k, j or i), so it stays valid while
+// the ray crosses faces of the other families: the march keeps the three crossings and, after each
+// step, evaluates again only the family it crossed (an emission peel-off crosses shells in ~94% of
+// its steps).  In FP32 the impact parameter p^2 is carried as an unevaluated FP32 pair built with
+// error-free products, so r^2 - p^2 keeps ~48 bits near grazing incidence; cone roots within TAN_EPS
+// of tangency are recomputed in FP64.
 #pragma once
 #include "common.cuh"
 
@@ -28,8 +32,13 @@ template <typename real> struct Ray {
     real B, dz2;            // zc dz and dz^2 (cone coefficients that depend on the ray only)
     real tau, tau_target;   // accumulated optical depth; interaction target (< 0: none)
     real tau2;              // continuous absorption: absorption optical depth along a flight
+    real tr, tl, tn;        // next crossing of the radial, latitude and longitude family (s)
+    int fc;                 // their faces (bits 0-7, 8-15, 16-23) and the families to evaluate again
     int i, j, k;            // current cell
 };
+
+// families whose next crossing must be evaluated again (bits of Ray::fc)
+constexpr int STALE_R = 1 << 24, STALE_LAT = 1 << 25, STALE_LON = 1 << 26, STALE_ALL = 7 << 24;
 
 // error-free product a*b = hi + lo
 // (the _rn intrinsics are never contracted into FMAs, which would break the error-free forms)
@@ -110,6 +119,7 @@ __device__ __forceinline__ void ray_setup(Ray<real> &R, real ox, real oy, real o
     R.Q = dz * dz + R.chz * R.chz;
     R.B = R.cz * dz;
     R.dz2 = dz * dz;
+    R.fc = STALE_ALL;
 }
 
 constexpr double TAN_EPS_CONE = 1e-5;
@@ -231,41 +241,82 @@ __device__ __forceinline__ real lat_exit(const DevGrid &G, const Tabs<real> &T, 
     return (to_hi || to_lo) ? t : inf;
 }
 
-// Exit of the current cell: returns the s of the exit point and the face.  Every candidate face is
-// evaluated with selects (both shells' discriminants, both cones, the half-plane ahead in azimuth),
-// so the lanes of a warp stay converged; ties go to the first face in the order r-, r+, lat-, lat+, lon.
+// Radial family: inward (s < 0) and still outside the inner shell -> inner root, else outer root.
 template <typename real>
-__device__ __forceinline__ real cell_exit(const DevGrid &G, const Tabs<real> &T, const Ray<real> &R, int &face)
+__device__ __forceinline__ real radial_exit(const Tabs<real> &T, const Ray<real> &R, int &face)
 {
-    const real inf = M<real>::inf();
-    // radial shells: inward (s < 0) and still outside the inner shell -> inner root, else outer root
     const auto ri = T.r2[R.k], ro = T.r2[R.k + 1];
     const real hin = (ri.x - R.p2hi) + (ri.y - R.p2lo);
     const real hout = (ro.x - R.p2hi) + (ro.y - R.p2lo);
     const bool inward = R.s < (real)0 && hin > (real)0;
     const real h = inward ? hin : fmax(hout, (real)0);
     const real rt = M<real>::sqrt_(h);
-    real best = inward ? -rt : rt;
     face = inward ? F_RIN : F_ROUT;
-    // latitude: the one cone the ray reaches first (both near the thresholds of that choice)
-    int flat = F_NONE;
-    const real tlat = lat_exit<real>(G, T, R, flat);
-    if (tlat < best) {
-        best = tlat;
-        face = flat;
-    }
-    // longitude: the azimuth along a line is monotone (sign of (o x d)_z), so only the edge ahead counts
+    return inward ? -rt : rt;
+}
+
+// Longitude family: the azimuth along a line is monotone (sign of (o x d)_z), so only the edge ahead
+// counts; +inf if the ray does not reach it.
+template <typename real>
+__device__ __forceinline__ real lon_exit(const Tabs<real> &T, const Ray<real> &R, int &face)
+{
     const bool east = R.crz > (real)0;
     const auto cs = T.cs[east ? R.i + 1 : R.i];
     const real nd = R.dy * cs.x - R.dx * cs.y;
     const real sr = M<real>::div_(-(R.cy * cs.x - R.cx * cs.y), nd);
     const bool lon_ok = T.nlon > 1 && R.crz != (real)0 && nd != (real)0 && sr > R.s &&
                         cs.x * (R.cx + sr * R.dx) + cs.y * (R.cy + sr * R.dy) > (real)0;
-    if (lon_ok && sr < best) {
-        best = sr;
-        face = east ? F_LONHI : F_LONLO;
+    face = east ? F_LONHI : F_LONLO;
+    return lon_ok ? sr : M<real>::inf();
+}
+
+// Exit of the current cell: returns the s of the exit point and the face.  The families marked stale
+// are evaluated (at the current s); ties go to the first face in the order r-, r+, lat-, lat+, lon,
+// as if all candidate faces were evaluated at every step.
+template <typename real>
+__device__ __forceinline__ real cell_exit(const DevGrid &G, const Tabs<real> &T, Ray<real> &R, int &face)
+{
+    int fc = R.fc;
+    if (fc & STALE_R) {
+        int f;
+        R.tr = radial_exit<real>(T, R, f);
+        fc = (fc & ~0xff) | f;
+    }
+    if (fc & STALE_LAT) {
+        int f = F_NONE;
+        R.tl = lat_exit<real>(G, T, R, f);
+        fc = (fc & ~0xff00) | (f << 8);
+    }
+    if (fc & STALE_LON) {
+        int f;
+        R.tn = lon_exit<real>(T, R, f);
+        fc = (fc & ~0xff0000) | (f << 16);
+    }
+    fc &= ~STALE_ALL;
+    R.fc = fc;
+    real best = R.tr;
+    face = fc & 0xff;
+    if (R.tl < best) {
+        best = R.tl;
+        face = (fc >> 8) & 0xff;
+    }
+    if (R.tn < best) {
+        best = R.tn;
+        face = (fc >> 16) & 0xff;
     }
     return best;
+}
+
+// After the ray has moved to R.s across `face`: the crossed family is evaluated again at the next step,
+// and so is any family whose crossing is not ahead of R.s (an exact tie that the face order gave to
+// another family: evaluated again, its root at R.s no longer counts).
+template <typename real> __device__ __forceinline__ void mark_crossed(Ray<real> &R, int face)
+{
+    int st = (face & 3) != 1 ? STALE_R : ((face >> 2) & 3) != 1 ? STALE_LAT : STALE_LON;
+    if (R.tr <= R.s) st |= STALE_R;
+    if (R.tl <= R.s) st |= STALE_LAT;
+    if (R.tn <= R.s) st |= STALE_LON;
+    R.fc |= st;
 }
 
 // Cross `face`: update the cell; returns E_CONT, E_ESCAPE or E_BOTTOM.

@@ -769,6 +769,7 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
     }
     S.trace(P.n, idx, seg);
     R.s = sx;
+    mark_crossed<real>(R, face);
     int e = cross_face(T, face, R.i, R.j, R.k);
     // the optical-depth cut-off applies to marches without an interaction target (peel-offs, chords;
     // every march of an absorber-only kernel)
