@@ -277,7 +277,8 @@ template <typename real>
 __device__ __forceinline__ real cell_exit(const DevGrid &G, const Tabs<real> &T, Ray<real> &R, int &face)
 {
     int fc = R.fc;
-    if (fc & STALE_R) {
+    {
+        // the radial family is short: evaluated at every step, without a branch (the same value as cached)
         int f;
         R.tr = radial_exit<real>(T, R, f);
         fc = (fc & ~0xff) | f;
