@@ -832,6 +832,13 @@ gcmc_status gcmc_upload_grid(gcmc_ctx *ctx, const gcmc_grid_desc *d, int *grid_i
     for (int j = 0; j <= nlat; ++j) slat_lo[j] = (float)(slat[j] - (double)slat_f[j]);
     for (int i = 0; i <= nlon; ++i) lon_lo[i] = (float)(G.lon[i] - (double)lon_f[i]);
     for (int j = 0; j < nlat; ++j) dslat[j] = (float)(slat[j + 1] - slat[j]);
+    std::vector<float> cb(nlat), cb_lo(nlat);
+    for (int j = 0; j < nlat; ++j) {
+        // 1 - |sin| at the band's lower edge (where the launch uniform is 0)
+        const double c = slat[j] >= 0.0 ? 1.0 - slat[j] : slat[j + 1] <= 0.0 ? 1.0 + slat[j] : 0.0;
+        cb[j] = (float)c;
+        cb_lo[j] = (float)(c - (double)cb[j]);
+    }
     for (int i = 0; i < nlon; ++i) dlon[i] = (float)(G.lon[i + 1] - G.lon[i]);
     std::vector<float2> r2p_f(nr + 1), slp_f(nlat + 1), csp_f(nlon + 1);
     std::vector<double2> r2p(nr + 1), slp(nlat + 1), csp(nlon + 1);
@@ -886,6 +893,8 @@ gcmc_status gcmc_upload_grid(gcmc_ctx *ctx, const gcmc_grid_desc *d, int *grid_i
     g.slat_lo_f = dput(ctx, G.owned, slat_lo.data(), nlat + 1, e);
     g.lon_lo_f = dput(ctx, G.owned, lon_lo.data(), nlon + 1, e);
     g.dslat_f = dput(ctx, G.owned, dslat.data(), nlat, e);
+    g.cb_f = dput(ctx, G.owned, cb.data(), nlat, e);
+    g.cb_lo_f = dput(ctx, G.owned, cb_lo.data(), nlat, e);
     g.dlon_f = dput(ctx, G.owned, dlon.data(), nlon, e);
     g.r2p_f = dput(ctx, G.owned, r2p_f.data(), nr + 1, e);
     g.slp_f = dput(ctx, G.owned, slp_f.data(), nlat + 1, e);

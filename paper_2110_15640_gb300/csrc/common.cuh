@@ -55,6 +55,10 @@ struct DevGrid {
     // low parts of the FP32 edges (edge = hi + lo to ~48 bits) and FP32 cell widths, so that
     // positions sampled inside a cell carry no edge rounding that repeats for every packet
     const float *r_lo_f, *slat_lo_f, *lon_lo_f, *dslat_f, *dlon_f;
+    // per latitude band j in one hemisphere, 1 - |sin| at its lower edge as FP32 hi + lo: cos(lat) =
+    // sqrt(c (2 - c)) from c = 1 - |sin(lat)| keeps full relative precision towards the poles, where
+    // sqrt(1 - sin^2) from an FP32 sin(lat) loses it (0 for the band across the equator)
+    const float *cb_f, *cb_lo_f;
     // the march's edge tables as pairs (one 8/16-byte load each), staged in shared memory by the kernels:
     // r2p = (r^2 hi, r^2 lo) [nr+1], slp = (sin lat, sin^2 lat) [nlat+1], csp = (cos lon, sin lon) [nlon+1]
     const float2 *r2p_f, *slp_f, *csp_f;

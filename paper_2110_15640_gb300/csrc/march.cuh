@@ -313,8 +313,8 @@ __device__ __forceinline__ real cell_exit(const DevGrid &G, const Tabs<real> &T,
 // another family: evaluated again, its root at R.s no longer counts).
 template <typename real> __device__ __forceinline__ void mark_crossed(Ray<real> &R, int face)
 {
-    int st = (face & 3) != 1 ? STALE_R : ((face >> 2) & 3) != 1 ? STALE_LAT : STALE_LON;
-    if (R.tr <= R.s) st |= STALE_R;
+    // (the radial family is evaluated at every step anyway)
+    int st = ((face >> 2) & 3) != 1 ? STALE_LAT : ((face >> 4) & 3) != 1 ? STALE_LON : 0;
     if (R.tl <= R.s) st |= STALE_LAT;
     if (R.tn <= R.s) st |= STALE_LON;
     R.fc |= st;

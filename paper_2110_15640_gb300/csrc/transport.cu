@@ -63,6 +63,10 @@ template <typename real, bool LOG> struct Sink {
     static constexpr bool is_log = LOG;
     unsigned long long *sm;   // this thread's first slot; slots are blockDim apart
     int stride;
+    // this thread's copy of the last three words of its packet's current flight draw (the scatterer,
+    // mu and azimuth words of the event whose first word sampled the flight's optical depth), blockDim
+    // apart: the interaction at the end of the flight reads them instead of drawing the event again
+    uint32_t *wc;
     LogOut lg;
 
     __device__ __forceinline__ void add(int slot, unsigned long long v) { sm[slot * stride] += v; }
@@ -139,6 +143,9 @@ __device__ __forceinline__ void start_flight(Packet<real> &P, const DevJob &J, S
                                              int mode = FL_NATURAL, real p = (real)1, real taum = (real)0)
 {
     const uint4 w = draw_words(J.seed, P.n, P.ev, J.key);
+    S.wc[0] = w.y;
+    S.wc[S.stride] = w.z;
+    S.wc[2 * S.stride] = w.w;
     real tau;
     if (mode == FL_NATURAL) {
         tau = -M<real>::log_(u01<real>(w.x));
@@ -361,6 +368,7 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
     const int i = rem - j * G.nlon;
     const real u1 = u01<real>(w.y), u2 = u01<real>(w.z), u3 = u01<real>(w.w);
     real r, sl, ph;
+    float cl_f = 0.0f;
     if constexpr (sizeof(real) == 8) {
         const double r1 = G.r[k], r2 = G.r[k + 1];
         r = cbrt(r1 * r1 * r1 + u1 * (r2 * r2 * r2 - r1 * r1 * r1));
@@ -378,10 +386,23 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
                                                                                                  x * (22.0f / 729.0f)))))
                                   : expm1f(log1pf(x) * (1.0f / 3.0f));
         r = r1 + __fmaf_rn(r1, t, __ldg(G.r_lo_f + k));
-        sl = __ldg(G.slat_f + j) + __fmaf_rn(u2, __ldg(G.dslat_f + j), __ldg(G.slat_lo_f + j));
         ph = __ldg(G.lon_f + i) + __fmaf_rn(u3, __ldg(G.dlon_f + i), __ldg(G.lon_lo_f + i));
+        const float s1 = __ldg(G.slat_f + j), s2 = __ldg(G.slat_f + j + 1), ds = __ldg(G.dslat_f + j);
+        if (s1 >= 0.0f || s2 <= 0.0f) {
+            // a band in one hemisphere: c = 1 - |sin(lat)| is uniform in the band like sin(lat), linear from
+            // its value at the lower edge; cos(lat) = sqrt(c (2 - c)) keeps its relative precision at the poles
+            const bool north = s1 >= 0.0f;
+            const float c = __fmaf_rn(north ? -u2 : u2, ds, __ldg(G.cb_f + j)) + __ldg(G.cb_lo_f + j);
+            sl = north ? 1.0f - c : c - 1.0f;
+            cl_f = sqrtf(c * (2.0f - c));
+        } else {
+            sl = s1 + __fmaf_rn(u2, ds, __ldg(G.slat_lo_f + j));
+            cl_f = sqrtf(fmaxf(0.0f, 1.0f - sl * sl));
+        }
     }
-    const real cl = M<real>::sqrt_(fmax((real)0, (real)1 - sl * sl));
+    real cl;
+    if constexpr (sizeof(real) == 8) cl = sqrt(fmax(0.0, 1.0 - sl * sl));
+    else cl = cl_f;
     real sp, cp;
     M<real>::sincos_(ph, &sp, &cp);
     P.ix = r * cl * cp;
@@ -442,8 +463,8 @@ __device__ void after_peels_scatter(Packet<real> &P, const DevJob &J, SinkT &S)
             }
         }
     }
-    const uint4 w = draw_words(J.seed, P.n, P.ev, J.key);
-    const real u1 = u01<real>(w.y), u2 = u01<real>(w.z), u3 = u01<real>(w.w);
+    // the words of this flight's event, drawn when the flight started
+    const real u1 = u01<real>(S.wc[0]), u2 = u01<real>(S.wc[S.stride]), u3 = u01<real>(S.wc[2 * S.stride]);
     real mu;
     if (u1 < P.pg) {
         mu = sample_rayleigh<real>(u2);
@@ -516,9 +537,9 @@ __device__ void after_peels_surface(Packet<real> &P, const DevJob &J, SinkT &S)
             }
         }
     }
-    const uint4 w = draw_words(J.seed, P.n, P.ev, J.key);
+    // the words of this flight's event, drawn when the flight started
     real dx = P.fx, dy = P.fy, dz = P.fz;
-    turn<real>(dx, dy, dz, M<real>::sqrt_(u01<real>(w.z)), (real)(2.0 * PI) * u01<real>(w.w));
+    turn<real>(dx, dy, dz, M<real>::sqrt_(u01<real>(S.wc[S.stride])), (real)(2.0 * PI) * u01<real>(S.wc[2 * S.stride]));
     ++P.ev;
     start_next_flight<real, true>(P, J, S, dx, dy, dz);
 }
@@ -829,11 +850,13 @@ __global__ void __launch_bounds__(256) k_transport_plain(const DevGrid *__restri
     Sink<real, LOG> S;
     S.sm = sacc + threadIdx.x;
     S.stride = blockDim.x;
+    S.wc = reinterpret_cast<uint32_t *>(sacc + NSLOT * blockDim.x) + threadIdx.x;
     S.lg = lg;
     for (int s = 0; s < NSLOT; ++s) S.sm[s * S.stride] = 0ull;
     const DevJob &J = *jobp;
     const DevGrid &G = grids[J.grid_slot];
-    auto *tab = reinterpret_cast<typename Pair<real>::type *>(sacc + NSLOT * blockDim.x);
+    auto *tab = reinterpret_cast<typename Pair<real>::type *>(reinterpret_cast<uint32_t *>(sacc + NSLOT * blockDim.x) +
+                                                              3 * blockDim.x);
     const Tabs<real> T = stage_tabs<real>(G, tab, threadIdx.x, blockDim.x);
     __syncthreads();
     const JobC<real> jc = job_consts<real>(J);
@@ -898,11 +921,13 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 2) k_transport
     Sink<real, false> S;
     S.sm = sacc + threadIdx.x;
     S.stride = blockDim.x;
+    S.wc = reinterpret_cast<uint32_t *>(sacc + NSLOT * blockDim.x) + threadIdx.x;
     for (int s = 0; s < NSLOT; ++s) S.sm[s * S.stride] = 0ull;
     const int lane = threadIdx.x & 31;
     // march tables in shared memory: one copy per block when every job uses the same grid, else one
     // per warp, restaged when the warp's work item comes from another grid
-    auto *tab0 = reinterpret_cast<typename Pair<real>::type *>(sacc + NSLOT * blockDim.x);
+    auto *tab0 = reinterpret_cast<typename Pair<real>::type *>(reinterpret_cast<uint32_t *>(sacc + NSLOT * blockDim.x) +
+                                                               3 * blockDim.x);
     Tabs<real> T;
     int cur_grid = -1;
     if (one_grid) {
@@ -975,9 +1000,12 @@ __global__ void __launch_bounds__(128, 4) k_transport_serve(const DevGrid *__res
     Sink<real, false> S;
     S.sm = sacc + threadIdx.x;
     S.stride = blockDim.x;
+    S.wc = reinterpret_cast<uint32_t *>(sacc + NSLOT * blockDim.x) + threadIdx.x;
     for (int s = 0; s < NSLOT; ++s) S.sm[s * S.stride] = 0ull;
     const int lane = threadIdx.x & 31;
-    auto *tabw = reinterpret_cast<typename Pair<real>::type *>(sacc + NSLOT * blockDim.x) + (threadIdx.x >> 5) * tab_n;
+    auto *tabw = reinterpret_cast<typename Pair<real>::type *>(reinterpret_cast<uint32_t *>(sacc + NSLOT * blockDim.x) +
+                                                               3 * blockDim.x) +
+                 (threadIdx.x >> 5) * tab_n;
     Tabs<real> T;
     int cur_grid = -1;
     long long empty = 0;
@@ -1065,7 +1093,7 @@ __global__ void __launch_bounds__(128, 4) k_transport_serve(const DevGrid *__res
 }
 
 // ------------------------------------------------------------------ host launchers
-size_t transport_smem(int block) { return (size_t)NSLOT * block * sizeof(unsigned long long); }
+size_t transport_smem(int block) { return (size_t)NSLOT * block * sizeof(unsigned long long) + (size_t)3 * block * 4; }
 
 static size_t tab_bytes(int precision, int entries) { return (size_t)entries * (precision == GCMC_FP64 ? 16 : 8); }
 
