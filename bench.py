@@ -8,9 +8,13 @@ jobs: cell tables (S1) and one persistent transport launch (S2-S8) with device t
 
 Prints ONE JSON line (rank 0): packet-steps/s of the batched form (value), the plain one-launch-
 per-job form beside it, spectra/s, the end-to-end number through the C ABI from pinned host
-buffers, the roofline of the transport kernel, the oracle's CPU baseline, the clocks seen, and a
-request-latency summary (p50/p99) of a 1000-request sample of the serving stream.
-`--impl reference` times the FP64 CPU oracle on the same workload instead.
+buffers, the transport kernel against the measured random-gather rate of this GPU (the gather
+roofline, `roofline`) and against its ALU issue ceiling (`alu_roofline`), the oracle's CPU baseline,
+the clocks seen, the other configuration workloads at full size (`workloads`: albedo 32x16x20 FP64,
+the 960-job phase curve, the 9532-wavelength transmission spectrum, transit with multiple
+scattering; batched and plain form, gather fraction and clocks of each), and the serving stream of
+10,000 Poisson-arriving mixed requests (p50/p99 latency and packet-steps/s of the server and of the
+plain form).  `--impl reference` times the FP64 CPU oracle on the same workload instead.
 
 Other workloads (--workload): albedo (32x16x20, FP64), phasecurve (40 wavelengths x 24 phases),
 transmission (9532 wavelengths, Doppler cross sections), transit-scatter (40 optical wavelengths in
@@ -33,11 +37,10 @@ if ROOT not in sys.path:
 
 OPS_PER_STEP = 64          # FP32-pipe operations of one cell step (counted from the formulas)
 # DRAM bytes (read + write) of the persistent transport kernel per emission job of the 128x64x50 grid,
-# from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 8-job band-0 launch: the traffic
-# grows with the number of job tables the launch touches
-TRAFFIC_PER_EMISSION_JOB = (47.92e6 + 0.32e6) / 8
-PEAK_FP32_OPS = 152 * 128 * 2.07e9   # GB300: SMs x FP32 lanes x max SM clock (an FMA counts as one op)
-PEAK_FP64_OPS = 152 * 2 * 2.07e9     # GB300: FP64 issue is 1/64 of FP32 (2 lanes per SM per clock)
+# from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 8-job band-0 launch of the current
+# kernel, or None when the kernel has changed since the counters were taken: the traffic grows with the
+# number of job tables the launch touches
+TRAFFIC_PER_EMISSION_JOB = None
 
 
 def parse():
@@ -64,8 +67,12 @@ def parse():
     ap.add_argument("--cont-abs", action="store_true", help="scattering workloads: continuous absorption")
     ap.add_argument("--requests", type=int, default=10_000, help="serving: requests in the stream")
     ap.add_argument("--hbm-budget-gb", type=float, default=16.0, help="serving: admitted workspace")
-    ap.add_argument("--serving-requests", type=int, default=1000,
-                    help="emission bench: requests of the serving sample in its JSON line (0: none)")
+    ap.add_argument("--serving-requests", type=int, default=10_000,
+                    help="emission bench: requests of the serving stream in its JSON line (0: none)")
+    ap.add_argument("--jobs", type=int, default=0,
+                    help="run only N jobs spread evenly over the workload's job list (profiling a small case)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="emission bench: skip the other configuration workloads in its JSON line")
     return ap.parse_args()
 
 
@@ -99,6 +106,9 @@ def workload(args, rank):
         wl.source.opts.forced_first = int(args.forced_first)
         wl.source.opts.cont_abs = int(args.cont_abs)
         wl.name += ("_forced" if args.forced_first else "") + ("_contabs" if args.cont_abs else "")
+    if getattr(args, "jobs", 0) and args.jobs < len(wl.jobs):
+        n = len(wl.jobs)
+        wl.jobs = [wl.jobs[(q * n) // args.jobs] for q in range(args.jobs)]
     wl.seed = shard.rank_seed(wl.seed, rank)
     return wl
 
@@ -106,8 +116,8 @@ def workload(args, rank):
 # oracle sample per workload for the CPU baseline: (jobs, packets per job or None for all)
 CPU_SAMPLE = {"emission": (48, 1_000_000), "albedo": (1, None), "phasecurve": (24, None), "transmission": (480, None),
               "transit-scatter": (8, 400_000), "band": (12, 1_000_000), "emission-hires": (40, None)}
-REF_SAMPLE = {"emission": (2, 200_000), "albedo": (1, None), "phasecurve": (2, None), "transmission": (96, None),
-              "transit-scatter": (2, 20_000), "band": (2, 200_000), "emission-hires": (4, None)}
+REF_SAMPLE = {"emission": (2, 1_000_000), "albedo": (1, None), "phasecurve": (2, None), "transmission": (96, None),
+              "transit-scatter": (2, None), "band": (2, 1_000_000), "emission-hires": (4, None)}
 
 
 class ClockSampler:
@@ -317,6 +327,169 @@ def serving_bench(args):
     return 0
 
 
+def device_sm_count(dev):
+    import torch
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def tune_cfg(args, ctx, jobs, stream):
+    """The launch configuration: the flags' fixed one, or the autotuner's (untimed; tallies do not depend on
+    the launch parameters)."""
+    from paper_2110_15640_gb300 import autotune, gcmc
+    if args.no_tune or args.block or args.chunk or args.interval or args.refill or args.blocks_per_sm:
+        cfg = gcmc.gcmc_launch_cfg(args.block, args.blocks_per_sm, args.chunk, args.interval, args.refill, 0)
+        tuned = {"block": args.block or 128, "blocks_per_sm": args.blocks_per_sm, "chunk": args.chunk or 1024,
+                 "interval": args.interval or 1, "refill_min": args.refill or 16}
+        return cfg, tuned
+    cfg, tuned, _ = autotune.tune(ctx, autotune.sample_jobs(jobs), stream, reps=2, full_jobs=jobs)
+    return cfg, tuned
+
+
+def measure(ctx, stream, jobs, cfg, steps, warmup, plain_steps, world=1, graph=False):
+    """Device-timed batched steps (max over ranks), then the plain one-launch-per-job form on the same jobs.
+    Returns a dict of the measurements; `clocks` is the nvidia-smi record of the batched timed region."""
+    import torch
+    from paper_2110_15640_gb300 import gcmc
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    with torch.cuda.stream(stream):
+        tall = torch.zeros((len(jobs), gcmc.MAX_OBS), dtype=torch.float64, device="cuda")
+        _, sts = ctx.run_batch(jobs, cfg=cfg)                       # untimed: exact packet-step count
+    steps_per_step = int(sum(s.steps for s in sts))
+    out = {"packet_steps_per_step": steps_per_step, "packets_per_step": int(sum(s.packets for s in sts)),
+           "capped_weight": float(sum(s.ledger[6] for s in sts))}
+    for _ in range(warmup):
+        ctx.run_batch(jobs, cfg=cfg, tallies=tall, stats=False)
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    l0 = gcmc.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_uuid(torch.cuda.current_device())) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.run_batch(jobs, cfg=cfg, tallies=tall, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    out["gpu_launches"] = gcmc.kernel_launches() - l0
+    prep_ms, tr_ms, ntr = ctx.get_profile()
+    ctx.set_profiling(False)
+    t = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        tt = torch.tensor([t], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t = float(tt.item())
+    out.update(value=steps_per_step * steps * world / t, ms_per_step=1e3 * t / steps, seconds=t,
+               kernel_ms=tr_ms / max(ntr, 1), prep_ms=prep_ms / max(ntr, 1), clocks=clk.summary())
+    out["spectra_per_s"] = world * steps / t          # one step computes the workload's whole spectrum
+    if graph:
+        gr = ctx.graph(jobs, cfg)
+        for _ in range(2):
+            gr.launch(tall)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(steps):
+            gr.launch(tall)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        tg = g0.elapsed_time(g1) / 1e3
+        gr.close()
+        out["graph_form"] = {"value": steps_per_step * steps / tg, "unit": "packet-steps/s",
+                             "ms_per_step": 1e3 * tg / steps}
+    if plain_steps:
+        outp = torch.zeros(gcmc.MAX_OBS, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            for j in jobs[:8]:
+                ctx.run_packets(j, tallies=outp)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(plain_steps):
+            for j in jobs:
+                ctx.run_packets(j, tallies=outp)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        tp = p0.elapsed_time(p1) / 1e3
+        out["plain_form"] = {"value": steps_per_step * plain_steps / tp, "unit": "packet-steps/s",
+                             "ms_per_step": 1e3 * tp / plain_steps, "launches_per_step": len(jobs)}
+        out["batched_over_plain"] = out["value"] / out["plain_form"]["value"]
+    return out
+
+
+def rooflines(ctx, wl, m, prec, dev, traffic):
+    """The transport kernel against its bound, the measured random-gather rate of this GPU for a table of the
+    job's size and record width (the gather roofline), with the ALU issue ceiling beside it.  The gather
+    roofline is stated in GB/s of algorithmic record bytes, so achieved / peak is packet-steps/s over
+    gathers/s."""
+    from paper_2110_15640_gb300 import gcmc
+    f64 = prec == gcmc.FP64
+    rec_bytes = 16 if wl.opac.kind == gcmc.OPAC_ALBEDO else 4
+    if f64:
+        rec_bytes *= 2
+    gather = ctx.gather_bench(wl.grid.ncell, 16 if wl.opac.kind == gcmc.OPAC_ALBEDO else 4, 1 << 30)
+    k_s = m["kernel_ms"] / 1e3
+    steps_s = m["packet_steps_per_step"] / k_s
+    nsm = device_sm_count(dev)
+    mhz = m["clocks"].get("sm_mhz") or m["clocks"].get("sm_max_mhz") or 2070.0
+    lanes = 2 if f64 else 128                      # FP64 / FP32 lanes per SM and clock
+    peak_ops = nsm * lanes * mhz * 1e6
+    roof = {"bound": "gather", "achieved": steps_s * rec_bytes / 1e9, "peak": gather * rec_bytes / 1e9, "unit": "GB/s",
+            "frac": steps_s / gather, "traffic": traffic,
+            "kernel": f"k_transport_persistent<{'double' if f64 else 'float'}>", "kernel_ms": m["kernel_ms"],
+            "prep_ms": m["prep_ms"], "packet_steps_per_s": steps_s, "gathers_per_s": gather,
+            "record_bytes": rec_bytes, "table_records": wl.grid.ncell,
+            "peak_source": "measured: gcmc_gather_bench on this GPU, random records of a table of the job's size"}
+    alu = {"bound": "fp64" if f64 else "alu", "achieved": OPS_PER_STEP * steps_s / 1e12, "peak": peak_ops / 1e12,
+           "unit": "TFLOP/s", "frac": OPS_PER_STEP * steps_s / peak_ops, "ops_per_step": OPS_PER_STEP, "sm_count": nsm,
+           "sm_mhz": mhz, "peak_source": "SMs x lanes x median SM clock sampled during the timed steps"}
+    if traffic:
+        roof["dram_GBps"] = traffic / k_s / 1e9
+        peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(peaks):
+            with open(peaks) as f:
+                hbm = json.load(f).get("hbm_gbs")
+            if hbm:
+                roof["dram_frac_of_measured_hbm"] = roof["dram_GBps"] / hbm
+    return roof, alu
+
+
+def workload_line(args, name, ctx, stream, dev):
+    """One workload of the configuration list at its full size: batched (autotuned) and plain form, gather
+    fraction and clocks; grids are released afterwards."""
+    import copy
+    from paper_2110_15640_gb300 import gcmc
+    a2 = copy.copy(args)
+    a2.workload = name
+    wl = workload(a2, 0)
+    prec = gcmc.FP64 if name == "albedo" else gcmc.FP32
+    with __import__("torch").cuda.stream(stream):
+        gid, oid, sid, jobs = gcmc.load_workload(ctx, wl, prec, device_inputs=True)
+    cfg, tuned = tune_cfg(a2, ctx, jobs, stream)
+    steps, plain = WORKLOAD_STEPS[name]
+    m = measure(ctx, stream, jobs, cfg, steps, 1, plain)
+    roof, alu = rooflines(ctx, wl, m, prec, dev, None)
+    g = wl.grid
+    ctx.release_grid(gid)
+    return {"workload": wl.name, "grid": f"{g.nlon}x{g.nlat}x{g.nr}", "jobs": len(jobs),
+            "dtype": "f64" if prec == gcmc.FP64 else "f32", "launch": tuned, "steps": steps,
+            "value": m["value"], "unit": "packet-steps/s", "ms_per_step": m["ms_per_step"],
+            "spectra_per_s": m["spectra_per_s"], "packet_steps_per_step": m["packet_steps_per_step"],
+            "plain_form": m.get("plain_form"), "batched_over_plain": m.get("batched_over_plain"),
+            "gather_roofline": {"frac": roof["frac"], "kernel_ms": roof["kernel_ms"],
+                                "gathers_per_s": roof["gathers_per_s"], "record_bytes": roof["record_bytes"]},
+            "alu_frac": alu["frac"], "clocks": m["clocks"]}
+
+
+# configuration workloads timed in the default line beside the emission batch: (timed steps, plain steps)
+WORKLOAD_STEPS = {"albedo": (5, 3), "phasecurve": (1, 1), "transmission": (3, 1), "transit-scatter": (2, 1)}
+
+
 def main():
     args = parse()
     if args.workload == "serving":
@@ -336,88 +509,14 @@ def main():
     if world > 1:
         torch.distributed.barrier()
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
     wl = workload(args, rank)
     prec = gcmc.FP64 if args.workload == "albedo" else gcmc.FP32     # the 32x16x20 albedo case runs FP64
     stream = torch.cuda.Stream()
     ctx = gcmc.Context(local, stream=stream)
-    from paper_2110_15640_gb300 import autotune
     with torch.cuda.stream(stream):
         gid, oid, sid, jobs = gcmc.load_workload(ctx, wl, prec, device_inputs=True)
-        tall = torch.zeros((len(jobs), gcmc.MAX_OBS), dtype=torch.float64, device="cuda")
-        if args.no_tune or args.block or args.chunk or args.interval or args.refill or args.blocks_per_sm:
-            cfg = gcmc.gcmc_launch_cfg(args.block, args.blocks_per_sm, args.chunk, args.interval, args.refill, 0)
-            tuned = {"block": args.block or 128, "blocks_per_sm": args.blocks_per_sm, "chunk": args.chunk or 1024,
-                     "interval": args.interval or 1, "refill_min": args.refill or 16}
-        else:   # untimed search on a sample spread over the job list (tallies do not depend on the launch parameters)
-            cfg, tuned, _ = autotune.tune(ctx, autotune.sample_jobs(jobs), stream, reps=2)
-        _, sts = ctx.run_batch(jobs, cfg=cfg)                       # untimed: exact packet-step count
-    steps_per_step = int(sum(s.steps for s in sts))
-    packets_per_step = int(sum(s.packets for s in sts))
-    capped = float(sum(s.ledger[6] for s in sts))
-
-    # ---------------- batched form: value
-    for _ in range(args.warmup):
-        ctx.run_batch(jobs, cfg=cfg, tallies=tall, stats=False)
-    torch.cuda.synchronize()
-    ctx.set_profiling(True)
-    l0 = gcmc.kernel_launches()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(gpu_uuid(local)) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            ctx.run_batch(jobs, cfg=cfg, tallies=tall, stats=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-    launches = gcmc.kernel_launches() - l0
-    prep_ms, tr_ms, ntr = ctx.get_profile()
-    ctx.set_profiling(False)
-    t = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        tt = torch.tensor([t], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t = float(tt.item())
-    value = steps_per_step * args.steps * world / t
-
-    # ---------------- the same batch captured into a CUDA graph and replayed
-    graph_line = None
-    if world == 1:
-        gr = ctx.graph(jobs, cfg)
-        for _ in range(2):
-            gr.launch(tall)
-        torch.cuda.synchronize()
-        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        g0.record(stream)
-        for _ in range(args.steps):
-            gr.launch(tall)
-        g1.record(stream)
-        torch.cuda.synchronize()
-        tg = g0.elapsed_time(g1) / 1e3
-        gr.close()
-        graph_line = {"value": steps_per_step * args.steps / tg, "unit": "packet-steps/s",
-                      "ms_per_step": 1e3 * tg / args.steps}
-
-    # ---------------- plain form: one launch per job (same work)
-    outp = torch.zeros(gcmc.MAX_OBS, dtype=torch.float64, device="cuda")
-    with torch.cuda.stream(stream):
-        for j in jobs[:8]:
-            ctx.run_packets(j, tallies=outp)
-    torch.cuda.synchronize()
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(stream)
-    for _ in range(args.plain_steps):
-        for j in jobs:
-            ctx.run_packets(j, tallies=outp)
-    p1.record(stream)
-    torch.cuda.synchronize()
-    t_plain = p0.elapsed_time(p1) / 1e3
-    plain_value = steps_per_step * args.plain_steps / t_plain if args.plain_steps else None
+    cfg, tuned = tune_cfg(args, ctx, jobs, stream)
+    m = measure(ctx, stream, jobs, cfg, args.steps, args.warmup, args.plain_steps, world=world, graph=world == 1)
 
     # ---------------- end to end through the C ABI from pinned host buffers
     ga, oa = gcmc.workload_arrays(wl, "pinned")
@@ -447,19 +546,21 @@ def main():
         ctx.release_grid(g2)
     torch.cuda.synchronize()
     t_e2e = (time.perf_counter() - te) / max(args.e2e_steps, 1)
-    e2e_value = steps_per_step / t_e2e if args.e2e_steps else None
+    e2e_value = m["packet_steps_per_step"] / t_e2e if args.e2e_steps else None
 
-    # ---------------- roofline of the transport kernel and the gather roofline
-    f64 = prec == gcmc.FP64
-    tr_avg = tr_ms / max(ntr, 1) / 1e3
-    achieved = OPS_PER_STEP * steps_per_step / tr_avg / 1e12
-    rec_bytes = 16 if wl.opac.kind == gcmc.OPAC_ALBEDO else 4
-    gather = ctx.gather_bench(wl.grid.ncell, rec_bytes, 1 << 30)
-    clocks = clk.summary()
+    g = wl.grid
+    traffic = (TRAFFIC_PER_EMISSION_JOB * len(jobs)
+               if TRAFFIC_PER_EMISSION_JOB and args.workload == "emission" and g.nlon * g.nlat * g.nr == 409600 else None)
+    roof, alu = rooflines(ctx, wl, m, prec, local, traffic)
+
+    workloads = None
+    if rank == 0 and world == 1 and args.workload == "emission" and not args.no_workloads:
+        ctx.release_grid(gid)
+        workloads = {name: workload_line(args, name, ctx, stream, local) for name in WORKLOAD_STEPS}
 
     serving = None
     if rank == 0 and world == 1 and args.workload == "emission" and args.serving_requests > 0:
-        # request-latency summary on a sample of the serving stream (the full stream: --workload serving)
+        # the serving stream: Poisson arrivals of mixed requests through the continuous-batching server
         serving = serving_run(args.serving_requests, args.hbm_budget_gb)
         del serving["grids"]
 
@@ -472,44 +573,37 @@ def main():
                "sample": f"{min(nj, len(jobs))} of {len(jobs)} jobs x {npk or 'all their'} packets, S1 + transport, "
                          f"{dt:.1f} s"}
     if rank == 0:
-        g = wl.grid
+        rec_bytes = 16 if wl.opac.kind == gcmc.OPAC_ALBEDO else 4
         tables = len(jobs) * (len(wl.opac.wg) if wl.mode == gcmc.EMISSION and wl.jobs[0].g_idx < 0 else 1)
         per_step_bytes = tables * g.ncell * (rec_bytes + (12 if wl.mode == gcmc.EMISSION else 0))
-        peak = (PEAK_FP64_OPS if f64 else PEAK_FP32_OPS) / 1e12
+        f64 = prec == gcmc.FP64
         line = {
-            "metric": "packet-steps/s", "value": value, "unit": "packet-steps/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "metric": "packet-steps/s", "value": m["value"], "unit": "packet-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if f64 else "f32",
             "data": "synthetic",
-            "spectra_per_s": world * args.steps / t,
-            "config": {"workload": wl.name, "jobs": len(jobs), "packets_per_step": packets_per_step,
-                       "grid": f"{g.nlon}x{g.nlat}x{g.nr}", "packet_steps_per_step": steps_per_step,
-                       "capped_weight": capped,
+            "spectra_per_s": m["spectra_per_s"],
+            "config": {"workload": wl.name, "jobs": len(jobs), "packets_per_step": m["packets_per_step"],
+                       "grid": f"{g.nlon}x{g.nlat}x{g.nr}", "packet_steps_per_step": m["packet_steps_per_step"],
+                       "capped_weight": m["capped_weight"],
                        "l2": (f"inputs larger than L2 (per-step cell tables {per_step_bytes / 1e9:.2f} GB)"
                               if per_step_bytes > 129e6 else
                               f"per-step cell tables {per_step_bytes / 1e6:.1f} MB fit in L2 (the workload's own size)"),
                        "precision": ("FP64 march, tables and tallies" if f64 else
                                      "FP32 march and opacities, FP64 luminosities, 64-bit fixed-point pdf and tallies"),
                        "launch": tuned},
-            "plain_form": {"value": plain_value, "unit": "packet-steps/s",
-                           "ms_per_step": 1e3 * t_plain / args.plain_steps if args.plain_steps else None,
-                           "launches_per_step": len(jobs)},
-            "batched_over_plain": value / plain_value if plain_value else None,
-            "graph_form": graph_line,
+            "plain_form": m.get("plain_form"),
+            "batched_over_plain": m.get("batched_over_plain"),
+            "graph_form": m.get("graph_form"),
             "e2e": {"value": e2e_value, "unit": "packet-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * t_e2e},
-            "roofline": {"bound": "fp64" if f64 else "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak,
-                         "traffic": (TRAFFIC_PER_EMISSION_JOB * len(jobs)
-                                     if args.workload == "emission" and g.nlon * g.nlat * g.nr == 409600 else None),
-                         "kernel": f"k_transport_persistent<{'double' if f64 else 'float'}>", "ops_per_step": OPS_PER_STEP,
-                         "kernel_ms": 1e3 * tr_avg, "prep_ms": prep_ms / max(ntr, 1)},
-            "gather_roofline": {"gathers_per_s": gather, "table_records": g.ncell, "record_bytes": rec_bytes,
-                                "frac": (steps_per_step / tr_avg) / gather},
+            "roofline": roof,
+            "alu_roofline": alu,
             "cpu_baseline": cpu,
-            "gpu_launches": launches,
-            "clocks": clocks,
+            "gpu_launches": m["gpu_launches"],
+            "clocks": m["clocks"],
             "observables": F_band,
+            "workloads": workloads,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)

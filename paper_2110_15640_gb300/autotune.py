@@ -46,9 +46,12 @@ def _time_cfg(ctx, jobs, cfg, reps, stream):
     return a.elapsed_time(b) / reps
 
 
-def tune(ctx, jobs, stream, space=None, reps=2, coordinate=True, log=None):
+def tune(ctx, jobs, stream, space=None, reps=2, coordinate=True, log=None, full_jobs=None, finalists=3):
     """Return (best gcmc_launch_cfg, table of (cfg dict, ms)).  coordinate=True searches one axis at a
-    time from the defaults, twice over (about thirty runs), instead of the full product."""
+    time from the defaults, twice over (about thirty runs), instead of the full product.  With full_jobs
+    (the whole batch the sample was drawn from), the `finalists` fastest configurations on the sample are
+    timed once more on the whole batch and the fastest there is returned: a sample can favour work-item
+    sizes and refill settings that do not carry over to the batch."""
     space = space or DEFAULT_SPACE
     best = {"block": 128, "blocks_per_sm": 6, "chunk": 512, "refill_min": 8, "interval": 4}
     table = []
@@ -80,6 +83,23 @@ def tune(ctx, jobs, stream, space=None, reps=2, coordinate=True, log=None):
             ms = run(c)
             if ms < best_ms:
                 best, best_ms = c, ms
+    if full_jobs is not None and len(full_jobs) > len(jobs):
+        seen, cands = set(), []
+        for c, _ in sorted(table, key=lambda t: t[1]):
+            key = tuple(sorted(c.items()))
+            if key not in seen:
+                seen.add(key)
+                cands.append(c)
+            if len(cands) == finalists:
+                break
+        best_full = float("inf")
+        for c in cands:
+            cfg = gcmc.gcmc_launch_cfg(c["block"], c["blocks_per_sm"], c["chunk"], c["interval"], c["refill_min"], 0)
+            ms = _time_cfg(ctx, full_jobs, cfg, 1, stream)
+            if log:
+                log(f"autotune (whole batch) {c} {ms:.2f} ms")
+            if ms < best_full:
+                best, best_full = c, ms
     cfg = gcmc.gcmc_launch_cfg(best["block"], best["blocks_per_sm"], best["chunk"], best["interval"], best["refill_min"], 0)
     return cfg, best, table
 
