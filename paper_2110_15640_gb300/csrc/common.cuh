@@ -184,8 +184,13 @@ template <typename real> struct M;
 template <> struct M<float> {
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
-    static __device__ __forceinline__ float exp_(float x) { return __expf(x); }
-    static __device__ __forceinline__ float log_(float x) { return __logf(x); }
+    // accurate expf / logf (a few ulp), not the __expf / __logf intrinsics: these run once per ray end or
+    // flight start, where the intrinsics' errors (an absolute 2^-21 in -ln(xi) for xi near 1, a relative
+    // 2^-24 |x| in e^-x up to the cut-off depth 50) would exceed the rounding of the march itself
+    static __device__ __forceinline__ float exp_(float x) { return expf(x); }
+    static __device__ __forceinline__ float log_(float x) { return logf(x); }
+    // 1 - e^-x with full relative precision for small x
+    static __device__ __forceinline__ float one_minus_exp_neg(float x) { return -expm1f(-x); }
     static __device__ __forceinline__ float cbrt_(float x) { return cbrtf(x); }
     static __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
     static __device__ __forceinline__ void sincos_(float x, float *s, float *c) { sincosf(x, s, c); }
@@ -197,6 +202,8 @@ template <> struct M<double> {
     static __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
     static __device__ __forceinline__ double exp_(double x) { return exp(x); }
     static __device__ __forceinline__ double log_(double x) { return log(x); }
+    // the FP64 path follows the definition term by term, as the oracle does
+    static __device__ __forceinline__ double one_minus_exp_neg(double x) { return 1.0 - exp(-x); }
     static __device__ __forceinline__ double cbrt_(double x) { return cbrt(x); }
     static __device__ __forceinline__ double div_(double a, double b) { return a / b; }
     static __device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }

@@ -711,7 +711,7 @@ __device__ void on_end(Packet<real> &P, const DevJob &J, SinkT &S, int e, int id
     // chord (column 0: W (1 - e^-tau) b / R_TOA)
     const bool through = e == E_ESCAPE || e == E_CUTOFF || e == E_BOTTOM;
     real c = (real)0;
-    if (e == E_ESCAPE) c = ((real)1 - M<real>::exp_(-R.tau)) * P.bimp;
+    if (e == E_ESCAPE) c = M<real>::one_minus_exp_neg(R.tau) * P.bimp;
     else if (through) c = P.bimp;
     if constexpr (SinkT::is_log) {
         if (S.lg.pk_tau) S.lg.pk_tau[P.n - S.lg.packet0] = (double)R.tau;
