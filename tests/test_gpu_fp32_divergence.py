@@ -10,9 +10,11 @@ the per-packet bar or whose cell sequence differs:
 
 * Divergent packets.  At the first differing segment, the oracle's ray (its positions are logged)
   and the GPU's leave the last common cell C at along-ray positions s_o and s_g; between them one side
-  places the ray in C, the other in the neighbour X beyond the face F between them.  On packets that
-  have not scattered (emission peel-offs, limb chords) the ray must stay within a rounding bound of F over
-  that interval (normal distance): DELTA_X = 64 m (8 FP32 ulps at the planetary radius) for shells and
+  places the ray in C, the other in the neighbour X beyond the face F between them.  Where the oracle's
+  ray went beyond F, the depth it reached beyond F over that interval (a grazing dip below a shell is
+  shallow however long); where the GPU's went beyond F, how close the oracle's ray came to F.  On packets
+  that have not scattered (emission peel-offs, limb chords) that distance must lie within a rounding bound
+  (normal to F): DELTA_X = 64 m (8 FP32 ulps at the planetary radius) for shells and
   half-planes; for cones DELTA_X plus the resolution of FP32 sin(latitude) (EPS32 / cos(latitude) radians:
   90 m at latitude 87 degrees).  On packets that have scattered, the FP32 ray may have drifted by the
   accumulated length differences D of the flights before it (interaction points are placed from FP32
@@ -92,6 +94,22 @@ def _dist(face, P):
     return np.abs(-math.sin(v) * P[..., 0] + math.cos(v) * P[..., 1])
 
 
+def _depth(grid, c, x, face, P):
+    """signed distance of points P beyond face F (between cell c and its neighbour x), positive on x's side"""
+    kind, v = face
+    ic, jc, kc = _ijk(grid, c)
+    ix, jx, kx = _ijk(grid, x)
+    if kind == "r":
+        d = np.linalg.norm(P, axis=-1) - v
+        return -d if kx < kc else d
+    if kind == "lat":
+        lat = np.arctan2(P[..., 2], np.hypot(P[..., 0], P[..., 1]))
+        d = np.linalg.norm(P, axis=-1) * np.sin(lat - v)
+        return d if jx > jc else -d
+    d = -math.sin(v) * P[..., 0] + math.cos(v) * P[..., 1]
+    return d if (ic + 1) % grid.nlon == ix else -d
+
+
 def _rays(cells):
     """(start, end) index ranges of the rays of a trace (a ray starts at a marker < 0)"""
     starts = [q for q, c in enumerate(cells) if c < 0] + [len(cells)]
@@ -123,10 +141,18 @@ def _divergence(grid, alpha, co, lo, po, cg, lg, multi):
     P = P0[None, :] + s[:, None] * d[None, :]
     if X >= 0:
         face = _face(grid, C, X)
+        dep = _depth(grid, C, X, face, P)
+        if so <= sg:
+            # the oracle's ray went beyond F into X while the GPU's stayed in C: how deep beyond F it went
+            # (a grazing dip below a shell is shallow however long the dip)
+            dist = float(max(dep.max(), 0.0))
+        else:
+            # the GPU's ray went beyond F while the oracle's stayed in C: how close the oracle's ray came to F
+            dist = float(max(-dep.max(), 0.0))
     else:   # that side's ray ended there: at a boundary shell, or (interaction, cut-off) inside C
         r_end = float(np.linalg.norm(P0 + min(so, sg) * d))
         face = ("r", grid.r_edges[-1] if abs(r_end - grid.r_edges[-1]) < abs(r_end - grid.r_edges[0]) else grid.r_edges[0])
-    dist = float(_dist(face, P).max())
+        dist = float(_dist(face, P).max())
     fb = _face_bound(face)
     dtau = float(alpha[C]) * abs(so - sg)
     tau_ray = float(np.dot(alpha[np.maximum(co[st + 1:m], 0)], lo[st + 1:m]))
