@@ -308,15 +308,23 @@ gcmc_status gcmc_submit(gcmc_ctx *ctx, const gcmc_job *jobs, int n_jobs, const g
                         uint64_t *ticket);
 gcmc_status gcmc_poll(gcmc_ctx *ctx, uint64_t ticket, double *tallies_out, gcmc_stats *stats_out);
 
+/* The number of tally columns `job` writes (into tallies_out of the run calls, and per packet into
+   pk_f of gcmc_run_packets_debug): its observer count (1 when obs_idx >= 0) for albedo and
+   emission jobs (Sect. 5.2, 5.3); for transmission jobs 1, or 2 with trans_scatter (the chord
+   integral of Sect. 5.1, then the scattered part).  Errors: those of the run calls' job checks
+   (GCMC_ERR_ARG). */
+gcmc_status gcmc_job_columns(gcmc_ctx *ctx, const gcmc_job *job, int32_t *n_cols);
+
 /* Parity/debug form of gcmc_run_packets: runs packets [packet0, packet0 + n_run) of `job` and
-   writes per-packet results to HOST arrays: pk_f [n_run][columns] (f per tally column, as in
-   gcmc_run_packets), pk_steps
-   [n_run], pk_tau [n_run] (optical depth of the packet's first peel-off or chord march), and for
-   the first n_trace packets the segment list: tr_cell [n_trace][max_trace] (flat cell index, or
-   -1 before a flight, -2 before a peel-off, -3 before a chord), tr_len, tr_n [n_trace].
-   Any output pointer may be NULL. */
+   writes per-packet results to HOST arrays: pk_f [n_run][pk_f_cols] (row-major; its first
+   gcmc_job_columns columns receive f per tally column, as in gcmc_run_packets, the rest are left
+   untouched), pk_steps [n_run], pk_tau [n_run] (optical depth of the packet's first peel-off or
+   chord march), and for the first n_trace packets the segment list: tr_cell [n_trace][max_trace]
+   (flat cell index, or -1 before a flight, -2 before a peel-off, -3 before a chord), tr_len,
+   tr_n [n_trace].  Any output pointer may be NULL.  A pk_f with fewer columns than the job
+   writes is refused (GCMC_ERR_ARG) before any work is queued. */
 gcmc_status gcmc_run_packets_debug(gcmc_ctx *ctx, const gcmc_job *job, int64_t packet0, int64_t n_run,
-                                   double *pk_f, int64_t *pk_steps, double *pk_tau, int32_t n_trace,
+                                   double *pk_f, int32_t pk_f_cols, int64_t *pk_steps, double *pk_tau, int32_t n_trace,
                                    int32_t max_trace, int32_t *tr_cell, double *tr_len, int32_t *tr_n,
                                    double *tallies_out, gcmc_stats *stats_out);
 

@@ -241,6 +241,14 @@ gcmc_status check_job(gcmc_ctx *ctx, const gcmc_job &j)
     return GCMC_OK;
 }
 
+// the tally columns of a checked job: observers (one when obs_idx >= 0), or the transit columns
+static int job_columns(const gcmc_ctx *ctx, const gcmc_job &j)
+{
+    const gcmc_source_desc &s = ctx->sources[j.source_id];
+    if (j.mode == GCMC_TRANSMISSION) return s.trans_scatter ? 2 : 1;
+    return j.obs_idx >= 0 ? 1 : s.n_obs;
+}
+
 gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan &P)
 {
     if (n <= 0 || !jobs) return fail(ctx, GCMC_ERR_ARG, "no jobs");
@@ -392,7 +400,7 @@ gcmc_status plan_run(gcmc_ctx *ctx, const gcmc_job *jobs, int n, int chunk, Plan
             d.tr_x = s.transit_xy[0];
             d.tr_y = s.transit_xy[1];
         }
-        d.n_tal = j.mode == GCMC_TRANSMISSION ? 1 + d.trans_scatter : d.n_obs;
+        d.n_tal = job_columns(ctx, j);
         d.forced_first = s.forced_first;
         d.path_bias = s.path_bias;
         d.cont_abs = s.cont_abs && d.rec4 ? 1 : 0;   // needs the scattering records' omega
@@ -1272,9 +1280,19 @@ gcmc_status gcmc_poll(gcmc_ctx *ctx, uint64_t ticket, double *tallies_out, gcmc_
     return GCMC_OK;
 }
 
+gcmc_status gcmc_job_columns(gcmc_ctx *ctx, const gcmc_job *job, int32_t *n_cols)
+{
+    if (!ctx || !job || !n_cols) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
+    const gcmc_status s = check_job(ctx, *job);
+    if (s) return s;
+    *n_cols = job_columns(ctx, *job);
+    return GCMC_OK;
+}
+
 gcmc_status gcmc_run_packets_debug(gcmc_ctx *ctx, const gcmc_job *job, int64_t packet0, int64_t n_run, double *pk_f,
-                                   int64_t *pk_steps, double *pk_tau, int32_t n_trace, int32_t max_trace, int32_t *tr_cell,
-                                   double *tr_len, int32_t *tr_n, double *tallies_out, gcmc_stats *stats_out)
+                                   int32_t pk_f_cols, int64_t *pk_steps, double *pk_tau, int32_t n_trace,
+                                   int32_t max_trace, int32_t *tr_cell, double *tr_len, int32_t *tr_n, double *tallies_out,
+                                   gcmc_stats *stats_out)
 {
     if (!ctx || !job) return fail(ctx, GCMC_ERR_ARG, "NULL argument");
     if (packet0 < 0 || n_run < 0 || packet0 + n_run > job->n_packets) return fail(ctx, GCMC_ERR_ARG, "packet range");
@@ -1283,6 +1301,7 @@ gcmc_status gcmc_run_packets_debug(gcmc_ctx *ctx, const gcmc_job *job, int64_t p
     Plan P;
     gcmc_status s = plan_run(ctx, job, 1, 128, P);
     if (s) return s;
+    if (pk_f && pk_f_cols < P.jobs[0].n_tal) return fail(ctx, GCMC_ERR_ARG, "pk_f has fewer columns than the job tallies");
     if ((s = ensure_arena(ctx, P.ws_bytes))) return s;
     char *base = (char *)ctx->arena;
     if ((s = stage(ctx, P, base))) return s;
@@ -1315,7 +1334,9 @@ gcmc_status gcmc_run_packets_debug(gcmc_ctx *ctx, const gcmc_job *job, int64_t p
         e = launch_plain(P.jobs[0].precision, P.scatter, P.feat, ctx->d_grids, dj, packet0, n_run, &hl, P.tab_n, ctx->stream);
     }
     if (e == cudaSuccess) {
-        if (pk_f) e = cudaMemcpyAsync(pk_f, hl.pk_f, (size_t)n_run * nobs * 8, cudaMemcpyDeviceToHost, ctx->stream);
+        if (pk_f && n_run > 0)
+            e = cudaMemcpy2DAsync(pk_f, (size_t)pk_f_cols * 8, hl.pk_f, (size_t)nobs * 8, (size_t)nobs * 8, (size_t)n_run,
+                                  cudaMemcpyDeviceToHost, ctx->stream);
         if (pk_steps && e == cudaSuccess)
             e = cudaMemcpyAsync(pk_steps, hl.pk_steps, (size_t)n_run * 8, cudaMemcpyDeviceToHost, ctx->stream);
         if (pk_tau && e == cudaSuccess)

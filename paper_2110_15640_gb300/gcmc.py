@@ -126,9 +126,10 @@ def lib():
             "gcmc_graph_read": ([C.c_void_p, C.c_void_p, P(gcmc_stats)], C.c_int),
             "gcmc_graph_destroy": ([C.c_void_p], C.c_int),
             "gcmc_poll": ([C.c_void_p, C.c_uint64, C.c_void_p, P(gcmc_stats)], C.c_int),
-            "gcmc_run_packets_debug": ([C.c_void_p, P(gcmc_job), C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
-                                        C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
-                                        C.c_void_p, P(gcmc_stats)], C.c_int),
+            "gcmc_job_columns": ([C.c_void_p, P(gcmc_job), P(C.c_int32)], C.c_int),
+            "gcmc_run_packets_debug": ([C.c_void_p, P(gcmc_job), C.c_int64, C.c_int64, C.c_void_p, C.c_int32,
+                                        C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, P(gcmc_stats)], C.c_int),
             "gcmc_prep_cells": ([C.c_void_p, P(gcmc_job)] + [C.c_void_p] * 7 + [P(gcmc_stats)], C.c_int),
             "gcmc_postscale": ([C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int64, C.c_double,
                                 P(gcmc_observables)], C.c_int),
@@ -162,7 +163,8 @@ def lib():
 EXPORTED = ["gcmc_create", "gcmc_destroy", "gcmc_set_stream", "gcmc_set_allocator", "gcmc_last_error",
             "gcmc_upload_grid", "gcmc_upload_opacity", "gcmc_set_source", "gcmc_run_packets", "gcmc_run_batch",
             "gcmc_submit", "gcmc_poll", "gcmc_run_contrib", "gcmc_graph_create", "gcmc_graph_launch",
-            "gcmc_graph_read", "gcmc_graph_destroy", "gcmc_run_packets_debug", "gcmc_prep_cells", "gcmc_postscale",
+            "gcmc_graph_read", "gcmc_graph_destroy", "gcmc_job_columns", "gcmc_run_packets_debug", "gcmc_prep_cells",
+            "gcmc_postscale",
             "gcmc_selftest_philox", "gcmc_version", "gcmc_release_grid", "gcmc_release_opacity",
             "gcmc_set_profiling", "gcmc_get_profile", "gcmc_kernel_launches", "gcmc_gather_bench",
             "gcmc_emission_pdf_noalloc", "gcmc_server_create", "gcmc_server_submit", "gcmc_server_progress",
@@ -396,8 +398,15 @@ class Context:
         self._check(st, "gcmc_poll")
         return out, sts
 
-    def run_debug(self, job, packet0=0, n_run=None, n_trace=0, max_trace=0, n_obs=1):
+    def job_columns(self, job):
+        n = C.c_int32(0)
+        self._check(lib().gcmc_job_columns(self.h, C.byref(job), C.byref(n)), "gcmc_job_columns")
+        return n.value
+
+    def run_debug(self, job, packet0=0, n_run=None, n_trace=0, max_trace=0, n_obs=None):
+        """per-packet results; pk_f has n_obs columns (default: the job's tally columns; fewer are refused)"""
         n_run = job.n_packets - packet0 if n_run is None else int(n_run)
+        n_obs = self.job_columns(job) if n_obs is None else int(n_obs)
         pk_f = np.zeros((n_run, n_obs))
         pk_steps = np.zeros(n_run, np.int64)
         pk_tau = np.zeros(n_run)
@@ -407,7 +416,7 @@ class Context:
         tr_n = np.zeros(max(n_trace, 1), np.int32)
         tally = np.zeros(MAX_OBS)
         st = gcmc_stats()
-        self._check(lib().gcmc_run_packets_debug(self.h, C.byref(job), int(packet0), n_run, _ptr(pk_f),
+        self._check(lib().gcmc_run_packets_debug(self.h, C.byref(job), int(packet0), n_run, _ptr(pk_f), n_obs,
                                                  _ptr(pk_steps), _ptr(pk_tau), n_trace, int(max_trace),
                                                  _ptr(tr_cell), _ptr(tr_len), _ptr(tr_n), _ptr(tally), C.byref(st)),
                     "gcmc_run_packets_debug")

@@ -148,3 +148,21 @@ def test_transit_argument_checks(G):
         src = dataclasses.replace(wl.source, opts=dataclasses.replace(wl.source.opts, **bad))
         with pytest.raises(gcmc.GcmcError):
             G.set_source(gid, src)
+
+
+def test_debug_output_columns(G):
+    """A transit job with multiple scattering tallies two columns: the library reports them, the
+    per-packet form fills that many by default, and a one-column pk_f is refused before any work."""
+    from paper_2110_15640_gb300 import gcmc
+    wl = cloudy_transit(500)
+    gid, oid, sid, jobs = _load(G, wl, gcmc.FP32)
+    assert G.job_columns(jobs[0]) == 2
+    got = G.run_debug(jobs[0])
+    assert got["pk_f"].shape == (500, 2)
+    wide = G.run_debug(jobs[0], n_obs=5)
+    np.testing.assert_array_equal(wide["pk_f"][:, :2], got["pk_f"])
+    assert not wide["pk_f"][:, 2:].any()
+    with pytest.raises(gcmc.GcmcError) as e:
+        G.run_debug(jobs[0], n_obs=1)
+    assert e.value.status == gcmc.ERR_ARG
+    G.run_packets(jobs[0])   # the context is still usable
