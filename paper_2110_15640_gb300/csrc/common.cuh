@@ -34,13 +34,6 @@ constexpr double FIX_SCALE = 4294967296.0;   // 2^32: fixed-point resolution of 
 // first flight's optical depth to the grid boundary
 enum { K_FLIGHT = 0, K_PEEL = 1, K_CHORD = 2, K_FORCE = 3 };
 enum { E_CONT = -1, E_INTERACT = 0, E_ESCAPE = 1, E_BOTTOM = 2, E_CUTOFF = 3, E_CAP = 4, E_LOST = 5 };
-// exit faces, encoded as the cell-index change they cause: bits 0-1 dk + 1, bits 2-3 dj + 1, bits 4-5 di + 1
-constexpr int face_code(int dk, int dj, int di) { return (dk + 1) | ((dj + 1) << 2) | ((di + 1) << 4); }
-enum {
-    F_RIN = face_code(-1, 0, 0), F_ROUT = face_code(1, 0, 0), F_LATLO = face_code(0, -1, 0),
-    F_LATHI = face_code(0, 1, 0), F_LONLO = face_code(0, 0, -1), F_LONHI = face_code(0, 0, 1),
-    F_NONE = face_code(0, 0, 0)
-};
 enum { FLAG_OVERFLOW = 1, FLAG_LOST = 2, FLAG_BAD = 4 };
 constexpr int GINFO_STRIDE = 32;    // doubles between the info blocks of a band job's g-ordinates
 constexpr int GTAB_ROW = 4;         // doubles per g row of a band job's sampling table

@@ -12,9 +12,9 @@
 // the latitude has at most one extremum (sign of dz p^2 - zc s), so a cell has one candidate exit
 // per face family: one shell, usually one cone, and one half-plane.  Each family's next crossing
 // depends only on the ray and the cell index of that family (k, j or i), so it stays valid while
-// the ray crosses faces of the other families: the march keeps the three crossings and, after each
-// step, evaluates again only the family it crossed (an emission peel-off crosses shells in ~94% of
-// its steps).  In FP32 the impact parameter p^2 is carried as an unevaluated FP32 pair built with
+// the ray crosses faces of the other families: the march keeps the cone and half-plane crossings and
+// evaluates one again only once the ray has reached it (the family just crossed, or an exact tie);
+// the shell crossing is short and is evaluated at every step.  In FP32 the impact parameter p^2 is carried as an unevaluated FP32 pair built with
 // error-free products, so r^2 - p^2 keeps ~48 bits near grazing incidence; cone roots within TAN_EPS
 // of tangency are recomputed in FP64.
 #pragma once
@@ -32,13 +32,11 @@ template <typename real> struct Ray {
     real B, dz2;            // zc dz and dz^2 (cone coefficients that depend on the ray only)
     real tau, tau_target;   // accumulated optical depth; interaction target (< 0: none)
     real tau2;              // continuous absorption: absorption optical depth along a flight
-    real tr, tl, tn;        // next crossing of the radial, latitude and longitude family (s)
-    int fc;                 // their faces (bits 0-7, 8-15, 16-23) and the families to evaluate again
+    real tl, tn;            // next crossing of the latitude and longitude family (s); at or behind s:
+                            // to be evaluated again (-inf on a new ray)
+    int lf, nf;             // the change of j at that cone crossing and of i at that half-plane (+-1)
     int i, j, k;            // current cell
 };
-
-// families whose next crossing must be evaluated again (bits of Ray::fc)
-constexpr int STALE_R = 1 << 24, STALE_LAT = 1 << 25, STALE_LON = 1 << 26, STALE_ALL = 7 << 24;
 
 // error-free product a*b = hi + lo
 // (the _rn intrinsics are never contracted into FMAs, which would break the error-free forms)
@@ -119,7 +117,8 @@ __device__ __forceinline__ void ray_setup(Ray<real> &R, real ox, real oy, real o
     R.Q = dz * dz + R.chz * R.chz;
     R.B = R.cz * dz;
     R.dz2 = dz * dz;
-    R.fc = STALE_ALL;
+    R.tl = -M<real>::inf();
+    R.tn = -M<real>::inf();
 }
 
 constexpr double TAN_EPS_CONE = 1e-5;
@@ -208,7 +207,7 @@ __device__ __forceinline__ real cone_root(const DevGrid &G, const Tabs<real> &T,
 // the same root and validity rules as before; when Q or dz lies within TAN_EPS of an edge's S^2 or S
 // (the boundaries of the choice, which are also the tangency cases) both cones are evaluated.
 template <typename real>
-__device__ __forceinline__ real lat_exit(const DevGrid &G, const Tabs<real> &T, const Ray<real> &R, int &face)
+__device__ __forceinline__ real lat_exit(const DevGrid &G, const Tabs<real> &T, const Ray<real> &R, int &dj)
 {
     const real inf = M<real>::inf();
     const bool has_lo = R.j > 0, has_hi = R.j + 1 < T.nlat;
@@ -222,7 +221,7 @@ __device__ __forceinline__ real lat_exit(const DevGrid &G, const Tabs<real> &T, 
     if (amb) {
         const real tlo = has_lo ? cone_root<real>(G, T, R, R.j, R.s) : inf;
         const real thi = has_hi ? cone_root<real>(G, T, R, R.j + 1, R.s) : inf;
-        face = thi < tlo ? F_LATHI : F_LATLO;
+        dj = thi < tlo ? 1 : -1;
         return thi < tlo ? thi : tlo;
     }
     const real g = dz * R.p2hi - R.s * R.cz;
@@ -237,13 +236,14 @@ __device__ __forceinline__ real lat_exit(const DevGrid &G, const Tabs<real> &T, 
         to_hi = !to_lo && ext_ahead && dz > Shi;
     }
     const real t = cone_root<real>(G, T, R, to_hi ? R.j + 1 : R.j, R.s);
-    face = to_hi ? F_LATHI : F_LATLO;
+    dj = to_hi ? 1 : -1;
     return (to_hi || to_lo) ? t : inf;
 }
 
-// Radial family: inward (s < 0) and still outside the inner shell -> inner root, else outer root.
+// Radial family: inward (s < 0) and still outside the inner shell -> inner root, else outer root;
+// dk the change of k at that crossing.
 template <typename real>
-__device__ __forceinline__ real radial_exit(const Tabs<real> &T, const Ray<real> &R, int &face)
+__device__ __forceinline__ real radial_exit(const Tabs<real> &T, const Ray<real> &R, int &dk)
 {
     const auto ri = T.r2[R.k], ro = T.r2[R.k + 1];
     const real hin = (ri.x - R.p2hi) + (ri.y - R.p2lo);
@@ -251,14 +251,14 @@ __device__ __forceinline__ real radial_exit(const Tabs<real> &T, const Ray<real>
     const bool inward = R.s < (real)0 && hin > (real)0;
     const real h = inward ? hin : fmax(hout, (real)0);
     const real rt = M<real>::sqrt_(h);
-    face = inward ? F_RIN : F_ROUT;
+    dk = inward ? -1 : 1;
     return inward ? -rt : rt;
 }
 
 // Longitude family: the azimuth along a line is monotone (sign of (o x d)_z), so only the edge ahead
-// counts; +inf if the ray does not reach it.
+// counts; +inf if the ray does not reach it; di the change of i at that crossing.
 template <typename real>
-__device__ __forceinline__ real lon_exit(const Tabs<real> &T, const Ray<real> &R, int &face)
+__device__ __forceinline__ real lon_exit(const Tabs<real> &T, const Ray<real> &R, int &di)
 {
     const bool east = R.crz > (real)0;
     const auto cs = T.cs[east ? R.i + 1 : R.i];
@@ -266,71 +266,45 @@ __device__ __forceinline__ real lon_exit(const Tabs<real> &T, const Ray<real> &R
     const real sr = M<real>::div_(-(R.cy * cs.x - R.cx * cs.y), nd);
     const bool lon_ok = T.nlon > 1 && R.crz != (real)0 && nd != (real)0 && sr > R.s &&
                         cs.x * (R.cx + sr * R.dx) + cs.y * (R.cy + sr * R.dy) > (real)0;
-    face = east ? F_LONHI : F_LONLO;
+    di = east ? 1 : -1;
     return lon_ok ? sr : M<real>::inf();
 }
 
-// Exit of the current cell: returns the s of the exit point and the face.  The families marked stale
-// are evaluated (at the current s); ties go to the first face in the order r-, r+, lat-, lat+, lon,
-// as if all candidate faces were evaluated at every step.
+// Exit of the current cell: the s of the exit point and its family, fam = 0 (shell, k changes by dk),
+// 1 (cone, j by R.lf) or 2 (half-plane, i by R.nf).  A cone or half-plane crossing at or behind R.s
+// (the family just crossed, or an exact tie that the order below gave to another family) is evaluated
+// again first, its root at R.s no longer counting; ties go to the shell, then the cone, as if every
+// family were evaluated at every step.
 template <typename real>
-__device__ __forceinline__ real cell_exit(const DevGrid &G, const Tabs<real> &T, Ray<real> &R, int &face)
+__device__ __forceinline__ real cell_exit(const DevGrid &G, const Tabs<real> &T, Ray<real> &R, int &fam, int &dk)
 {
-    int fc = R.fc;
-    {
-        // the radial family is short: evaluated at every step, without a branch (the same value as cached)
-        int f;
-        R.tr = radial_exit<real>(T, R, f);
-        fc = (fc & ~0xff) | f;
-    }
-    if (fc & STALE_LAT) {
-        int f = F_NONE;
-        R.tl = lat_exit<real>(G, T, R, f);
-        fc = (fc & ~0xff00) | (f << 8);
-    }
-    if (fc & STALE_LON) {
-        int f;
-        R.tn = lon_exit<real>(T, R, f);
-        fc = (fc & ~0xff0000) | (f << 16);
-    }
-    fc &= ~STALE_ALL;
-    R.fc = fc;
-    real best = R.tr;
-    face = fc & 0xff;
+    if (R.tl <= R.s) R.tl = lat_exit<real>(G, T, R, R.lf);
+    if (R.tn <= R.s) R.tn = lon_exit<real>(T, R, R.nf);
+    real best = radial_exit<real>(T, R, dk);
+    fam = 0;
     if (R.tl < best) {
         best = R.tl;
-        face = (fc >> 8) & 0xff;
+        fam = 1;
     }
     if (R.tn < best) {
         best = R.tn;
-        face = (fc >> 16) & 0xff;
+        fam = 2;
     }
     return best;
 }
 
-// After the ray has moved to R.s across `face`: the crossed family is evaluated again at the next step,
-// and so is any family whose crossing is not ahead of R.s (an exact tie that the face order gave to
-// another family: evaluated again, its root at R.s no longer counts).
-template <typename real> __device__ __forceinline__ void mark_crossed(Ray<real> &R, int face)
+// Cross the exit of family `fam` (cell_exit): update the cell; returns E_CONT, or E_ESCAPE / E_BOTTOM
+// (the cell is left unchanged) for a shell crossing out of the grid.
+template <typename real, class GT>
+__device__ __forceinline__ int cross_face(const GT &G, Ray<real> &R, int fam, int dk)
 {
-    // (the radial family is evaluated at every step anyway)
-    int st = ((face >> 2) & 3) != 1 ? STALE_LAT : ((face >> 4) & 3) != 1 ? STALE_LON : 0;
-    if (R.tl <= R.s) st |= STALE_LAT;
-    if (R.tn <= R.s) st |= STALE_LON;
-    R.fc |= st;
-}
-
-// Cross `face`: update the cell; returns E_CONT, E_ESCAPE or E_BOTTOM.
-template <class GT> __device__ __forceinline__ int cross_face(const GT &G, int face, int &i, int &j, int &k)
-{
-    const int nk = k + (face & 3) - 1;
-    if (nk < 0) return E_BOTTOM;
-    if (nk >= G.nr) return E_ESCAPE;
-    k = nk;
-    j += ((face >> 2) & 3) - 1;
-    const int ni = i + ((face >> 4) & 3) - 1;
-    i = ni < 0 ? G.nlon - 1 : ni == G.nlon ? 0 : ni;
-    return E_CONT;
+    const int nk = R.k + (fam == 0 ? dk : 0);
+    const int e = nk < 0 ? E_BOTTOM : nk >= G.nr ? E_ESCAPE : E_CONT;
+    R.k = e == E_CONT ? nk : R.k;
+    R.j += fam == 1 ? R.lf : 0;
+    const int ni = R.i + (fam == 2 ? R.nf : 0);
+    R.i = ni < 0 ? G.nlon - 1 : ni == G.nlon ? 0 : ni;
+    return e;
 }
 
 // ------------------------------------------------------------------ samplers (Sect. 3)
