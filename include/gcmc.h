@@ -235,7 +235,12 @@ typedef struct {
     double l_tot;             /* emission: total luminosity of the emitting cells, W/m (Sect. 5.3) */
     double cdf_total;         /* emission: total of the hybrid pdf (1 up to rounding) */
     int64_t n_emit_cells;     /* emission: cells above the tau_vert cut */
+    int64_t flags;            /* GCMC_FLAG_* bits raised by any packet of the job (0: none) */
 } gcmc_stats;
+
+/* gcmc_stats.flags: a peel-off or chord contribution that was not a number, negative or at least 1e9
+   (left out of the tallies) */
+enum { GCMC_FLAG_TALLY_RANGE = 1 };
 
 typedef struct {
     int32_t grid_id, opac_id, source_id, mode;

@@ -652,6 +652,7 @@ void unpack(const unsigned long long *acc, const double *info, int n_obs, double
         st->l_tot = info[0];
         st->n_emit_cells = (int64_t)info[1];
         st->cdf_total = info[2];
+        st->flags = (int64_t)acc[ACC_FLAGS];
     }
 }
 

@@ -34,7 +34,7 @@ constexpr double FIX_SCALE = 4294967296.0;   // 2^32: fixed-point resolution of 
 // first flight's optical depth to the grid boundary
 enum { K_FLIGHT = 0, K_PEEL = 1, K_CHORD = 2, K_FORCE = 3 };
 enum { E_CONT = -1, E_INTERACT = 0, E_ESCAPE = 1, E_BOTTOM = 2, E_CUTOFF = 3, E_CAP = 4, E_LOST = 5 };
-enum { FLAG_OVERFLOW = 1, FLAG_LOST = 2, FLAG_BAD = 4 };
+enum { FLAG_OVERFLOW = GCMC_FLAG_TALLY_RANGE, FLAG_LOST = 2, FLAG_BAD = 4 };   // reported in gcmc_stats.flags
 constexpr int GINFO_STRIDE = 32;    // doubles between the info blocks of a band job's g-ordinates
 constexpr int GTAB_ROW = 4;         // doubles per g row of a band job's sampling table
 

@@ -119,6 +119,8 @@ __device__ __forceinline__ void ray_setup(Ray<real> &R, real ox, real oy, real o
     R.dz2 = dz * dz;
     R.tl = -M<real>::inf();
     R.tn = -M<real>::inf();
+    R.lf = 0;
+    R.nf = 0;
 }
 
 constexpr double TAN_EPS_CONE = 1e-5;
@@ -278,8 +280,10 @@ __device__ __forceinline__ real lon_exit(const Tabs<real> &T, const Ray<real> &R
 template <typename real>
 __device__ __forceinline__ real cell_exit(const DevGrid &G, const Tabs<real> &T, Ray<real> &R, int &fam, int &dk)
 {
-    if (R.tl <= R.s) R.tl = lat_exit<real>(G, T, R, R.lf);
-    if (R.tn <= R.s) R.tn = lon_exit<real>(T, R, R.nf);
+    // (not strictly ahead: also true for a ray whose position is not a number, so a family is never
+    // taken without having been evaluated for the current ray)
+    if (!(R.tl > R.s)) R.tl = lat_exit<real>(G, T, R, R.lf);
+    if (!(R.tn > R.s)) R.tn = lon_exit<real>(T, R, R.nf);
     real best = radial_exit<real>(T, R, dk);
     fam = 0;
     if (R.tl < best) {

@@ -391,8 +391,13 @@ __device__ void launch(Packet<real> &P, const DevJob &J, const DevGrid &G, int64
         if (s1 >= 0.0f || s2 <= 0.0f) {
             // a band in one hemisphere: c = 1 - |sin(lat)| is uniform in the band like sin(lat), linear from
             // its value at the lower edge; cos(lat) = sqrt(c (2 - c)) keeps its relative precision at the poles
+            // The largest uniform, 1 - 2^-25, rounds to 1 in FP32; at the north pole band's top that would
+            // put c at 0 or, through the rounding of the edge, a hair below it (cos(lat) not a number), or
+            // the point on the polar axis, where the azimuth and so the longitude cell are undefined.  So
+            // the uniform is kept below 1 (1 - 2^-24, its FP32 neighbour) and c at or above 0.
             const bool north = s1 >= 0.0f;
-            const float c = __fmaf_rn(north ? -u2 : u2, ds, __ldg(G.cb_f + j)) + __ldg(G.cb_lo_f + j);
+            const float ub = fminf(u2, 0x1.fffffep-1f);
+            const float c = fmaxf(__fmaf_rn(north ? -ub : ub, ds, __ldg(G.cb_f + j)) + __ldg(G.cb_lo_f + j), 0.0f);
             sl = north ? 1.0f - c : c - 1.0f;
             cl_f = sqrtf(c * (2.0f - c));
         } else {

@@ -57,7 +57,7 @@ class gcmc_source_desc(C.Structure):
 
 class gcmc_stats(C.Structure):
     _fields_ = [("packets", C.c_int64), ("steps", C.c_int64), ("ledger", C.c_double * 8), ("l_tot", C.c_double),
-                ("cdf_total", C.c_double), ("n_emit_cells", C.c_int64)]
+                ("cdf_total", C.c_double), ("n_emit_cells", C.c_int64), ("flags", C.c_int64)]
 
 
 class gcmc_job(C.Structure):

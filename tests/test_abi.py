@@ -44,7 +44,7 @@ def test_struct_layouts_match_header():
     assert C.sizeof(gcmc.gcmc_grid_desc) == 16 + 7 * 8
     assert C.sizeof(gcmc.gcmc_job) == 8 * 4 + 16
     assert C.sizeof(gcmc.gcmc_launch_cfg) == 24
-    assert C.sizeof(gcmc.gcmc_stats) == 16 + 64 + 16 + 8
+    assert C.sizeof(gcmc.gcmc_stats) == 16 + 64 + 16 + 8 + 8
     assert C.sizeof(gcmc.gcmc_source_desc) == 24 + 8 + 8 * 3 * 8 + 6 * 8 + 8 + 8 + 8 + 8 + 8 + 4 * 8 + 2 * 8 + 2 * 8 + 8 + 8 + 8 + 8
     assert C.sizeof(gcmc.gcmc_transit_obs) == 8 * 8
     assert C.sizeof(gcmc.gcmc_server_cfg) == 6 * 4 + 8 + 2 * 4
