@@ -200,6 +200,47 @@ __device__ __forceinline__ real cone_root(const DevGrid &G, const Tabs<real> &T,
     return a1 < a2 ? a1 : a2;
 }
 
+// Rays parallel to the equatorial plane (dz = 0: every peel-off and limb chord towards an observer in that
+// plane) keep z = zc, so |sin(lat)| = |zc| / sqrt(p^2 + s^2), largest at s = 0.  Edge S (on the nappe where
+// z has the sign of S) is met where p^2 + s^2 = zc^2 / S^2, at s = -/+ t with t = (p / |S|) sqrt(Q - S^2),
+// Q = (zc / p)^2, and not at all when Q <= S^2.  Smallest such root > R.s of edge e, +inf if none; in FP32
+// within TAN_EPS of tangency the roots are recomputed in FP64, as for any cone.
+template <typename real>
+__device__ __forceinline__ real flat_cone_root(const DevGrid &G, const Tabs<real> &T, const Ray<real> &R, int e)
+{
+    const real inf = M<real>::inf();
+    const auto sp = T.sl[e];
+    const real S = sp.x, S2 = sp.y;
+    const real dn = R.Q - S2;
+    if constexpr (sizeof(real) == 4) {
+        if (dn >= (real)0 && dn < (real)TAN_EPS_CONE) {
+            double r[2];
+            const int m = cone_roots64(R.cx, R.cy, R.cz, R.dx, R.dy, R.dz, __ldg(G.slat + e), __ldg(G.s2lat + e), r);
+            real best = inf;
+            for (int i = 0; i < m; ++i) {
+                const real rf = (real)r[i];
+                if (rf > R.s && rf < best) best = rf;
+            }
+            return best;
+        }
+    }
+    const real t = M<real>::div_(R.p * M<real>::sqrt_(fmax(dn, (real)0)), fabs(S));
+    const real a = -t > R.s ? -t : t > R.s ? t : inf;
+    return dn > (real)0 && R.cz * S > (real)0 ? a : inf;
+}
+
+// Latitude exit of a ray parallel to the equatorial plane: the nearer crossing of the band's two edges
+// (the poles are not surfaces); dj the change of j there.
+template <typename real>
+__device__ __forceinline__ real lat_exit_flat(const DevGrid &G, const Tabs<real> &T, const Ray<real> &R, int &dj)
+{
+    const real inf = M<real>::inf();
+    const real tlo = R.j > 0 ? flat_cone_root<real>(G, T, R, R.j) : inf;
+    const real thi = R.j + 1 < T.nlat ? flat_cone_root<real>(G, T, R, R.j + 1) : inf;
+    dj = thi < tlo ? 1 : -1;
+    return thi < tlo ? thi : tlo;
+}
+
 // Latitude exit of the current cell.  Along the line, f(s) = sin(lat) = (zc + s dz) / sqrt(p^2 + s^2)
 // has f' of the sign of g(s) = dz p^2 - s zc, so a single extremum, f = sign(zc) sqrt(Q), at
 // g = 0, and the limits -dz, +dz at s -> -inf, +inf.  Moving up (g > 0) the ray crosses the upper
@@ -211,6 +252,7 @@ __device__ __forceinline__ real cone_root(const DevGrid &G, const Tabs<real> &T,
 template <typename real>
 __device__ __forceinline__ real lat_exit(const DevGrid &G, const Tabs<real> &T, const Ray<real> &R, int &dj)
 {
+    if (R.dz == (real)0) return lat_exit_flat<real>(G, T, R, dj);
     const real inf = M<real>::inf();
     const bool has_lo = R.j > 0, has_hi = R.j + 1 < T.nlat;
     // the poles are not surfaces: sentinels outside [-1, 1] make them unreachable below
