@@ -34,7 +34,7 @@ template <typename real> struct Ray {
     real tau2;              // continuous absorption: absorption optical depth along a flight
     real tl, tn;            // next crossing of the latitude and longitude family (s); at or behind s:
                             // to be evaluated again (-inf on a new ray)
-    int lf, nf;             // the change of j at that cone crossing and of i at that half-plane (+-1)
+    int lj, li;             // j after that cone crossing, i after that half-plane crossing (wrapped)
     int i, j, k;            // current cell
 };
 
@@ -119,8 +119,8 @@ __device__ __forceinline__ void ray_setup(Ray<real> &R, real ox, real oy, real o
     R.dz2 = dz * dz;
     R.tl = -M<real>::inf();
     R.tn = -M<real>::inf();
-    R.lf = 0;
-    R.nf = 0;
+    R.lj = 0;
+    R.li = 0;
 }
 
 constexpr double TAN_EPS_CONE = 1e-5;
@@ -314,43 +314,47 @@ __device__ __forceinline__ real lon_exit(const Tabs<real> &T, const Ray<real> &R
     return lon_ok ? sr : M<real>::inf();
 }
 
-// Exit of the current cell: the s of the exit point and its family, fam = 0 (shell, k changes by dk),
-// 1 (cone, j by R.lf) or 2 (half-plane, i by R.nf).  A cone or half-plane crossing at or behind R.s
-// (the family just crossed, or an exact tie that the order below gave to another family) is evaluated
-// again first, its root at R.s no longer counting; ties go to the shell, then the cone, as if every
-// family were evaluated at every step.
+// Exit of the current cell: the s of the exit point; to_lat / to_lon tell a cone (j becomes R.lj) or a
+// half-plane (i becomes R.li) from a shell (k changes by dk).  A cone or half-plane crossing at or behind
+// R.s (the family just crossed, or an exact tie that the order below gave to another family) is
+// evaluated again first, its root at R.s no longer counting; ties go to the shell, then the cone, as if
+// every family were evaluated at every step.
 template <typename real>
-__device__ __forceinline__ real cell_exit(const DevGrid &G, const Tabs<real> &T, Ray<real> &R, int &fam, int &dk)
+__device__ __forceinline__ real cell_exit(const DevGrid &G, const Tabs<real> &T, Ray<real> &R, bool &to_lat,
+                                          bool &to_lon, int &dk)
 {
     // (not strictly ahead: also true for a ray whose position is not a number, so a family is never
     // taken without having been evaluated for the current ray)
-    if (!(R.tl > R.s)) R.tl = lat_exit<real>(G, T, R, R.lf);
-    if (!(R.tn > R.s)) R.tn = lon_exit<real>(T, R, R.nf);
-    real best = radial_exit<real>(T, R, dk);
-    fam = 0;
-    if (R.tl < best) {
-        best = R.tl;
-        fam = 1;
+    if (!(R.tl > R.s)) {
+        int dj;
+        R.tl = lat_exit<real>(G, T, R, dj);
+        R.lj = R.j + dj;
     }
-    if (R.tn < best) {
-        best = R.tn;
-        fam = 2;
+    if (!(R.tn > R.s)) {
+        int di;
+        R.tn = lon_exit<real>(T, R, di);
+        const int ni = R.i + di;
+        R.li = ni < 0 ? T.nlon - 1 : ni == T.nlon ? 0 : ni;
     }
-    return best;
+    const real sr = radial_exit<real>(T, R, dk);
+    to_lat = R.tl < sr;
+    const real b = to_lat ? R.tl : sr;
+    to_lon = R.tn < b;
+    return to_lon ? R.tn : b;
 }
 
-// Cross the exit of family `fam` (cell_exit): update the cell; returns E_CONT, or E_ESCAPE / E_BOTTOM
-// (the cell is left unchanged) for a shell crossing out of the grid.
+// Cross the exit that cell_exit chose: update the cell; returns E_CONT, or E_ESCAPE / E_BOTTOM (the cell
+// is left unchanged) for a shell crossing out of the grid.
 template <typename real, class GT>
-__device__ __forceinline__ int cross_face(const GT &G, Ray<real> &R, int fam, int dk)
+__device__ __forceinline__ int cross_face(const GT &G, Ray<real> &R, bool to_lat, bool to_lon, int dk)
 {
-    const int nk = R.k + (fam == 0 ? dk : 0);
-    const int e = nk < 0 ? E_BOTTOM : nk >= G.nr ? E_ESCAPE : E_CONT;
-    R.k = e == E_CONT ? nk : R.k;
-    R.j += fam == 1 ? R.lf : 0;
-    const int ni = R.i + (fam == 2 ? R.nf : 0);
-    R.i = ni < 0 ? G.nlon - 1 : ni == G.nlon ? 0 : ni;
-    return e;
+    const bool shell = !(to_lat || to_lon);
+    const int nk = R.k + dk;
+    const bool in = (unsigned)nk < (unsigned)G.nr;
+    R.k = shell && in ? nk : R.k;
+    R.j = to_lat && !to_lon ? R.lj : R.j;
+    R.i = to_lon ? R.li : R.i;
+    return shell && !in ? (nk < 0 ? E_BOTTOM : E_ESCAPE) : E_CONT;
 }
 
 // ------------------------------------------------------------------ samplers (Sect. 3)

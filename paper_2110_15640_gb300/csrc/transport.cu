@@ -771,8 +771,9 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
     } else {
         a = __ldg(jc.rec + idx + go);
     }
-    int fam, dk;
-    const real sx = cell_exit<real>(G, T, R, fam, dk);
+    bool to_lat, to_lon;
+    int dk;
+    const real sx = cell_exit<real>(G, T, R, to_lat, to_lon, dk);
     const real seg = sx - R.s;
     if constexpr (SCAT) {
         if (R.tau_target >= (real)0 && a > (real)0 && R.tau + a * seg >= R.tau_target) {
@@ -795,7 +796,7 @@ __device__ __forceinline__ void step(Packet<real> &P, const DevJob &J, const Dev
     }
     S.trace(P.n, idx, seg);
     R.s = sx;
-    int e = cross_face<real>(T, R, fam, dk);
+    int e = cross_face<real>(T, R, to_lat, to_lon, dk);
     // the optical-depth cut-off applies to marches without an interaction target (peel-offs, chords;
     // every march of an absorber-only kernel)
     if (e == E_CONT && (!SCAT || R.tau_target < (real)0) && R.tau > jc.tau_cut) e = E_CUTOFF;
