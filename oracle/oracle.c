@@ -884,13 +884,17 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
         x[2] = r * sl;
         W = W0 = Wg * wcell[idx];
         kahan(&acc->ledger[0], &acc->ledger_c[0], W0);
+        int capped = 0;
         for (int o = 0; o < S->n_obs; ++o) {
             double tau;
             int st;
             trace_put(&M, -2, 0.0, x);
             double e = peel(&M, x, c, S->obs[o], S->tau_peel_cut, &tau, &st, -1);
             if (first_tau < 0) first_tau = tau;
-            if (st == END_CAP) break;
+            if (st == END_CAP) {
+                capped = 1;
+                break;
+            }
             f_obs[o] += W * e / (4.0 * ORC_PI);
             if (A->cf) cf_put(acc, idx, 0, o, W * e / (4.0 * ORC_PI));
         }
@@ -904,7 +908,8 @@ static void run_packet(const job_t *J, int64_t n, acc_t *acc, double *pk_f, int6
             d[2] = mu;
             entry = -1;
             transport = 1;
-        } else if (M.steps >= M.max_steps) {
+        } else if (capped || (S->scatter_emission && M.steps >= M.max_steps)) {
+            /* stopped by the step cap: a peel-off it cut, or (followed packets) no step left to go on */
             kahan(&acc->ledger[6], &acc->ledger_c[6], W);
         }
     }

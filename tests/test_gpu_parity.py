@@ -335,6 +335,32 @@ def test_heavy_roulette_per_packet_parity(G):
         assert L[5] > 0.01 * L[0]
 
 
+@pytest.mark.parametrize("maker,cap", [(small_albedo, 9), (small_emission, 6), (small_transmission, 4)])
+def test_step_cap_per_packet_parity(G, maker, cap):
+    """A per-packet step cap small enough to stop most packets: the cap ends a packet's ray before the
+    step that would exceed it (the oracle's march rule), in the middle of a ray or at the start of the
+    next one (a peel-off after a flight).  FP64 per-packet steps and f, the capped weight of the ledger,
+    and the batched kernel (whose lanes are refilled) equal to the plain one."""
+    from paper_2110_15640_gb300 import gcmc
+    wl = maker(n=3000)
+    wl.source.opts.max_steps = cap
+    job = wl.jobs[0]
+    nobs = len(O.job_observers(wl, job))
+    gid, oid, sid, jobs = _load(G, wl, gcmc.FP64)
+    ref = O.run(wl, job, per_packet=True, nthreads=8)
+    got = G.run_debug(jobs[0], n_obs=nobs)
+    np.testing.assert_array_equal(got["pk_steps"], ref["pk_steps"])
+    assert np.mean(ref["pk_steps"] == cap) > 0.3            # the cap does stop packets
+    np.testing.assert_allclose(got["pk_f"], ref["pk_f"], rtol=1e-10, atol=1e-300)
+    L = ref["ledger"]
+    assert L[6] > 0
+    np.testing.assert_allclose(list(got["stats"].ledger), L, rtol=1e-12, atol=64 * job.n_packets * 2.0 ** -33)
+    tp, sp = G.run_packets(jobs[0])
+    tb, sb = G.run_batch(jobs, cfg=gcmc.gcmc_launch_cfg(64, 0, 96, 3, 7, 0))
+    assert np.array_equal(tp, tb[0]) and sp.steps == sb[0].steps == ref["steps"]
+    assert list(sp.ledger) == list(sb[0].ledger)
+
+
 # ------------------------------------------------------------------ full-size grid, sampled packets
 
 def test_full_size_emission_sampled_packets(G):
