@@ -16,10 +16,14 @@ from . import gcmc
 DEFAULT_SPACE = {
     "block": [64, 128, 256],
     "blocks_per_sm": [0, 6, 8],
-    "chunk": [32, 64, 128, 256, 512, 1024],
+    "chunk": [32, 64, 128, 256, 512, 1024, 2048],
     "refill_min": [4, 8, 16, 32],
-    "interval": [2, 4, 8, 16],
+    "interval": [2, 4, 8, 16, 24, 32],
 }
+# where the coordinate search starts: 128-thread blocks, 8 per SM where the kernel fits them (the
+# scattering kernels hold 4), 512-packet work items, refill at 16 idle lanes every 16 steps (the region
+# of the fastest launches measured for the emission and phase-curve batches on a GB300)
+DEFAULT_START = {"block": 128, "blocks_per_sm": 8, "chunk": 512, "refill_min": 16, "interval": 16}
 
 
 def sample_jobs(jobs, min_jobs=16, min_packets=16_000_000):
@@ -53,7 +57,7 @@ def tune(ctx, jobs, stream, space=None, reps=2, coordinate=True, log=None, full_
     timed once more on the whole batch and the fastest there is returned: a sample can favour work-item
     sizes and refill settings that do not carry over to the batch."""
     space = space or DEFAULT_SPACE
-    best = {"block": 128, "blocks_per_sm": 6, "chunk": 512, "refill_min": 8, "interval": 4}
+    best = dict(DEFAULT_START)
     table = []
 
     def run(c):
