@@ -26,10 +26,11 @@ DEFAULT_SPACE = {
 DEFAULT_START = {"block": 128, "blocks_per_sm": 8, "chunk": 512, "refill_min": 16, "interval": 16}
 
 
-def sample_jobs(jobs, min_jobs=16, min_packets=16_000_000):
+def sample_jobs(jobs, min_jobs=16, min_packets=64_000_000):
     """Jobs spread evenly over the list, at least min_jobs of them and at least min_packets packets in
-    all (or every job): enough work items to fill the GPU at every chunk size the search tries, so
-    workloads of many small jobs are tuned on the load they present."""
+    all (or every job): enough work items that every resident warp takes a dozen even at the largest
+    chunk size the search tries (a smaller sample ends in a tail of half-empty waves that favours
+    small items), so workloads of many small jobs are tuned on the load they present."""
     n = len(jobs)
     mean = max(1.0, sum(j.n_packets for j in jobs) / max(n, 1))
     want = min(n, max(min_jobs, int(-(-min_packets // mean))))
@@ -50,7 +51,7 @@ def _time_cfg(ctx, jobs, cfg, reps, stream):
     return a.elapsed_time(b) / reps
 
 
-def tune(ctx, jobs, stream, space=None, reps=2, coordinate=True, log=None, full_jobs=None, finalists=3):
+def tune(ctx, jobs, stream, space=None, reps=2, coordinate=True, log=None, full_jobs=None, finalists=4):
     """Return (best gcmc_launch_cfg, table of (cfg dict, ms)).  coordinate=True searches one axis at a
     time from the defaults, twice over (about thirty runs), instead of the full product.  With full_jobs
     (the whole batch the sample was drawn from), the `finalists` fastest configurations on the sample are
@@ -99,7 +100,7 @@ def tune(ctx, jobs, stream, space=None, reps=2, coordinate=True, log=None, full_
         best_full = float("inf")
         for c in cands:
             cfg = gcmc.gcmc_launch_cfg(c["block"], c["blocks_per_sm"], c["chunk"], c["interval"], c["refill_min"], 0)
-            ms = _time_cfg(ctx, full_jobs, cfg, 1, stream)
+            ms = _time_cfg(ctx, full_jobs, cfg, 2, stream)
             if log:
                 log(f"autotune (whole batch) {c} {ms:.2f} ms")
             if ms < best_full:

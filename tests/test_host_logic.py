@@ -10,15 +10,15 @@ def _jobs(n, packets):
     return [S.Job(lam_idx=q, g_idx=0, n_packets=packets, key=q) for q in range(n)]
 
 
-@pytest.mark.parametrize("n,packets", [(9532, 10_000), (240, 1_000_000), (960, 500_000), (5, 100), (1, 10)])
+@pytest.mark.parametrize("n,packets", [(9532, 10_000), (240, 1_000_000), (960, 500_000), (40, 1_000_000), (5, 100), (1, 10)])
 def test_sample_jobs_fills_the_gpu_or_takes_everything(n, packets):
     jobs = _jobs(n, packets)
     s = autotune.sample_jobs(jobs)
     assert len(s) == len({id(j) for j in s})
     assert all(j in jobs for j in s)
     total = sum(j.n_packets for j in s)
-    if n * packets >= 16_000_000 and n >= 16:
-        assert total >= 16_000_000 * (1 - 1.0 / len(s)) and len(s) >= 16
+    if n * packets >= 64_000_000 and n >= 16:
+        assert total >= 64_000_000 * (1 - 1.0 / len(s)) and len(s) >= 16
     else:
         assert s == jobs
     # spread evenly over the list, not its head
