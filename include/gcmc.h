@@ -266,7 +266,10 @@ gcmc_status gcmc_run_packets(gcmc_ctx *ctx, const gcmc_job *job, double *tallies
 
 typedef struct {
     int32_t block;            /* threads per block (multiple of 32), 0 = default */
-    int32_t blocks_per_sm;    /* resident blocks per SM of the persistent grid, 0 = default */
+    int32_t blocks_per_sm;    /* resident blocks per SM of the persistent grid, 0 = as many as fit; with
+                                 128-thread blocks, FP32 kernels compiled for more resident blocks (fewer
+                                 registers) run from 6 (absorber-only marches: 6 and 8; scattering: 5 and 6)
+                                 and 5 (scattering); a value above what fits is lowered to it */
     int32_t chunk;            /* packets per warp work item (multiple of 32), 0 = default (1024) */
     int32_t interval;         /* march steps between warp refill checks, 0 = default (1) */
     int32_t refill_min;       /* refill a warp's idle lanes only when at least this many (1..32) are idle,

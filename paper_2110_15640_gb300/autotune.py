@@ -1,8 +1,8 @@
 """Launch-parameter autotuner for the persistent transport kernel.
 
-Searches block size, packets per work item (chunk), refill threshold and refill interval of
-gcmc_run_batch on a sample of the caller's jobs, timing each candidate with CUDA events on the
-context's stream, and returns the fastest gcmc_launch_cfg.  Results do not depend on the launch
+Searches the launch shape (block size and blocks per SM), packets per work item (chunk), refill
+threshold and refill interval of gcmc_run_batch on a sample of the caller's jobs, timing each
+candidate with CUDA events on the context's stream, and returns the fastest gcmc_launch_cfg.  Results do not depend on the launch
 parameters (tallies are order-independent fixed point), so tuning never changes a spectrum.
 """
 from __future__ import annotations
@@ -13,17 +13,26 @@ import os
 
 from . import gcmc
 
+# The block size and the blocks per SM form one axis (launch shapes): a kernel holds as many blocks per
+# SM as its registers allow, so with one axis per parameter a coordinate search could stop at a block
+# size whose best blocks-per-SM value lies on another block size's row.  blocks_per_sm 0: as many as fit.
+SHAPES = [(128, 8), (128, 6), (128, 5), (128, 0), (64, 0), (256, 0)]
 DEFAULT_SPACE = {
-    "block": [64, 128, 256],
-    "blocks_per_sm": [0, 6, 8],
+    "shape": SHAPES,
     "chunk": [32, 64, 128, 256, 512, 1024, 2048],
     "refill_min": [4, 8, 16, 32],
     "interval": [2, 4, 8, 16, 24, 32],
 }
 # where the coordinate search starts: 128-thread blocks, 8 per SM where the kernel fits them (the
-# scattering kernels hold 4), 512-packet work items, refill at 16 idle lanes every 16 steps (the region
+# scattering kernels hold 5), 512-packet work items, refill at 16 idle lanes every 16 steps (the region
 # of the fastest launches measured for the emission and phase-curve batches on a GB300)
-DEFAULT_START = {"block": 128, "blocks_per_sm": 8, "chunk": 512, "refill_min": 16, "interval": 16}
+DEFAULT_START = {"shape": (128, 8), "chunk": 512, "refill_min": 16, "interval": 16}
+
+
+def as_cfg_dict(c):
+    """a search point as the launch configuration's fields"""
+    return {"block": c["shape"][0], "blocks_per_sm": c["shape"][1], "chunk": c["chunk"], "refill_min": c["refill_min"],
+            "interval": c["interval"]}
 
 
 def sample_jobs(jobs, min_jobs=16, min_packets=64_000_000):
@@ -62,11 +71,12 @@ def tune(ctx, jobs, stream, space=None, reps=2, coordinate=True, log=None, full_
     table = []
 
     def run(c):
-        cfg = gcmc.gcmc_launch_cfg(c["block"], c["blocks_per_sm"], c["chunk"], c["interval"], c["refill_min"], 0)
+        d = as_cfg_dict(c)
+        cfg = gcmc.gcmc_launch_cfg(d["block"], d["blocks_per_sm"], d["chunk"], d["interval"], d["refill_min"], 0)
         ms = _time_cfg(ctx, jobs, cfg, reps, stream)
-        table.append((dict(c), ms))
+        table.append((d, ms))
         if log:
-            log(f"autotune {c} {ms:.2f} ms")
+            log(f"autotune {d} {ms:.2f} ms")
         return ms
 
     if coordinate:
@@ -88,6 +98,7 @@ def tune(ctx, jobs, stream, space=None, reps=2, coordinate=True, log=None, full_
             ms = run(c)
             if ms < best_ms:
                 best, best_ms = c, ms
+    best = as_cfg_dict(best)
     if full_jobs is not None and len(full_jobs) > len(jobs):
         seen, cands = set(), []
         for c, _ in sorted(table, key=lambda t: t[1]):

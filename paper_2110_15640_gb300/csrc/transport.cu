@@ -1201,7 +1201,15 @@ static cudaError_t persistent_dispatch(int block, int blocks_per_sm, int nsm, co
     }
     // FP32 absorber-only batches (the emission and limb-chord hot path) have variants compiled for
     // 6 and 8 resident 128-thread blocks per SM (register caps 80 and 64); blocks_per_sm selects them.
-    // (Capped scattering variants spill and ran slower on the phase curve.)
+    // FP32 scattering batches: 5 and 6 blocks (register caps 102 and 85).
+    if constexpr (sizeof(real) == 4 && SCAT) {
+        if (block <= 128 && blocks_per_sm >= 6)
+            return persistent_run<real, SCAT, 6, 0>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+                                                 interval, refill_min, one_grid, tab_n, work, st);
+        if (block <= 128 && blocks_per_sm == 5)
+            return persistent_run<real, SCAT, 5, 0>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,
+                                                 interval, refill_min, one_grid, tab_n, work, st);
+    }
     if constexpr (sizeof(real) == 4 && !SCAT) {
         if (block <= 128 && blocks_per_sm >= 8)
             return persistent_run<real, SCAT, 8, 0>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items, chunk,

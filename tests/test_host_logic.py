@@ -31,20 +31,33 @@ def test_sample_jobs_fills_the_gpu_or_takes_everything(n, packets):
 
 def test_coordinate_search_finds_a_separable_minimum(monkeypatch):
     """With a cost that is a sum over the axes, the coordinate search reaches the global minimum."""
-    target = {"block": 256, "blocks_per_sm": 8, "chunk": 128, "refill_min": 16, "interval": 8}
+    target = {"shape": (64, 0), "chunk": 128, "refill_min": 16, "interval": 8}
     space = autotune.DEFAULT_SPACE
 
     def cost(cfg):
-        c = {"block": cfg.block, "blocks_per_sm": cfg.blocks_per_sm, "chunk": cfg.chunk,
-             "refill_min": cfg.refill_min, "interval": cfg.interval}
+        c = {"shape": (cfg.block, cfg.blocks_per_sm), "chunk": cfg.chunk, "refill_min": cfg.refill_min,
+             "interval": cfg.interval}
         return 10.0 + sum(abs(space[k].index(c[k]) - space[k].index(target[k])) for k in target)
 
     monkeypatch.setattr(autotune, "_time_cfg", lambda ctx, jobs, cfg, reps, stream: cost(cfg))
     cfg, best, table = autotune.tune(None, [], None)
-    assert best == target
+    assert best == autotune.as_cfg_dict(target)
+    assert (cfg.block, cfg.blocks_per_sm, cfg.chunk, cfg.refill_min, cfg.interval) == (64, 0, 128, 16, 8)
     assert min(ms for _, ms in table) == 10.0
     # two passes over the axes; a value is re-run at most once per axis after the best one moved
     assert len(table) <= 1 + 2 * sum(len(v) for v in space.values())
+
+
+def test_launch_shape_is_one_axis(monkeypatch):
+    """A cost whose best blocks-per-SM value depends on the block size (as occupancy does): searching the
+    block size and the blocks per SM as one axis of shapes still finds the minimum from the start point."""
+    def cost(cfg):
+        shape = {(128, 6): 1.0, (256, 0): 2.0, (128, 8): 5.0}.get((cfg.block, cfg.blocks_per_sm), 9.0)
+        return shape + abs(cfg.chunk - 256) / 1e4
+
+    monkeypatch.setattr(autotune, "_time_cfg", lambda ctx, jobs, cfg, reps, stream: cost(cfg))
+    cfg, best, table = autotune.tune(None, [], None)
+    assert (best["block"], best["blocks_per_sm"], best["chunk"]) == (128, 6, 256)
 
 
 def test_saved_configuration_round_trips(tmp_path):
