@@ -192,10 +192,27 @@ def test_batched_equals_plain_bitwise(G):
         tp, sp = G.run_packets(job)
         assert tp[0] == tb[q][0]
         assert sp.steps == sb[q].steps and sp.packets == sb[q].packets == job.n_packets
-    # independent of the work-item size and refill interval
+    # independent of the work-item size and refill interval, and of the kernel variant the blocks per SM
+    # select (scattering kernels compiled for 5 and 6 resident 128-thread blocks)
     from paper_2110_15640_gb300 import gcmc
     tc, _ = G.run_batch(jobs, cfg=gcmc.gcmc_launch_cfg(64, 0, 96, 3, 7, 0))
     assert np.array_equal(tc, tb)
+    for bps in (5, 6, 8):
+        tv, _ = G.run_batch(jobs, cfg=gcmc.gcmc_launch_cfg(128, bps, 512, 16, 8, 0))
+        assert np.array_equal(tv, tb), bps
+
+
+def test_batched_variants_equal_plain_bitwise_emission(G):
+    """Absorber-only kernels compiled for 6 and 8 resident blocks per SM, and the uncapped one, give the
+    plain form's tallies bit for bit."""
+    from paper_2110_15640_gb300 import gcmc
+    wl = small_emission(n=20000)
+    gid, oid, sid, jobs = _load(G, wl, _fp("FP32"))
+    tp, sp = G.run_packets(jobs[0])
+    for shape in ((128, 0), (128, 6), (128, 8), (256, 0)):
+        tv, sv = G.run_batch(jobs, cfg=gcmc.gcmc_launch_cfg(shape[0], shape[1], 512, 24, 16, 0))
+        assert np.array_equal(tv[0], tp), shape
+        assert sv[0].steps == sp.steps
 
 
 def test_async_submit_poll_matches_batch(G):
