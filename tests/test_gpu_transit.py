@@ -166,3 +166,16 @@ def test_debug_output_columns(G):
         G.run_debug(jobs[0], n_obs=1)
     assert e.value.status == gcmc.ERR_ARG
     G.run_packets(jobs[0])   # the context is still usable
+
+
+def test_transit_kernel_variants_equal_plain_bitwise(G):
+    """The optional-physics scattering kernel in its variant for 5 resident blocks per SM and uncapped gives
+    the plain form's tallies bit for bit (multiple scattering, TTHG clouds, a surface, limb darkening)."""
+    from paper_2110_15640_gb300 import gcmc
+    wl = cloudy_transit(20000)
+    gid, oid, sid, jobs = _load(G, wl, gcmc.FP32)
+    tp, sp = G.run_packets(jobs[0])
+    for shape in ((128, 5), (128, 0), (256, 0)):
+        tv, sv = G.run_batch(jobs, cfg=gcmc.gcmc_launch_cfg(shape[0], shape[1], 512, 16, 8, 0))
+        assert np.array_equal(tv[0], tp), shape
+        assert sv[0].steps == sp.steps
