@@ -229,14 +229,39 @@ __device__ __forceinline__ real flat_cone_root(const DevGrid &G, const Tabs<real
     return dn > (real)0 && R.cz * S > (real)0 ? a : inf;
 }
 
+// the closed-form root of flat_cone_root away from tangency, for an edge (S, S^2) with dn = Q - S^2;
+// straight-line code
+template <typename real>
+__device__ __forceinline__ real flat_root(const Ray<real> &R, typename Pair<real>::type sp, real dn, bool has)
+{
+    const real t = M<real>::div_(R.p * M<real>::sqrt_(fmax(dn, (real)0)), fabs(sp.x));
+    const real a = -t > R.s ? -t : t > R.s ? t : M<real>::inf();
+    return has && dn > (real)0 && R.cz * sp.x > (real)0 ? a : M<real>::inf();
+}
+
 // Latitude exit of a ray parallel to the equatorial plane: the nearer crossing of the band's two edges
-// (the poles are not surfaces); dj the change of j there.
+// (the poles are not surfaces); dj the change of j there.  Both edges in straight-line code; only when
+// one of them lies within TAN_EPS of tangency (FP32) is it evaluated as flat_cone_root does.
 template <typename real>
 __device__ __forceinline__ real lat_exit_flat(const DevGrid &G, const Tabs<real> &T, const Ray<real> &R, int &dj)
 {
     const real inf = M<real>::inf();
-    const real tlo = R.j > 0 ? flat_cone_root<real>(G, T, R, R.j) : inf;
-    const real thi = R.j + 1 < T.nlat ? flat_cone_root<real>(G, T, R, R.j + 1) : inf;
+    const bool has_lo = R.j > 0, has_hi = R.j + 1 < T.nlat;
+    const auto lo = T.sl[R.j], hi = T.sl[R.j + 1];
+    const real dnl = R.Q - lo.y, dnh = R.Q - hi.y;
+    real tlo, thi;
+    if constexpr (sizeof(real) == 4) {
+        const bool nl = has_lo && dnl >= (real)0 && dnl < (real)TAN_EPS_CONE;
+        const bool nh = has_hi && dnh >= (real)0 && dnh < (real)TAN_EPS_CONE;
+        if (nl || nh) {
+            tlo = has_lo ? flat_cone_root<real>(G, T, R, R.j) : inf;
+            thi = has_hi ? flat_cone_root<real>(G, T, R, R.j + 1) : inf;
+            dj = thi < tlo ? 1 : -1;
+            return thi < tlo ? thi : tlo;
+        }
+    }
+    tlo = flat_root<real>(R, lo, dnl, has_lo);
+    thi = flat_root<real>(R, hi, dnh, has_hi);
     dj = thi < tlo ? 1 : -1;
     return thi < tlo ? thi : tlo;
 }
