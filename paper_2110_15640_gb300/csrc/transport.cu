@@ -1188,14 +1188,18 @@ static cudaError_t persistent_dispatch(int block, int blocks_per_sm, int nsm, co
                                                                chunk, interval, refill_min, one_grid, tab_n, work, st);
         }
         if constexpr (sizeof(real) == 4 && SCAT) {
-            // the optional physics without continuous absorption (transit with scattering, surfaces, TTHG,
-            // forcing) also in a variant for 5 resident 128-thread blocks per SM
+            // the optional physics (transit with scattering, surfaces, TTHG, forcing; with and without
+            // continuous absorption) also in variants for 5 resident 128-thread blocks per SM
             if (feat == FEAT_EXT && block <= 128 && blocks_per_sm >= 5)
                 return persistent_run<real, SCAT, 5, FEAT_EXT>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items,
                                                                chunk, interval, refill_min, one_grid, tab_n, work, st);
             if (feat == FEAT_EXT)
                 return persistent_run<real, SCAT, 0, FEAT_EXT>(block, blocks_per_sm, nsm, grids, jobs, n_jobs, total_items,
                                                                chunk, interval, refill_min, one_grid, tab_n, work, st);
+            if (feat == (FEAT_EXT | FEAT_CABS) && block <= 128 && blocks_per_sm >= 5)
+                return persistent_run<real, SCAT, 5, FEAT_EXT | FEAT_CABS>(block, blocks_per_sm, nsm, grids, jobs, n_jobs,
+                                                                           total_items, chunk, interval, refill_min,
+                                                                           one_grid, tab_n, work, st);
             if (feat == (FEAT_EXT | FEAT_CABS))
                 return persistent_run<real, SCAT, 0, FEAT_EXT | FEAT_CABS>(block, blocks_per_sm, nsm, grids, jobs, n_jobs,
                                                                            total_items, chunk, interval, refill_min,

@@ -114,3 +114,19 @@ def test_fp64_slab_with_both_options_vs_adding_doubling(G):
     est, sig = f.mean(), f.std() / math.sqrt(len(f))
     ref = R.AddingDoubling([1.0, 0.0, 0.5], 0.6, 0.3, n=40).geometric_albedo()
     assert abs(est - ref) < 3 * sig + 1e-5 * ref, (est, ref, sig)
+
+
+@pytest.mark.parametrize("transit", [False, True])
+def test_kernel_variants_equal_bitwise(G, transit):
+    """The kernel built with continuous absorption, in its variant for 5 resident blocks per SM, gives the
+    uncapped variant's tallies bit for bit (the same code; only the register budget differs)."""
+    from paper_2110_15640_gb300 import gcmc
+    wl = cloudy(20000, transit=transit, ff=2, pb=2)
+    gid, oid, sid, jobs = _load(G, wl, gcmc.FP32)
+    out = {}
+    for shape in ((128, 5), (128, 0), (256, 0)):
+        tv, sv = G.run_batch(jobs, cfg=gcmc.gcmc_launch_cfg(shape[0], shape[1], 512, 16, 8, 0))
+        out[shape] = (tv[0].copy(), sv[0].steps, list(sv[0].ledger))
+    ref = out[(128, 0)]
+    for shape, v in out.items():
+        assert np.array_equal(v[0], ref[0]) and v[1] == ref[1] and v[2] == ref[2], shape
