@@ -446,24 +446,129 @@ __global__ void k_emis_cdf_add(int64_t ncell, const PrepJob *__restrict__ jobs)
     else pj.cdf[idx] = v;
 }
 
+// One pass per job over its cells: the hybrid pdf and launch weights of k_emis_pdf and the fixed-point
+// cumulative pdf, a block per job sweeping its cells in tiles of 4 cells per thread with the running
+// total carried from tile to tile (the next tile's luminosities are loaded before the current tile is
+// scanned), and the job's total into info.  The same integers as k_emis_pdf + k_emis_scan_blocks +
+// k_emis_cdf_add (integer prefix sums are exact in any order) with one read of L_i and one write of the
+// cumulative pdf and the weights per cell.
+constexpr int EMIS_SWEEP_BLOCK = 1024;
+constexpr int EMIS_SWEEP_TILE = 4 * EMIS_SWEEP_BLOCK;
+
+// the 4 luminosities of cells i0 .. i0 + 3 (16-byte loads when vec), -1 past the last cell
+__device__ __forceinline__ void emis_load4(const double *__restrict__ Lp, int64_t i0, int64_t ncell, bool vec, double L[4])
+{
+    if (vec && i0 + 3 < ncell) {
+        const double2 a = *reinterpret_cast<const double2 *>(Lp + i0), b = *reinterpret_cast<const double2 *>(Lp + i0 + 2);
+        L[0] = a.x;
+        L[1] = a.y;
+        L[2] = b.x;
+        L[3] = b.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) L[q] = i0 + q < ncell ? Lp[i0 + q] : -1.0;
+    }
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(EMIS_SWEEP_BLOCK) k_emis_sweep(int64_t ncell, const PrepJob *__restrict__ jobs,
+                                                                 double beta)
+{
+    constexpr int NW = EMIS_SWEEP_BLOCK / 32;
+    __shared__ long long ws[NW];
+    const PrepJob &pj = jobs[blockIdx.x];
+    const double *Lp = reinterpret_cast<const double *>(pj.cdf);   // L_i in place, read before written
+    WT *wp = reinterpret_cast<WT *>(pj.wcell);
+    // 16-byte loads and stores when every job array of this block is aligned for them
+    const bool vec = ((reinterpret_cast<uintptr_t>(pj.cdf) | reinterpret_cast<uintptr_t>(pj.wcell)) & 15) == 0;
+    const double Ltot = pj.info[INFO_LTOT], nincl = pj.info[INFO_NINCL];
+    const double qa = pj.info[INFO_QA], qb = pj.info[INFO_QB], invl = pj.info[INFO_INVL];
+    const float bn = (float)pj.info[INFO_BN], omb = (float)(1.0 - beta);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long carry = 0;
+    double L[4];
+    emis_load4(Lp, 4 * (int64_t)threadIdx.x, ncell, vec, L);
+    for (int64_t base = 0; base < ncell; base += EMIS_SWEEP_TILE) {
+        const int64_t i0 = base + 4 * (int64_t)threadIdx.x;
+        long long Q[4];
+        WT w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            Q[q] = 0;
+            w[q] = (WT)0;
+            if constexpr (sizeof(WT) == 8) {
+                if (L[q] >= 0.0 && nincl > 0.0) {
+                    double qq;
+                    if (Ltot > 0.0) {
+                        qq = (1.0 - beta) * L[q] / Ltot + beta / nincl;
+                        w[q] = qq > 0.0 ? (L[q] / Ltot) / qq : 0.0;
+                    } else {
+                        qq = 1.0 / nincl;
+                    }
+                    Q[q] = __double2ll_rn(qq * CDF_FIX);
+                }
+            } else {
+                if (L[q] >= 0.0) {
+                    Q[q] = __double2ll_rn(fma(qa, L[q], qb));
+                    const float pp = (float)(L[q] * invl);
+                    const float qf = fmaf(omb, pp, bn);
+                    w[q] = qf > 0.0f ? pp / qf : 0.0f;
+                }
+            }
+        }
+        // the next tile's luminosities in flight while this one is scanned
+        if (base + EMIS_SWEEP_TILE < ncell) emis_load4(Lp, i0 + EMIS_SWEEP_TILE, ncell, vec, L);
+        const long long s1 = Q[0] + Q[1], s2 = s1 + Q[2], t = s2 + Q[3];
+        const long long inc = warp_incl_scan_ll(t);
+        if (lane == 31) ws[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const long long v = warp_incl_scan_ll(lane < NW ? ws[lane] : 0ll);
+            if (lane < NW) ws[lane] = v;
+        }
+        __syncthreads();
+        const long long pre = carry + (warp ? ws[warp - 1] : 0ll) + inc - t;
+        const long long c[4] = {pre + Q[0], pre + s1, pre + s2, pre + t};
+        if (vec && i0 + 3 < ncell) {
+            *reinterpret_cast<longlong2 *>(pj.cdf + i0) = make_longlong2(c[0], c[1]);
+            *reinterpret_cast<longlong2 *>(pj.cdf + i0 + 2) = make_longlong2(c[2], c[3]);
+            if constexpr (sizeof(WT) == 8) {
+                *reinterpret_cast<double2 *>(wp + i0) = make_double2(w[0], w[1]);
+                *reinterpret_cast<double2 *>(wp + i0 + 2) = make_double2(w[2], w[3]);
+            } else {
+                *reinterpret_cast<float4 *>(wp + i0) = make_float4(w[0], w[1], w[2], w[3]);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (i0 + q < ncell) {
+                    pj.cdf[i0 + q] = c[q];
+                    wp[i0 + q] = w[q];
+                }
+        }
+        carry += ws[NW - 1];
+        __syncthreads();     // ws is written again by the next tile
+    }
+    if (threadIdx.x == 0) {
+        pj.info[INFO_CDFTOT] = (double)carry / CDF_FIX;
+        reinterpret_cast<long long *>(pj.info)[INFO_QTOT] = carry;
+    }
+}
+
 // the hybrid pdf, fixed-point CDF and launch weights from the column kernels' luminosities and sums
 static cudaError_t emission_pdf(bool f64, const DevGrid &hg, const PrepJob *djobs, int njobs, int ncolb, double beta,
                                 cudaStream_t st)
 {
     k_emis_total<<<(njobs + 127) / 128, 128, 0, st>>>(ncolb, djobs, njobs, beta);
-    const int nblk = (int)((hg.ncell + EMIS_SCAN_BLOCK - 1) / EMIS_SCAN_BLOCK);
-    const dim3 g3((unsigned)nblk, (unsigned)njobs);
-    if (f64) k_emis_pdf<double><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
-    else k_emis_pdf<float><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
-    k_emis_scan_blocks<<<(njobs + 3) / 4, 128, 0, st>>>(nblk, djobs, njobs);
-    k_emis_cdf_add<long long><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs);
+    if (f64) k_emis_sweep<double><<<(unsigned)njobs, EMIS_SWEEP_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
+    else k_emis_sweep<float><<<(unsigned)njobs, EMIS_SWEEP_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
     return cudaGetLastError();
 }
 
 cudaError_t prep_emission(int precision, const DevGrid &hg, const KtabDev &kt, const PrepJob *djobs, int njobs,
                           double tau_vert_max, double beta, cudaStream_t st)
 {
-    count_launch(5);
+    count_launch(3);
     const bool f64 = precision == GCMC_FP64;
     const int ncolb = emis_col_blocks(hg);
     const dim3 gc((unsigned)ncolb, (unsigned)njobs);
@@ -479,7 +584,7 @@ cudaError_t prep_emission_xsec(int precision, const DevGrid &hg, const XsecDev &
 {
     cudaError_t e = prep_xsec(precision, hg, xs, djobs, njobs, st);
     if (e != cudaSuccess) return e;
-    count_launch(5);
+    count_launch(3);
     const bool f64 = precision == GCMC_FP64;
     const int ncolb = emis_col_blocks(hg);
     const dim3 gc((unsigned)ncolb, (unsigned)njobs);
