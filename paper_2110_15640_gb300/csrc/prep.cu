@@ -560,15 +560,32 @@ static cudaError_t emission_pdf(bool f64, const DevGrid &hg, const PrepJob *djob
                                 cudaStream_t st)
 {
     k_emis_total<<<(njobs + 127) / 128, 128, 0, st>>>(ncolb, djobs, njobs, beta);
-    if (f64) k_emis_sweep<double><<<(unsigned)njobs, EMIS_SWEEP_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
-    else k_emis_sweep<float><<<(unsigned)njobs, EMIS_SWEEP_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
+    // one sweep block per job keeps one SM busy per job: for batches that fill the GPU with jobs; fewer
+    // jobs (a single job of the plain form or of the server) take the per-block pdf and scan, whose
+    // blocks spread every job over the whole GPU
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (3 * njobs >= 2 * nsm) {
+        count_launch(2);
+        if (f64) k_emis_sweep<double><<<(unsigned)njobs, EMIS_SWEEP_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
+        else k_emis_sweep<float><<<(unsigned)njobs, EMIS_SWEEP_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
+        return cudaGetLastError();
+    }
+    count_launch(4);
+    const int nblk = (int)((hg.ncell + EMIS_SCAN_BLOCK - 1) / EMIS_SCAN_BLOCK);
+    const dim3 g3((unsigned)nblk, (unsigned)njobs);
+    if (f64) k_emis_pdf<double><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
+    else k_emis_pdf<float><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs, beta);
+    k_emis_scan_blocks<<<(njobs + 3) / 4, 128, 0, st>>>(nblk, djobs, njobs);
+    k_emis_cdf_add<long long><<<g3, EMIS_SCAN_BLOCK, 0, st>>>(hg.ncell, djobs);
     return cudaGetLastError();
 }
 
 cudaError_t prep_emission(int precision, const DevGrid &hg, const KtabDev &kt, const PrepJob *djobs, int njobs,
                           double tau_vert_max, double beta, cudaStream_t st)
 {
-    count_launch(3);
+    count_launch(1);
     const bool f64 = precision == GCMC_FP64;
     const int ncolb = emis_col_blocks(hg);
     const dim3 gc((unsigned)ncolb, (unsigned)njobs);
@@ -584,7 +601,7 @@ cudaError_t prep_emission_xsec(int precision, const DevGrid &hg, const XsecDev &
 {
     cudaError_t e = prep_xsec(precision, hg, xs, djobs, njobs, st);
     if (e != cudaSuccess) return e;
-    count_launch(3);
+    count_launch(1);
     const bool f64 = precision == GCMC_FP64;
     const int ncolb = emis_col_blocks(hg);
     const dim3 gc((unsigned)ncolb, (unsigned)njobs);

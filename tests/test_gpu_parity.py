@@ -504,3 +504,17 @@ def test_full_size_phase_curve_split_by_packet(G):
               f"rel {rel:.2e}; diverged remainder {n_run - n_same} packets, |diff| / sigma {z:.2f}")
         assert rel < 1e-5
         assert z < 3.0
+
+
+def test_emission_pdf_sweep_equals_per_block_scan(G):
+    """A batch of enough emission jobs to fill the GPU builds each job's fixed-point cumulative pdf in one
+    sweep per job; a single job (the plain form) with the per-block pdf and scan.  The pdf is integers,
+    so the two give the same launch cells, and tallies, steps, L_tot and the pdf total agree bit for bit."""
+    wl = S.config2_emission(n_packets=3000, nlon=16, nlat=8, nr=12, nb=30, ng=8)
+    gid, oid, sid, jobs = _load(G, wl, _fp("FP32"))
+    assert len(jobs) >= 200
+    tb, sb = G.run_batch(jobs)
+    for q in range(0, len(jobs), 37):
+        tp, sp = G.run_packets(jobs[q])
+        assert np.array_equal(tp, tb[q]), q
+        assert sp.steps == sb[q].steps and sp.l_tot == sb[q].l_tot and sp.cdf_total == sb[q].cdf_total, q
