@@ -5,18 +5,20 @@
 // centre (c0 . d = 0, |c0| = p) and s the signed distance from c0.  In that frame
 //   radial shell r:          s = -/+ sqrt(r^2 - p^2)
 //   latitude cone sin(th)=S: (dz^2 - S^2) s^2 + 2 (zc dz) s + (zc^2 - S^2 p^2) = 0, disc = S^2 p^2 (Q - S^2),
-//                            Q = dz^2 + (zc/p)^2, valid on the nappe where z has the sign of S
+//                            Q = dz^2 + (zc/p)^2, valid on the nappe where z has the sign of S;
+//                            for dz = 0 (a ray parallel to the equatorial plane) s = -/+ (p/|S|) sqrt(Q - S^2)
 //   equator plane:           s = -zc / dz
 //   longitude half-plane:    s = -(n . c0) / (n . d), n = (-sin phi, cos phi, 0), on the phi side
 // Along a straight line the radius is convex in s, the azimuth is monotone (sign of (o x d)_z) and
 // the latitude has at most one extremum (sign of dz p^2 - zc s), so a cell has one candidate exit
 // per face family: one shell, usually one cone, and one half-plane.  Each family's next crossing
 // depends only on the ray and the cell index of that family (k, j or i), so it stays valid while
-// the ray crosses faces of the other families: the march keeps the cone and half-plane crossings and
-// evaluates one again only once the ray has reached it (the family just crossed, or an exact tie);
-// the shell crossing is short and is evaluated at every step.  In FP32 the impact parameter p^2 is carried as an unevaluated FP32 pair built with
-// error-free products, so r^2 - p^2 keeps ~48 bits near grazing incidence; cone roots within TAN_EPS
-// of tangency are recomputed in FP64.
+// the ray crosses faces of the other families: the march keeps the cone and half-plane crossings (and
+// the cell index after each) and evaluates one again only once the ray has reached it (the family just
+// crossed, or an exact tie); the shell crossing is short and is evaluated at every step.  In FP32 the
+// impact parameter p^2 is carried as an unevaluated FP32 pair built with error-free products, so
+// r^2 - p^2 keeps ~48 bits near grazing incidence; cone roots within TAN_EPS of tangency are recomputed
+// in FP64.
 #pragma once
 #include "common.cuh"
 
