@@ -40,7 +40,7 @@ OPS_PER_STEP = 64          # FP32-pipe operations of one cell step (counted from
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 8-job band-0 launch of the current
 # kernel, or None when the kernel has changed since the counters were taken: the traffic grows with the
 # number of job tables the launch touches
-TRAFFIC_PER_EMISSION_JOB = (48.637952e6 + 1.339392e6) / 8
+TRAFFIC_PER_EMISSION_JOB = (48.625408e6 + 1.36704e6) / 8
 
 
 def parse():
