@@ -465,7 +465,7 @@ def test_full_size_phase_curve_split_by_packet(G):
     """The full-size phase curve (128 x 64 x 50 cells, cloud deck, multiple scattering) in FP32 against
     the FP64 oracle, split by packet.  On four jobs spread over the 960, the first 200,000 packets are
     traced on both sides (windows of 10,000): packets whose cell sequences agree with the oracle's must
-    give the same sum of peel-off contributions within 1e-5 relative (the benchmark spec bar on identical
+    give the same sum of peel-off contributions within 1e-5 relative (the tally bar on identical
     packets); the packets whose FP32 sequence left the oracle's (a launch or interaction within metres of
     a face, then an independent path) are reported against the Monte Carlo standard error of their own
     sum, and their difference must stay below 3 of it."""
