@@ -463,3 +463,25 @@ def test_uniform_translation_shifts_the_spectrum_by_whole_bins():
         np.testing.assert_allclose(c["alpha"], still[i - k], rtol=1e-6)
     # the line centre moves by lambda_c v / c to first order
     assert abs(lam[80 + k] - lam[80] - lam[80] * v / 2.99792458e8) < 1e-4 * lam[80] * v / 2.99792458e8
+
+
+def test_step_cap_books_exactly_the_packets_it_cuts():
+    """Per-packet step cap (not in the paper; the design's reading of it): the weight booked as step-capped
+    is that of the packets whose peel-off needs more cell steps than the cap allows, found by running the
+    same packets without a cap; a packet whose ray ends on exactly its last allowed step is not booked,
+    and every other packet keeps its uncapped contribution."""
+    wl = S.config2_emission(n_packets=4000, nlon=16, nlat=8, nr=12, nb=2, ng=2, bands=[1], gpoints=[1])
+    job = wl.jobs[0]
+    cells = O.prep_cells(wl, job)
+    free = O.run(wl, job, cells=cells, per_packet=True, n_trace=4000, max_trace=400)
+    cap = int(np.median(free["pk_steps"]))
+    wl.source.opts.max_steps = cap
+    capped = O.run(wl, job, cells=cells, per_packet=True)
+    first = np.array([c[c >= 0][0] for c in (free["tr_cell"][q, :free["tr_n"][q]] for q in range(4000))])
+    W = np.asarray(cells["wcell"])[first]                 # launch weight of each packet (one g-ordinate)
+    cut = free["pk_steps"] > cap
+    assert cut.any() and (free["pk_steps"] == cap).any()
+    assert capped["ledger"][6] == pytest.approx(W[cut].sum(), rel=1e-12)
+    np.testing.assert_array_equal(capped["pk_steps"], np.minimum(free["pk_steps"], cap))
+    np.testing.assert_array_equal(capped["pk_f"][~cut], free["pk_f"][~cut])
+    assert np.all(capped["pk_f"][cut] == 0.0)
