@@ -506,13 +506,19 @@ def test_full_size_phase_curve_split_by_packet(G):
         assert z < 3.0
 
 
-def test_emission_pdf_sweep_equals_per_block_scan(G):
+@pytest.mark.parametrize("grid,ng", [((16, 8, 12), 8), ((31, 15, 21), 4)])
+def test_emission_pdf_sweep_equals_per_block_scan(G, grid, ng):
     """A batch of enough emission jobs to fill the GPU builds each job's fixed-point cumulative pdf in one
     sweep per job; a single job (the plain form) with the per-block pdf and scan.  The pdf is integers,
-    so the two give the same launch cells, and tallies, steps, L_tot and the pdf total agree bit for bit."""
-    wl = S.config2_emission(n_packets=3000, nlon=16, nlat=8, nr=12, nb=30, ng=8)
+    so the two give the same launch cells, and tallies, steps, L_tot and the pdf total agree bit for bit.
+    Grids of one tile (1,536 cells) and of two tiles and a ragged tail (9,765 cells: the running total
+    carried across tiles, the last thread's four cells straddling the end)."""
+    nlon, nlat, nr = grid
+    wl = S.config2_emission(n_packets=3000, nlon=nlon, nlat=nlat, nr=nr, nb=30, ng=ng)
     gid, oid, sid, jobs = _load(G, wl, _fp("FP32"))
-    assert len(jobs) >= 200
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    assert 3 * len(jobs) >= 2 * nsm            # the batch takes the one-sweep-per-job path
     tb, sb = G.run_batch(jobs)
     for q in range(0, len(jobs), 37):
         tp, sp = G.run_packets(jobs[q])
