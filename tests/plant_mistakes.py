@@ -125,6 +125,8 @@ MUTATIONS = [
      "w_core = limb(law, coef, 1.0 - q) if q < 1.0 else 0.0"),
     ("transit_area_core", P, "area = w_core * g.R0 ** 2 + 2.0 * I_p", "area = g.R0 ** 2 + 2.0 * I_p"),
     ("transit_scattered_sign", P, "I_p = I_dir - omega_star * I_sca", "I_p = I_dir + omega_star * I_sca"),
+    ("emission_capped_booking", C, "} else if (capped || (S->scatter_emission && M.steps >= M.max_steps)) {",
+     "} else if (M.steps >= M.max_steps) {"),
 ]
 
 # plantings that do not change what the oracle computes, with the reason
